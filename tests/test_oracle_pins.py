@@ -1,0 +1,308 @@
+"""Pins of the CPU oracle to things other than itself (CPU only).
+
+* exhaustive rounding rule of the integer distances (number theory),
+* hand-worked examples under tests/golden/ (each cites its passage),
+* the paper's concatenation operator (Section 4.3) against the forward
+  simulation of the time-warp definition, and its associativity,
+* an independent pure-Python brute force over whole candidate sets,
+* closed-form candidate counts, textbook CVRP deltas, and geometry
+  (2-opt on points in convex position ends in convex order),
+* invariants of a descent (cost bookkeeping, one visit per customer, load
+  conservation, fixed fleet, local optimality).
+"""
+import json
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_17357_gb300 import instances as I
+from tests.brute import brute_moves, route_cost as py_route_cost
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def _inst_from_golden(g):
+    tw = "tw_early" in g
+    return I.instance_from_arrays(
+        "golden", np.array(g["dist"]), g["demand"], g["capacity"],
+        service=g.get("service"), tw_early=g.get("tw_early"), tw_late=g.get("tw_late"),
+        coords=g.get("coords")) if tw else I.instance_from_arrays(
+        "golden", np.array(g["dist"]), g["demand"], g["capacity"], coords=g.get("coords"))
+
+
+def _sol(tour, rs):
+    return I.Solution(np.asarray(tour, np.int32), np.asarray(rs, np.int32))
+
+
+def _tiny(kind, n, seed, m_extra_empty=1):
+    inst = I.vrptw(n, seed) if kind == "vrptw" else I.cvrp_uniform(n, seed)
+    # a few multi-customer routes even at tiny n
+    inst.capacity = 100 if kind == "vrptw" else -(-int(inst.demand.sum()) // 3)
+    sol = I.random_split_solution(inst, seed + 11)
+    rs = list(sol.route_start) + [n] * m_extra_empty   # trailing empty routes
+    return inst, _sol(sol.tour, rs)
+
+
+# ----------------------------------------------------------------------------
+def test_round_sqrt_exhaustive():
+    """c = round(sqrt(S)) for every S up to 2*1000^2: the nearest integer c
+    satisfies (c-1/2)^2 <= S < (c+1/2)^2, i.e. c^2-c < S <= c^2+c."""
+    s = np.arange(0, 2 * 1000 * 1000 + 1, dtype=np.int64)
+    c = I.round_sqrt(s)
+    assert c[0] == 0
+    ok = (c[1:] * c[1:] - c[1:] < s[1:]) & (s[1:] <= c[1:] * c[1:] + c[1:])
+    assert bool(ok.all())
+    for v in (1, 2, 3, 24, 25, 26, 2 * 10 ** 6, 999_999):
+        assert int(c[v]) == int(math.floor(math.sqrt(v) + 0.5))
+
+
+def test_distance_matrix_properties():
+    inst = I.cvrp_uniform(50, 3)
+    d = inst.dist.astype(np.int64)
+    assert (d == d.T).all() and (np.diag(d) == 0).all()
+    xy = inst.coords.astype(np.float64)
+    exact = np.sqrt(((xy[:, None, :] - xy[None, :, :]) ** 2).sum(-1))
+    assert np.abs(d - exact).max() <= 0.5
+
+
+def test_generator_is_deterministic():
+    a, sa = I.config1(7)
+    b, sb = I.config1(7)
+    assert (a.dist == b.dist).all() and (sa.tour == sb.tour).all()
+    assert sorted(sa.tour.tolist()) == list(range(1, a.n + 1))
+    assert a.capacity == -(-int(a.demand.sum()) // 8)
+
+
+# ----------------------------------------------------------------------------
+def test_hand_cvrp_swap():
+    g = _golden("hand_cvrp_swap.json")
+    inst = _inst_from_golden(g)
+    sol = _sol(g["tour"], g["route_start"])
+    ex = g["expected"]
+    assert O.solution_cost(inst, sol) == ex["solution_cost"]
+    assert [O.route_cost(inst, r) for r in sol.routes()] == ex["route_costs"]
+    assert O.count_candidates(inst, sol, g["op_mask"]) == ex["n_candidates"]
+    W = inst.n + 1 + sol.n_routes
+    for method in ("def", "concat"):
+        idx, dl = O.list_moves(inst, sol, g["op_mask"], method)
+        got = {}
+        for i, d in zip(idx.tolist(), dl.tolist()):
+            a, b = (i - W * W) // W, (i - W * W) % W
+            got[f"{a},{b}"] = d
+        assert got == ex["swap_deltas"]
+        bm = O.best_move(inst, sol, g["op_mask"], method)
+        assert {k: bm[k] for k in ("delta", "idx", "op", "a", "b")} == ex["best"]
+
+
+def test_hand_vrptw_warp():
+    g = _golden("hand_vrptw_warp.json")
+    inst = _inst_from_golden(g)
+    sol = _sol(g["tour"], g["route_start"])
+    ex = g["expected"]
+    assert O.route_warp(inst, [1, 2]) == ex["warp"]
+    assert O.route_warp(inst, [2, 1]) == ex["reversed_warp"]
+    assert [O.route_cost(inst, r) for r in sol.routes()] == ex["route_costs"]
+    assert O.count_candidates(inst, sol, g["op_mask"]) == ex["n_candidates"]
+    for method in ("def", "concat"):
+        bm = O.best_move(inst, sol, g["op_mask"], method)
+        assert {k: bm[k] for k in ("delta", "idx", "op", "a", "b")} == ex["best"]
+
+
+# ----------------------------------------------------------------------------
+def _fold(inst, nodes):
+    s = O.seg_node(inst, nodes[0])
+    for x in nodes[1:]:
+        s = O.seg_concat(inst, s, O.seg_node(inst, x))
+    return s
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_concat_equals_forward_simulation(seed):
+    """Section 4.3: folding the concatenation operator over (0, route, 0)
+    gives the route's distance, load and time warp of the forward simulation
+    (travel time = distance, waiting allowed, late arrival warps back)."""
+    inst = I.vrptw(40, 100 + seed)
+    rng = random.Random(seed)
+    for _ in range(200):
+        L = rng.randint(1, 12)
+        route = rng.sample(range(1, inst.n + 1), L)
+        s = _fold(inst, [0] + route + [0])
+        seq = [0] + route + [0]
+        assert s[0] == sum(int(inst.dist[seq[k], seq[k + 1]]) for k in range(len(seq) - 1))
+        assert s[1] == sum(int(inst.demand[x]) for x in route)
+        assert s[5] == O.route_warp(inst, route)
+        assert py_route_cost(inst, route) == O.route_cost(inst, route)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_concat_associative(seed):
+    inst = I.vrptw(30, 200 + seed)
+    rng = random.Random(seed)
+    for _ in range(300):
+        nodes = rng.sample(range(0, inst.n + 1), rng.randint(3, 9))
+        cut1 = rng.randint(1, len(nodes) - 2)
+        cut2 = rng.randint(cut1 + 1, len(nodes) - 1)
+        a, b, c = _fold(inst, nodes[:cut1]), _fold(inst, nodes[cut1:cut2]), _fold(inst, nodes[cut2:])
+        left = O.seg_concat(inst, O.seg_concat(inst, a, b), c)
+        right = O.seg_concat(inst, a, O.seg_concat(inst, b, c))
+        assert (left == right).all()
+
+
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["cvrp", "vrptw"])
+@pytest.mark.parametrize("seed", range(5))
+def test_candidate_sets_against_brute_force(kind, seed):
+    """Every candidate (move index -> delta) equals a from-scratch recompute of
+    the whole neighbour solution built by independent Python list surgery."""
+    n = 5 + seed % 4
+    inst, sol = _tiny(kind, n, 300 + seed, m_extra_empty=1)
+    routes = sol.routes()
+    expect = brute_moves(inst, routes, I.MASK_ALL)
+    for method in ("def", "concat"):
+        idx, dl = O.list_moves(inst, sol, I.MASK_ALL, method)
+        got = dict(zip(idx.tolist(), dl.tolist()))
+        assert got == expect, method
+    bm = O.best_move(inst, sol, I.MASK_ALL, "def")
+    best = min((d, i) for i, d in expect.items())
+    assert (bm["delta"], bm["idx"]) == best
+
+
+def _closed_form_count(n, lens, mask):
+    m = len(lens)
+    A = n + m
+    c = 0
+    if mask & 1:
+        c += n * (A - 2)
+    if mask & 2:
+        c += n * (n - 1) // 2
+    if mask & 4:
+        c += sum(L * (L - 1) // 2 for L in lens)
+    if mask & 8:
+        c += (A * A - sum((L + 1) ** 2 for L in lens)) // 2
+    if mask & 16:
+        c += sum(max(0, L - 1) for L in lens) * (A - 3)
+    if mask & 32:
+        c += sum(max(0, L - 2) for L in lens) * (A - 4)
+    return c
+
+
+@pytest.mark.parametrize("mask", [1, 2, 4, 8, 16, 32, I.MASK_ALL, I.MASK_CONFIG1, I.MASK_CONFIG3])
+def test_candidate_counts_closed_form(mask):
+    for kind, n, seed in (("cvrp", 40, 1), ("vrptw", 60, 2), ("cvrp", 7, 3)):
+        inst, sol = _tiny(kind, n, seed, m_extra_empty=2)
+        lens = [len(r) for r in sol.routes()]
+        assert O.count_candidates(inst, sol, mask) == _closed_form_count(n, lens, mask)
+
+
+def test_textbook_cvrp_deltas():
+    """CVRP special cases that reduce to textbook edge formulas:
+    2-opt: c(u-,v)+c(u,v+)-c(u-,u)-c(v,v+); inter-route relocate:
+    c(u-,u+)-c(u-,u)-c(u,u+)+c(v,u)+c(u,v+)-c(v,v+) plus the load-penalty
+    change of both routes."""
+    inst, sol = _tiny("cvrp", 30, 9, m_extra_empty=0)
+    c = inst.dist.astype(np.int64)
+    routes = sol.routes()
+    n, m = inst.n, len(routes)
+    W = n + 1 + m
+    idx, dl = O.list_moves(inst, sol, 4 | 1, "def")
+    got = dict(zip(idx.tolist(), dl.tolist()))
+    pos = {x: (r, i) for r, rt in enumerate(routes) for i, x in enumerate(rt)}
+    loads = [sum(int(inst.demand[x]) for x in rt) for rt in routes]
+    pen = lambda L: inst.w_load * max(0, L - inst.capacity)
+    checked = 0
+    for rt in routes:
+        full = [0] + rt + [0]
+        for i in range(1, len(full) - 1):
+            for j in range(i + 1, len(full) - 1):
+                u, v = full[i], full[j]
+                want = c[full[i - 1], v] + c[u, full[j + 1]] - c[full[i - 1], u] - c[v, full[j + 1]]
+                assert got[2 * W * W + u * W + v] == want
+                checked += 1
+    for u in range(1, n + 1):
+        ra, i = pos[u]
+        fa = [0] + routes[ra] + [0]
+        um, up = fa[i], fa[i + 2]
+        for rb in range(m):
+            if rb == ra:
+                continue
+            fb = [0] + routes[rb] + [0]
+            for j in range(len(fb) - 1):
+                v, vp = fb[j], fb[j + 1]
+                anchor = n + 1 + rb if j == 0 else v
+                want = (c[um, up] - c[um, u] - c[u, up] + c[v, u] + c[u, vp] - c[v, vp]
+                        + pen(loads[ra] - inst.demand[u]) - pen(loads[ra])
+                        + pen(loads[rb] + inst.demand[u]) - pen(loads[rb]))
+                assert got[u * W + anchor] == want
+                checked += 1
+    assert checked > 500
+
+
+def test_two_opt_descent_reaches_convex_order():
+    """Points in convex position: a tour is optimal iff it has no crossing
+    edges, and every crossing can be removed by an improving 2-opt move, so
+    a 2-opt local optimum is the angular order (either direction)."""
+    k = 14
+    pts = [(int(round(5000 + 5000 * math.cos(2 * math.pi * t / (k + 1)))),
+            int(round(5000 + 5000 * math.sin(2 * math.pi * t / (k + 1))))) for t in range(k + 1)]
+    dist = I.rounded_euclidean(np.array(pts, np.int64))     # node 0 (depot) is on the circle too
+    inst = I.instance_from_arrays("circle", dist, [0] + [1] * (dist.shape[0] - 1), 10 ** 6)
+    n = inst.n
+    rng = random.Random(5)
+    perm = list(range(1, n + 1))
+    rng.shuffle(perm)
+    sol = _sol(perm, [0, n])
+    final, steps, log, _ = O.descend(inst, sol, 4, "def")
+    tour = final.tour.tolist()
+    assert steps > 0
+    assert tour == sorted(tour) or tour == sorted(tour, reverse=True)
+
+
+@pytest.mark.parametrize("kind,n,seed,mask", [
+    ("cvrp", 25, 1, I.MASK_CONFIG1), ("vrptw", 30, 2, I.MASK_ALL),
+    ("cvrp", 40, 3, I.MASK_CONFIG3), ("vrptw", 45, 4, I.MASK_ALL)])
+def test_descent_invariants(kind, n, seed, mask):
+    inst, sol = _tiny(kind, n, seed, m_extra_empty=1)
+    c0 = O.solution_cost(inst, sol)
+    final, steps, log, cands = O.descend(inst, sol, mask, "def")
+    deltas = [O.unpack_key(k)[0] for k in log]
+    assert len(log) == steps + 1
+    assert all(d < 0 for d in deltas[:-1]) and deltas[-1] >= 0
+    assert O.solution_cost(inst, final) == c0 + sum(deltas[:-1])
+    assert O.check_solution(inst, final) == 0
+    assert final.n_routes == sol.n_routes
+    assert sorted(final.tour.tolist()) == list(range(1, n + 1))
+    assert sum(int(inst.demand[x]) for x in final.tour) == int(inst.demand.sum())
+    bm = O.best_move(inst, final, mask, "def")
+    assert bm["delta"] >= 0 and bm["key"] == int(log[-1])
+    # the concatenation evaluator follows the identical trajectory
+    final2, steps2, log2, cands2 = O.descend(inst, sol, mask, "concat")
+    assert steps2 == steps and (log2 == log).all() and cands2 == cands
+    assert (final2.tour == final.tour).all()
+
+
+def test_empty_neighbourhood():
+    inst = I.instance_from_arrays("one", np.array([[0, 3], [3, 0]]), [0, 1], 5)
+    sol = _sol([1], [0, 1])
+    assert O.count_candidates(inst, sol, I.MASK_ALL) == 0
+    assert O.best_move(inst, sol, I.MASK_ALL)["found"] is False
+    final, steps, log, _ = O.descend(inst, sol, I.MASK_ALL)
+    assert steps == 0 and int(log[0]) == O.NO_MOVE_KEY
+
+
+def test_apply_rejects_non_candidates():
+    inst, sol = _tiny("cvrp", 10, 1, m_extra_empty=0)
+    route = next(r for r in sol.routes() if len(r) >= 2)
+    u, pred = route[1], route[0]
+    with pytest.raises(ValueError):
+        O.apply_move(inst, sol, 0, u, pred)         # v == pred(u)
+    with pytest.raises(ValueError):
+        O.apply_move(inst, sol, 1, 5, 5)            # swap needs a < b
