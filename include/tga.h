@@ -1,0 +1,180 @@
+/*
+ * libtga -- best-improvement VRP local search on one GB300 (sm_103a).
+ *
+ * One local-search step evaluates the whole neighbourhood of the current
+ * solution -- relocate, swap, intra-route 2-opt, inter-route 2-opt* and
+ * or-opt (runs of 2 and 3 customers) -- scores every candidate with an
+ * exact integer O(1) delta of distance + w_load * capacity excess +
+ * w_tw * time warp, reduces to the best move, and applies it on the device.
+ * The method is the node-based tensorised move evaluation of the paper
+ * (Section 5.3, "node-based extraction", Eqs. "node_based1"/"node_based2"),
+ * built on sequence concatenation (Section 4.3) over an attribute-based
+ * solution representation (Section 5.2), with best improvement
+ * (Section 5.3.4, Eq. "min_obj") and the descent loop of the appendix
+ * algorithm "Feasible and infeasible search".
+ *
+ * Conventions shared by every call:
+ *  - Nodes: depot 0, customers 1..n.  Distances are int32, row-major
+ *    (n+1)*(n+1), symmetric with a zero diagonal; travel time equals
+ *    distance.
+ *  - Solution: a giant tour tour[n] (customers in route order) plus
+ *    route_start[m+1]: route r is tour[route_start[r] .. route_start[r+1]-1]
+ *    between two depot visits (Section 2, "S = {R_1..R_M}").  Empty routes
+ *    are allowed and keep their slot; m never changes.
+ *  - Anchors: customers 1..n; the start depot of route r is anchor n+1+r;
+ *    W = n+1+m.  A move is (op, a, b) with op ranks
+ *      0 relocate  (a customer, b anchor: move a to just after b)
+ *      1 swap      (customers a < b)
+ *      2 2-opt     (customers of one route, pos(a) < pos(b): reverse a..b)
+ *      3 2-opt*    (anchors, route(a) < route(b): exchange the tails after a, b)
+ *      4 or-opt 2, 5 or-opt 3 (a = first customer of the run, b anchor
+ *        outside the run, b != pred(a): move the run after b)
+ *    and move index idx = op*W*W + a*W + b (requires 6*W*W < 2^32).
+ *  - The best move is the smallest (delta, idx); a move is accepted iff
+ *    delta < 0.
+ *  - All pointers in tga_instance / tga_solution are DEVICE pointers owned by
+ *    the caller; they must stay valid until tga_destroy.  The solution
+ *    arrays are updated in place by tga_apply_move / tga_descend.
+ *  - Every call is asynchronous on the context's stream unless stated;
+ *    errors found on the device are reported by the next synchronising call
+ *    (tga_descend, tga_sync, tga_get_stats).
+ *  - Integer range: the library rejects (TGA_ERR_RANGE) a state in which a
+ *    route built from two current routes plus three moved customers could
+ *    cost 2^27 or more, so every delta fits in int32 with room for the
+ *    invalid-candidate offset.
+ */
+#ifndef TGA_H
+#define TGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (cudaStream_t); NULL is the legacy default stream. */
+typedef struct CUstream_st *tga_stream_t;
+
+typedef struct tga_ctx tga_ctx;
+
+enum {
+    TGA_OK = 0,
+    TGA_ERR_INVALID = 1,   /* bad sizes, ids, op mask, non-candidate move, bad solution */
+    TGA_ERR_RANGE = 2,     /* int32 headroom or move-index bound violated */
+    TGA_ERR_NOMEM = 3,     /* device allocation failed */
+    TGA_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+    TGA_ERR_TIMEOUT = 5,   /* a bounded device-side wait ran out */
+    TGA_ERR_STATE = 6      /* call not allowed in the context's current state */
+};
+
+/* Problem data (Section 2).  has_tw = 0 is the CVRP: service, tw_early and
+ * tw_late may then be NULL.  w_load / w_tw are the penalty weights of the
+ * penalised objective; both must be >= 0. */
+typedef struct {
+    int32_t n_customers;       /* n >= 1 */
+    int32_t n_routes;          /* m >= 1 */
+    int32_t capacity;          /* Q >= 0 */
+    int32_t has_tw;            /* 0 CVRP, 1 VRPTW */
+    int32_t w_load, w_tw;
+    const int32_t *dist;       /* device, (n+1)*(n+1) */
+    const int32_t *demand;     /* device, n+1, demand[0] = 0 */
+    const int32_t *service;    /* device, n+1 (VRPTW), service[0] = 0 */
+    const int32_t *tw_early;   /* device, n+1 (VRPTW), [0] = depot opening */
+    const int32_t *tw_late;    /* device, n+1 (VRPTW), [0] = latest return */
+} tga_instance;
+
+typedef struct {
+    int32_t *tour;             /* device, n */
+    int32_t *route_start;      /* device, m+1 */
+} tga_solution;
+
+/* A decoded move.  delta is the objective change (negative = improving);
+ * valid = 0 means the neighbourhood was empty. */
+typedef struct {
+    int32_t delta;
+    uint32_t move_index;
+    int32_t op, a, b;
+    int32_t valid;
+} tga_move;
+
+typedef struct {
+    int64_t steps;             /* applied moves */
+    int64_t candidates;        /* candidate moves evaluated, all evaluations */
+    int64_t initial_cost;      /* cost when the attributes were (re)built */
+    int64_t final_cost;        /* current cost */
+    int32_t status;            /* TGA_OK or the first device-side error */
+    int32_t local_optimum;     /* 1 if the last evaluation found no delta < 0 */
+    int64_t evaluations;       /* neighbourhood evaluations */
+} tga_stats;
+
+/* Create a context for one instance + solution.
+ *  op_mask: bit k enables op rank k (0x3F = all); must be non-zero and
+ *  < 64.  Validates sizes on the host (TGA_ERR_INVALID / TGA_ERR_RANGE for
+ *  W too large), allocates the context's device workspace (about
+ *  4*(n+1)*(n+m+257) bytes for the position-ordered distance copy plus
+ *  O(n+m)), and returns *out.  Nothing is computed until tga_build_attrs.
+ *  Ownership: the caller keeps the instance and solution memory. */
+int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_mask,
+               tga_stream_t stream, tga_ctx **out);
+
+/* Build the attribute representation from the caller's solution
+ * (Section 5.2 "solution tensor", node-based positional index P_r/P_pi of
+ * Section 5.3.1): positions, per-anchor forward/backward segment attributes
+ * (distance, load, T_D/T_E/T_L/T_V in the form of Section 4.3), route
+ * totals, and the position-ordered distance copy.  Also validates the
+ * solution (permutation, route bounds), the matrix (symmetry, zero diagonal,
+ * non-negative) and the integer headroom; failures are reported by the next
+ * synchronising call.  Resets the step counters and the initial cost. */
+int tga_build_attrs(tga_ctx *ctx);
+
+/* Evaluate the whole neighbourhood (Section 5.3 Extraction, Concatenation,
+ * Differencing, Evaluation) and write the best move to out_dev (DEVICE
+ * memory, one tga_move).  Asynchronous. */
+int tga_eval_best_move(tga_ctx *ctx, tga_move *out_dev);
+
+/* Apply a move given in DEVICE memory (Section 5.3.5 "Tensor update", done
+ * on the device): rewrite tour/route_start in place, update positions and
+ * rebuild the attributes of the touched routes only.  A move with
+ * valid == 0 or delta >= 0 is a no-op that marks the context as being at a
+ * local optimum.  A move that is not a candidate sets TGA_ERR_INVALID. */
+int tga_apply_move(tga_ctx *ctx, const tga_move *move_dev);
+
+/* Best-improvement descent: repeat evaluate + apply until no move has
+ * delta < 0 or max_steps moves were applied in this call.  The loop runs on
+ * the device as a CUDA graph with a conditional while node (no host round
+ * trip per step).  Builds the attributes first if they were never built.
+ * Synchronises the stream at the end and fills *out_host (may be NULL). */
+int tga_descend(tga_ctx *ctx, int64_t max_steps, tga_stats *out_host);
+
+/* Descend every context to a local optimum (at most max_steps moves each).
+ * Contexts on different streams run concurrently; the call waits for all.
+ * out_host: n entries (may be NULL).  Returns the first error. */
+int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_host);
+
+/* Wait for the context's stream and report the device status. */
+int tga_sync(tga_ctx *ctx);
+
+/* Synchronise and copy the counters (steps, candidates, costs, status). */
+int tga_get_stats(tga_ctx *ctx, tga_stats *out_host);
+
+/* Record one packed key ((uint32)(delta + 2^31) << 32 | idx) per
+ * evaluation into a caller-owned DEVICE buffer of `capacity` entries
+ * (NULL disables).  Used to compare whole trajectories. */
+int tga_set_move_log(tga_ctx *ctx, uint64_t *log_dev, int64_t capacity);
+
+/* Choose the inter-route tile shape: rows per tile (16, 32 or 64) and warps
+ * per block (2, 4 or 8; 32 columns each); 0, 0 runs the built-in autotuner
+ * (times every shape on the current state).  Call after tga_build_attrs. */
+int tga_set_tile(tga_ctx *ctx, int32_t rows, int32_t warps);
+int tga_get_tile(tga_ctx *ctx, int32_t *rows, int32_t *warps);
+
+/* Release the context's workspace (not the caller's arrays). */
+int tga_destroy(tga_ctx *ctx);
+
+const char *tga_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

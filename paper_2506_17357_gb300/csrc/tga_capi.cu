@@ -1,0 +1,400 @@
+// libtga C-ABI: context lifetime, the descent loop as a CUDA graph with a
+// device-driven conditional while node, and the tile-shape autotuner.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tga_internal.cuh"
+
+using namespace tga;
+
+struct tga_ctx {
+    Dev d{};
+    cudaStream_t stream = nullptr;     // caller's stream
+    cudaStream_t cap = nullptr;        // private stream used only for graph capture
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int device = 0;
+    bool built = false;
+    // inter-route tiles
+    int tile_rows = 0, tile_warps = 0, ntiles = 0;
+    int2 *tiles = nullptr;
+    // descent graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_ready = false;
+    bool graph_failed = false;
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? TGA_OK : TGA_ERR_CUDA; }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int check_launch() {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "libtga: CUDA error: %s\n", cudaGetErrorString(e));
+        return TGA_ERR_CUDA;
+    }
+    return TGA_OK;
+}
+
+void drop_graph(tga_ctx *c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+    c->graph_ready = false;
+}
+
+int set_tiles(tga_ctx *c, int rows, int warps) {
+    if (!(rows == 16 || rows == 32 || rows == 64) || !(warps == 2 || warps == 4 || warps == 8))
+        return TGA_ERR_INVALID;
+    const int Wa = c->d.Wp - 1;   // anchor positions
+    const int TC = warps * 32;
+    const int nrt = (Wa + rows - 1) / rows, nct = (Wa + TC - 1) / TC;
+    std::vector<int2> t;
+    t.reserve((size_t)nrt * nct / 2 + nrt + 8);
+    for (int I = 0; I < nrt; ++I)
+        for (int J = 0; J < nct; ++J)
+            if ((long long)(J + 1) * TC - 1 > (long long)I * rows) t.push_back(make_int2(I, J));
+    if (c->tiles) cudaFree(c->tiles);
+    c->tiles = nullptr;
+    c->ntiles = (int)t.size();
+    if (!t.empty()) {
+        if (cudaMalloc(&c->tiles, t.size() * sizeof(int2)) != cudaSuccess) return TGA_ERR_NOMEM;
+        if (cudaMemcpy(c->tiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return TGA_ERR_CUDA;
+    }
+    c->tile_rows = rows;
+    c->tile_warps = warps;
+    drop_graph(c);
+    return TGA_OK;
+}
+
+void default_tiles(tga_ctx *c) {
+    const long long pairs = (long long)c->d.Wp * c->d.Wp / 2;
+    if (pairs < 2000000) set_tiles(c, 16, 2);
+    else if (pairs < 20000000) set_tiles(c, 32, 4);
+    else set_tiles(c, 32, 8);
+}
+
+int step_once(tga_ctx *c, unsigned long long cond, int use_cond, cudaStream_t s) {
+    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, s);
+    launch_apply(c->d, nullptr, cond, use_cond, s);
+    launch_band(c->d, s);
+    return check_launch();
+}
+
+int build_graph(tga_ctx *c) {
+    if (c->graph_ready) return TGA_OK;
+    if (c->graph_failed) return TGA_ERR_CUDA;
+    cudaError_t e = cudaGraphCreate(&c->graph, 0);
+    cudaGraphConditionalHandle h = 0;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, c->graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, c->graph, nullptr, nullptr, 0, &cp);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap);
+            launch_apply(c->d, nullptr, h, 1, c->cap);
+            launch_band(c->d, c->cap);
+            cudaGraph_t outg = body;
+            e = cudaStreamEndCapture(c->cap, &outg);
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, c->graph, 0);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "libtga: graph build failed (%s); using host-driven steps\n", cudaGetErrorString(e));
+        cudaGetLastError();
+        drop_graph(c);
+        c->graph_failed = true;
+        return TGA_ERR_CUDA;
+    }
+    c->graph_ready = true;
+    return TGA_OK;
+}
+
+int read_control(tga_ctx *c, Control *out) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return TGA_ERR_CUDA;
+    e = cudaMemcpy(out, c->d.ctl, sizeof(Control), cudaMemcpyDeviceToHost);
+    return cuda_err(e);
+}
+
+void fill_stats(const Control &C, tga_stats *s) {
+    s->steps = C.steps;
+    s->candidates = C.cand_total;
+    s->initial_cost = C.initial_cost;
+    s->final_cost = C.cost;
+    s->status = C.status;
+    s->local_optimum = C.local_opt;
+    s->evaluations = C.evals;
+}
+
+int descend_launch(tga_ctx *c, int64_t max_steps) {
+    if (!c->built) {
+        int rc = tga_build_attrs(c);
+        if (rc) return rc;
+    }
+    if (!c->tiles && c->d.Wp > 2) default_tiles(c);
+    launch_begin(c->d, max_steps, c->stream);
+    if (build_graph(c) == TGA_OK) {
+        if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return TGA_ERR_CUDA;
+        return check_launch();
+    }
+    // host-driven fallback: chunks of steps, stop when the device says done
+    Control C;
+    int64_t done_steps = 0;
+    while (done_steps < max_steps) {
+        const int chunk = 64;
+        for (int k = 0; k < chunk; ++k) {
+            int rc = step_once(c, 0, 0, c->stream);
+            if (rc) return rc;
+        }
+        done_steps += chunk;
+        int rc = read_control(c, &C);
+        if (rc) return rc;
+        if (C.done) break;
+    }
+    return TGA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tga_strerror(int code) {
+    switch (code) {
+        case TGA_OK: return "ok";
+        case TGA_ERR_INVALID: return "invalid argument, instance, solution or move";
+        case TGA_ERR_RANGE: return "integer range or move-index bound exceeded";
+        case TGA_ERR_NOMEM: return "device allocation failed";
+        case TGA_ERR_CUDA: return "CUDA runtime error";
+        case TGA_ERR_TIMEOUT: return "bounded device wait expired";
+        case TGA_ERR_STATE: return "call not allowed in the current state";
+        case 7: return "internal consistency check failed (applied delta differs from evaluated delta)";
+        default: return "unknown error";
+    }
+}
+
+int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_mask, tga_stream_t stream,
+               tga_ctx **out) {
+    if (!inst || !sol || !out) return TGA_ERR_INVALID;
+    *out = nullptr;
+    const long long n = inst->n_customers, m = inst->n_routes;
+    if (n < 1 || m < 1 || inst->capacity < 0 || inst->w_load < 0 || inst->w_tw < 0) return TGA_ERR_INVALID;
+    if (op_mask == 0 || op_mask >= 64u) return TGA_ERR_INVALID;
+    if (!inst->dist || !inst->demand || !sol->tour || !sol->route_start) return TGA_ERR_INVALID;
+    if (inst->has_tw && (!inst->service || !inst->tw_early || !inst->tw_late)) return TGA_ERR_INVALID;
+    const long long W = n + 1 + m;
+    if (W > kMaxW) return TGA_ERR_RANGE;
+
+    tga_ctx *c = new (std::nothrow) tga_ctx();
+    if (!c) return TGA_ERR_NOMEM;
+    cudaGetDevice(&c->device);
+    c->stream = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return TGA_ERR_CUDA;
+    }
+    Dev &d = c->d;
+    d.n = (int)n; d.m = (int)m; d.W = (int)W; d.Wp = (int)(n + m + 1);
+    d.Q = inst->capacity; d.wL = inst->w_load; d.wT = inst->w_tw; d.has_tw = inst->has_tw ? 1 : 0;
+    d.op_mask = op_mask;
+    d.dist = inst->dist; d.demand = inst->demand;
+    d.service = inst->service; d.early = inst->tw_early; d.late = inst->tw_late;
+    d.tour = sol->tour; d.route_start = sol->route_start;
+    d.ldp = (int)(align_up((size_t)d.Wp, kMaxTileCols) + 16);
+    d.log = nullptr; d.log_cap = 0;
+
+    // one workspace allocation, carved into 256-byte aligned pieces
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t o_ctl = take(sizeof(Control));
+    const size_t o_seq = take(sizeof(int) * (size_t)d.Wp);
+    const size_t o_pos = take(sizeof(int) * (size_t)(W + 1));
+    const size_t o_brec = take(sizeof(BRec) * (size_t)(W + 1));
+    const size_t o_erec = take(sizeof(ERec) * (size_t)(W + 1));
+    const size_t o_rrec = take(sizeof(RouteRec) * (size_t)m);
+    const size_t o_chg = take(sizeof(int2) * (size_t)d.Wp);
+    const size_t o_sa = take(sizeof(int) * (size_t)d.Wp);
+    const size_t o_sr = take(sizeof(int) * (size_t)d.Wp);
+    const size_t o_ss = take(sizeof(int) * (size_t)d.Wp);
+    const size_t o_seen = take(sizeof(int) * (size_t)(n + 1));
+    const size_t o_pcol = take(sizeof(int) * (size_t)(n + 1) * (size_t)d.ldp);
+    c->ws_bytes = off;
+    if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamDestroy(c->cap);
+        delete c;
+        return TGA_ERR_NOMEM;
+    }
+    char *base = (char *)c->ws;
+    d.ctl = (Control *)(base + o_ctl);
+    d.seq = (int *)(base + o_seq);
+    d.pos_of = (int *)(base + o_pos);
+    d.brec = (BRec *)(base + o_brec);
+    d.erec = (ERec *)(base + o_erec);
+    d.rrec = (RouteRec *)(base + o_rrec);
+    d.chg = (int2 *)(base + o_chg);
+    d.scr_anchor = (int *)(base + o_sa);
+    d.scr_route = (int *)(base + o_sr);
+    d.scr_src = (int *)(base + o_ss);
+    d.seen = (int *)(base + o_seen);
+    d.pcol = (int *)(base + o_pcol);
+    if (cudaMemsetAsync(d.ctl, 0, sizeof(Control), c->stream) != cudaSuccess ||
+        setup_kernel_attrs(d.Wp) != 0) {
+        cudaFree(c->ws);
+        cudaStreamDestroy(c->cap);
+        delete c;
+        return TGA_ERR_CUDA;
+    }
+    *out = c;
+    return TGA_OK;
+}
+
+int tga_build_attrs(tga_ctx *c) {
+    if (!c) return TGA_ERR_INVALID;
+    if (cudaMemsetAsync(c->d.ctl, 0, sizeof(Control), c->stream) != cudaSuccess) return TGA_ERR_CUDA;
+    launch_check_instance(c->d, c->stream);
+    launch_build(c->d, c->stream);
+    c->built = true;
+    return check_launch();
+}
+
+int tga_eval_best_move(tga_ctx *c, tga_move *out_dev) {
+    if (!c || !out_dev) return TGA_ERR_INVALID;
+    if (!c->built) return TGA_ERR_STATE;
+    if (!c->tiles && c->d.Wp > 2) default_tiles(c);
+    launch_begin(c->d, 1, c->stream);
+    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);
+    launch_finalize(c->d, out_dev, c->stream);
+    return check_launch();
+}
+
+int tga_apply_move(tga_ctx *c, const tga_move *move_dev) {
+    if (!c || !move_dev) return TGA_ERR_INVALID;
+    if (!c->built) return TGA_ERR_STATE;
+    launch_apply(c->d, move_dev, 0, 0, c->stream);
+    launch_band(c->d, c->stream);
+    return check_launch();
+}
+
+int tga_descend(tga_ctx *c, int64_t max_steps, tga_stats *out_host) {
+    if (!c || max_steps < 0) return TGA_ERR_INVALID;
+    int rc = descend_launch(c, max_steps);
+    if (rc) return rc;
+    Control C;
+    rc = read_control(c, &C);
+    if (rc) return rc;
+    if (out_host) fill_stats(C, out_host);
+    return C.status;
+}
+
+int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_host) {
+    if (!ctxs || n < 0 || max_steps < 0) return TGA_ERR_INVALID;
+    int first = TGA_OK;
+    for (int i = 0; i < n; ++i) {
+        int rc = descend_launch(ctxs[i], max_steps);
+        if (rc && !first) first = rc;
+    }
+    for (int i = 0; i < n; ++i) {
+        Control C;
+        int rc = read_control(ctxs[i], &C);
+        if (rc && !first) first = rc;
+        if (!rc) {
+            if (out_host) fill_stats(C, out_host + i);
+            if (C.status && !first) first = C.status;
+        }
+    }
+    return first;
+}
+
+int tga_sync(tga_ctx *c) {
+    if (!c) return TGA_ERR_INVALID;
+    Control C;
+    int rc = read_control(c, &C);
+    return rc ? rc : C.status;
+}
+
+int tga_get_stats(tga_ctx *c, tga_stats *out_host) {
+    if (!c || !out_host) return TGA_ERR_INVALID;
+    Control C;
+    int rc = read_control(c, &C);
+    if (rc) return rc;
+    fill_stats(C, out_host);
+    return TGA_OK;
+}
+
+int tga_set_move_log(tga_ctx *c, uint64_t *log_dev, int64_t capacity) {
+    if (!c || capacity < 0) return TGA_ERR_INVALID;
+    c->d.log = (unsigned long long *)log_dev;
+    c->d.log_cap = log_dev ? capacity : 0;
+    drop_graph(c);
+    return TGA_OK;
+}
+
+int tga_set_tile(tga_ctx *c, int32_t rows, int32_t warps) {
+    if (!c) return TGA_ERR_INVALID;
+    if (rows != 0 || warps != 0) return set_tiles(c, rows, warps);
+    if (!c->built) return TGA_ERR_STATE;
+    // autotune: time every shape on the current state (evaluation only; the
+    // solution is not touched), keep the fastest.
+    static const int shapes[][2] = {{16, 2}, {32, 2}, {16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float bestms = 1e30f;
+    int br = 32, bw = 4;
+    for (const auto &s : shapes) {
+        if (set_tiles(c, s[0], s[1]) != TGA_OK) continue;
+        launch_begin(c->d, 1, c->stream);
+        launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);
+        cudaEventRecord(e0, c->stream);
+        for (int k = 0; k < 3; ++k) launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < bestms) { bestms = ms; br = s[0]; bw = s[1]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // leave the context as it was before tuning (no pending key)
+    cudaMemsetAsync(&c->d.ctl->best_key, 0xff, sizeof(unsigned long long), c->stream);
+    int rc = set_tiles(c, br, bw);
+    if (rc) return rc;
+    return check_launch();
+}
+
+int tga_get_tile(tga_ctx *c, int32_t *rows, int32_t *warps) {
+    if (!c || !rows || !warps) return TGA_ERR_INVALID;
+    if (!c->tiles && c->built && c->d.Wp > 2) default_tiles(c);
+    *rows = c->tile_rows;
+    *warps = c->tile_warps;
+    return TGA_OK;
+}
+
+int tga_destroy(tga_ctx *c) {
+    if (!c) return TGA_ERR_INVALID;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graph(c);
+    if (c->tiles) cudaFree(c->tiles);
+    if (c->ws) cudaFree(c->ws);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+    return TGA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,199 @@
+// Internal device-side layout of libtga (not part of the public ABI).
+//
+// Representation (Section 5.2 "attribute-based solution tensor", redesigned
+// for one GPU): instead of a dense I x J x K x K tensor the context keeps
+//   * the position sequence seq[p] of the giant tour with the start depot of
+//     every route interleaved (route r occupies positions
+//     route_start[r]+r .. route_start[r+1]+r, depot first), plus a sentinel
+//     depot at position n+m -- the positional index P_r / P_pi of the
+//     node-based extraction (Section 5.3.1, Eqs. "node_based1/2");
+//   * per anchor the attributes of its prefix (start depot .. x) and of the
+//     suffix after it (x+ .. end depot): distance, load and the time-window
+//     attributes of Section 4.3.3 (T_D, T_E, T_L, T_V);
+//   * hoisted per-anchor constants that make every candidate an O(1)
+//     integer expression (ERec);
+//   * a copy of the distance matrix whose columns are in position order
+//     (pcol[node][position]), so a tile of candidate pairs reads its distances
+//     as contiguous row segments.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tga.h"
+
+namespace tga {
+
+constexpr int kBig = 1 << 29;                 // offset that marks an invalid candidate
+constexpr int kBestInit = (1 << 28) - 1;      // every valid |delta| is below 2^28
+constexpr long long kRouteCostLim = 1LL << 27;
+constexpr unsigned long long kNoKey = ~0ull;
+constexpr int kColOff = 4;                    // pcol storage column of position q is q + 4
+constexpr int kMaxTileCols = 256;             // widest tile (8 warps x 32 columns)
+constexpr int kMaxW = 26754;                  // 6 * W^2 < 2^32
+
+// Per-anchor base attributes (prefix through x, suffix after x).
+struct __align__(16) BRec {
+    int node, route, idx, pad0;               // idx: 0 for the start depot, 1..L customers
+    int tau, twf, distf, loadf;               // prefix: departure time after x, warp, distance, load
+    int Lg, twg, distg, loadg;                // suffix after x: latest arrival (T_L), warp, distance, load
+    int pad1, pad2, pad3, pad4;
+};
+
+// Per-anchor hoisted constants of the inter-route candidate expressions.
+// Groups g0..g3 are all a CVRP evaluation reads; g4..g6 add the time fields.
+struct __align__(16) ERec {
+    int route, d, rem1, K1;                   // g0
+    int LQ, K2, LQd, Fc;                      // g1
+    int Gc, loadf, loadgQ, anchor;            // g2
+    int C2, ld2, C3, ld3;                     // g3
+    int e, l, s, tau;                         // g4
+    int Lg, tauP, E2, L2;                     // g5
+    int Dm2, E3, L3, Dm3;                     // g6
+    int node, idx, pad0, pad1;                // g7
+};
+
+struct RouteRec {
+    int start, len, load, dist, tw, cost, pad0, pad1;
+};
+
+struct Control {
+    unsigned long long best_key;              // min packed key of the running evaluation
+    long long steps, evals, cand_total, cost, initial_cost, step_limit, cand_per_eval;
+    long long sumL2, sumLm1, sumLm2;          // sum L^2, sum max(0,L-1), sum max(0,L-2)
+    int done, status, chg_count, local_opt;
+    int maxL, maxLoad;                        // monotone upper bounds for the range check
+    int maxc, maxl, maxs, maxd, maxe, built;
+    int last_op, last_a, last_b, last_delta;
+    int pad[4];
+};
+
+// Everything a kernel needs, passed by value.
+struct Dev {
+    int n, m, W, Wp, ldp;
+    int Q, wL, wT, has_tw;
+    unsigned op_mask;
+    const int *dist, *demand, *service, *early, *late;
+    int *tour, *route_start;
+    int *seq;                 // [Wp]  anchor at each position (sentinel: W)
+    int *pos_of;              // [W+1]
+    BRec *brec;               // [W+1] (index W is the dummy record)
+    ERec *erec;               // [W+1]
+    RouteRec *rrec;           // [m]
+    int *pcol;                // [(n+1) * ldp]
+    Control *ctl;
+    unsigned long long *log;  // optional key log
+    long long log_cap;
+    int2 *chg;                // [Wp] position changes (dst, src) of the last move
+    int *scr_anchor;          // [Wp] apply scratch
+    int *scr_route;           // [Wp]
+    int *scr_src;             // [Wp]
+    int *seen;                // [n+1] permutation check scratch
+};
+
+__host__ __device__ inline int node_of(int anchor, int n) { return anchor <= n ? anchor : 0; }
+
+__device__ __forceinline__ int dmat(const Dev &d, int i, int j) {
+    return __ldg(d.dist + (size_t)i * (d.n + 1) + j);
+}
+
+// Time-window segment in the form of Section 4.3.3: earliest start E,
+// latest start L, duration D (service + travel + waiting), warp TW; plus
+// distance and load.  "out" carries the length of the edge leaving the
+// segment's last node, so a chain of consecutive route elements can be
+// concatenated by a scan without looking the edge up again.
+struct Seg {
+    int E, L, D, TW, dist, load, out;
+};
+
+// a (+) b, the concatenation of Section 4.3 with travel time a.out between
+// them.  Delta_t = T_D(a) - T_V(a) + t (the printed extra "T_W(a)" names no
+// attribute; waiting is already inside T_D, so it is read as absent).
+__device__ __forceinline__ Seg seg_cat(const Seg &a, const Seg &b) {
+    const int t = a.out;
+    const int dt = a.D - a.TW + t;
+    const int dw = max(b.E - dt - a.L, 0);
+    const int dv = max(a.E + dt - b.L, 0);
+    Seg s;
+    s.D = a.D + t + dw + b.D;
+    s.E = max(b.E - dt, a.E) - dw;
+    s.L = min(b.L - dt, a.L) + dv;
+    s.TW = a.TW + dv + b.TW;
+    s.dist = a.dist + t + b.dist;
+    s.load = a.load + b.load;
+    s.out = b.out;
+    return s;
+}
+
+__device__ __forceinline__ Seg seg_node(const Dev &d, int node, int out) {
+    Seg s;
+    if (d.has_tw) {
+        s.E = __ldg(d.early + node); s.L = __ldg(d.late + node); s.D = __ldg(d.service + node);
+    } else {
+        s.E = 0; s.L = 0; s.D = 0;
+    }
+    s.TW = 0; s.dist = 0; s.load = __ldg(d.demand + node); s.out = out;
+    return s;
+}
+
+__device__ __forceinline__ unsigned long long pack_key(int delta, unsigned idx) {
+    return ((unsigned long long)(unsigned)(delta + (int)0x80000000u) << 32) | idx;
+}
+
+__device__ __forceinline__ int key_delta(unsigned long long k) {
+    return (int)((unsigned)(k >> 32) - 0x80000000u);
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, v, off);
+        v = o < v ? o : v;
+    }
+    return v;
+}
+
+// Block-wide min of a packed key, one atomicMin per block into *dst.
+__device__ inline void block_min_to(unsigned long long key, unsigned long long *dst) {
+    __shared__ unsigned long long s_red[32];
+    key = warp_min_u64(key);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) s_red[warp] = key;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        unsigned long long v = lane < nw ? s_red[lane] : kNoKey;
+        v = warp_min_u64(v);
+        if (lane == 0 && v != kNoKey) atomicMin(dst, v);
+    }
+}
+
+// Candidates of one evaluation from the route-length sums (closed form).
+__host__ __device__ inline long long candidate_count(long long n, long long m, unsigned mask,
+                                                     long long sumL2, long long sumLm1,
+                                                     long long sumLm2) {
+    const long long A = n + m;
+    long long c = 0;
+    if (mask & 1u) c += n * (A - 2);
+    if (mask & 2u) c += n * (n - 1) / 2;
+    if (mask & 4u) c += (sumL2 - n) / 2;
+    if (mask & 8u) c += (A * A - (sumL2 + 2 * n + m)) / 2;
+    if (mask & 16u) c += sumLm1 * (A - 3);
+    if (mask & 32u) c += sumLm2 * (A - 4);
+    return c;
+}
+
+// Kernel entry points (tga_kernels.cu).
+void launch_check_instance(const Dev &d, cudaStream_t s);
+void launch_build(const Dev &d, cudaStream_t s);
+void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
+                 cudaStream_t s);
+void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond,
+                  cudaStream_t s);
+void launch_band(const Dev &d, cudaStream_t s);
+void launch_finalize(const Dev &d, tga_move *out, cudaStream_t s);
+void launch_begin(const Dev &d, long long max_steps, cudaStream_t s);
+size_t inter_smem_bytes(int rows, int warps);
+int setup_kernel_attrs(int max_band);
+
+}  // namespace tga

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libtga (the C-ABI declared in include/tga.h).
+
+Functions keep the C names (``tga_create``, ``tga_build_attrs``,
+``tga_eval_best_move``, ``tga_apply_move``, ``tga_descend``,
+``tga_descend_batch``, ...) and only marshal arguments: every step of the
+local search runs in the CUDA kernels of libtga.so.  PyTorch supplies device
+memory and streams.  There is no CPU fallback: if libtga.so is missing or no
+GPU is present, calls raise.
+
+``LocalSearch`` is a convenience wrapper that owns the device copies of one
+instance + solution (torch tensors) and one context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtga.so")
+
+TGA_OK, TGA_ERR_INVALID, TGA_ERR_RANGE, TGA_ERR_NOMEM, TGA_ERR_CUDA = 0, 1, 2, 3, 4
+TGA_ERR_TIMEOUT, TGA_ERR_STATE = 5, 6
+NO_MOVE_KEY = (1 << 64) - 1
+
+
+class TGAError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        msg = _lib().tga_strerror(code).decode() if _LIB is not None else str(code)
+        super().__init__(f"{where}: libtga error {code} ({msg})")
+
+
+class tga_instance(ctypes.Structure):
+    _fields_ = [("n_customers", ctypes.c_int32), ("n_routes", ctypes.c_int32),
+                ("capacity", ctypes.c_int32), ("has_tw", ctypes.c_int32),
+                ("w_load", ctypes.c_int32), ("w_tw", ctypes.c_int32),
+                ("dist", ctypes.c_void_p), ("demand", ctypes.c_void_p),
+                ("service", ctypes.c_void_p), ("tw_early", ctypes.c_void_p),
+                ("tw_late", ctypes.c_void_p)]
+
+
+class tga_solution(ctypes.Structure):
+    _fields_ = [("tour", ctypes.c_void_p), ("route_start", ctypes.c_void_p)]
+
+
+class tga_move(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_int32), ("move_index", ctypes.c_uint32),
+                ("op", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32),
+                ("valid", ctypes.c_int32)]
+
+
+class tga_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("initial_cost", ctypes.c_int64), ("final_cost", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("local_optimum", ctypes.c_int32),
+                ("evaluations", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# (name, restype, argtypes) of every exported entry point in include/tga.h
+_P = ctypes.c_void_p
+EXPORTS = [
+    ("tga_create", ctypes.c_int, [ctypes.POINTER(tga_instance), ctypes.POINTER(tga_solution),
+                                  ctypes.c_uint32, _P, ctypes.POINTER(_P)]),
+    ("tga_build_attrs", ctypes.c_int, [_P]),
+    ("tga_eval_best_move", ctypes.c_int, [_P, _P]),
+    ("tga_apply_move", ctypes.c_int, [_P, _P]),
+    ("tga_descend", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(tga_stats)]),
+    ("tga_descend_batch", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64,
+                                         ctypes.POINTER(tga_stats)]),
+    ("tga_sync", ctypes.c_int, [_P]),
+    ("tga_get_stats", ctypes.c_int, [_P, ctypes.POINTER(tga_stats)]),
+    ("tga_set_move_log", ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    ("tga_set_tile", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    ("tga_get_tile", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    ("tga_destroy", ctypes.c_int, [_P]),
+    ("tga_strerror", ctypes.c_char_p, [ctypes.c_int]),
+]
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtga.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, res, args in EXPORTS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def _check(rc, where):
+    if rc != TGA_OK:
+        raise TGAError(rc, where)
+
+
+# ---------------------------------------------------------------------------
+# C-ABI wrappers (same names)
+
+def tga_create(inst: tga_instance, sol: tga_solution, op_mask: int, stream: int = 0) -> int:
+    out = _P()
+    _check(_lib().tga_create(ctypes.byref(inst), ctypes.byref(sol), op_mask, _P(stream or None),
+                             ctypes.byref(out)), "tga_create")
+    return out.value
+
+
+def tga_build_attrs(ctx: int):
+    _check(_lib().tga_build_attrs(_P(ctx)), "tga_build_attrs")
+
+
+def tga_eval_best_move(ctx: int, out_dev_ptr: int):
+    _check(_lib().tga_eval_best_move(_P(ctx), _P(out_dev_ptr)), "tga_eval_best_move")
+
+
+def tga_apply_move(ctx: int, move_dev_ptr: int):
+    _check(_lib().tga_apply_move(_P(ctx), _P(move_dev_ptr)), "tga_apply_move")
+
+
+def tga_descend(ctx: int, max_steps: int = (1 << 62)) -> dict:
+    st = tga_stats()
+    _check(_lib().tga_descend(_P(ctx), max_steps, ctypes.byref(st)), "tga_descend")
+    return st.as_dict()
+
+
+def tga_descend_batch(ctxs, max_steps: int = (1 << 62)):
+    arr = (_P * len(ctxs))(*[_P(c) for c in ctxs])
+    stats = (tga_stats * len(ctxs))()
+    _check(_lib().tga_descend_batch(arr, len(ctxs), max_steps, stats), "tga_descend_batch")
+    return [s.as_dict() for s in stats]
+
+
+def tga_sync(ctx: int):
+    _check(_lib().tga_sync(_P(ctx)), "tga_sync")
+
+
+def tga_get_stats(ctx: int) -> dict:
+    st = tga_stats()
+    _check(_lib().tga_get_stats(_P(ctx), ctypes.byref(st)), "tga_get_stats")
+    return st.as_dict()
+
+
+def tga_set_move_log(ctx: int, log_dev_ptr: int, capacity: int):
+    _check(_lib().tga_set_move_log(_P(ctx), _P(log_dev_ptr or None), capacity), "tga_set_move_log")
+
+
+def tga_set_tile(ctx: int, rows: int = 0, warps: int = 0):
+    _check(_lib().tga_set_tile(_P(ctx), rows, warps), "tga_set_tile")
+
+
+def tga_get_tile(ctx: int):
+    r, w = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().tga_get_tile(_P(ctx), ctypes.byref(r), ctypes.byref(w)), "tga_get_tile")
+    return r.value, w.value
+
+
+def tga_destroy(ctx: int):
+    _check(_lib().tga_destroy(_P(ctx)), "tga_destroy")
+
+
+def tga_strerror(code: int) -> str:
+    return _lib().tga_strerror(code).decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience owner of device memory (torch) + one context
+
+class LocalSearch:
+    """Device-resident instance + solution + libtga context.
+
+    ``inst`` / ``sol`` are ``instances.Instance`` / ``instances.Solution``
+    (host numpy).  Arrays are copied to ``device`` with torch on ``stream``
+    (a torch.cuda.Stream or None for the current stream)."""
+
+    def __init__(self, inst, sol, op_mask: int, device="cuda:0", stream=None, log_capacity: int = 0,
+                 pinned: bool = False):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.n = int(inst.n)
+        self.m = int(np.asarray(sol.route_start).shape[0] - 1)
+        self.W = self.n + 1 + self.m
+        self.op_mask = int(op_mask)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32))
+        with torch.cuda.stream(self.stream):
+            host = [t(inst.dist).reshape(-1), t(inst.demand), t(inst.service), t(inst.tw_early),
+                    t(inst.tw_late), t(sol.tour), t(sol.route_start)]
+            if pinned:
+                host = [h.pin_memory() for h in host]
+            dev = [h.to(self.device, non_blocking=pinned) for h in host]
+            (self.dist, self.demand, self.service, self.early, self.late,
+             self.tour, self.route_start) = dev
+            self.move = torch.zeros(6, dtype=torch.int32, device=self.device)   # one tga_move
+            self.log = (torch.full((log_capacity,), -1, dtype=torch.int64, device=self.device)
+                        if log_capacity else None)
+        self.c_inst = tga_instance(self.n, self.m, int(inst.capacity), int(bool(inst.has_tw)),
+                                   int(inst.w_load), int(inst.w_tw), self.dist.data_ptr(),
+                                   self.demand.data_ptr(),
+                                   self.service.data_ptr() if inst.has_tw else None,
+                                   self.early.data_ptr() if inst.has_tw else None,
+                                   self.late.data_ptr() if inst.has_tw else None)
+        self.c_sol = tga_solution(self.tour.data_ptr(), self.route_start.data_ptr())
+        self.ctx = tga_create(self.c_inst, self.c_sol, self.op_mask, self.stream.cuda_stream)
+        if self.log is not None:
+            tga_set_move_log(self.ctx, self.log.data_ptr(), log_capacity)
+
+    # -- calls
+    def build(self):
+        tga_build_attrs(self.ctx)
+        return self
+
+    def eval_best_move(self) -> dict:
+        tga_eval_best_move(self.ctx, self.move.data_ptr())
+        self.stream.synchronize()
+        v = self.move.cpu().numpy()
+        return dict(delta=int(v[0]), move_index=int(np.uint32(v[1].view(np.uint32))), op=int(v[2]),
+                    a=int(v[3]), b=int(v[4]), valid=bool(v[5]))
+
+    def apply_current_move(self):
+        """Apply the move last written by eval_best_move (device memory)."""
+        tga_apply_move(self.ctx, self.move.data_ptr())
+
+    def descend(self, max_steps: int = (1 << 62)) -> dict:
+        return tga_descend(self.ctx, max_steps)
+
+    def stats(self) -> dict:
+        return tga_get_stats(self.ctx)
+
+    def set_tile(self, rows=0, warps=0):
+        tga_set_tile(self.ctx, rows, warps)
+        return tga_get_tile(self.ctx)
+
+    def solution(self):
+        self.stream.synchronize()
+        return self.tour.cpu().numpy().copy(), self.route_start.cpu().numpy().copy()
+
+    def move_log(self):
+        self.stream.synchronize()
+        st = self.stats()
+        k = min(int(st["evaluations"]), self.log.shape[0])
+        return self.log[:k].cpu().numpy().view(np.uint64).copy()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            tga_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unpack_key(key: int):
+    return (int(key) >> 32) - (1 << 31), int(key) & 0xFFFFFFFF

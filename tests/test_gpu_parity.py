@@ -1,0 +1,261 @@
+"""GPU path vs the CPU oracle, through the C-ABI (marked gpu).
+
+The bar is bit-exact: every evaluation's (delta, move index) equals the
+oracle's, every applied move leaves the same tour/route_start, and the final
+cost equals the oracle's recomputation.  Full-size workloads are checked by
+replaying the GPU's own move log with the oracle's route surgery and
+re-evaluating the neighbourhood with the oracle at every (config 2) or at
+sampled (config 3) steps in a spawn process pool.
+"""
+import multiprocessing as mp
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_17357_gb300 import instances as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2506_17357_gb300.tga import LocalSearch, TGAError  # noqa: E402
+
+
+def _sol(tour, rs):
+    return I.Solution(np.asarray(tour, np.int32), np.asarray(rs, np.int32))
+
+
+def _random_case(kind, n, seed, extra_empty):
+    inst = I.vrptw(n, seed) if kind == "vrptw" else I.cvrp_uniform(n, seed)
+    rng = np.random.default_rng(seed)
+    inst.capacity = int(rng.integers(60, 200)) if kind == "vrptw" else -(-int(inst.demand.sum()) // int(rng.integers(2, 6)))
+    sol = I.random_split_solution(inst, seed + 17)
+    rs = list(sol.route_start)
+    for _ in range(extra_empty):      # empty routes at random slots
+        at = int(rng.integers(0, len(rs)))
+        rs.insert(at, rs[at] if at < len(rs) else n)
+    rs = sorted(rs)
+    rs[0], rs[-1] = 0, n
+    return inst, _sol(sol.tour, rs)
+
+
+def _stepwise(inst, sol, mask, max_steps=10 ** 6):
+    ls = LocalSearch(inst, sol, mask).build()
+    cur = sol.copy()
+    steps = 0
+    try:
+        while steps < max_steps:
+            mv = ls.eval_best_move()
+            om = O.best_move(inst, cur, mask, "def")
+            assert mv["valid"] == om["found"]
+            if not om["found"]:
+                break
+            assert (mv["delta"], mv["move_index"]) == (om["delta"], om["idx"]), (steps, mv, om)
+            assert (mv["op"], mv["a"], mv["b"]) == (om["op"], om["a"], om["b"])
+            ls.apply_current_move()
+            if om["delta"] >= 0:
+                break
+            cur = O.apply_move(inst, cur, om["op"], om["a"], om["b"])
+            tour, rs = ls.solution()
+            assert np.array_equal(tour, cur.tour) and np.array_equal(rs, cur.route_start), steps
+            steps += 1
+        st = ls.stats()
+        assert st["status"] == 0, st
+        assert st["final_cost"] == O.solution_cost(inst, cur)
+        assert st["steps"] == steps
+        return steps
+    finally:
+        ls.close()
+
+
+@pytest.mark.parametrize("kind", ["cvrp", "vrptw"])
+@pytest.mark.parametrize("seed", range(8))
+def test_stepwise_small_random(kind, seed):
+    """Every step on random instances with n in [3, 60], extra empty routes,
+    all six operator ranks."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(3, 61))
+    inst, sol = _random_case(kind, n, 500 + seed, extra_empty=int(rng.integers(0, 3)))
+    _stepwise(inst, sol, I.MASK_ALL)
+
+
+@pytest.mark.parametrize("mask", [1, 2, 4, 8, 16, 32, I.MASK_CONFIG1, I.MASK_CONFIG3])
+def test_stepwise_single_operators(mask):
+    for kind in ("cvrp", "vrptw"):
+        inst, sol = _random_case(kind, 40, 77 + mask, extra_empty=1)
+        _stepwise(inst, sol, mask)
+
+
+def test_long_routes_multi_chunk_scans():
+    """Routes longer than a warp (scan in chunks) and a single long route."""
+    inst = I.cvrp_uniform(150, 9)
+    inst.capacity = int(inst.demand.sum())            # one route of 150 customers
+    sol = I.random_split_solution(inst, 10)
+    assert sol.n_routes == 1
+    _stepwise(inst, _sol(sol.tour, [0, 75, 150]), I.MASK_ALL, max_steps=60)
+    inst2 = I.vrptw(120, 3)
+    inst2.capacity = 10 ** 6
+    sol2 = I.random_split_solution(inst2, 4)
+    _stepwise(inst2, _sol(sol2.tour, [0, 40, 120, 120]), I.MASK_ALL, max_steps=60)
+
+
+def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None):
+    ls = LocalSearch(inst, sol, mask, log_capacity=cap).build()
+    try:
+        if tile is not None:
+            ls.set_tile(*tile)
+        st = ls.descend()
+        log = ls.move_log()
+        tour, rs = ls.solution()
+        return st, log, _sol(tour, rs)
+    finally:
+        ls.close()
+
+
+@pytest.mark.parametrize("tile", [None, (16, 2), (32, 4), (64, 8), (0, 0)])
+def test_config1_full_trajectory(tile):
+    inst, sol = I.config1(1)
+    st, log, fin = _descend_gpu(inst, sol, I.MASK_CONFIG1, tile=tile)
+    ofin, steps, olog, ocands = O.descend(inst, sol, I.MASK_CONFIG1, "def")
+    assert st["status"] == 0 and st["local_optimum"] == 1
+    assert st["steps"] == steps and np.array_equal(log, olog)
+    assert np.array_equal(fin.tour, ofin.tour) and np.array_equal(fin.route_start, ofin.route_start)
+    assert st["final_cost"] == O.solution_cost(inst, ofin)
+    assert st["candidates"] == ocands
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_small_vrptw_full_trajectory(seed):
+    inst = I.vrptw(200, seed)
+    sol = I.random_split_solution(inst, I.solution_seed(seed))
+    st, log, fin = _descend_gpu(inst, sol, I.MASK_ALL)
+    ofin, steps, olog, ocands = O.descend(inst, sol, I.MASK_ALL, "concat")
+    assert st["steps"] == steps and np.array_equal(log, olog)
+    assert np.array_equal(fin.tour, ofin.tour)
+    assert st["candidates"] == ocands
+
+
+def test_apply_arbitrary_candidates():
+    """tga_apply_move on non-best candidates of every op type: the result
+    equals the oracle's route surgery and the cost follows the delta."""
+    rng = np.random.default_rng(3)
+    for kind in ("cvrp", "vrptw"):
+        inst, sol = _random_case(kind, 30, 31, extra_empty=1)
+        ls = LocalSearch(inst, sol, I.MASK_ALL).build()
+        cur = sol.copy()
+        cost = O.solution_cost(inst, cur)
+        try:
+            for _ in range(60):
+                idx, dl = O.list_moves(inst, cur, I.MASK_ALL, "def")
+                pick = int(rng.integers(0, len(idx)))
+                W = inst.n + 1 + cur.n_routes
+                ix, delta = int(idx[pick]), int(dl[pick])
+                op, a, b = ix // (W * W), (ix % (W * W)) // W, ix % W
+                if delta >= 0:          # only improving moves change the solution
+                    continue
+                mv = torch.tensor([delta, np.int32(np.uint32(ix).view(np.int32)), op, a, b, 1],
+                                  dtype=torch.int32, device="cuda:0")
+                from paper_2506_17357_gb300.tga import tga_apply_move
+                tga_apply_move(ls.ctx, mv.data_ptr())
+                cur = O.apply_move(inst, cur, op, a, b)
+                cost += delta
+                tour, rs = ls.solution()
+                assert np.array_equal(tour, cur.tour) and np.array_equal(rs, cur.route_start)
+                assert ls.stats()["final_cost"] == cost == O.solution_cost(inst, cur)
+                # attributes after the apply drive the next evaluation correctly
+                mvb = ls.eval_best_move()
+                om = O.best_move(inst, cur, I.MASK_ALL)
+                assert (mvb["delta"], mvb["move_index"]) == (om["delta"], om["idx"])
+        finally:
+            ls.close()
+
+
+def test_invalid_inputs_reported():
+    inst, sol = I.config1(1)
+    bad = I.Instance(**{**inst.__dict__})
+    bad.dist = inst.dist.copy()
+    bad.dist[3, 5] += 1                       # asymmetric
+    ls = LocalSearch(bad, sol, I.MASK_CONFIG1)
+    with pytest.raises(TGAError) as e:
+        ls.descend()
+    assert e.value.code == 1
+    ls.close()
+    dup = sol.copy()
+    dup.tour = dup.tour.copy()
+    dup.tour[1] = dup.tour[0]                 # not a permutation
+    ls = LocalSearch(inst, dup, I.MASK_CONFIG1)
+    with pytest.raises(TGAError):
+        ls.descend()
+    ls.close()
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads: GPU trajectory verified by the oracle in a spawn pool
+
+_W = {}
+
+
+def _worker_init(cfg, seed):
+    _W["inst"], _ = {2: I.config2, 3: I.config3}[cfg](seed)
+
+
+def _worker_eval(args):
+    tour, rs, mask, method = args
+    return O.best_move(_W["inst"], _sol(tour, rs), mask, method)["key"]
+
+
+def _replay(inst, sol, log, W):
+    states = [sol]
+    cur = sol
+    for k in log[:-1]:
+        delta, idx = O.unpack_key(int(k))
+        assert delta < 0
+        op, a, b = idx // (W * W), (idx % (W * W)) // W, idx % W
+        cur = O.apply_move(inst, cur, op, a, b)
+        states.append(cur)
+    return states
+
+
+def _verify_pool(cfg, seed, states, log, picks, mask, method):
+    procs = min(len(picks), max(1, (os.cpu_count() or 2) - 1))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs, initializer=_worker_init, initargs=(cfg, seed)) as pool:
+        keys = pool.map(_worker_eval, [(states[k].tour, states[k].route_start, mask, method) for k in picks],
+                        chunksize=1)
+    for k, key in zip(picks, keys):
+        assert key == int(log[k]), f"step {k}: gpu {int(log[k]):#x} oracle {key:#x}"
+
+
+def test_config2_full_trajectory_every_step():
+    inst, sol = I.config2(1)
+    st, log, fin = _descend_gpu(inst, sol, I.MASK_CONFIG2)
+    assert st["status"] == 0 and st["local_optimum"] == 1
+    assert len(log) == st["steps"] + 1
+    states = _replay(inst, sol, log, inst.n + 1 + sol.n_routes)
+    assert np.array_equal(states[-1].tour, fin.tour) and np.array_equal(states[-1].route_start, fin.route_start)
+    assert st["final_cost"] == O.solution_cost(inst, fin)
+    assert O.check_solution(inst, fin) == 0
+    budget = int(os.environ.get("TGA_C2_CHECK_STEPS", "0"))
+    picks = list(range(len(log)))
+    if budget and budget < len(picks):        # optional cap for slow hosts: first, last, spread
+        picks = sorted(set(picks[:budget // 2] + picks[-1:] + picks[::max(1, len(picks) // (budget // 2))]))
+    _verify_pool(2, 1, states, log, picks, I.MASK_CONFIG2, "concat")
+
+
+def test_config3_sampled_steps_and_local_optimum():
+    inst, sol = I.config3(1)
+    st, log, fin = _descend_gpu(inst, sol, I.MASK_CONFIG3)
+    assert st["status"] == 0 and st["local_optimum"] == 1
+    assert len(log) == st["steps"] + 1
+    W = inst.n + 1 + sol.n_routes
+    states = _replay(inst, sol, log, W)
+    assert np.array_equal(states[-1].tour, fin.tour)
+    assert st["final_cost"] == O.solution_cost(inst, fin)
+    assert O.check_solution(inst, fin) == 0
+    n = len(log)
+    picks = sorted(set([0, 1, 2, n // 4, n // 2, 3 * n // 4, n - 2, n - 1]) - {-1})
+    _verify_pool(3, 1, states, log, [p for p in picks if 0 <= p < n], I.MASK_CONFIG3, "concat")
