@@ -169,6 +169,14 @@ int tga_set_move_log(tga_ctx *ctx, uint64_t *log_dev, int64_t capacity);
 int tga_set_tile(tga_ctx *ctx, int32_t rows, int32_t warps);
 int tga_get_tile(tga_ctx *ctx, int32_t *rows, int32_t *warps);
 
+/* Diagnostic: synchronise and copy one internal array to host memory.
+ * what: 0 control block, 1 positions (int32 anchor per position), 2 anchor
+ * positions, 3 base attributes (64 B per anchor), 4 hoisted constants
+ * (128 B per anchor), 5 route records (32 B per route), 6 position-ordered
+ * distance copy ((n+1) rows of row_pitch int32), 7 tile list (int2).
+ * Copies min(bytes, size) bytes; *size_out (may be NULL) gets the size. */
+int tga_debug_read(tga_ctx *ctx, int32_t what, void *host_dst, size_t bytes, size_t *size_out);
+
 /* Release the context's workspace (not the caller's arrays). */
 int tga_destroy(tga_ctx *ctx);
 

@@ -386,6 +386,31 @@ int tga_get_tile(tga_ctx *c, int32_t *rows, int32_t *warps) {
     return TGA_OK;
 }
 
+int tga_debug_read(tga_ctx *c, int32_t what, void *host_dst, size_t bytes, size_t *size_out) {
+    if (!c) return TGA_ERR_INVALID;
+    const Dev &d = c->d;
+    const void *src = nullptr;
+    size_t size = 0;
+    switch (what) {
+        case 0: src = d.ctl; size = sizeof(Control); break;
+        case 1: src = d.seq; size = sizeof(int) * (size_t)d.Wp; break;
+        case 2: src = d.pos_of; size = sizeof(int) * (size_t)(d.W + 1); break;
+        case 3: src = d.brec; size = sizeof(BRec) * (size_t)(d.W + 1); break;
+        case 4: src = d.erec; size = sizeof(ERec) * (size_t)(d.W + 1); break;
+        case 5: src = d.rrec; size = sizeof(RouteRec) * (size_t)d.m; break;
+        case 6: src = d.pcol; size = sizeof(int) * (size_t)(d.n + 1) * (size_t)d.ldp; break;
+        case 7: src = c->tiles; size = sizeof(int2) * (size_t)c->ntiles; break;
+        default: return TGA_ERR_INVALID;
+    }
+    if (size_out) *size_out = size;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TGA_ERR_CUDA;
+    if (host_dst && bytes && src) {
+        if (cudaMemcpy(host_dst, src, bytes < size ? bytes : size, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return TGA_ERR_CUDA;
+    }
+    return TGA_OK;
+}
+
 int tga_destroy(tga_ctx *c) {
     if (!c) return TGA_ERR_INVALID;
     if (c->stream) cudaStreamSynchronize(c->stream);

@@ -62,7 +62,7 @@ struct Control {
     long long steps, evals, cand_total, cost, initial_cost, step_limit, cand_per_eval;
     long long sumL2, sumLm1, sumLm2;          // sum L^2, sum max(0,L-1), sum max(0,L-2)
     int done, status, chg_count, local_opt;
-    int maxL, maxLoad;                        // monotone upper bounds for the range check
+    int maxL, maxLoad;                        // longest route and heaviest load (range check)
     int maxc, maxl, maxs, maxd, maxe, built;
     int last_op, last_a, last_b, last_delta;
     int pad[4];
@@ -137,7 +137,7 @@ __device__ __forceinline__ Seg seg_node(const Dev &d, int node, int out) {
 }
 
 __device__ __forceinline__ unsigned long long pack_key(int delta, unsigned idx) {
-    return ((unsigned long long)(unsigned)(delta + (int)0x80000000u) << 32) | idx;
+    return ((unsigned long long)((unsigned)delta + 0x80000000u) << 32) | idx;
 }
 
 __device__ __forceinline__ int key_delta(unsigned long long k) {

@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
     __shared__ int s_act, s_cnt;
     __shared__ int s_lo, s_hi, s_delta_len, s_n1, s_n2, s_b1, s_b2;
     __shared__ long long s_oldcost;
-    __shared__ int s_oldLA, s_oldLB;
+    __shared__ int s_oldLA, s_oldLB, s_maxL, s_maxLoad;
     const int tid = threadIdx.x;
     if (tid == 0) {
         int act = 0;
@@ -861,6 +861,8 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
         }
         s_act = act;
         s_cnt = 0;
+        s_maxL = 0;
+        s_maxLoad = 0;
     }
     __syncthreads();
     if (s_act) {
@@ -923,6 +925,16 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
         if (warp == 0) rebuild_route(d, pl.A, lane);
         if (warp == 1 && pl.B != pl.A) rebuild_route(d, pl.B, lane);
         __syncthreads();
+        // exact longest route and heaviest load for the integer headroom check
+        int mL = 0, mLoad = 0;
+        for (int r = tid; r < d.m; r += blockDim.x) {
+            mL = max(mL, d.rrec[r].len);
+            mLoad = max(mLoad, d.rrec[r].load);
+        }
+        mL = __reduce_max_sync(0xffffffffu, mL);
+        mLoad = __reduce_max_sync(0xffffffffu, mLoad);
+        if (lane == 0) { atomicMax(&s_maxL, mL); atomicMax(&s_maxLoad, mLoad); }
+        __syncthreads();
     }
     if (tid == 0) {
         if (s_act) {
@@ -937,10 +949,10 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
                 C->sumL2 += sq(pl.nLA) + sq(pl.nLB) - sq(s_oldLA) - sq(s_oldLB);
                 C->sumLm1 += max(pl.nLA - 1, 0) + max(pl.nLB - 1, 0) - max(s_oldLA - 1, 0) - max(s_oldLB - 1, 0);
                 C->sumLm2 += max(pl.nLA - 2, 0) + max(pl.nLB - 2, 0) - max(s_oldLA - 2, 0) - max(s_oldLB - 2, 0);
-                C->maxL = max(C->maxL, max(pl.nLA, pl.nLB));
-                C->maxLoad = max(C->maxLoad, max(d.rrec[pl.A].load, d.rrec[pl.B].load));
                 C->cand_per_eval = candidate_count(d.n, d.m, d.op_mask, C->sumL2, C->sumLm1, C->sumLm2);
             }
+            C->maxL = s_maxL;
+            C->maxLoad = s_maxLoad;
             if (!range_ok(d, C)) { set_status(C, TGA_ERR_RANGE); C->done = 1; }
             C->chg_count = s_cnt;
         } else {

@@ -77,6 +77,8 @@ EXPORTS = [
     ("tga_set_move_log", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("tga_set_tile", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tga_get_tile", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    ("tga_debug_read", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t,
+                                      ctypes.POINTER(ctypes.c_size_t)]),
     ("tga_destroy", ctypes.c_int, [_P]),
     ("tga_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -160,6 +162,15 @@ def tga_get_tile(ctx: int):
     r, w = ctypes.c_int32(), ctypes.c_int32()
     _check(_lib().tga_get_tile(_P(ctx), ctypes.byref(r), ctypes.byref(w)), "tga_get_tile")
     return r.value, w.value
+
+
+def tga_debug_read(ctx: int, what: int) -> np.ndarray:
+    """Copy an internal array (see include/tga.h) as raw int32 values."""
+    size = ctypes.c_size_t()
+    _check(_lib().tga_debug_read(_P(ctx), what, None, 0, ctypes.byref(size)), "tga_debug_read")
+    buf = np.zeros(max(1, size.value // 4), dtype=np.int32)
+    _check(_lib().tga_debug_read(_P(ctx), what, buf.ctypes.data, size.value, None), "tga_debug_read")
+    return buf
 
 
 def tga_destroy(ctx: int):

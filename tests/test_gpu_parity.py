@@ -51,7 +51,7 @@ def _stepwise(inst, sol, mask, max_steps=10 ** 6):
         while steps < max_steps:
             mv = ls.eval_best_move()
             om = O.best_move(inst, cur, mask, "def")
-            assert mv["valid"] == om["found"]
+            assert mv["valid"] == om["found"], (steps, mv, om, ls.stats())
             if not om["found"]:
                 break
             assert (mv["delta"], mv["move_index"]) == (om["delta"], om["idx"]), (steps, mv, om)
@@ -91,16 +91,32 @@ def test_stepwise_single_operators(mask):
 
 
 def test_long_routes_multi_chunk_scans():
-    """Routes longer than a warp (scan in chunks) and a single long route."""
+    """Routes longer than a warp (scans run in chunks with a carry)."""
     inst = I.cvrp_uniform(150, 9)
-    inst.capacity = int(inst.demand.sum())            # one route of 150 customers
+    inst.capacity = int(inst.demand.sum())            # no capacity pressure
     sol = I.random_split_solution(inst, 10)
     assert sol.n_routes == 1
     _stepwise(inst, _sol(sol.tour, [0, 75, 150]), I.MASK_ALL, max_steps=60)
-    inst2 = I.vrptw(120, 3)
+    inst2 = I.vrptw(105, 3)
     inst2.capacity = 10 ** 6
     sol2 = I.random_split_solution(inst2, 4)
-    _stepwise(inst2, _sol(sol2.tour, [0, 40, 120, 120]), I.MASK_ALL, max_steps=60)
+    # 35-customer VRPTW routes (37 scan elements); the descent stays within the
+    # integer headroom (no route above 57 customers) for its first 20 steps
+    _stepwise(inst2, _sol(sol2.tour, [0, 35, 70, 105, 105]), I.MASK_ALL, max_steps=20)
+
+
+def test_integer_headroom_is_enforced():
+    """A VRPTW state whose routes are so long that a candidate route could
+    cost 2^27 or more is refused with TGA_ERR_RANGE instead of risking int32
+    overflow."""
+    inst = I.vrptw(120, 3)
+    inst.capacity = 10 ** 6
+    sol = I.random_split_solution(inst, 4)
+    ls = LocalSearch(inst, _sol(sol.tour, [0, 120, 120]), I.MASK_ALL)
+    with pytest.raises(TGAError) as e:
+        ls.descend(max_steps=10)
+    assert e.value.code == 2
+    ls.close()
 
 
 def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None):
