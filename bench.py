@@ -1,0 +1,381 @@
+"""Benchmark: best-improvement descent to a local optimum on one GB300.
+
+One bench step = one whole pass of the hot path over one synthetic instance:
+build the attribute representation from the initial solution, then evaluate
+the full neighbourhood (relocate, swap, 2-opt, 2-opt*, or-opt), apply the best
+move on the device, and repeat until no move improves (a local optimum).
+
+Default workload: VRPTW, 1 depot + 1000 customers (all five operators).
+metric = candidate moves evaluated per second over the whole descent; the
+line also carries time-to-local-optimum.  Inputs are device resident when the
+timed region starts; L2 (129 MB) is flushed between timed steps by writing a
+512 MB buffer.  ``e2e`` repeats the measurement through the public Python API
+with host arrays: pinned H2D copies of the instance and solution, build,
+descent, and a D2H read of the final tour, route boundaries and counters.
+
+``--impl reference`` times the CPU oracle (test infrastructure) on the host
+cores on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank runs an independent replica on its own
+instance seed (replicas only; the path is not sharded); value is the sum of
+all ranks' candidates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2506_17357_gb300 import instances as I  # noqa: E402
+
+WORKLOADS = {
+    "vrptw1000": ("VRPTW 1 depot + 1000 customers, all five operators", I.config2, I.MASK_CONFIG2),
+    "cvrp100": ("CVRP 1 depot + 100 customers, relocate/swap/2-opt/2-opt*", I.config1, I.MASK_CONFIG1),
+    "cvrp10000": ("clustered CVRP 1 depot + 10000 customers, relocate/swap/2-opt*/or-opt", I.config3,
+                  I.MASK_CONFIG3),
+}
+
+# Integer operations per inter-route candidate, counted from the delta
+# expressions (adds/subs, min/max, multiplies, plus one compare for the
+# running argmin).  Index: op rank.  CVRP and VRPTW (time-warp terms added).
+OPS_CVRP = {0: 8, 1: 13, 3: 13, 4: 8, 5: 8}
+OPS_TW = {0: 20, 1: 36, 3: 22, 4: 20, 5: 20}
+
+
+def inter_candidates(n, lens, mask):
+    """Valid inter-route candidates per op for route lengths ``lens``."""
+    m = len(lens)
+    A = n + m
+    lens = np.asarray(lens, dtype=np.int64)
+    other = A - (lens + 1)                      # anchors outside the route
+    out = {}
+    if mask & 1:
+        out[0] = int((lens * other).sum())
+    if mask & 2:
+        out[1] = int((n * n - (lens * lens).sum()) // 2)
+    if mask & 8:
+        out[3] = int((A * A - ((lens + 1) ** 2).sum()) // 2)
+    if mask & 16:
+        out[4] = int((np.maximum(lens - 1, 0) * other).sum())
+    if mask & 32:
+        out[5] = int((np.maximum(lens - 2, 0) * other).sum())
+    return out
+
+
+def algorithmic_ops(n, lens, mask, has_tw):
+    table = OPS_TW if has_tw else OPS_CVRP
+    return sum(table[op] * c for op, c in inter_candidates(n, lens, mask).items())
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("tga_kernels.cu", "tga_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2506_17357_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    """DRAM bytes per inter-kernel launch from the committed ncu summary, or
+    None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "k_eval_inter_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(workload)
+    if not ent or ent.get("source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def bench_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2506_17357_gb300 import tga as T
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    desc, make, mask = WORKLOADS[args.workload]
+    seed = args.seed + rank
+    inst, sol = make(seed)
+    stream = torch.cuda.Stream(dev)
+    ls = T.LocalSearch(inst, sol, mask, device=dev, stream=stream).build()
+    tile = ls.set_tile(0, 0)                                   # autotune on the initial state
+    torch.cuda.synchronize()
+    tour0 = ls.tour.clone()
+    rs0 = ls.route_start.clone()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def restore():
+        with torch.cuda.stream(stream):
+            ls.tour.copy_(tour0)
+            ls.route_start.copy_(rs0)
+
+    def one_step():
+        T.tga_build_attrs(ls.ctx)
+        return T.tga_descend(ls.ctx)
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        restore()
+        one_step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    times, cands, steps, stats = [], 0, [], None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1)                                      # evict L2 between timed steps
+            restore()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            stats = one_step()                                  # synchronises at its end
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            cands += stats["candidates"]
+            steps.append(stats["steps"])
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    total = float(sum(times))
+    t_max = total
+    c_all = cands
+    if ws > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        c = torch.tensor([cands], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        c_all = float(c.item())
+    value = c_all / t_max
+    tlo_ms = 1e3 * total / args.steps
+    evals = stats["evaluations"]
+    # gpu launches per descent: build (check, positions, perm, routes, finish,
+    # pcol init) + begin + 4 per evaluation (inter, intra, apply, band)
+    launches_per_step = 6 + 1 + 4 * evals
+
+    # ---- end to end through the public API with host buffers
+    e2e_times = []
+    h2d = d2h = 0
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = ls.reload(inst, sol)                         # pinned H2D + build
+        st = T.tga_descend(ls.ctx)
+        tour, rs = ls.solution()                           # D2H of the result
+        t1 = time.perf_counter()
+        d2h = (tour.nbytes + rs.nbytes + 48)
+        if k >= args.warmup:
+            e2e_times.append(t1 - t0)
+        assert st["candidates"] == stats["candidates"]
+    e2e_value = stats["candidates"] * len(e2e_times) / sum(e2e_times)
+
+    # ---- roofline of the dominant kernel (inter-route evaluation), timed live
+    # with CUDA events on the context's stream at states along the trajectory
+    peaks, peak_src = load_peaks()
+    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = 152 * 4 * 32 * sm_mhz_max * 1e6              # INT32 lane-ops/s at issue peak
+    restore()
+    T.tga_build_attrs(ls.ctx)
+    total_ops = 0.0
+    total_ms = 0.0
+    probes = 5
+    n_steps = steps[-1]
+    for j in range(probes):
+        ms = T.tga_profile_inter(ls.ctx, reps=20)
+        tour_h, rs_h = ls.solution()
+        lens = np.diff(rs_h)
+        total_ops += algorithmic_ops(inst.n, lens, mask, inst.has_tw)
+        total_ms += ms
+        if j + 1 < probes:
+            T.tga_descend(ls.ctx, max_steps=max(1, n_steps // (probes - 1)))
+    achieved = total_ops / (total_ms / 1e3)
+    roof = {"bound": "alu", "kernel": "k_eval_inter", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+            "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops,
+            "peak_source": f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz_max:.0f} MHz (issue peak)",
+            "ms_per_launch": total_ms / probes, "ops_per_launch": total_ops / probes,
+            "traffic": measured_traffic(args.workload), "kernel_source_hash": kernel_source_hash()}
+    ls.close()
+
+    if ws > 1:
+        dist.barrier()
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    line = {
+        "metric": "move evals/s", "value": value, "unit": "candidate moves/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "time_to_local_optimum_ms": tlo_ms, "moves_applied": steps[-1], "evaluations": evals,
+        "candidates_per_descent": stats["candidates"], "initial_cost": stats["initial_cost"],
+        "final_cost": stats["final_cost"],
+        "config": {"workload": args.workload, "desc": desc, "instance_seed": args.seed,
+                   "op_mask": mask, "tile_rows_warps": list(tile), "parallelism": f"replicas x{ws}",
+                   "l2": "flushed between timed steps (512 MB write)"},
+        "e2e": {"value": e2e_value, "unit": "candidate moves/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "time_to_local_optimum_ms": 1e3 * float(np.mean(e2e_times))},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clocks,
+        "roofline": roof,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, seconds=args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, seconds=15.0):
+    """The oracle's concatenation evaluator (plain single-threaded C) on the
+    host: best-improvement steps of the same workload from the same initial
+    solution, as many as fit in ``seconds``."""
+    import oracle as O
+    desc, make, mask = WORKLOADS[args.workload]
+    inst, sol = make(args.seed)
+    cur = sol
+    t0 = time.perf_counter()
+    cands = 0
+    k = 0
+    while time.perf_counter() - t0 < seconds:
+        bm = O.best_move(inst, cur, mask, "concat")
+        cands += bm["candidates"]
+        k += 1
+        if not bm["found"] or bm["delta"] >= 0:
+            break
+        cur = O.apply_move(inst, cur, bm["op"], bm["a"], bm["b"])
+    dt = time.perf_counter() - t0
+    return {"value": cands / dt, "unit": "candidate moves/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {k} best-improvement evaluations of {args.workload} seed {args.seed} "
+                      f"(concatenation evaluator), {dt:.1f} s"}
+
+
+def bench_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    desc, make, mask = WORKLOADS[args.workload]
+    per = max(2.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        cpu_baseline(args, seconds=min(per, 2.0))
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args, seconds=per))
+    dt = time.perf_counter() - t0
+    value = float(np.mean([v["value"] for v in vals]))
+    line = {"impl": "reference", "metric": "move evals/s", "value": value, "unit": "candidate moves/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": desc, "instance_seed": args.seed,
+                                            "op_mask": mask},
+            "cpu_baseline": {"value": value, "unit": "candidate moves/s", "cores": 1, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": "candidate moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tga", choices=["tga", "reference"])
+    ap.add_argument("--workload", default="vrptw1000", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -169,6 +169,12 @@ int tga_set_move_log(tga_ctx *ctx, uint64_t *log_dev, int64_t capacity);
 int tga_set_tile(tga_ctx *ctx, int32_t rows, int32_t warps);
 int tga_get_tile(tga_ctx *ctx, int32_t *rows, int32_t *warps);
 
+/* Time the inter-route evaluation kernel alone on the current state:
+ * `reps` launches bracketed by CUDA events on the context's stream; writes the
+ * mean milliseconds per launch.  Leaves no pending move behind.  Used to
+ * report the kernel's roofline fraction. */
+int tga_profile_inter(tga_ctx *ctx, int32_t reps, float *ms_per_launch);
+
 /* Diagnostic: synchronise and copy one internal array to host memory.
  * what: 0 control block, 1 positions (int32 anchor per position), 2 anchor
  * positions, 3 base attributes (64 B per anchor), 4 hoisted constants

@@ -386,6 +386,38 @@ int tga_get_tile(tga_ctx *c, int32_t *rows, int32_t *warps) {
     return TGA_OK;
 }
 
+int tga_profile_inter(tga_ctx *c, int32_t reps, float *ms_per_launch) {
+    if (!c || reps < 1 || !ms_per_launch) return TGA_ERR_INVALID;
+    if (!c->built) return TGA_ERR_STATE;
+    if (!c->tiles && c->d.Wp > 2) default_tiles(c);
+    Control C;
+    int rc = read_control(c, &C);
+    if (rc) return rc;
+    const int was_done = C.done;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TGA_ERR_CUDA;
+    // the kernel returns immediately on a finished context: clear the flag
+    cudaMemsetAsync(&c->d.ctl->done, 0, sizeof(int), c->stream);
+    launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);   // warm-up
+    cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < reps; ++k) launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_launch = ms / reps;
+    cudaMemsetAsync(&c->d.ctl->best_key, 0xff, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(&c->d.ctl->done, 0, sizeof(int), c->stream);
+    if (was_done) {
+        int one = 1;
+        cudaMemcpyAsync(&c->d.ctl->done, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    return check_launch();
+}
+
 int tga_debug_read(tga_ctx *c, int32_t what, void *host_dst, size_t bytes, size_t *size_out) {
     if (!c) return TGA_ERR_INVALID;
     const Dev &d = c->d;

@@ -188,6 +188,8 @@ void launch_check_instance(const Dev &d, cudaStream_t s);
 void launch_build(const Dev &d, cudaStream_t s);
 void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
                  cudaStream_t s);
+void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
+                  cudaStream_t s);
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond,
                   cudaStream_t s);
 void launch_band(const Dev &d, cudaStream_t s);

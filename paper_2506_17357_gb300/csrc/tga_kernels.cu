@@ -1047,18 +1047,21 @@ void launch_build(const Dev &d, cudaStream_t s) {
     k_pcol_init<<<(int)blocks, 256, 0, s>>>(d);
 }
 
-void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s) {
+void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s) {
+    if (ntiles <= 0) return;
     const size_t sm = inter_smem_bytes(rows, warps);
     const bool orr = (d.op_mask & 48u) != 0;
-    if (ntiles > 0) {
-        if (d.has_tw) {
-            if (orr) k_eval_inter<true, true><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
-            else k_eval_inter<true, false><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
-        } else {
-            if (orr) k_eval_inter<false, true><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
-            else k_eval_inter<false, false><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
-        }
+    if (d.has_tw) {
+        if (orr) k_eval_inter<true, true><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
+        else k_eval_inter<true, false><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
+    } else {
+        if (orr) k_eval_inter<false, true><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
+        else k_eval_inter<false, false><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
     }
+}
+
+void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s) {
+    launch_inter(d, tiles, ntiles, rows, warps, s);
     const int nb = (d.Wp - 1 + 127) / 128;
     if (d.has_tw) k_eval_intra<true><<<nb, 128, 0, s>>>(d);
     else k_eval_intra<false><<<nb, 128, 0, s>>>(d);

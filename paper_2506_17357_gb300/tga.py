@@ -77,6 +77,7 @@ EXPORTS = [
     ("tga_set_move_log", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("tga_set_tile", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tga_get_tile", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    ("tga_profile_inter", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     ("tga_debug_read", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t)]),
     ("tga_destroy", ctypes.c_int, [_P]),
@@ -164,6 +165,13 @@ def tga_get_tile(ctx: int):
     return r.value, w.value
 
 
+def tga_profile_inter(ctx: int, reps: int = 10) -> float:
+    """Mean milliseconds per launch of the inter-route evaluation kernel."""
+    ms = ctypes.c_float()
+    _check(_lib().tga_profile_inter(_P(ctx), reps, ctypes.byref(ms)), "tga_profile_inter")
+    return ms.value
+
+
 def tga_debug_read(ctx: int, what: int) -> np.ndarray:
     """Copy an internal array (see include/tga.h) as raw int32 values."""
     size = ctypes.c_size_t()
@@ -223,6 +231,34 @@ class LocalSearch:
         self.ctx = tga_create(self.c_inst, self.c_sol, self.op_mask, self.stream.cuda_stream)
         if self.log is not None:
             tga_set_move_log(self.ctx, self.log.data_ptr(), log_capacity)
+
+    # -- reuse the device buffers for another solution / instance of the same size
+    def reload(self, inst=None, sol=None):
+        """Copy new host arrays into the existing device tensors (same shapes)
+        and rebuild the attributes.  Host arrays are staged in pinned memory so
+        the copies are asynchronous on the context's stream."""
+        torch = self.torch
+        pairs = []
+        if inst is not None:
+            pairs += [(self.dist, inst.dist), (self.demand, inst.demand), (self.service, inst.service),
+                      (self.early, inst.tw_early), (self.late, inst.tw_late)]
+        if sol is not None:
+            pairs += [(self.tour, sol.tour), (self.route_start, sol.route_start)]
+        if not hasattr(self, "_pinned"):
+            self._pinned = {}
+        nbytes = 0
+        with torch.cuda.stream(self.stream):
+            for dev, host in pairs:
+                key = dev.data_ptr()
+                buf = self._pinned.get(key)
+                if buf is None:
+                    buf = torch.empty(dev.numel(), dtype=torch.int32).pin_memory()
+                    self._pinned[key] = buf
+                buf.numpy()[:] = np.ascontiguousarray(host, dtype=np.int32).reshape(-1)
+                dev.view(-1).copy_(buf, non_blocking=True)
+                nbytes += dev.numel() * 4
+        tga_build_attrs(self.ctx)
+        return nbytes
 
     # -- calls
     def build(self):
