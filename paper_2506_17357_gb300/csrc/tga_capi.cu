@@ -149,7 +149,11 @@ int descend_launch(tga_ctx *c, int64_t max_steps) {
     }
     if (!c->tiles && c->d.Wp > 2) default_tiles(c);
     launch_begin(c->d, max_steps, c->stream);
-    if (build_graph(c) == TGA_OK) {
+    // TGA_GRAPH=0 launches the same per-step kernels from the host (for
+    // profilers that do not trace kernels inside conditional graph bodies)
+    const char *env = getenv("TGA_GRAPH");
+    const bool use_graph = !(env && env[0] == '0');
+    if (use_graph && build_graph(c) == TGA_OK) {
         if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return TGA_ERR_CUDA;
         return check_launch();
     }
@@ -232,6 +236,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     const size_t o_sr = take(sizeof(int) * (size_t)d.Wp);
     const size_t o_ss = take(sizeof(int) * (size_t)d.Wp);
     const size_t o_seen = take(sizeof(int) * (size_t)(n + 1));
+    const size_t o_intra = take(sizeof(int) * 10 * (size_t)(d.Wp + m));
     const size_t o_pcol = take(sizeof(int) * (size_t)(n + 1) * (size_t)d.ldp);
     c->ws_bytes = off;
     if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
@@ -252,6 +257,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.scr_route = (int *)(base + o_sr);
     d.scr_src = (int *)(base + o_ss);
     d.seen = (int *)(base + o_seen);
+    d.scr_intra = (int *)(base + o_intra);
     d.pcol = (int *)(base + o_pcol);
     if (cudaMemsetAsync(d.ctl, 0, sizeof(Control), c->stream) != cudaSuccess ||
         setup_kernel_attrs(d.Wp) != 0) {

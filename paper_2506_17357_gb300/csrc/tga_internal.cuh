@@ -89,6 +89,7 @@ struct Dev {
     int *scr_route;           // [Wp]
     int *scr_src;             // [Wp]
     int *seen;                // [n+1] permutation check scratch
+    int *scr_intra;           // [10 * (Wp+m)] per-element arrays of routes too long for shared memory
 };
 
 __host__ __device__ inline int node_of(int anchor, int n) { return anchor <= n ? anchor : 0; }

@@ -232,17 +232,35 @@ __device__ bool range_ok(const Dev &d, const Control *C) {
 // ---------------------------------------------------------------------------
 // build
 
-__global__ void k_check_instance(Dev d) {
+// Symmetry / diagonal / sign check of the distance matrix, tile by tile:
+// block (32 x 8 threads) loads tile (I, J) and tile (J, I) with coalesced row
+// reads into shared memory and compares one against the transpose of the other.
+__global__ void __launch_bounds__(256) k_check_instance(Dev d) {
     Control *C = d.ctl;
-    const long long n1 = d.n + 1, tot = n1 * n1;
+    __shared__ int A[32][33], B[32][33];
+    const int n1 = d.n + 1, nt = (n1 + 31) / 32;
+    const long long ntiles = (long long)nt * nt;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     int mx = 0;
     bool bad = false;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long i = t / n1, j = t - i * n1;
-        const int v = d.dist[t];
-        if (v < 0 || (i == j && v != 0) || v != d.dist[j * n1 + i]) bad = true;
-        mx = max(mx, v);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int I = (int)(t / nt), J = (int)(t - (long long)I * nt);
+        for (int rr = ty; rr < 32; rr += 8) {
+            const int i = I * 32 + rr, j = J * 32 + tx;
+            A[rr][tx] = (i < n1 && j < n1) ? d.dist[(size_t)i * n1 + j] : 0;
+            const int i2 = J * 32 + rr, j2 = I * 32 + tx;
+            B[rr][tx] = (i2 < n1 && j2 < n1) ? d.dist[(size_t)i2 * n1 + j2] : 0;
+        }
+        __syncthreads();
+        for (int rr = ty; rr < 32; rr += 8) {
+            const int i = I * 32 + rr, j = J * 32 + tx;
+            if (i < n1 && j < n1) {
+                const int v = A[rr][tx];
+                if (v < 0 || (i == j && v != 0) || v != B[tx][rr]) bad = true;
+                mx = max(mx, v);
+            }
+        }
+        __syncthreads();
     }
     int md = 0, ml = 0, ms = 0, me = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n1;
@@ -251,9 +269,9 @@ __global__ void k_check_instance(Dev d) {
         if (dm < 0 || (i == 0 && dm != 0)) bad = true;
         md = max(md, dm);
         if (d.has_tw) {
-            const int e = d.early[i], l = d.late[i], s = d.service[i];
-            if (e < 0 || l < 0 || s < 0 || (i == 0 && s != 0)) bad = true;
-            ml = max(ml, l); ms = max(ms, s); me = max(me, e);
+            const int e = d.early[i], l = d.late[i], sv = d.service[i];
+            if (e < 0 || l < 0 || sv < 0 || (i == 0 && sv != 0)) bad = true;
+            ml = max(ml, l); ms = max(ms, sv); me = max(me, e);
         }
     }
     mx = __reduce_max_sync(0xffffffffu, mx);
@@ -548,166 +566,216 @@ __global__ void __launch_bounds__(256) k_eval_inter(Dev d, const int2 *__restric
 
 // ---------------------------------------------------------------------------
 // intra-route evaluation
+//
+// One warp per route.  The route's elements (0 = start depot, 1..L
+// customers, L+1 = end depot) are staged in shared memory with their node
+// data, the prefix/suffix attributes of every anchor, and -- when it fits --
+// the route's (L+2) x (L+2) distance block, read as contiguous row segments
+// of the position-ordered distance copy.  Lane i then sweeps the other end
+// of every move that starts (or ends) at element i, maintaining the middle
+// segment incrementally with the concatenation operator, so each candidate
+// is O(1) (route-based extraction of Section 5.3.1 with the attribute-matrix
+// rows of Section 4.2 built on the fly).
+
+constexpr int kIntraWarps = 4;
+constexpr int kIntraSmemPerWarp = 2816;      // ints (11 KB)
+constexpr int kIntraVec = 10;                // staged per-element int arrays
+
+struct RouteView {
+    const Dev *d;
+    int r, L, E, st;
+    bool inS;                 // distance block in shared memory
+    const int *node, *e, *l, *s, *tau, *twf, *distf, *Lg, *twg, *distg;
+    const int *D;             // E x E (if inS)
+    __device__ __forceinline__ int c(int a, int b) const {
+        if (inS) return D[a * E + b];
+        return __ldg(d->pcol + (size_t)node[a] * d->ldp + kColOff + st + b);
+    }
+    __device__ __forceinline__ int anchor(int k) const { return k == 0 ? d->n + 1 + r : node[k]; }
+    __device__ __forceinline__ Seg seg(int k, int out) const {
+        Seg x;
+        x.E = e[k]; x.L = l[k]; x.D = s[k]; x.TW = 0; x.dist = 0; x.load = 0; x.out = out;
+        return x;
+    }
+};
 
 template <bool TW>
-__global__ void __launch_bounds__(256) k_eval_intra(Dev d) {
-    if (*(volatile int *)&d.ctl->done) return;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    int best = kBestInit;
-    unsigned bidx = 0xffffffffu;
-    if (p < d.Wp - 1) {
-        const unsigned W = (unsigned)d.W, W2 = W * W;
-        const unsigned mask = d.op_mask;
-        const int ax = d.seq[p];
-        const BRec bx = d.brec[ax];
-        const int r = bx.route;
-        const RouteRec R = d.rrec[r];
-        const int L = R.len, st = R.start, i = bx.idx;
-        const int wT = TW ? d.wT : 0;
-        const int baseDist = R.dist, baseTw = R.tw;
-        auto nodeAt = [&](int k) { return route_node(d, st, L, k); };
-        if (i >= 1) {
-            // ---------------- moves that take the customer x_i forward
-            const int xi = ax;
-            const int xm = nodeAt(i - 1);
-            const BRec bp = d.brec[route_anchor(d, r, st, L, i - 1)];
-            const int ei = TW ? __ldg(d.early + xi) : 0, li = TW ? __ldg(d.late + xi) : 0;
-            const int si = TW ? __ldg(d.service + xi) : 0;
-            // relocate / or-opt of the run x_i..x_{i+k-1} to after x_j, j >= i+k
-            for (int k = 1; k <= 3; ++k) {
-                const int op = k == 1 ? 0 : k + 2;
-                if (!(mask & (1u << op)) || i + k - 1 > L) continue;
-                Seg run = seg_node(d, xi, dmat(d, xi, nodeAt(i + 1)));
-                for (int t = 1; t < k; ++t) {
-                    const int y = nodeAt(i + t);
-                    run = seg_cat(run, seg_node(d, y, dmat(d, y, nodeAt(i + t + 1))));
+__device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, int baseDist, int baseTw,
+                             unsigned W, unsigned W2, int &best, unsigned &bidx) {
+    const int L = V.L;
+    if (i >= 1) {
+        // ---------------- moves that take the customer at element i forward
+        const unsigned xi = (unsigned)V.node[i];
+        const int ptau = V.tau[i - 1], ptwf = V.twf[i - 1], pdist = V.distf[i - 1];
+        // relocate / or-opt of the run i..i+k-1 to after element j, j >= i+k
+        for (int k = 1; k <= 3; ++k) {
+            const int op = k == 1 ? 0 : k + 2;
+            if (!(mask & (1u << op)) || i + k - 1 > L) continue;
+            Seg run = V.seg(i, V.c(i, i + 1));
+            for (int t = 1; t < k; ++t) run = seg_cat(run, V.seg(i + t, V.c(i + t, i + t + 1)));
+            int tau = ptau, tw = ptwf, dist = pdist, last = i - 1;
+            for (int j = i + k; j <= L; ++j) {
+                const int c1 = V.c(last, j);
+                dist += c1;
+                if (TW) {
+                    const int a = tau + c1;
+                    const int w = max(a - V.l[j], 0);
+                    tau = max(a, V.e[j]) - w + V.s[j];
+                    tw += w;
                 }
-                const int wlast = nodeAt(i + k - 1);
-                int tau = bp.tau, tw = bp.twf, dist = bp.distf, last = xm;
-                for (int j = i + k; j <= L; ++j) {
-                    const int xj = nodeAt(j);
-                    const int c1 = dmat(d, last, xj);
-                    dist += c1;
-                    if (TW) {
-                        const int a = tau + c1;
-                        const int w = max(a - __ldg(d.late + xj), 0);
-                        tau = max(a, __ldg(d.early + xj)) - w + __ldg(d.service + xj);
-                        tw += w;
-                    }
-                    last = xj;
-                    const BRec bj = d.brec[xj];
-                    const int xn = nodeAt(j + 1);
-                    const int cA = dmat(d, xj, xi), cB = dmat(d, wlast, xn);
-                    int delta = dist + cA + run.dist + cB + bj.distg - baseDist;
-                    if (TW) {
-                        const int a1 = tau + cA, w1 = max(a1 - run.L, 0);
-                        const int a2 = max(a1, run.E) - w1 + run.D - run.TW + cB;
-                        const int w2 = max(a2 - bj.Lg, 0);
-                        delta += wT * (tw + w1 + run.TW + w2 + bj.twg - baseTw);
-                    }
-                    TGA_TRY(delta, (unsigned)op * W2 + (unsigned)xi * W + (unsigned)xj);
+                last = j;
+                const int cA = V.c(j, i), cB = V.c(i + k - 1, j + 1);
+                int delta = dist + cA + run.dist + cB + V.distg[j] - baseDist;
+                if (TW) {
+                    const int a1 = tau + cA, w1 = max(a1 - run.L, 0);
+                    const int a2 = max(a1, run.E) - w1 + run.D - run.TW + cB;
+                    const int w2 = max(a2 - V.Lg[j], 0);
+                    delta += wT * (tw + w1 + run.TW + w2 + V.twg[j] - baseTw);
                 }
-            }
-            // swap x_i <-> x_j, j > i
-            if (mask & 2u) {
-                Seg M{};
-                bool hasM = false;
-                for (int j = i + 1; j <= L; ++j) {
-                    const int xj = nodeAt(j);
-                    if (j > i + 1) {
-                        const int y = nodeAt(j - 1);
-                        const Seg nd = seg_node(d, y, dmat(d, y, xj));
-                        M = hasM ? seg_cat(M, nd) : nd;
-                        hasM = true;
-                    }
-                    const int xn = nodeAt(j + 1);
-                    const BRec bj = d.brec[xj];
-                    const int ca = dmat(d, xm, xj);
-                    int dist = bp.distf + ca + bj.distg;
-                    int tau = 0, tw = 0;
-                    if (TW) {
-                        const int a = bp.tau + ca, w = max(a - __ldg(d.late + xj), 0);
-                        tau = max(a, __ldg(d.early + xj)) - w + __ldg(d.service + xj);
-                        tw = bp.twf + w;
-                    }
-                    int last = xj;
-                    if (hasM) {
-                        const int cb = dmat(d, xj, nodeAt(i + 1));
-                        dist += cb + M.dist;
-                        if (TW) {
-                            const int a = tau + cb, w = max(a - M.L, 0);
-                            tau = max(a, M.E) - w + M.D - M.TW;
-                            tw += w + M.TW;
-                        }
-                        last = nodeAt(j - 1);
-                    }
-                    const int cc = dmat(d, last, xi), cd = dmat(d, xi, xn);
-                    dist += cc + cd;
-                    int delta = dist - baseDist;
-                    if (TW) {
-                        const int a = tau + cc, w = max(a - li, 0);
-                        const int t2 = max(a, ei) - w + si;
-                        const int w4 = max(t2 + cd - bj.Lg, 0);
-                        delta += wT * (tw + w + w4 + bj.twg - baseTw);
-                    }
-                    TGA_TRY(delta, W2 + (unsigned)min(xi, xj) * W + (unsigned)max(xi, xj));
-                }
-            }
-            // 2-opt: reverse x_i..x_j, j > i
-            if (mask & 4u) {
-                Seg Rv = seg_node(d, xi, 0);
-                for (int j = i + 1; j <= L; ++j) {
-                    const int xj = nodeAt(j);
-                    Rv = seg_cat(seg_node(d, xj, dmat(d, xj, nodeAt(j - 1))), Rv);
-                    const int xn = nodeAt(j + 1);
-                    const BRec bj = d.brec[xj];
-                    const int ca = dmat(d, xm, xj), cb = dmat(d, xi, xn);
-                    int delta = bp.distf + ca + Rv.dist + cb + bj.distg - baseDist;
-                    if (TW) {
-                        const int a1 = bp.tau + ca, w1 = max(a1 - Rv.L, 0);
-                        const int a2 = max(a1, Rv.E) - w1 + Rv.D - Rv.TW + cb;
-                        const int w2 = max(a2 - bj.Lg, 0);
-                        delta += wT * (bp.twf + w1 + Rv.TW + w2 + bj.twg - baseTw);
-                    }
-                    TGA_TRY(delta, 2u * W2 + (unsigned)xi * W + (unsigned)xj);
-                }
+                TGA_TRY(delta, (unsigned)op * W2 + xi * W + (unsigned)V.node[j]);
             }
         }
-        // ---------------- moves whose destination is this anchor x_j (j = i):
-        // the run x_t..x_{t+k-1}, t >= j+2, moves back to just after x_j.
-        {
-            const int j = i, xj = node_of(ax, d.n);
-            for (int k = 1; k <= 3; ++k) {
-                const int op = k == 1 ? 0 : k + 2;
-                if (!(mask & (1u << op)) || j + 2 + k - 1 > L) continue;
-                const int xj1 = nodeAt(j + 1);
-                Seg M = seg_node(d, xj1, dmat(d, xj1, nodeAt(j + 2)));
-                for (int t = j + 2; t + k - 1 <= L; ++t) {
-                    if (t > j + 2) {
-                        const int y = nodeAt(t - 1);
-                        M = seg_cat(M, seg_node(d, y, dmat(d, y, nodeAt(t))));
-                    }
-                    const int xt = nodeAt(t);
-                    Seg run = seg_node(d, xt, dmat(d, xt, nodeAt(t + 1)));
-                    for (int u = 1; u < k; ++u) {
-                        const int y = nodeAt(t + u);
-                        run = seg_cat(run, seg_node(d, y, dmat(d, y, nodeAt(t + u + 1))));
-                    }
-                    const int wl = nodeAt(t + k - 1), xn = nodeAt(t + k);
-                    const BRec bw = d.brec[wl];
-                    const int ca = dmat(d, xj, xt), cb = dmat(d, wl, xj1), cc = dmat(d, nodeAt(t - 1), xn);
-                    int delta = bx.distf + ca + run.dist + cb + M.dist + cc + bw.distg - baseDist;
+        // swap element i <-> element j, j > i
+        if (mask & 2u) {
+            Seg M{};
+            for (int j = i + 1; j <= L; ++j) {
+                if (j > i + 2) M = seg_cat(M, V.seg(j - 1, V.c(j - 1, j)));
+                else if (j == i + 2) M = V.seg(i + 1, V.c(i + 1, j));
+                const bool hasM = j > i + 1;
+                const int ca = V.c(i - 1, j);
+                int dist = pdist + ca + V.distg[j];
+                int tau = 0, tw = 0;
+                if (TW) {
+                    const int a = ptau + ca, w = max(a - V.l[j], 0);
+                    tau = max(a, V.e[j]) - w + V.s[j];
+                    tw = ptwf + w;
+                }
+                int last = j;
+                if (hasM) {
+                    const int cb = V.c(j, i + 1);
+                    dist += cb + M.dist;
                     if (TW) {
-                        const int a1 = bx.tau + ca, w1 = max(a1 - run.L, 0);
-                        const int a2 = max(a1, run.E) - w1 + run.D - run.TW + cb;
-                        const int w2 = max(a2 - M.L, 0);
-                        const int a3 = max(a2, M.E) - w2 + M.D - M.TW + cc;
-                        const int w3 = max(a3 - bw.Lg, 0);
-                        delta += wT * (bx.twf + w1 + run.TW + w2 + M.TW + w3 + bw.twg - baseTw);
+                        const int a = tau + cb, w = max(a - M.L, 0);
+                        tau = max(a, M.E) - w + M.D - M.TW;
+                        tw += w + M.TW;
                     }
-                    TGA_TRY(delta, (unsigned)op * W2 + (unsigned)xt * W + (unsigned)ax);
+                    last = j - 1;
+                }
+                const int cc = V.c(last, i), cd = V.c(i, j + 1);
+                dist += cc + cd;
+                int delta = dist - baseDist;
+                if (TW) {
+                    const int a = tau + cc, w = max(a - V.l[i], 0);
+                    const int t2 = max(a, V.e[i]) - w + V.s[i];
+                    const int w4 = max(t2 + cd - V.Lg[j], 0);
+                    delta += wT * (tw + w + w4 + V.twg[j] - baseTw);
+                }
+                const unsigned xj = (unsigned)V.node[j];
+                TGA_TRY(delta, W2 + min(xi, xj) * W + max(xi, xj));
+            }
+        }
+        // 2-opt: reverse elements i..j, j > i
+        if (mask & 4u) {
+            Seg Rv = V.seg(i, 0);
+            for (int j = i + 1; j <= L; ++j) {
+                Rv = seg_cat(V.seg(j, V.c(j, j - 1)), Rv);
+                const int ca = V.c(i - 1, j), cb = V.c(i, j + 1);
+                int delta = pdist + ca + Rv.dist + cb + V.distg[j] - baseDist;
+                if (TW) {
+                    const int a1 = ptau + ca, w1 = max(a1 - Rv.L, 0);
+                    const int a2 = max(a1, Rv.E) - w1 + Rv.D - Rv.TW + cb;
+                    const int w2 = max(a2 - V.Lg[j], 0);
+                    delta += wT * (ptwf + w1 + Rv.TW + w2 + V.twg[j] - baseTw);
+                }
+                TGA_TRY(delta, 2u * W2 + xi * W + (unsigned)V.node[j]);
+            }
+        }
+    }
+    // ---------------- moves whose destination is element j = i: the run
+    // t..t+k-1, t >= j+2, moves back to just after element j.
+    const int j = i;
+    const unsigned aj = (unsigned)V.anchor(j);
+    for (int k = 1; k <= 3; ++k) {
+        const int op = k == 1 ? 0 : k + 2;
+        if (!(mask & (1u << op)) || j + 2 + k - 1 > L) continue;
+        Seg M = V.seg(j + 1, V.c(j + 1, j + 2));
+        for (int t = j + 2; t + k - 1 <= L; ++t) {
+            if (t > j + 2) M = seg_cat(M, V.seg(t - 1, V.c(t - 1, t)));
+            Seg run = V.seg(t, V.c(t, t + 1));
+            for (int u = 1; u < k; ++u) run = seg_cat(run, V.seg(t + u, V.c(t + u, t + u + 1)));
+            const int w = t + k - 1;
+            const int ca = V.c(j, t), cb = V.c(w, j + 1), cc = V.c(t - 1, t + k);
+            int delta = V.distf[j] + ca + run.dist + cb + M.dist + cc + V.distg[w] - baseDist;
+            if (TW) {
+                const int a1 = V.tau[j] + ca, w1 = max(a1 - run.L, 0);
+                const int a2 = max(a1, run.E) - w1 + run.D - run.TW + cb;
+                const int w2 = max(a2 - M.L, 0);
+                const int a3 = max(a2, M.E) - w2 + M.D - M.TW + cc;
+                const int w3 = max(a3 - V.Lg[w], 0);
+                delta += wT * (V.twf[j] + w1 + run.TW + w2 + M.TW + w3 + V.twg[w] - baseTw);
+            }
+            TGA_TRY(delta, (unsigned)op * W2 + (unsigned)V.node[t] * W + aj);
+        }
+    }
+}
+
+template <bool TW>
+__global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d) {
+    if (*(volatile int *)&d.ctl->done) return;
+    __shared__ int smem[kIntraWarps * kIntraSmemPerWarp];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * kIntraWarps + warp;
+    int best = kBestInit;
+    unsigned bidx = 0xffffffffu;
+    if (r < d.m) {
+        const RouteRec R = d.rrec[r];
+        const int L = R.len;
+        if (L >= 2) {
+            int *S = smem + warp * kIntraSmemPerWarp;
+            RouteView V;
+            V.d = &d; V.r = r; V.L = L; V.E = L + 2; V.st = R.start;
+            const int E = V.E;
+            const bool vecS = kIntraVec * E <= kIntraSmemPerWarp;
+            V.inS = vecS && kIntraVec * E + E * E <= kIntraSmemPerWarp;
+            // per-element arrays: shared memory when they fit, else this
+            // route's own slice [start+r, start+r+E) of the global scratch
+            int *base = vecS ? S : d.scr_intra + (R.start + r);
+            const int stride = vecS ? E : d.Wp + d.m;
+            int *node = base, *e = base + stride, *l = base + 2 * stride, *s = base + 3 * stride;
+            int *tau = base + 4 * stride, *twf = base + 5 * stride, *distf = base + 6 * stride;
+            int *Lg = base + 7 * stride, *twg = base + 8 * stride, *distg = base + 9 * stride;
+            V.node = node; V.e = e; V.l = l; V.s = s; V.tau = tau; V.twf = twf; V.distf = distf;
+            V.Lg = Lg; V.twg = twg; V.distg = distg;
+            for (int k = lane; k < E; k += 32) {
+                const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[V.st + k] : -1);
+                const int x = (k >= 1 && k <= L) ? a : 0;
+                node[k] = x;
+                if (TW) { e[k] = __ldg(d.early + x); l[k] = __ldg(d.late + x); s[k] = __ldg(d.service + x); }
+                else { e[k] = 0; l[k] = 0; s[k] = 0; }
+                if (a >= 0) {
+                    const BRec b = d.brec[a];
+                    tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
+                    Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
+                } else {
+                    tau[k] = 0; twf[k] = 0; distf[k] = 0; Lg[k] = 0; twg[k] = 0; distg[k] = 0;
                 }
             }
+            __syncwarp();
+            if (V.inS) {
+                int *D = S + kIntraVec * E;
+                for (int t = lane; t < E * E; t += 32) {
+                    const int a = t / E, b = t - a * E;
+                    D[t] = d.pcol[(size_t)node[a] * d.ldp + kColOff + V.st + b];
+                }
+                V.D = D;
+            } else {
+                V.D = nullptr;
+            }
+            __syncwarp();
+            const unsigned W = (unsigned)d.W, W2 = W * W;
+            const int wT = TW ? d.wT : 0;
+            for (int i = lane; i <= L; i += 32)
+                intra_anchor<TW>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx);
         }
     }
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
@@ -1029,8 +1097,8 @@ int setup_kernel_attrs(int max_band) {
 }
 
 void launch_check_instance(const Dev &d, cudaStream_t s) {
-    const long long tot = (long long)(d.n + 1) * (d.n + 1);
-    long long blocks = (tot + 255) / 256;
+    const long long nt = (d.n + 1 + 31) / 32;
+    long long blocks = nt * nt;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_check_instance<<<(int)blocks, 256, 0, s>>>(d);
 }
@@ -1062,9 +1130,9 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
 
 void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s) {
     launch_inter(d, tiles, ntiles, rows, warps, s);
-    const int nb = (d.Wp - 1 + 127) / 128;
-    if (d.has_tw) k_eval_intra<true><<<nb, 128, 0, s>>>(d);
-    else k_eval_intra<false><<<nb, 128, 0, s>>>(d);
+    const int nb = (d.m + kIntraWarps - 1) / kIntraWarps;
+    if (d.has_tw) k_eval_intra<true><<<nb, kIntraWarps * 32, 0, s>>>(d);
+    else k_eval_intra<false><<<nb, kIntraWarps * 32, 0, s>>>(d);
 }
 
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond, cudaStream_t s) {
