@@ -175,6 +175,25 @@ int tga_get_tile(tga_ctx *ctx, int32_t *rows, int32_t *warps);
  * report the kernel's roofline fraction. */
 int tga_profile_inter(tga_ctx *ctx, int32_t reps, float *ms_per_launch);
 
+/* Best move of one instance + solution WITHOUT allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (a host framework that owns every device
+ * allocation, a plugin handed only a stream and its buffers, a service that
+ * forbids cudaMalloc after start-up).  Inputs are as for tga_create (device
+ * pointers, caller-owned; the solution is read, never written); out_dev is
+ * one tga_move in caller-owned DEVICE memory.
+ * Scratch: a file-scope device array inside the library (about 7 MB; every
+ * GPU that loads libtga holds it until the process exits).  Sizes with
+ * n + m + 1 > 1280 are rejected with TGA_ERR_RANGE.  No cudaMalloc,
+ * cudaFree or allocating library routine is called.
+ * The first call on a device looks up the array's device address for that
+ * device; make that first call before any stream capture.  Every call
+ * shares the one array and overwrites it, so calls whose GPU work overlaps
+ * (other streams, other threads) race: serialise them.  Synchronous: waits
+ * for `stream`, then returns TGA_OK or the device-side error. */
+int tga_eval_best_move_noalloc(const tga_instance *inst, const tga_solution *sol, uint32_t op_mask,
+                               tga_stream_t stream, tga_move *out_dev);
+
 /* Diagnostic: synchronise and copy one internal array to host memory.
  * what: 0 control block, 1 positions (int32 anchor per position), 2 anchor
  * positions, 3 base attributes (64 B per anchor), 4 hoisted constants

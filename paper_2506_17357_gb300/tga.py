@@ -77,6 +77,8 @@ EXPORTS = [
     ("tga_set_move_log", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("tga_set_tile", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tga_get_tile", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    ("tga_eval_best_move_noalloc", ctypes.c_int, [ctypes.POINTER(tga_instance), ctypes.POINTER(tga_solution),
+                                                  ctypes.c_uint32, _P, _P]),
     ("tga_profile_inter", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     ("tga_debug_read", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t)]),
@@ -163,6 +165,15 @@ def tga_get_tile(ctx: int):
     r, w = ctypes.c_int32(), ctypes.c_int32()
     _check(_lib().tga_get_tile(_P(ctx), ctypes.byref(r), ctypes.byref(w)), "tga_get_tile")
     return r.value, w.value
+
+
+def tga_eval_best_move_noalloc(inst: tga_instance, sol: tga_solution, op_mask: int, stream: int,
+                               out_dev_ptr: int):
+    """Allocation-free best-move evaluation (scratch in a fixed device array
+    inside the library; n + m + 1 <= 1280).  Synchronous."""
+    _check(_lib().tga_eval_best_move_noalloc(ctypes.byref(inst), ctypes.byref(sol), op_mask,
+                                             _P(stream or None), _P(out_dev_ptr)),
+           "tga_eval_best_move_noalloc")
 
 
 def tga_profile_inter(ctx: int, reps: int = 10) -> float:

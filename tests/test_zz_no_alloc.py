@@ -1,0 +1,62 @@
+"""Allocation-free best-move evaluation (tga_eval_best_move_noalloc).
+
+Callers that cannot allocate device memory get the best move of an
+instance + solution from a fixed scratch array inside the library.  Its
+result must equal the context-based tga_eval_best_move exactly, also when
+two calls in a row leave the shared scratch holding another instance's data.
+This file is collected last so a failure here never hides another test.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2506_17357_gb300 import instances as I  # noqa: E402
+from paper_2506_17357_gb300 import tga as T  # noqa: E402
+
+
+def _noalloc(ls, mask):
+    out = torch.zeros(6, dtype=torch.int32, device=ls.device)
+    ls.stream.synchronize()
+    T.tga_eval_best_move_noalloc(ls.c_inst, ls.c_sol, mask, ls.stream.cuda_stream, out.data_ptr())
+    v = out.cpu().numpy()
+    return dict(delta=int(v[0]), move_index=int(np.uint32(v[1].view(np.uint32))), op=int(v[2]),
+                a=int(v[3]), b=int(v[4]), valid=bool(v[5]))
+
+
+def test_noalloc_equals_context_path_on_consecutive_calls():
+    inst2, sol2 = I.config2(1)                       # VRPTW, 1000 customers
+    inst1 = I.cvrp_uniform(300, 7)
+    sol1 = I.random_split_solution(inst1, 8)
+    cases = [(inst2, sol2, I.MASK_CONFIG2), (inst1, sol1, I.MASK_CVRP_MIXED)]
+    for inst, sol, mask in cases:                    # two calls in a row, different data
+        ls = T.LocalSearch(inst, sol, mask).build()
+        try:
+            ref = ls.eval_best_move()
+            got = _noalloc(ls, mask)
+            assert got == ref
+            # move the context one step on and compare again
+            ls.apply_current_move()
+            ref2 = ls.eval_best_move()
+            got2 = _noalloc(ls, mask)
+            assert got2 == ref2 and got2 != got
+        finally:
+            ls.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    inst = I.cvrp_uniform(1300, 3)                   # n + m + 1 > 1280
+    sol = I.random_split_solution(inst, 4)
+    ls = T.LocalSearch(inst, sol, I.MASK_CONFIG1)
+    try:
+        out = torch.zeros(6, dtype=torch.int32, device=ls.device)
+        with pytest.raises(T.TGAError) as e:
+            T.tga_eval_best_move_noalloc(ls.c_inst, ls.c_sol, I.MASK_CONFIG1, ls.stream.cuda_stream,
+                                         out.data_ptr())
+        assert e.value.code == T.TGA_ERR_RANGE
+    finally:
+        ls.close()
