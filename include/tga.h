@@ -147,10 +147,22 @@ int tga_apply_move(tga_ctx *ctx, const tga_move *move_dev);
  * Synchronises the stream at the end and fills *out_host (may be NULL). */
 int tga_descend(tga_ctx *ctx, int64_t max_steps, tga_stats *out_host);
 
-/* Descend every context to a local optimum (at most max_steps moves each).
- * Contexts on different streams run concurrently; the call waits for all.
+/* Descend every context to a local optimum (at most max_steps moves each) in
+ * ONE persistent launch on ctxs[0]'s stream (all contexts on one device).
+ * Each context is (re)built from its caller solution inside the launch.
+ * Per step a job is split into chunks (row tiles of its pair triangle, groups
+ * of 8 routes); resident CTAs take chunks of any job and the CTA finishing a
+ * job's last chunk applies its move, so large jobs spread over many SMs.
+ * Idle CTAs poll under a 20 s limit (TGA_ERR_TIMEOUT).  Results per context
+ * equal tga_descend's bit for bit.  Waits for completion.
  * out_host: n entries (may be NULL).  Returns the first error. */
 int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_host);
+
+/* Autotune the batched tile rows (16/32/64) per size bucket (n+m+1 below 400,
+ * 800, 1400, above): times evaluation-only batched launches of each bucket's
+ * median context and keeps the fastest shape for the whole bucket.
+ * rows_out: n entries (may be NULL).  Leaves the contexts to be rebuilt. */
+int tga_batch_autotune(tga_ctx **ctxs, int n, int32_t *rows_out);
 
 /* Wait for the context's stream and report the device status. */
 int tga_sync(tga_ctx *ctx);

@@ -20,6 +20,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtga.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The batched kernel reads job state that other SMs rewrite during the same
+# launch: its global loads must bypass the (non-coherent) L1.
+PER_FILE_FLAGS = {"tga_batch.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def _nvcc() -> str:
@@ -54,7 +57,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + common + ["-c", src, "-o", obj]
+        cmd = [nvcc] + common + PER_FILE_FLAGS.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

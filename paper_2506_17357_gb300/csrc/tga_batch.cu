@@ -1,0 +1,245 @@
+// Batched descent: many independent instances in one persistent launch.
+//
+// Every job (context) is split, per local-search step, into chunks: one
+// chunk per row tile of its inter-route pair triangle and one per group of
+// eight routes for the intra-route moves.  Resident CTAs take chunks of any
+// job from the job's counter, fold the chunk's candidates into the job's
+// packed best key, and count the chunk as done; the CTA that completes a
+// job's last chunk of a step applies that step's best move (the same device
+// functions as the single-instance path) and then releases the job's next
+// step.  Big jobs therefore spread over many SMs while small jobs finish in
+// a few chunks, and no CTA ever waits for another: a CTA that finds no free
+// chunk only polls again, under a time limit that reports TGA_ERR_TIMEOUT.
+//
+// Jobs are built inside the same launch (one CTA per job) before their
+// chunks are released.  Compiled with L1 caching of global loads disabled,
+// since a job's state is rewritten by whichever SM applied the last move.
+#define TGA_LDG(p) (*(p))
+#include "tga_device.cuh"
+
+namespace tga {
+
+namespace {
+
+__device__ __forceinline__ long long now_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Build one job with the whole block (positions, validation, attributes of
+// every route, the position-ordered distance copy), then arm its step limit.
+__device__ void build_job(const Dev &d, long long max_steps) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    check_instance_tiles(d, 0, 1);
+    __syncthreads();
+    for (int x = tid; x <= d.n; x += nthr) d.seen[x] = 0;
+    __syncthreads();
+    for (int r = tid; r < d.m; r += nthr) build_positions_route(d, r);
+    __syncthreads();
+    for (int x = tid + 1; x <= d.n; x += nthr) check_perm_one(d, x);
+    __syncthreads();
+    const int st = *(volatile int *)&d.ctl->status;
+    if (st == 0)
+        for (int r = warp; r < d.m; r += nw) rebuild_route(d, r, lane);
+    __syncthreads();
+    finish_block(d);
+    __syncthreads();
+    pcol_init_range(d, tid, nthr);
+    __syncthreads();
+    if (tid == 0) {
+        Control *C = d.ctl;
+        C->step_limit = max_steps;
+        if (C->status != 0) C->done = 1;
+    }
+    __syncthreads();
+}
+
+template <bool TW>
+__device__ void run_chunk(const BatchJob &J, int c, int *smem, int &best, unsigned &bidx) {
+    const Dev &d = J.d;
+    const bool OR = (d.op_mask & 48u) != 0;
+    if (c < J.nrt) {
+        const int I = c, TC = blockDim.x, TR = J.tr;
+        long long j0 = ((long long)I * TR + 1 + TC - 1) / TC - 1;
+        if (j0 < 0) j0 = 0;
+        for (int Jc = (int)j0; Jc < J.nct; ++Jc) {
+            if (OR) inter_tile<TW, true>(d, I * TR, Jc * TC, TR, smem, best, bidx);
+            else inter_tile<TW, false>(d, I * TR, Jc * TC, TR, smem, best, bidx);
+        }
+    } else {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        __syncthreads();
+        const int r = (c - J.nrt) * nw + warp;
+        if (r < d.m) intra_route<TW>(d, r, lane, smem + warp * kIntraSmemPerWarp, best, bidx);
+    }
+}
+
+}  // namespace
+
+__global__ void k_batch_init(const BatchJob *jobs, int njobs, BatchState *B) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j == 0) { B->build_next = 0; B->jobs_done = 0; B->status = 0; B->pad = 0; }
+    if (j >= njobs) return;
+    Control *C = jobs[j].d.ctl;
+    C->next_chunk = 0x3fffffff;                 // no chunk before the job is built
+    C->done_chunks = 0;
+    C->finished = 0;
+}
+
+// Copy job j's descriptor into shared memory (the device functions read its
+// fields constantly; immutable for the whole launch).
+__device__ __forceinline__ void load_job(const BatchJob *jobs, int j, BatchJob *sJ) {
+    const int words = (int)(sizeof(BatchJob) / sizeof(int));
+    const int *src = reinterpret_cast<const int *>(jobs + j);
+    int *dst = reinterpret_cast<int *>(sJ);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restrict__ jobs, int njobs,
+                                                         BatchState *B, long long max_steps, int mode,
+                                                         long long idle_limit_ns) {
+    extern __shared__ __align__(16) int smem[];
+    __shared__ __align__(16) BatchJob sJ;
+    __shared__ int s_j, s_c, s_last, s_stop;
+    const int tid = threadIdx.x;
+    const bool eval_only = mode != 0;
+
+    // ---- build: one job per CTA at a time
+    for (;;) {
+        if (tid == 0) s_j = atomicAdd(&B->build_next, 1);
+        __syncthreads();
+        const int j = s_j;
+        __syncthreads();
+        if (j >= njobs) break;
+        load_job(jobs, j, &sJ);
+        if (mode != 2) {
+            build_job(sJ.d, max_steps);
+        } else if (tid == 0) {
+            sJ.d.ctl->best_key = kNoKey;
+        }
+        if (tid == 0) {
+            Control *C = sJ.d.ctl;
+            __threadfence();
+            if (C->status != 0 || max_steps <= 0) {
+                C->finished = 1;
+                atomicAdd(&B->jobs_done, 1);
+            } else {
+                atomicExch(&C->next_chunk, 0);
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- descend: take chunks of any job until every job is finished
+    int start = blockIdx.x % njobs;
+    long long idle_since = -1;
+    for (;;) {
+        if (tid == 0) {
+            s_j = -1;
+            s_stop = (*(volatile int *)&B->jobs_done >= njobs) || (*(volatile int *)&B->status != 0);
+            if (!s_stop) {
+                for (int k = 0; k < njobs; ++k) {
+                    const int jj = (start + k) % njobs;
+                    Control *C = jobs[jj].d.ctl;
+                    const int nch = jobs[jj].nchunks;
+                    if (*(volatile int *)&C->next_chunk >= nch) continue;
+                    const int c = atomicAdd(&C->next_chunk, 1);
+                    if (c < nch) { s_j = jj; s_c = c; break; }
+                }
+                if (s_j < 0) {
+                    const long long t = now_ns();
+                    if (idle_since < 0) idle_since = t;
+                    else if (t - idle_since > idle_limit_ns) {
+                        atomicCAS(&B->status, 0, TGA_ERR_TIMEOUT);
+                        s_stop = 1;
+                    }
+                } else {
+                    idle_since = -1;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int jj = s_j, c = s_c;
+        if (jj < 0) {
+            __nanosleep(256);
+            __syncthreads();
+            continue;
+        }
+        start = jj;
+        __threadfence();   // acquire the job state released with next_chunk
+        load_job(jobs, jj, &sJ);
+        const BatchJob &J = sJ;
+        int best = kBestInit;
+        unsigned bidx = 0xffffffffu;
+        if (J.d.has_tw) run_chunk<true>(J, c, smem, best, bidx);
+        else run_chunk<false>(J, c, smem, best, bidx);
+        const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
+        block_min_to(key, &J.d.ctl->best_key);
+        if (tid == 0) {
+            __threadfence();
+            s_last = atomicAdd(&J.d.ctl->done_chunks, 1) == J.nchunks - 1;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const Dev &d = J.d;
+            if (!eval_only) {
+                apply_block(d, nullptr, 0, 0);
+                __syncthreads();
+                band_rows(d, 0, 1, smem);
+                __syncthreads();
+            } else if (tid == 0) {
+                Control *C = d.ctl;
+                if (d.log && C->evals < d.log_cap) d.log[C->evals] = C->best_key;
+                C->evals += 1;
+                C->cand_total += C->cand_per_eval;
+            }
+            if (tid == 0) {
+                Control *C = d.ctl;
+                if (eval_only || C->done || C->steps >= C->step_limit) {
+                    C->finished = 1;
+                    __threadfence();
+                    atomicAdd(&B->jobs_done, 1);
+                } else {
+                    C->done_chunks = 0;
+                    __threadfence();
+                    atomicExch(&C->next_chunk, 0);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+size_t batch_smem_bytes(int max_tr, int max_wp) {
+    size_t a = inter_smem_bytes(max_tr, kBatchThreads / 32);
+    const size_t b = (size_t)(kBatchThreads / 32) * kIntraSmemPerWarp * sizeof(int);
+    const size_t c = (size_t)max_wp * sizeof(int);
+    if (b > a) a = b;
+    if (c > a) a = c;
+    return a;
+}
+
+int launch_batch(const BatchJob *jobs_dev, int njobs, BatchState *state_dev, long long max_steps, int mode,
+                 int max_tr, int max_wp, cudaStream_t s) {
+    const size_t sm = batch_smem_bytes(max_tr, max_wp);
+    if (sm > 200 * 1024) return TGA_ERR_RANGE;
+    if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return TGA_ERR_CUDA;
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, kBatchThreads, sm);
+    if (per < 1) return TGA_ERR_RANGE;
+    const int grid = nsm * per;
+    k_batch_init<<<(njobs + 127) / 128, 128, 0, s>>>(jobs_dev, njobs, state_dev);
+    k_batch<<<grid, kBatchThreads, sm, s>>>(jobs_dev, njobs, state_dev, max_steps, mode,
+                                            20LL * 1000 * 1000 * 1000);
+    return cudaGetLastError() == cudaSuccess ? TGA_OK : TGA_ERR_CUDA;
+}
+
+}  // namespace tga

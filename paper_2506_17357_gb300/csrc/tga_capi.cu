@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "tga_internal.cuh"
@@ -14,6 +15,8 @@ struct tga_ctx {
     Dev d{};
     cudaStream_t stream = nullptr;     // caller's stream
     cudaStream_t cap = nullptr;        // private stream used only for graph capture
+    cudaStream_t cap2 = nullptr;       // second capture stream: the intra-route branch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void *ws = nullptr;
     size_t ws_bytes = 0;
     int device = 0;
@@ -26,6 +29,7 @@ struct tga_ctx {
     cudaGraphExec_t gexec = nullptr;
     bool graph_ready = false;
     bool graph_failed = false;
+    int batch_tr = 0;                  // tile rows in batched descents (0: by size)
 };
 
 namespace {
@@ -106,7 +110,14 @@ int build_graph(tga_ctx *c) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap);
+            // inter-route tiles and intra-route routes run as parallel
+            // branches; both fold into the same packed best key
+            cudaEventRecord(c->ev_fork, c->cap);
+            cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
+            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap);
+            launch_intra(c->d, c->cap2);
+            cudaEventRecord(c->ev_join, c->cap2);
+            cudaStreamWaitEvent(c->cap, c->ev_join, 0);
             launch_apply(c->d, nullptr, h, 1, c->cap);
             launch_band(c->d, c->cap);
             cudaGraph_t outg = body;
@@ -174,6 +185,55 @@ int descend_launch(tga_ctx *c, int64_t max_steps) {
     return TGA_OK;
 }
 
+int default_batch_tr(int Wp) { return Wp < 600 ? 16 : (Wp < 2000 ? 32 : 64); }
+
+// One persistent launch over all contexts (see tga_batch.cu).
+int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *tr_override) {
+    cudaStream_t s = ctxs[0]->stream;
+    for (int i = 0; i < n; ++i)
+        if (ctxs[i]->stream != s && cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return TGA_ERR_CUDA;
+    std::vector<BatchJob> jobs((size_t)n);
+    int max_tr = 16, max_wp = 1;
+    for (int i = 0; i < n; ++i) {
+        tga_ctx *c = ctxs[i];
+        const int tr = tr_override ? tr_override[i] : (c->batch_tr ? c->batch_tr : default_batch_tr(c->d.Wp));
+        BatchJob &J = jobs[(size_t)i];
+        J.d = c->d;
+        J.tr = tr;
+        const int Wa = c->d.Wp - 1;
+        J.nrt = (Wa + tr - 1) / tr;
+        J.nct = (Wa + kBatchThreads - 1) / kBatchThreads;
+        J.nchunks = J.nrt + (c->d.m + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+        if (tr > max_tr) max_tr = tr;
+        if (c->d.Wp > max_wp) max_wp = c->d.Wp;
+        if (mode != 2 && cudaMemsetAsync(c->d.ctl, 0, sizeof(Control), s) != cudaSuccess) return TGA_ERR_CUDA;
+    }
+    // largest jobs first: their chunks are taken before the small jobs'
+    std::vector<BatchJob> ordered(jobs);
+    std::vector<int> order((size_t)n);
+    for (int i = 0; i < n; ++i) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return jobs[(size_t)a].d.Wp > jobs[(size_t)b].d.Wp; });
+    for (int i = 0; i < n; ++i) ordered[(size_t)i] = jobs[(size_t)order[(size_t)i]];
+    char *buf = nullptr;
+    const size_t jb = align_up(sizeof(BatchJob) * (size_t)n, 256);
+    if (cudaMalloc(&buf, jb + sizeof(BatchState)) != cudaSuccess) { cudaGetLastError(); return TGA_ERR_NOMEM; }
+    BatchJob *jdev = (BatchJob *)buf;
+    BatchState *sdev = (BatchState *)(buf + jb);
+    int rc = TGA_OK;
+    if (cudaMemcpyAsync(jdev, ordered.data(), sizeof(BatchJob) * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        rc = TGA_ERR_CUDA;
+    if (!rc) rc = launch_batch(jdev, n, sdev, max_steps, mode, max_tr, max_wp, s);
+    BatchState st{};
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = rc ? rc : TGA_ERR_CUDA;
+    if (cudaMemcpy(&st, sdev, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) rc = rc ? rc : TGA_ERR_CUDA;
+    cudaFree(buf);
+    if (mode != 2)
+        for (int i = 0; i < n; ++i) ctxs[i]->built = true;
+    if (!rc && st.status) rc = st.status;
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -208,7 +268,14 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     if (!c) return TGA_ERR_NOMEM;
     cudaGetDevice(&c->device);
     c->stream = (cudaStream_t)stream;
-    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        if (c->cap) cudaStreamDestroy(c->cap);
+        if (c->cap2) cudaStreamDestroy(c->cap2);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
         delete c;
         return TGA_ERR_CUDA;
     }
@@ -241,8 +308,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     c->ws_bytes = off;
     if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
         cudaGetLastError();
-        cudaStreamDestroy(c->cap);
-        delete c;
+        tga_destroy(c);
         return TGA_ERR_NOMEM;
     }
     char *base = (char *)c->ws;
@@ -261,9 +327,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.pcol = (int *)(base + o_pcol);
     if (cudaMemsetAsync(d.ctl, 0, sizeof(Control), c->stream) != cudaSuccess ||
         setup_kernel_attrs(d.Wp) != 0) {
-        cudaFree(c->ws);
-        cudaStreamDestroy(c->cap);
-        delete c;
+        tga_destroy(c);
         return TGA_ERR_CUDA;
     }
     *out = c;
@@ -310,11 +374,12 @@ int tga_descend(tga_ctx *c, int64_t max_steps, tga_stats *out_host) {
 
 int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_host) {
     if (!ctxs || n < 0 || max_steps < 0) return TGA_ERR_INVALID;
-    int first = TGA_OK;
+    if (n == 0) return TGA_OK;
     for (int i = 0; i < n; ++i) {
-        int rc = descend_launch(ctxs[i], max_steps);
-        if (rc && !first) first = rc;
+        if (!ctxs[i]) return TGA_ERR_INVALID;
+        if (ctxs[i]->device != ctxs[0]->device) return TGA_ERR_INVALID;
     }
+    int first = run_batch(ctxs, n, max_steps, 0, nullptr);
     for (int i = 0; i < n; ++i) {
         Control C;
         int rc = read_control(ctxs[i], &C);
@@ -325,6 +390,47 @@ int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_h
         }
     }
     return first;
+}
+
+int tga_batch_autotune(tga_ctx **ctxs, int n, int32_t *rows_out) {
+    if (!ctxs || n < 0) return TGA_ERR_INVALID;
+    static const int bounds[] = {400, 800, 1400, 1 << 30};
+    static const int trs[] = {16, 32, 64};
+    int lo = 0;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TGA_ERR_CUDA;
+    int rc = TGA_OK;
+    for (int bi = 0; bi < 4 && !rc; ++bi) {
+        std::vector<int> members;
+        for (int i = 0; i < n; ++i)
+            if (ctxs[i]->d.Wp >= lo && ctxs[i]->d.Wp < bounds[bi]) members.push_back(i);
+        lo = bounds[bi];
+        if (members.empty()) continue;
+        std::sort(members.begin(), members.end(), [&](int a, int b) { return ctxs[a]->d.Wp < ctxs[b]->d.Wp; });
+        tga_ctx *rep = ctxs[members[members.size() / 2]];
+        int t16 = 16;
+        rc = run_batch(&rep, 1, 1, 1, &t16);                // build once
+        if (rc) break;
+        float best = 1e30f;
+        int best_tr = default_batch_tr(rep->d.Wp);
+        for (int tr : trs) {
+            cudaEventRecord(e0, rep->stream);
+            for (int k = 0; k < 3 && !rc; ++k) rc = run_batch(&rep, 1, 1, 2, &tr);
+            cudaEventRecord(e1, rep->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!rc && ms < best) { best = ms; best_tr = tr; }
+        }
+        for (int i : members) ctxs[i]->batch_tr = best_tr;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rows_out)
+        for (int i = 0; i < n; ++i) rows_out[i] = ctxs[i]->batch_tr ? ctxs[i]->batch_tr : default_batch_tr(ctxs[i]->d.Wp);
+    // the tuning evaluations leave finished contexts behind: rebuild on next use
+    for (int i = 0; i < n; ++i) ctxs[i]->built = false;
+    return rc;
 }
 
 int tga_sync(tga_ctx *c) {
@@ -456,6 +562,9 @@ int tga_destroy(tga_ctx *c) {
     if (c->tiles) cudaFree(c->tiles);
     if (c->ws) cudaFree(c->ws);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->cap2) cudaStreamDestroy(c->cap2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
     return TGA_OK;
 }

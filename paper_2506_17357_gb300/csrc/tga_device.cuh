@@ -1,0 +1,1026 @@
+// Block- and warp-level device functions of libtga, shared by the
+// single-instance kernels (tga_kernels.cu) and the persistent batched kernel
+// (tga_batch.cu).
+//
+// TGA_LDG(p) loads data that the search mutates (positions, attribute
+// records, the position-ordered distance copy).  The single-instance kernels
+// define it as __ldg: their state changes only between launches.  The
+// batched kernel, where several SMs read a job's state that another SM
+// rewrote during the same launch, defines it as a plain load and is compiled
+// with L1 caching of global loads disabled (-dlcm=cg), so every such read is
+// served by L2.
+#pragma once
+#ifndef TGA_LDG
+#error "define TGA_LDG before including tga_device.cuh"
+#endif
+
+#include "tga_internal.cuh"
+
+namespace tga {
+// internal linkage: each translation unit compiles these with its own TGA_LDG
+namespace {
+
+
+// ---------------------------------------------------------------------------
+// helpers
+
+__device__ __forceinline__ void set_status(Control *C, int code) {
+    atomicCAS(&C->status, 0, code);
+}
+
+__device__ __forceinline__ Seg shfl_seg_up(const Seg &s, int off) {
+    Seg o;
+    o.E = __shfl_up_sync(0xffffffffu, s.E, off);
+    o.L = __shfl_up_sync(0xffffffffu, s.L, off);
+    o.D = __shfl_up_sync(0xffffffffu, s.D, off);
+    o.TW = __shfl_up_sync(0xffffffffu, s.TW, off);
+    o.dist = __shfl_up_sync(0xffffffffu, s.dist, off);
+    o.load = __shfl_up_sync(0xffffffffu, s.load, off);
+    o.out = __shfl_up_sync(0xffffffffu, s.out, off);
+    return o;
+}
+
+__device__ __forceinline__ Seg shfl_seg_down(const Seg &s, int off) {
+    Seg o;
+    o.E = __shfl_down_sync(0xffffffffu, s.E, off);
+    o.L = __shfl_down_sync(0xffffffffu, s.L, off);
+    o.D = __shfl_down_sync(0xffffffffu, s.D, off);
+    o.TW = __shfl_down_sync(0xffffffffu, s.TW, off);
+    o.dist = __shfl_down_sync(0xffffffffu, s.dist, off);
+    o.load = __shfl_down_sync(0xffffffffu, s.load, off);
+    o.out = __shfl_down_sync(0xffffffffu, s.out, off);
+    return o;
+}
+
+__device__ __forceinline__ Seg shfl_seg_idx(const Seg &s, int src) {
+    Seg o;
+    o.E = __shfl_sync(0xffffffffu, s.E, src);
+    o.L = __shfl_sync(0xffffffffu, s.L, src);
+    o.D = __shfl_sync(0xffffffffu, s.D, src);
+    o.TW = __shfl_sync(0xffffffffu, s.TW, src);
+    o.dist = __shfl_sync(0xffffffffu, s.dist, src);
+    o.load = __shfl_sync(0xffffffffu, s.load, src);
+    o.out = __shfl_sync(0xffffffffu, s.out, src);
+    return o;
+}
+
+__device__ __forceinline__ int route_node(const Dev &d, int start, int L, int k) {
+    return (k <= 0 || k > L) ? 0 : d.seq[start + k];
+}
+
+__device__ __forceinline__ int route_anchor(const Dev &d, int r, int start, int L, int k) {
+    return k == 0 ? d.n + 1 + r : route_node(d, start, L, k);
+}
+
+// Rebuild every attribute of route r with one warp (all 32 lanes must call).
+// Elements of the route: 0 = start depot, 1..L customers, L+1 = end depot.
+// Forward inclusive scan gives the prefix F(x) of every anchor, backward
+// inclusive scan the suffix; the route's totals are the prefix of the end
+// depot.  Routes longer than 32 elements are scanned in chunks with a carry.
+__device__ void rebuild_route(const Dev &d, int r, int lane) {
+    const RouteRec rr = d.rrec[r];
+    const int st = rr.start, L = rr.len, E = L + 2;
+    const bool tw = d.has_tw != 0;
+    const int wTe = tw ? d.wT : 0;
+    // ---- forward scan: prefixes
+    Seg carry{};
+    bool have = false;
+    for (int base = 0; base < E; base += 32) {
+        const int k = base + lane;
+        const bool valid = k < E;
+        const int x = valid ? route_node(d, st, L, k) : 0;
+        const int nx = (k + 1 < E) ? route_node(d, st, L, k + 1) : 0;
+        const int out = (valid && k + 1 < E) ? dmat(d, x, nx) : 0;
+        Seg s = seg_node(d, x, out);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            Seg o = shfl_seg_up(s, off);
+            if (lane >= off) s = seg_cat(o, s);
+        }
+        if (have) s = seg_cat(carry, s);
+        if (valid) {
+            if (k <= L) {
+                const int a = route_anchor(d, r, st, L, k);
+                BRec *b = d.brec + a;
+                b->node = x; b->route = r; b->idx = k;
+                b->tau = tw ? s.E + s.D - s.TW : 0;
+                b->twf = tw ? s.TW : 0;
+                b->distf = s.dist;
+                b->loadf = s.load;
+            } else {
+                RouteRec *R = d.rrec + r;
+                const int twr = tw ? s.TW : 0;
+                R->load = s.load;
+                R->dist = s.dist;
+                R->tw = twr;
+                R->cost = L == 0 ? 0 : s.dist + d.wL * max(s.load - d.Q, 0) + wTe * twr;
+            }
+        }
+        carry = shfl_seg_idx(s, 31);
+        have = true;
+    }
+    // ---- backward scan: suffix after each anchor
+    have = false;
+    const int nch = (E + 31) >> 5;
+    for (int c = nch - 1; c >= 0; --c) {
+        const int k = c * 32 + lane;
+        const bool valid = k < E;
+        const int x = valid ? route_node(d, st, L, k) : 0;
+        const int nx = (k + 1 < E) ? route_node(d, st, L, k + 1) : 0;
+        const int out = (valid && k + 1 < E) ? dmat(d, x, nx) : 0;
+        Seg s = seg_node(d, x, out);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            Seg o = shfl_seg_down(s, off);
+            if (lane + off < 32 && k + off < E) s = seg_cat(s, o);
+        }
+        if (have && valid) s = seg_cat(s, carry);
+        if (valid && k >= 1) {
+            const int a = route_anchor(d, r, st, L, k - 1);
+            BRec *b = d.brec + a;
+            b->Lg = tw ? s.L : 0;
+            b->twg = tw ? s.TW : 0;
+            b->distg = s.dist;
+            b->loadg = s.load;
+        }
+        carry = shfl_seg_idx(s, 0);
+        have = true;
+    }
+    __syncwarp();
+    // ---- hoisted constants per anchor
+    const RouteRec R = d.rrec[r];
+    const unsigned mask = d.op_mask;
+    for (int k = lane; k <= L; k += 32) {
+        const int a = route_anchor(d, r, st, L, k);
+        const int x = k == 0 ? 0 : a;
+        const BRec b = d.brec[a];
+        ERec e;
+        e.route = r; e.anchor = a; e.node = x; e.idx = k; e.pad0 = 0; e.pad1 = 0;
+        e.d = __ldg(d.demand + x);
+        e.e = tw ? __ldg(d.early + x) : 0;
+        e.l = tw ? __ldg(d.late + x) : 0;
+        e.s = tw ? __ldg(d.service + x) : 0;
+        e.tau = b.tau;
+        e.Lg = b.Lg;
+        const int Fc = b.distf + wTe * b.twf - R.cost;
+        const int Gc = b.distg + wTe * b.twg;
+        e.K1 = Fc + Gc;
+        e.Fc = Fc + ((mask & 8u) ? 0 : kBig);
+        e.Gc = Gc;
+        e.LQ = R.load - d.Q;
+        e.loadf = b.loadf;
+        e.loadgQ = b.loadg - d.Q;
+        e.C2 = kBig; e.ld2 = 0; e.E2 = 0; e.L2 = 0; e.Dm2 = 0;
+        e.C3 = kBig; e.ld3 = 0; e.E3 = 0; e.L3 = 0; e.Dm3 = 0;
+        if (k == 0) {
+            e.rem1 = kBig; e.K2 = kBig; e.LQd = 0; e.tauP = 0;
+        } else {
+            const int xm = route_node(d, st, L, k - 1);
+            const BRec bp = d.brec[route_anchor(d, r, st, L, k - 1)];
+            const int xn = route_node(d, st, L, k + 1);
+            const int cmn = dmat(d, xm, xn);
+            const int twr = tw ? bp.twf + b.twg + max(bp.tau + cmn - b.Lg, 0) : 0;
+            const int c1 = bp.distf + cmn + b.distg + d.wL * max(R.load - e.d - d.Q, 0) + wTe * twr;
+            e.rem1 = c1 - R.cost + ((mask & 1u) ? 0 : kBig);
+            e.K2 = bp.distf + b.distg + wTe * (bp.twf + b.twg) - R.cost + ((mask & 2u) ? 0 : kBig);
+            e.LQd = R.load - e.d - d.Q;
+            e.tauP = bp.tau;
+            for (int K = 2; K <= 3; ++K) {
+                if (k + K - 1 > L || !(mask & (1u << (K + 2)))) continue;
+                Seg run = seg_node(d, x, dmat(d, x, route_node(d, st, L, k + 1)));
+                for (int t = 1; t < K; ++t) {
+                    const int y = route_node(d, st, L, k + t);
+                    run = seg_cat(run, seg_node(d, y, dmat(d, y, route_node(d, st, L, k + t + 1))));
+                }
+                const int w = route_node(d, st, L, k + K - 1);
+                const BRec bw = d.brec[w];
+                const int wn = route_node(d, st, L, k + K);
+                const int c2 = dmat(d, xm, wn);
+                const int twk = tw ? bp.twf + bw.twg + max(bp.tau + c2 - bw.Lg, 0) : 0;
+                const int ck = bp.distf + c2 + bw.distg + d.wL * max(R.load - run.load - d.Q, 0) +
+                               wTe * twk - R.cost;
+                const int CK = ck + run.dist + wTe * (tw ? run.TW : 0);
+                if (K == 2) {
+                    e.C2 = CK; e.ld2 = run.load;
+                    e.E2 = tw ? run.E : 0; e.L2 = tw ? run.L : 0; e.Dm2 = tw ? run.D - run.TW : 0;
+                } else {
+                    e.C3 = CK; e.ld3 = run.load;
+                    e.E3 = tw ? run.E : 0; e.L3 = tw ? run.L : 0; e.Dm3 = tw ? run.D - run.TW : 0;
+                }
+            }
+        }
+        d.erec[a] = e;
+    }
+}
+
+__device__ bool range_ok(const Dev &d, const Control *C) {
+    if (C->maxc >= (1 << 24) || C->maxl >= (1 << 24) || C->maxe >= (1 << 24) ||
+        C->maxs >= (1 << 24) || C->maxd >= (1 << 24))
+        return false;
+    const long long L2 = 2LL * C->maxL + 4;
+    long long b = L2 * C->maxc + (long long)d.wL * (2LL * C->maxLoad + 3LL * C->maxd);
+    if (d.has_tw) b += (long long)d.wT * L2 * ((long long)C->maxl + C->maxs + C->maxc);
+    return b < kRouteCostLim;
+}
+
+// ---------------------------------------------------------------------------
+// build
+
+// Symmetry / diagonal / sign check of the distance matrix, tile by tile:
+// block (32 x 8 threads) loads tile (I, J) and tile (J, I) with coalesced row
+// reads into shared memory and compares one against the transpose of the other.
+__device__ void check_instance_tiles(const Dev &d, int part, int nparts) {
+    Control *C = d.ctl;
+    __shared__ int A[32][33], B[32][33];
+    const int n1 = d.n + 1, nt = (n1 + 31) / 32;
+    const long long ntiles = (long long)nt * nt;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    int mx = 0;
+    bool bad = false;
+    const int nwarps = blockDim.x >> 5;
+    for (long long t = part; t < ntiles; t += nparts) {
+        const int I = (int)(t / nt), J = (int)(t - (long long)I * nt);
+        for (int rr = ty; rr < 32; rr += nwarps) {
+            const int i = I * 32 + rr, j = J * 32 + tx;
+            A[rr][tx] = (i < n1 && j < n1) ? d.dist[(size_t)i * n1 + j] : 0;
+            const int i2 = J * 32 + rr, j2 = I * 32 + tx;
+            B[rr][tx] = (i2 < n1 && j2 < n1) ? d.dist[(size_t)i2 * n1 + j2] : 0;
+        }
+        __syncthreads();
+        for (int rr = ty; rr < 32; rr += nwarps) {
+            const int i = I * 32 + rr, j = J * 32 + tx;
+            if (i < n1 && j < n1) {
+                const int v = A[rr][tx];
+                if (v < 0 || (i == j && v != 0) || v != B[tx][rr]) bad = true;
+                mx = max(mx, v);
+            }
+        }
+        __syncthreads();
+    }
+    int md = 0, ml = 0, ms = 0, me = 0;
+    for (long long i = part * (long long)blockDim.x + threadIdx.x; i < n1;
+         i += (long long)nparts * blockDim.x) {
+        const int dm = d.demand[i];
+        if (dm < 0 || (i == 0 && dm != 0)) bad = true;
+        md = max(md, dm);
+        if (d.has_tw) {
+            const int e = d.early[i], l = d.late[i], sv = d.service[i];
+            if (e < 0 || l < 0 || sv < 0 || (i == 0 && sv != 0)) bad = true;
+            ml = max(ml, l); ms = max(ms, sv); me = max(me, e);
+        }
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    md = __reduce_max_sync(0xffffffffu, md);
+    ml = __reduce_max_sync(0xffffffffu, ml);
+    ms = __reduce_max_sync(0xffffffffu, ms);
+    me = __reduce_max_sync(0xffffffffu, me);
+    const bool anybad = __any_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&C->maxc, mx); atomicMax(&C->maxd, md); atomicMax(&C->maxl, ml);
+        atomicMax(&C->maxs, ms); atomicMax(&C->maxe, me);
+        if (anybad) set_status(C, TGA_ERR_INVALID);
+    }
+}
+
+__device__ void build_positions_route(const Dev &d, int r) {
+    Control *C = d.ctl;
+    if (r == 0) {
+        if (d.route_start[0] != 0 || d.route_start[d.m] != d.n) set_status(C, TGA_ERR_INVALID);
+        d.seq[d.n + d.m] = d.W;   // sentinel (end depot of the last route)
+    }
+    if (r >= d.m) return;
+    const int a = d.route_start[r], b = d.route_start[r + 1];
+    if (a < 0 || b < a || b > d.n) { set_status(C, TGA_ERR_INVALID); return; }
+    const int p = a + r;
+    d.seq[p] = d.n + 1 + r;
+    d.pos_of[d.n + 1 + r] = p;
+    d.rrec[r].start = p;
+    d.rrec[r].len = b - a;
+    for (int t = a; t < b; ++t) {
+        const int x = d.tour[t];
+        if (x < 1 || x > d.n) { set_status(C, TGA_ERR_INVALID); continue; }
+        d.seq[t + r + 1] = x;
+        d.pos_of[x] = t + r + 1;
+        atomicAdd(&d.seen[x], 1);
+    }
+}
+
+__device__ __forceinline__ void check_perm_one(const Dev &d, int x) {
+    if (x >= 1 && x <= d.n && d.seen[x] != 1) set_status(d.ctl, TGA_ERR_INVALID);
+}
+
+
+__device__ void finish_block(const Dev &d) {
+    Control *C = d.ctl;
+    __shared__ long long s_cost[32], s_l2[32], s_l1[32], s_lm2[32];
+    __shared__ int s_maxL[32], s_maxLoad[32];
+    long long cost = 0, l2 = 0, l1 = 0, lm2 = 0;
+    int maxL = 0, maxLoad = 0;
+    if (C->status == 0) {
+        for (int r = threadIdx.x; r < d.m; r += blockDim.x) {
+            const RouteRec R = d.rrec[r];
+            cost += R.cost;
+            l2 += (long long)R.len * R.len;
+            l1 += max(R.len - 1, 0);
+            lm2 += max(R.len - 2, 0);
+            maxL = max(maxL, R.len);
+            maxLoad = max(maxLoad, R.load);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        cost += __shfl_xor_sync(0xffffffffu, cost, off);
+        l2 += __shfl_xor_sync(0xffffffffu, l2, off);
+        l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+        lm2 += __shfl_xor_sync(0xffffffffu, lm2, off);
+        maxL = max(maxL, __shfl_xor_sync(0xffffffffu, maxL, off));
+        maxLoad = max(maxLoad, __shfl_xor_sync(0xffffffffu, maxLoad, off));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        s_cost[warp] = cost; s_l2[warp] = l2; s_l1[warp] = l1; s_lm2[warp] = lm2;
+        s_maxL[warp] = maxL; s_maxLoad[warp] = maxLoad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
+            cost += s_cost[w]; l2 += s_l2[w]; l1 += s_l1[w]; lm2 += s_lm2[w];
+            maxL = max(maxL, s_maxL[w]); maxLoad = max(maxLoad, s_maxLoad[w]);
+        }
+        C->cost = cost; C->initial_cost = cost;
+        C->sumL2 = l2; C->sumLm1 = l1; C->sumLm2 = lm2;
+        C->maxL = maxL; C->maxLoad = maxLoad;
+        C->steps = 0; C->evals = 0; C->cand_total = 0;
+        C->done = 0; C->local_opt = 0; C->chg_count = 0;
+        C->best_key = kNoKey;
+        C->step_limit = 0x7fffffffffffffffLL;
+        C->cand_per_eval = candidate_count(d.n, d.m, d.op_mask, l2, l1, lm2);
+        if (C->status == 0 && !range_ok(d, C)) set_status(C, TGA_ERR_RANGE);
+        if (C->status != 0) C->done = 1;
+        C->built = 1;
+        // dummy record (sentinel position and every position past the end)
+        ERec e{};
+        e.route = -1; e.anchor = d.W;
+        e.rem1 = kBig; e.K1 = kBig; e.K2 = kBig; e.Fc = kBig; e.C2 = kBig; e.C3 = kBig;
+        d.erec[d.W] = e;
+        BRec b{};
+        b.route = -1;
+        d.brec[d.W] = b;
+    }
+}
+
+// pcol[x][q + kColOff] = dist[x][node at position q]; columns outside the
+// position range hold the depot distance (read only by masked candidates).
+__device__ void pcol_init_range(const Dev &d, long long t0, long long stride) {
+    const long long tot = (long long)(d.n + 1) * d.ldp;
+    for (long long t = t0; t < tot; t += stride) {
+        const int x = (int)(t / d.ldp), c = (int)(t - (long long)x * d.ldp);
+        const int q = c - kColOff;
+        const int node = (q >= 0 && q < d.Wp) ? node_of(d.seq[q], d.n) : 0;
+        d.pcol[t] = dmat(d, x, node);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// inter-route evaluation
+
+#define TGA_TRY(dl, ix)                                                    \
+    do {                                                                   \
+        const int _d = (dl);                                               \
+        const unsigned _i = (ix);                                          \
+        if (_d < best || (_d == best && _i < bidx)) { best = _d; bidx = _i; } \
+    } while (0)
+
+// One tile of the inter-route pair triangle: rows p0..p0+TR-1, columns
+// q0..q0+32*NW-1 (NW = warps of the block).  Every thread folds its column's
+// candidates into (best, bidx); smem must hold inter_smem_bytes(TR, NW).
+template <bool TW, bool OR>
+__device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int *smem, int &best, unsigned &bidx) {
+    const int NW = blockDim.x >> 5, TC = NW * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int LDT = TC + 8;
+    int *sT = smem;                                           // (TR+4) x LDT distances
+    int4 *sR = reinterpret_cast<int4 *>(smem + (TR + 4) * LDT);   // TR row records
+    __syncthreads();                                          // previous user of smem is done
+
+    // Extraction: rows p0-1 .. p0+TR+2, positions q0-4 .. q0+TC+3
+    for (int rr = warp; rr < TR + 4; rr += NW) {
+        const int p = p0 - 1 + rr;
+        const int node = (p >= 0 && p < d.Wp) ? node_of(d.seq[p], d.n) : 0;
+        const int4 *src = reinterpret_cast<const int4 *>(d.pcol + (size_t)node * d.ldp + q0);
+        int4 *dst = reinterpret_cast<int4 *>(sT + rr * LDT);
+        for (int c = lane; c < (LDT >> 2); c += 32) dst[c] = TGA_LDG(src + c);
+    }
+    for (int i = threadIdx.x; i < TR * 8; i += blockDim.x) {
+        const int p = p0 + (i >> 3);
+        const int a = (p < d.Wp) ? d.seq[p] : d.W;
+        sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + (i & 7));
+    }
+    const int q = q0 + warp * 32 + lane;
+    const int av = (q < d.Wp) ? d.seq[q] : d.W;
+    const int4 *vr = reinterpret_cast<const int4 *>(d.erec + av);
+    const int4 v0 = TGA_LDG(vr + 0), v1 = TGA_LDG(vr + 1), v2 = TGA_LDG(vr + 2);
+    int4 v3 = make_int4(0, 0, 0, 0), v4 = v3, v5 = v3, v6 = v3;
+    if (OR) v3 = TGA_LDG(vr + 3);
+    if (TW) { v4 = TGA_LDG(vr + 4); v5 = TGA_LDG(vr + 5); }
+    if (TW && OR) v6 = TGA_LDG(vr + 6);
+    // column fields
+    const int Vroute = v0.x, Vd = v0.y, Vrem1 = v0.z, VK1 = v0.w;
+    const int VLQ = v1.x, VK2 = v1.y, VLQd = v1.z, VFc = v1.w;
+    const int VGc = v2.x, Vloadf = v2.y, VloadgQ = v2.z;
+    const int VC2 = v3.x, Vld2 = v3.y, VC3 = v3.z, Vld3 = v3.w;
+    const int Ve = v4.x, Vl = v4.y, Vs = v4.z, Vtau = v4.w;
+    const int VLg = v5.x, VtauP = v5.y, VE2 = v5.z, VL2 = v5.w;
+    const int VDm2 = v6.x, VE3 = v6.y, VL3 = v6.z, VDm3 = v6.w;
+    __syncthreads();
+
+    const int wL = d.wL, wT = d.wT;
+    const unsigned W = (unsigned)d.W, W2 = W * W;
+    const int *col = sT + warp * 32 + lane + 4;
+    int tm10 = col[0];
+    int t0m1 = col[LDT - 1], t00 = col[LDT], t01 = col[LDT + 1];
+    int t10 = col[2 * LDT], t11 = col[2 * LDT + 1], t12 = col[2 * LDT + 2];
+    int t21 = col[3 * LDT + 1];
+
+#pragma unroll 1
+    for (int i = 0; i < TR; ++i) {
+        const int p = p0 + i;
+        const int4 u0 = sR[i * 8 + 0], u1 = sR[i * 8 + 1], u2 = sR[i * 8 + 2];
+        const int Uroute = u0.x, Ud = u0.y, Urem1 = u0.z, UK1 = u0.w;
+        const int ULQ = u1.x, UK2 = u1.y, ULQd = u1.z, UFc = u1.w;
+        const int UGc = u2.x, Uloadf = u2.y, UloadgQ = u2.z;
+        // distances of the stencil (symmetric matrix):
+        //   c(u,v)=t00 c(u,v+)=t01 c(u+,v)=t10 c(u+,v+)=t11 c(u++,v+)=t21
+        //   c(u+,v++)=t12 c(u-,v)=tm10 c(u,v-)=t0m1
+        // relocate u -> after v, relocate v -> after u
+        int dR1 = Urem1 + VK1 + t00 + t01 + wL * max(VLQ + Ud, 0);
+        int dR2 = Vrem1 + UK1 + t00 + t10 + wL * max(ULQ + Vd, 0);
+        // swap u <-> v
+        int dS = UK2 + VK2 + tm10 + t10 + t0m1 + t01 +
+                 wL * (max(ULQd + Vd, 0) + max(VLQd + Ud, 0));
+        // 2-opt*: head(u)+tail after v, head(v)+tail after u
+        int dX = UFc + VGc + VFc + UGc + t01 + t10 +
+                 wL * (max(Uloadf + VloadgQ, 0) + max(Vloadf + UloadgQ, 0));
+        int dO2a = 0, dO2b = 0, dO3a = 0, dO3b = 0;
+        int4 u3 = make_int4(0, 0, 0, 0);
+        if (OR) {
+            u3 = sR[i * 8 + 3];
+            const int UC2 = u3.x, Uld2 = u3.y, UC3 = u3.z, Uld3 = u3.w;
+            dO2a = UC2 + VK1 + t00 + t11 + wL * max(VLQ + Uld2, 0);
+            dO2b = VC2 + UK1 + t00 + t11 + wL * max(ULQ + Vld2, 0);
+            dO3a = UC3 + VK1 + t00 + t21 + wL * max(VLQ + Uld3, 0);
+            dO3b = VC3 + UK1 + t00 + t12 + wL * max(ULQ + Vld3, 0);
+        }
+        if (TW) {
+            const int4 u4 = sR[i * 8 + 4], u5 = sR[i * 8 + 5];
+            const int Ue = u4.x, Ul = u4.y, Us = u4.z, Utau = u4.w;
+            const int ULg = u5.x, UtauP = u5.y;
+            {   // u inserted between v and v+
+                const int a1 = Vtau + t00, w1 = max(a1 - Ul, 0);
+                const int a2 = max(a1, Ue) - w1 + Us + t01, w2 = max(a2 - VLg, 0);
+                dR1 += wT * (w1 + w2);
+            }
+            {   // v inserted between u and u+
+                const int a1 = Utau + t00, w1 = max(a1 - Vl, 0);
+                const int a2 = max(a1, Ve) - w1 + Vs + t10, w2 = max(a2 - ULg, 0);
+                dR2 += wT * (w1 + w2);
+            }
+            {   // v between u- and u+, u between v- and v+
+                const int a1 = UtauP + tm10, w1 = max(a1 - Vl, 0);
+                const int a2 = max(a1, Ve) - w1 + Vs + t10, w2 = max(a2 - ULg, 0);
+                const int b1 = VtauP + t0m1, x1 = max(b1 - Ul, 0);
+                const int b2 = max(b1, Ue) - x1 + Us + t01, x2 = max(b2 - VLg, 0);
+                dS += wT * (w1 + w2 + x1 + x2);
+            }
+            dX += wT * (max(Utau + t01 - VLg, 0) + max(Vtau + t10 - ULg, 0));
+            if (OR) {
+                const int UE2 = u5.z, UL2 = u5.w;
+                const int4 u6 = sR[i * 8 + 6];
+                const int UDm2 = u6.x, UE3 = u6.y, UL3 = u6.z, UDm3 = u6.w;
+                {
+                    const int a1 = Vtau + t00, w1 = max(a1 - UL2, 0);
+                    const int a2 = max(a1, UE2) - w1 + UDm2 + t11, w2 = max(a2 - VLg, 0);
+                    dO2a += wT * (w1 + w2);
+                }
+                {
+                    const int a1 = Utau + t00, w1 = max(a1 - VL2, 0);
+                    const int a2 = max(a1, VE2) - w1 + VDm2 + t11, w2 = max(a2 - ULg, 0);
+                    dO2b += wT * (w1 + w2);
+                }
+                {
+                    const int a1 = Vtau + t00, w1 = max(a1 - UL3, 0);
+                    const int a2 = max(a1, UE3) - w1 + UDm3 + t21, w2 = max(a2 - VLg, 0);
+                    dO3a += wT * (w1 + w2);
+                }
+                {
+                    const int a1 = Utau + t00, w1 = max(a1 - VL3, 0);
+                    const int a2 = max(a1, VE3) - w1 + VDm3 + t12, w2 = max(a2 - ULg, 0);
+                    dO3b += wT * (w1 + w2);
+                }
+            }
+        }
+        int m = min(min(dR1, dR2), min(dS, dX));
+        if (OR) m = min(m, min(min(dO2a, dO2b), min(dO3a, dO3b)));
+        const bool skip = (Uroute == Vroute) | (p >= q);
+        if (!skip && m <= best) {
+            const unsigned au = (unsigned)u2.w, avu = (unsigned)av;
+            TGA_TRY(dR1, au * W + avu);
+            TGA_TRY(dR2, avu * W + au);
+            TGA_TRY(dS, W2 + min(au, avu) * W + max(au, avu));
+            TGA_TRY(dX, 3u * W2 + (Uroute < Vroute ? au * W + avu : avu * W + au));
+            if (OR) {
+                TGA_TRY(dO2a, 4u * W2 + au * W + avu);
+                TGA_TRY(dO2b, 4u * W2 + avu * W + au);
+                TGA_TRY(dO3a, 5u * W2 + au * W + avu);
+                TGA_TRY(dO3b, 5u * W2 + avu * W + au);
+            }
+        }
+        // slide the stencil window one row down
+        tm10 = t00;
+        t0m1 = col[(i + 2) * LDT - 1];
+        t00 = t10;
+        t01 = t11;
+        t10 = col[(i + 3) * LDT];
+        t11 = t21;
+        t12 = col[(i + 3) * LDT + 2];
+        t21 = col[(i + 4) * LDT + 1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// intra-route evaluation
+//
+// One warp per route.  The route's elements (0 = start depot, 1..L
+// customers, L+1 = end depot) are staged in shared memory with their node
+// data, the prefix/suffix attributes of every anchor, and -- when it fits --
+// the route's (L+2) x (L+2) distance block, read as contiguous row segments
+// of the position-ordered distance copy.  Lane i then sweeps the other end
+// of every move that starts (or ends) at element i, maintaining the middle
+// segment incrementally with the concatenation operator, so each candidate
+// is O(1) (route-based extraction of Section 5.3.1 with the attribute-matrix
+// rows of Section 4.2 built on the fly).
+
+constexpr int kIntraWarps = 4;
+constexpr int kIntraSmemPerWarp = 2816;      // ints (11 KB)
+constexpr int kIntraVec = 10;                // staged per-element int arrays
+
+struct RouteView {
+    const Dev *d;
+    int r, L, E, st;
+    bool inS;                 // distance block in shared memory
+    const int *node, *e, *l, *s, *tau, *twf, *distf, *Lg, *twg, *distg;
+    const int *D;             // E x E (if inS)
+    __device__ __forceinline__ int c(int a, int b) const {
+        if (inS) return D[a * E + b];
+        return TGA_LDG(d->pcol + (size_t)node[a] * d->ldp + kColOff + st + b);
+    }
+    __device__ __forceinline__ int anchor(int k) const { return k == 0 ? d->n + 1 + r : node[k]; }
+    __device__ __forceinline__ Seg seg(int k, int out) const {
+        Seg x;
+        x.E = e[k]; x.L = l[k]; x.D = s[k]; x.TW = 0; x.dist = 0; x.load = 0; x.out = out;
+        return x;
+    }
+};
+
+template <bool TW>
+__device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, int baseDist, int baseTw,
+                             unsigned W, unsigned W2, int &best, unsigned &bidx) {
+    const int L = V.L;
+    if (i >= 1) {
+        // ---------------- moves that take the customer at element i forward
+        const unsigned xi = (unsigned)V.node[i];
+        const int ptau = V.tau[i - 1], ptwf = V.twf[i - 1], pdist = V.distf[i - 1];
+        // relocate / or-opt of the run i..i+k-1 to after element j, j >= i+k
+        for (int k = 1; k <= 3; ++k) {
+            const int op = k == 1 ? 0 : k + 2;
+            if (!(mask & (1u << op)) || i + k - 1 > L) continue;
+            Seg run = V.seg(i, V.c(i, i + 1));
+            for (int t = 1; t < k; ++t) run = seg_cat(run, V.seg(i + t, V.c(i + t, i + t + 1)));
+            int tau = ptau, tw = ptwf, dist = pdist, last = i - 1;
+            for (int j = i + k; j <= L; ++j) {
+                const int c1 = V.c(last, j);
+                dist += c1;
+                if (TW) {
+                    const int a = tau + c1;
+                    const int w = max(a - V.l[j], 0);
+                    tau = max(a, V.e[j]) - w + V.s[j];
+                    tw += w;
+                }
+                last = j;
+                const int cA = V.c(j, i), cB = V.c(i + k - 1, j + 1);
+                int delta = dist + cA + run.dist + cB + V.distg[j] - baseDist;
+                if (TW) {
+                    const int a1 = tau + cA, w1 = max(a1 - run.L, 0);
+                    const int a2 = max(a1, run.E) - w1 + run.D - run.TW + cB;
+                    const int w2 = max(a2 - V.Lg[j], 0);
+                    delta += wT * (tw + w1 + run.TW + w2 + V.twg[j] - baseTw);
+                }
+                TGA_TRY(delta, (unsigned)op * W2 + xi * W + (unsigned)V.node[j]);
+            }
+        }
+        // swap element i <-> element j, j > i
+        if (mask & 2u) {
+            Seg M{};
+            for (int j = i + 1; j <= L; ++j) {
+                if (j > i + 2) M = seg_cat(M, V.seg(j - 1, V.c(j - 1, j)));
+                else if (j == i + 2) M = V.seg(i + 1, V.c(i + 1, j));
+                const bool hasM = j > i + 1;
+                const int ca = V.c(i - 1, j);
+                int dist = pdist + ca + V.distg[j];
+                int tau = 0, tw = 0;
+                if (TW) {
+                    const int a = ptau + ca, w = max(a - V.l[j], 0);
+                    tau = max(a, V.e[j]) - w + V.s[j];
+                    tw = ptwf + w;
+                }
+                int last = j;
+                if (hasM) {
+                    const int cb = V.c(j, i + 1);
+                    dist += cb + M.dist;
+                    if (TW) {
+                        const int a = tau + cb, w = max(a - M.L, 0);
+                        tau = max(a, M.E) - w + M.D - M.TW;
+                        tw += w + M.TW;
+                    }
+                    last = j - 1;
+                }
+                const int cc = V.c(last, i), cd = V.c(i, j + 1);
+                dist += cc + cd;
+                int delta = dist - baseDist;
+                if (TW) {
+                    const int a = tau + cc, w = max(a - V.l[i], 0);
+                    const int t2 = max(a, V.e[i]) - w + V.s[i];
+                    const int w4 = max(t2 + cd - V.Lg[j], 0);
+                    delta += wT * (tw + w + w4 + V.twg[j] - baseTw);
+                }
+                const unsigned xj = (unsigned)V.node[j];
+                TGA_TRY(delta, W2 + min(xi, xj) * W + max(xi, xj));
+            }
+        }
+        // 2-opt: reverse elements i..j, j > i
+        if (mask & 4u) {
+            Seg Rv = V.seg(i, 0);
+            for (int j = i + 1; j <= L; ++j) {
+                Rv = seg_cat(V.seg(j, V.c(j, j - 1)), Rv);
+                const int ca = V.c(i - 1, j), cb = V.c(i, j + 1);
+                int delta = pdist + ca + Rv.dist + cb + V.distg[j] - baseDist;
+                if (TW) {
+                    const int a1 = ptau + ca, w1 = max(a1 - Rv.L, 0);
+                    const int a2 = max(a1, Rv.E) - w1 + Rv.D - Rv.TW + cb;
+                    const int w2 = max(a2 - V.Lg[j], 0);
+                    delta += wT * (ptwf + w1 + Rv.TW + w2 + V.twg[j] - baseTw);
+                }
+                TGA_TRY(delta, 2u * W2 + xi * W + (unsigned)V.node[j]);
+            }
+        }
+    }
+    // ---------------- moves whose destination is element j = i: the run
+    // t..t+k-1, t >= j+2, moves back to just after element j.
+    const int j = i;
+    const unsigned aj = (unsigned)V.anchor(j);
+    for (int k = 1; k <= 3; ++k) {
+        const int op = k == 1 ? 0 : k + 2;
+        if (!(mask & (1u << op)) || j + 2 + k - 1 > L) continue;
+        Seg M = V.seg(j + 1, V.c(j + 1, j + 2));
+        for (int t = j + 2; t + k - 1 <= L; ++t) {
+            if (t > j + 2) M = seg_cat(M, V.seg(t - 1, V.c(t - 1, t)));
+            Seg run = V.seg(t, V.c(t, t + 1));
+            for (int u = 1; u < k; ++u) run = seg_cat(run, V.seg(t + u, V.c(t + u, t + u + 1)));
+            const int w = t + k - 1;
+            const int ca = V.c(j, t), cb = V.c(w, j + 1), cc = V.c(t - 1, t + k);
+            int delta = V.distf[j] + ca + run.dist + cb + M.dist + cc + V.distg[w] - baseDist;
+            if (TW) {
+                const int a1 = V.tau[j] + ca, w1 = max(a1 - run.L, 0);
+                const int a2 = max(a1, run.E) - w1 + run.D - run.TW + cb;
+                const int w2 = max(a2 - M.L, 0);
+                const int a3 = max(a2, M.E) - w2 + M.D - M.TW + cc;
+                const int w3 = max(a3 - V.Lg[w], 0);
+                delta += wT * (V.twf[j] + w1 + run.TW + w2 + M.TW + w3 + V.twg[w] - baseTw);
+            }
+            TGA_TRY(delta, (unsigned)op * W2 + (unsigned)V.node[t] * W + aj);
+        }
+    }
+}
+
+// Intra-route candidates of route r with one warp (all 32 lanes call);
+// S is this warp's kIntraSmemPerWarp ints of shared memory.
+template <bool TW>
+__device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, unsigned &bidx) {
+    const RouteRec R = d.rrec[r];
+    const int L = R.len;
+    if (L < 2) return;
+    RouteView V;
+    V.d = &d; V.r = r; V.L = L; V.E = L + 2; V.st = R.start;
+    const int E = V.E;
+    const bool vecS = kIntraVec * E <= kIntraSmemPerWarp;
+    V.inS = vecS && kIntraVec * E + E * E <= kIntraSmemPerWarp;
+    // per-element arrays: shared memory when they fit, else this
+    // route's own slice [start+r, start+r+E) of the global scratch
+    int *base = vecS ? S : d.scr_intra + (R.start + r);
+    const int stride = vecS ? E : d.Wp + d.m;
+    int *node = base, *e = base + stride, *l = base + 2 * stride, *s = base + 3 * stride;
+    int *tau = base + 4 * stride, *twf = base + 5 * stride, *distf = base + 6 * stride;
+    int *Lg = base + 7 * stride, *twg = base + 8 * stride, *distg = base + 9 * stride;
+    V.node = node; V.e = e; V.l = l; V.s = s; V.tau = tau; V.twf = twf; V.distf = distf;
+    V.Lg = Lg; V.twg = twg; V.distg = distg;
+    for (int k = lane; k < E; k += 32) {
+        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[V.st + k] : -1);
+        const int x = (k >= 1 && k <= L) ? a : 0;
+        node[k] = x;
+        if (TW) { e[k] = __ldg(d.early + x); l[k] = __ldg(d.late + x); s[k] = __ldg(d.service + x); }
+        else { e[k] = 0; l[k] = 0; s[k] = 0; }
+        if (a >= 0) {
+            const BRec b = d.brec[a];
+            tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
+            Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
+        } else {
+            tau[k] = 0; twf[k] = 0; distf[k] = 0; Lg[k] = 0; twg[k] = 0; distg[k] = 0;
+        }
+    }
+    __syncwarp();
+    if (V.inS) {
+        int *D = S + kIntraVec * E;
+        for (int t = lane; t < E * E; t += 32) {
+            const int a = t / E, b = t - a * E;
+            D[t] = d.pcol[(size_t)node[a] * d.ldp + kColOff + V.st + b];
+        }
+        V.D = D;
+    } else {
+        V.D = nullptr;
+    }
+    __syncwarp();
+    const unsigned W = (unsigned)d.W, W2 = W * W;
+    const int wT = TW ? d.wT : 0;
+    for (int i = lane; i <= L; i += 32)
+        intra_anchor<TW>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx);
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// apply (one block)
+
+struct MovePlan {
+    int op, a, b, delta;
+    int A, B, i, j, k;        // routes, 1-based indices (0 = depot), run length
+    int LA, LB, pA, pB;       // old lengths and depot positions
+    int nLA, nLB;             // new lengths
+};
+
+// Old position of the anchor that sits at index t (1-based) of the new
+// route X (X is plan.A or plan.B).
+__device__ __forceinline__ int new_src(const MovePlan &P, bool isA, int t) {
+    const int op = P.op;
+    if (P.A == P.B) {   // intra-route: index map inside route A
+        int f = t;
+        if (op == 0 || op == 4 || op == 5) {
+            const int i = P.i, j = P.j, k = P.k;
+            if (j >= i + k) {
+                if (t < i) f = t;
+                else if (t <= j - k) f = t + k;
+                else if (t <= j) f = i + (t - (j - k + 1));
+                else f = t;
+            } else {    // j <= i - 2
+                if (t <= j) f = t;
+                else if (t <= j + k) f = i + (t - j - 1);
+                else if (t <= i + k - 1) f = t - k;
+                else f = t;
+            }
+        } else if (op == 1) {
+            f = (t == P.i) ? P.j : (t == P.j ? P.i : t);
+        } else if (op == 2) {
+            f = (t >= P.i && t <= P.j) ? P.i + P.j - t : t;
+        }
+        return P.pA + f;
+    }
+    if (op == 0 || op == 4 || op == 5) {
+        if (isA) return t < P.i ? P.pA + t : P.pA + t + P.k;
+        if (t <= P.j) return P.pB + t;
+        if (t <= P.j + P.k) return P.pA + P.i + (t - P.j - 1);
+        return P.pB + t - P.k;
+    }
+    if (op == 1) {
+        if (isA) return t == P.i ? P.pB + P.j : P.pA + t;
+        return t == P.j ? P.pA + P.i : P.pB + t;
+    }
+    // op 3 (2-opt*), A < B
+    if (isA) return t <= P.i ? P.pA + t : P.pB + P.j + (t - P.i);
+    return t <= P.j ? P.pB + t : P.pA + P.i + (t - P.j);
+}
+
+// Apply the best move (from *ext, or the context's packed best key) with the
+// whole block; at least 2 warps.
+__device__ void apply_block(const Dev &d, const tga_move *ext, cudaGraphConditionalHandle cond, int use_cond) {
+    Control *C = d.ctl;
+    __shared__ MovePlan P;
+    __shared__ int s_act, s_cnt;
+    __shared__ int s_lo, s_hi, s_delta_len, s_n1, s_n2, s_b1, s_b2;
+    __shared__ long long s_oldcost;
+    __shared__ int s_oldLA, s_oldLB, s_maxL, s_maxLoad;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        int act = 0;
+        if (!C->done || ext) {
+            unsigned long long key;
+            if (ext) {
+                key = ext->valid ? pack_key(ext->delta, ext->move_index) : kNoKey;
+            } else {
+                key = C->best_key;
+                if (d.log && C->evals < d.log_cap) d.log[C->evals] = key;
+                C->evals += 1;
+                C->cand_total += C->cand_per_eval;
+            }
+            C->best_key = kNoKey;
+            if (key == kNoKey || key_delta(key) >= 0) {
+                C->done = 1;
+                C->local_opt = 1;
+            } else {
+                const unsigned idx = (unsigned)(key & 0xffffffffu);
+                const unsigned W = (unsigned)d.W, W2 = W * W;
+                MovePlan pl;
+                pl.op = (int)(idx / W2);
+                pl.a = (int)((idx % W2) / W);
+                pl.b = (int)(idx % W);
+                pl.delta = key_delta(key);
+                bool ok = pl.op < 6 && ((d.op_mask >> pl.op) & 1u) && pl.a >= 1 && pl.b >= 1;
+                if (ok) {
+                    const BRec ba = d.brec[pl.a], bb = d.brec[pl.b];
+                    pl.A = ba.route; pl.B = bb.route; pl.i = ba.idx; pl.j = bb.idx;
+                    ok = pl.A >= 0 && pl.B >= 0;
+                    if (ok) {
+                        pl.LA = d.rrec[pl.A].len; pl.LB = d.rrec[pl.B].len;
+                        pl.pA = d.rrec[pl.A].start; pl.pB = d.rrec[pl.B].start;
+                    }
+                }
+                if (ok) {
+                    const int op = pl.op;
+                    pl.k = 1;
+                    if (op == 0 || op == 4 || op == 5) {
+                        pl.k = op == 0 ? 1 : op - 2;
+                        ok = pl.a <= d.n && pl.i + pl.k - 1 <= pl.LA &&
+                             !(pl.A == pl.B && pl.j >= pl.i - 1 && pl.j <= pl.i + pl.k - 1);
+                        pl.nLA = pl.A == pl.B ? pl.LA : pl.LA - pl.k;
+                        pl.nLB = pl.A == pl.B ? pl.LB : pl.LB + pl.k;
+                    } else if (op == 1) {
+                        ok = pl.a < pl.b && pl.b <= d.n;
+                        pl.nLA = pl.LA; pl.nLB = pl.LB;
+                        if (ok && pl.A == pl.B && pl.i > pl.j) { int t = pl.i; pl.i = pl.j; pl.j = t; }
+                    } else if (op == 2) {
+                        ok = pl.a <= d.n && pl.b <= d.n && pl.A == pl.B && pl.i < pl.j;
+                        pl.nLA = pl.LA; pl.nLB = pl.LB;
+                    } else {
+                        ok = pl.A < pl.B;
+                        pl.nLA = pl.i + pl.LB - pl.j;
+                        pl.nLB = pl.j + pl.LA - pl.i;
+                    }
+                }
+                if (!ok) {
+                    set_status(C, TGA_ERR_INVALID);
+                    C->done = 1;
+                } else {
+                    P = pl;
+                    act = 1;
+                    C->last_op = pl.op; C->last_a = pl.a; C->last_b = pl.b; C->last_delta = pl.delta;
+                    s_oldcost = (long long)d.rrec[pl.A].cost + (pl.A != pl.B ? d.rrec[pl.B].cost : 0);
+                    s_oldLA = pl.LA; s_oldLB = pl.LB;
+                    if (pl.A == pl.B) {
+                        s_lo = pl.A; s_hi = pl.A; s_delta_len = 0;
+                        s_b1 = pl.pA + 1; s_n1 = pl.LA; s_b2 = 0; s_n2 = 0;
+                    } else {
+                        const bool aLo = pl.A < pl.B;
+                        const int lo = aLo ? pl.A : pl.B, hi = aLo ? pl.B : pl.A;
+                        const int Llo = aLo ? pl.LA : pl.LB, nLlo = aLo ? pl.nLA : pl.nLB;
+                        const int plo = aLo ? pl.pA : pl.pB, phi = aLo ? pl.pB : pl.pA;
+                        const int Lhi = aLo ? pl.LB : pl.LA;
+                        s_lo = lo; s_hi = hi;
+                        s_delta_len = nLlo - Llo;
+                        if (s_delta_len != 0) {
+                            s_b1 = plo + 1; s_n1 = phi + Lhi - plo; s_b2 = 0; s_n2 = 0;
+                        } else {
+                            s_b1 = plo + 1; s_n1 = Llo; s_b2 = phi + 1; s_n2 = Lhi;
+                        }
+                    }
+                }
+            }
+        }
+        s_act = act;
+        s_cnt = 0;
+        s_maxL = 0;
+        s_maxLoad = 0;
+    }
+    __syncthreads();
+    if (s_act) {
+        const MovePlan pl = P;
+        const int dl = s_delta_len, lo = s_lo, hi = s_hi;
+        const int tot = s_n1 + s_n2;
+        const bool aLo = pl.A <= pl.B;
+        const int plo = aLo ? pl.pA : pl.pB, phi = aLo ? pl.pB : pl.pA;
+        const int nLlo = aLo ? pl.nLA : pl.nLB;
+        // pass 1: where does every changed position take its anchor from
+        for (int u = tid; u < tot; u += blockDim.x) {
+            const int q = u < s_n1 ? s_b1 + u : s_b2 + (u - s_n1);
+            int src, route;
+            if (pl.A == pl.B) {
+                src = new_src(pl, true, q - pl.pA);
+                route = pl.A;
+            } else if (q <= plo + nLlo) {
+                src = new_src(pl, lo == pl.A, q - plo);
+                route = lo;
+            } else if (q < phi + dl) {
+                src = q - dl;
+                route = d.brec[d.seq[src]].route;
+            } else if (q == phi + dl) {
+                src = phi;
+                route = hi;
+            } else {
+                src = new_src(pl, hi == pl.A, q - (phi + dl));
+                route = hi;
+            }
+            d.scr_src[u] = src;
+            d.scr_anchor[u] = d.seq[src];
+            d.scr_route[u] = route;
+        }
+        __syncthreads();
+        // pass 2: write positions, tour, change list
+        for (int u = tid; u < tot; u += blockDim.x) {
+            const int q = u < s_n1 ? s_b1 + u : s_b2 + (u - s_n1);
+            const int a = d.scr_anchor[u], route = d.scr_route[u], src = d.scr_src[u];
+            d.seq[q] = a;
+            d.pos_of[a] = q;
+            if (a <= d.n) d.tour[q - route - 1] = a;
+            if (src != q) {
+                const int slot = atomicAdd(&s_cnt, 1);
+                d.chg[slot] = make_int2(q, src);
+            }
+        }
+        if (dl != 0) {
+            for (int r = lo + 1 + tid; r <= hi; r += blockDim.x) {
+                d.route_start[r] += dl;
+                d.rrec[r].start += dl;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            d.rrec[pl.A].len = pl.nLA;
+            if (pl.B != pl.A) d.rrec[pl.B].len = pl.nLB;
+        }
+        __syncthreads();
+        const int warp = tid >> 5, lane = tid & 31;
+        if (warp == 0) rebuild_route(d, pl.A, lane);
+        if (warp == 1 && pl.B != pl.A) rebuild_route(d, pl.B, lane);
+        __syncthreads();
+        // exact longest route and heaviest load for the integer headroom check
+        int mL = 0, mLoad = 0;
+        for (int r = tid; r < d.m; r += blockDim.x) {
+            mL = max(mL, d.rrec[r].len);
+            mLoad = max(mLoad, d.rrec[r].load);
+        }
+        mL = __reduce_max_sync(0xffffffffu, mL);
+        mLoad = __reduce_max_sync(0xffffffffu, mLoad);
+        if (lane == 0) { atomicMax(&s_maxL, mL); atomicMax(&s_maxLoad, mLoad); }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (s_act) {
+            const MovePlan pl = P;
+            const long long newcost = (long long)d.rrec[pl.A].cost + (pl.A != pl.B ? d.rrec[pl.B].cost : 0);
+            const long long dact = newcost - s_oldcost;
+            if (!ext && dact != pl.delta) set_status(C, 7);
+            C->cost += dact;
+            C->steps += 1;
+            if (pl.A != pl.B) {
+                auto sq = [](long long x) { return x * x; };
+                C->sumL2 += sq(pl.nLA) + sq(pl.nLB) - sq(s_oldLA) - sq(s_oldLB);
+                C->sumLm1 += max(pl.nLA - 1, 0) + max(pl.nLB - 1, 0) - max(s_oldLA - 1, 0) - max(s_oldLB - 1, 0);
+                C->sumLm2 += max(pl.nLA - 2, 0) + max(pl.nLB - 2, 0) - max(s_oldLA - 2, 0) - max(s_oldLB - 2, 0);
+                C->cand_per_eval = candidate_count(d.n, d.m, d.op_mask, C->sumL2, C->sumLm1, C->sumLm2);
+            }
+            C->maxL = s_maxL;
+            C->maxLoad = s_maxLoad;
+            if (!range_ok(d, C)) { set_status(C, TGA_ERR_RANGE); C->done = 1; }
+            C->chg_count = s_cnt;
+        } else {
+            C->chg_count = 0;
+        }
+        if (C->status != 0) C->done = 1;
+        if (use_cond)
+            cudaGraphSetConditional(cond, (!C->done && C->steps < C->step_limit) ? 1u : 0u);
+    }
+}
+
+// Permute the changed columns of rows x0, x0+xs, ... of the position-ordered
+// copy (whole block; sv holds Wp ints).
+__device__ void band_rows(const Dev &d, int x0, int xs, int *sv) {
+    const int K = *(volatile int *)&d.ctl->chg_count;
+    if (K == 0) return;
+    const int2 *chg = d.chg;
+    for (int x = x0; x <= d.n; x += xs) {
+        int *row = d.pcol + (size_t)x * d.ldp + kColOff;
+        for (int e = threadIdx.x; e < K; e += blockDim.x) sv[e] = row[chg[e].y];
+        __syncthreads();
+        for (int e = threadIdx.x; e < K; e += blockDim.x) row[chg[e].x] = sv[e];
+        __syncthreads();
+    }
+}
+
+
+}  // namespace
+}  // namespace tga

@@ -65,7 +65,7 @@ struct Control {
     int maxL, maxLoad;                        // longest route and heaviest load (range check)
     int maxc, maxl, maxs, maxd, maxe, built;
     int last_op, last_a, last_b, last_delta;
-    int pad[4];
+    int next_chunk, done_chunks, finished, pad;   // batched descent: chunk scheduling of this job
 };
 
 // Everything a kernel needs, passed by value.
@@ -184,6 +184,20 @@ __host__ __device__ inline long long candidate_count(long long n, long long m, u
     return c;
 }
 
+// Batched descent (tga_batch.cu): one persistent launch over many contexts.
+constexpr int kBatchThreads = 256;            // 8 warps: 256-column inter tiles
+struct BatchJob {
+    Dev d;
+    int tr, nrt, nct, nchunks;                // tile rows; row/column tiles; chunks per step
+};
+struct BatchState {
+    int build_next, jobs_done, status, pad;
+};
+// mode 0: build + descend; 1: build + one evaluation; 2: one evaluation of
+// already-built jobs (autotuner timing)
+int launch_batch(const BatchJob *jobs_dev, int njobs, BatchState *state_dev, long long max_steps, int mode,
+                 int max_tr, int max_wp, cudaStream_t s);
+
 // Kernel entry points (tga_kernels.cu).
 void launch_check_instance(const Dev &d, cudaStream_t s);
 void launch_build(const Dev &d, cudaStream_t s);
@@ -191,6 +205,7 @@ void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warp
                  cudaStream_t s);
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
                   cudaStream_t s);
+void launch_intra(const Dev &d, cudaStream_t s);
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond,
                   cudaStream_t s);
 void launch_band(const Dev &d, cudaStream_t s);

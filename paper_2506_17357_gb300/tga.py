@@ -72,6 +72,7 @@ EXPORTS = [
     ("tga_descend", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(tga_stats)]),
     ("tga_descend_batch", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(tga_stats)]),
+    ("tga_batch_autotune", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
     ("tga_sync", ctypes.c_int, [_P]),
     ("tga_get_stats", ctypes.c_int, [_P, ctypes.POINTER(tga_stats)]),
     ("tga_set_move_log", ctypes.c_int, [_P, _P, ctypes.c_int64]),
@@ -141,6 +142,13 @@ def tga_descend_batch(ctxs, max_steps: int = (1 << 62)):
     stats = (tga_stats * len(ctxs))()
     _check(_lib().tga_descend_batch(arr, len(ctxs), max_steps, stats), "tga_descend_batch")
     return [s.as_dict() for s in stats]
+
+
+def tga_batch_autotune(ctxs):
+    arr = (_P * len(ctxs))(*[_P(c) for c in ctxs])
+    rows = (ctypes.c_int32 * len(ctxs))()
+    _check(_lib().tga_batch_autotune(arr, len(ctxs), rows), "tga_batch_autotune")
+    return list(rows)
 
 
 def tga_sync(ctx: int):
