@@ -56,23 +56,42 @@ __device__ void build_job(const Dev &d, long long max_steps) {
     __syncthreads();
 }
 
+// Evaluation chunk c of a job.  c < ninter: row tiles chunk_t0[c] ..
+// chunk_t0[c+1]-1 of its pair triangle; a job with a single such chunk also
+// evaluates all its intra-route moves there (a small job's whole step in one
+// chunk).  Larger jobs get separate intra chunks: 8 routes (VRPTW) or 8 moved
+// positions (CVRP) each, so long routes spread over many SMs.
 template <bool TW>
 __device__ void run_chunk(const BatchJob &J, int c, int *smem, int &best, unsigned &bidx) {
     const Dev &d = J.d;
     const bool OR = (d.op_mask & 48u) != 0;
-    if (c < J.nrt) {
-        const int I = c, TC = blockDim.x, TR = J.tr;
-        long long j0 = ((long long)I * TR + 1 + TC - 1) / TC - 1;
-        if (j0 < 0) j0 = 0;
-        for (int Jc = (int)j0; Jc < J.nct; ++Jc) {
-            if (OR) inter_tile<TW, true>(d, I * TR, Jc * TC, TR, smem, best, bidx);
-            else inter_tile<TW, false>(d, I * TR, Jc * TC, TR, smem, best, bidx);
+    const int TC = blockDim.x, TR = J.tr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int r_lo = 0, r_hi = 0, p_lo = 0, p_hi = 0;
+    if (c < J.ninter) {
+        const int t0 = J.chunk_t0[c], t1 = J.chunk_t0[c + 1];
+        for (int I = t0; I < t1; ++I) {
+            long long j0 = ((long long)I * TR + 1 + TC - 1) / TC - 1;
+            if (j0 < 0) j0 = 0;
+            for (int Jc = (int)j0; Jc < J.nct; ++Jc) {
+                if (OR) inter_tile<TW, true>(d, I * TR, Jc * TC, TR, smem, best, bidx);
+                else inter_tile<TW, false>(d, I * TR, Jc * TC, TR, smem, best, bidx);
+            }
         }
+        if (J.ninter > 1) return;
+        r_hi = d.m;
+        p_hi = d.Wp - 1;
     } else {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        __syncthreads();
-        const int r = (c - J.nrt) * nw + warp;
-        if (r < d.m) intra_route<TW>(d, r, lane, smem + warp * kIntraSmemPerWarp, best, bidx);
+        const int g = c - J.ninter;
+        r_lo = g * nw; r_hi = min(r_lo + nw, d.m);
+        p_lo = g * nw; p_hi = min(p_lo + nw, d.Wp - 1);
+    }
+    __syncthreads();
+    if (!TW) {
+        for (int p = p_lo + warp; p < p_hi; p += nw) intra_cvrp_position(d, p, lane, best, bidx);
+    } else {
+        for (int r = r_lo + warp; r < r_hi; r += nw)
+            intra_route<TW>(d, r, lane, smem + warp * kIntraSmemPerWarp, best, bidx);
     }
 }
 
@@ -85,6 +104,8 @@ __global__ void k_batch_init(const BatchJob *jobs, int njobs, BatchState *B) {
     Control *C = jobs[j].d.ctl;
     C->next_chunk = 0x3fffffff;                 // no chunk before the job is built
     C->done_chunks = 0;
+    C->band_next = 0x3fffffff;
+    C->band_done = 0;
     C->finished = 0;
 }
 
@@ -103,7 +124,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
                                                          long long idle_limit_ns) {
     extern __shared__ __align__(16) int smem[];
     __shared__ __align__(16) BatchJob sJ;
-    __shared__ int s_j, s_c, s_last, s_stop;
+    __shared__ int s_j, s_c, s_ph, s_last, s_stop;
     const int tid = threadIdx.x;
     const bool eval_only = mode != 0;
 
@@ -136,6 +157,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
     // ---- descend: take chunks of any job until every job is finished
     int start = blockIdx.x % njobs;
     long long idle_since = -1;
+    int cached = -1;                                  // job whose descriptor sJ holds
     for (;;) {
         if (tid == 0) {
             s_j = -1;
@@ -144,10 +166,14 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
                 for (int k = 0; k < njobs; ++k) {
                     const int jj = (start + k) % njobs;
                     Control *C = jobs[jj].d.ctl;
-                    const int nch = jobs[jj].nchunks;
-                    if (*(volatile int *)&C->next_chunk >= nch) continue;
-                    const int c = atomicAdd(&C->next_chunk, 1);
-                    if (c < nch) { s_j = jj; s_c = c; break; }
+                    const int nch = jobs[jj].nchunks, nb = jobs[jj].nband;
+                    if (*(volatile int *)&C->next_chunk < nch) {
+                        const int c = atomicAdd(&C->next_chunk, 1);
+                        if (c < nch) { s_j = jj; s_c = c; s_ph = 0; break; }
+                    } else if (*(volatile int *)&C->band_next < nb) {
+                        const int c = atomicAdd(&C->band_next, 1);
+                        if (c < nb) { s_j = jj; s_c = c; s_ph = 1; break; }
+                    }
                 }
                 if (s_j < 0) {
                     const long long t = now_ns();
@@ -163,25 +189,45 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
         }
         __syncthreads();
         if (s_stop) break;
-        const int jj = s_j, c = s_c;
+        const int jj = s_j, c = s_c, ph = s_ph;
         if (jj < 0) {
             __nanosleep(256);
             __syncthreads();
             continue;
         }
         start = jj;
-        __threadfence();   // acquire the job state released with next_chunk
-        load_job(jobs, jj, &sJ);
+        __threadfence();   // acquire the job state released with the chunk counter
+        if (jj != cached) {
+            load_job(jobs, jj, &sJ);
+            cached = jj;
+        }
         const BatchJob &J = sJ;
+        Control *C = J.d.ctl;
+        if (ph == 1) {
+            // column-permutation chunk of the move just applied
+            band_rows(J.d, c * kBandRowsPerChunk, 1, smem, (c + 1) * kBandRowsPerChunk);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                if (atomicAdd(&C->band_done, 1) == J.nband - 1) {
+                    __threadfence();
+                    C->done_chunks = 0;
+                    __threadfence();
+                    atomicExch(&C->next_chunk, 0);          // release the next evaluation
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         int best = kBestInit;
         unsigned bidx = 0xffffffffu;
         if (J.d.has_tw) run_chunk<true>(J, c, smem, best, bidx);
         else run_chunk<false>(J, c, smem, best, bidx);
         const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
-        block_min_to(key, &J.d.ctl->best_key);
+        block_min_to(key, &C->best_key);
         if (tid == 0) {
             __threadfence();
-            s_last = atomicAdd(&J.d.ctl->done_chunks, 1) == J.nchunks - 1;
+            s_last = atomicAdd(&C->done_chunks, 1) == J.nchunks - 1;
         }
         __syncthreads();
         if (s_last) {
@@ -190,24 +236,24 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
             if (!eval_only) {
                 apply_block(d, nullptr, 0, 0);
                 __syncthreads();
-                band_rows(d, 0, 1, smem);
-                __syncthreads();
             } else if (tid == 0) {
-                Control *C = d.ctl;
                 if (d.log && C->evals < d.log_cap) d.log[C->evals] = C->best_key;
                 C->evals += 1;
                 C->cand_total += C->cand_per_eval;
             }
             if (tid == 0) {
-                Control *C = d.ctl;
                 if (eval_only || C->done || C->steps >= C->step_limit) {
                     C->finished = 1;
                     __threadfence();
                     atomicAdd(&B->jobs_done, 1);
-                } else {
+                } else if (C->chg_count == 0) {
                     C->done_chunks = 0;
                     __threadfence();
                     atomicExch(&C->next_chunk, 0);
+                } else {
+                    C->band_done = 0;
+                    __threadfence();
+                    atomicExch(&C->band_next, 0);          // release the permutation chunks
                 }
             }
             __syncthreads();

@@ -193,7 +193,9 @@ int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *t
     for (int i = 0; i < n; ++i)
         if (ctxs[i]->stream != s && cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return TGA_ERR_CUDA;
     std::vector<BatchJob> jobs((size_t)n);
+    std::vector<std::vector<int>> bounds((size_t)n);
     int max_tr = 16, max_wp = 1;
+    size_t nbounds = 0;
     for (int i = 0; i < n; ++i) {
         tga_ctx *c = ctxs[i];
         const int tr = tr_override ? tr_override[i] : (c->batch_tr ? c->batch_tr : default_batch_tr(c->d.Wp));
@@ -203,7 +205,24 @@ int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *t
         const int Wa = c->d.Wp - 1;
         J.nrt = (Wa + tr - 1) / tr;
         J.nct = (Wa + kBatchThreads - 1) / kBatchThreads;
-        J.nchunks = J.nrt + (c->d.m + kBatchThreads / 32 - 1) / (kBatchThreads / 32);
+        // group consecutive row tiles into chunks of about kChunkPairs pairs
+        std::vector<int> &b = bounds[(size_t)i];
+        b.push_back(0);
+        long long acc = 0;
+        for (int I = 0; I < J.nrt; ++I) {
+            long long j0 = ((long long)I * tr + 1 + kBatchThreads - 1) / kBatchThreads - 1;
+            if (j0 < 0) j0 = 0;
+            acc += (long long)(J.nct - j0) * tr * kBatchThreads;
+            if (acc >= kChunkPairs && I + 1 < J.nrt) { b.push_back(I + 1); acc = 0; }
+        }
+        b.push_back(J.nrt);
+        J.ninter = (int)b.size() - 1;
+        const int nw = kBatchThreads / 32;
+        const int nintra = J.ninter == 1 ? 0 : ((c->d.has_tw ? c->d.m : Wa) + nw - 1) / nw;
+        J.nchunks = J.ninter + nintra;
+        J.nband = (c->d.n + 1 + kBandRowsPerChunk - 1) / kBandRowsPerChunk;
+        J.chunk_t0 = nullptr;
+        nbounds += b.size();
         if (tr > max_tr) max_tr = tr;
         if (c->d.Wp > max_wp) max_wp = c->d.Wp;
         if (mode != 2 && cudaMemsetAsync(c->d.ctl, 0, sizeof(Control), s) != cudaSuccess) return TGA_ERR_CUDA;
@@ -217,11 +236,22 @@ int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *t
     for (int i = 0; i < n; ++i) ordered[(size_t)i] = jobs[(size_t)order[(size_t)i]];
     char *buf = nullptr;
     const size_t jb = align_up(sizeof(BatchJob) * (size_t)n, 256);
-    if (cudaMalloc(&buf, jb + sizeof(BatchState)) != cudaSuccess) { cudaGetLastError(); return TGA_ERR_NOMEM; }
+    const size_t sb = align_up(sizeof(BatchState), 256);
+    if (cudaMalloc(&buf, jb + sb + sizeof(int) * nbounds) != cudaSuccess) { cudaGetLastError(); return TGA_ERR_NOMEM; }
     BatchJob *jdev = (BatchJob *)buf;
     BatchState *sdev = (BatchState *)(buf + jb);
+    int *bdev = (int *)(buf + jb + sb);
+    std::vector<int> flat;
+    flat.reserve(nbounds);
+    for (int i = 0; i < n; ++i) {
+        BatchJob &J = ordered[(size_t)i];
+        const std::vector<int> &b = bounds[(size_t)order[(size_t)i]];
+        J.chunk_t0 = bdev + flat.size();
+        flat.insert(flat.end(), b.begin(), b.end());
+    }
     int rc = TGA_OK;
-    if (cudaMemcpyAsync(jdev, ordered.data(), sizeof(BatchJob) * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(jdev, ordered.data(), sizeof(BatchJob) * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(bdev, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
         rc = TGA_ERR_CUDA;
     if (!rc) rc = launch_batch(jdev, n, sdev, max_steps, mode, max_tr, max_wp, s);
     BatchState st{};

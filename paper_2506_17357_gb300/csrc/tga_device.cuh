@@ -755,6 +755,78 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
     __syncwarp();
 }
 
+// Intra-route candidates of a CVRP whose moved element is the customer at
+// position p, with one warp (all lanes call): every delta is an O(1) edge
+// formula (loads do not change inside a route), lanes take the other end j
+// of the move, and each distance comes from a row segment of the
+// position-ordered copy indexed by j, so a warp's loads are contiguous.
+//   relocate/or-opt run i..i+k-1 after j: rem_k + c(x_j,x_i) + c(x_{i+k-1},x_{j+1}) - c(x_j,x_{j+1})
+//   swap i<j (adjacent or not), 2-opt i<j (reversal of i..j).
+__device__ void intra_cvrp_position(const Dev &d, int p, int lane, int &best, unsigned &bidx) {
+    if (p >= d.Wp - 1) return;
+    const int ax = d.seq[p];
+    if (ax > d.n) return;                               // a start depot is never moved
+    const BRec bx = d.brec[ax];
+    const int r = bx.route, i = bx.idx;
+    const RouteRec R = d.rrec[r];
+    const int L = R.len, st = R.start;
+    if (L < 2) return;
+    const unsigned mask = d.op_mask;
+    const unsigned W = (unsigned)d.W, W2 = W * W;
+    auto nodeAt = [&](int k) { return (k <= 0 || k > L) ? 0 : d.seq[st + k]; };
+    auto rowOf = [&](int node) { return d.pcol + (size_t)node * d.ldp + kColOff + st; };
+    // distance from the prefix through element k to element k+1
+    auto dfAt = [&](int k) {
+        if (k > L) return R.dist;
+        return d.brec[k == 0 ? d.n + 1 + r : d.seq[st + k]].distf;
+    };
+    const int xi = ax, xm = nodeAt(i - 1), xn = nodeAt(i + 1);
+    const int *rowI = rowOf(xi), *rowP = rowOf(xm), *rowN = rowOf(xn);
+    const int e_prev = dfAt(i) - dfAt(i - 1);            // c(x_{i-1}, x_i)
+    const int e_next = dfAt(i + 1) - dfAt(i);            // c(x_i, x_{i+1})
+    // removal gains of runs of length 1..3 starting at i
+    int remk[4] = {0, 0, 0, 0};
+    const int *rowW[4] = {rowI, rowI, rowI, rowI};
+    for (int k = 1; k <= 3; ++k) {
+        if (i + k - 1 > L) break;
+        const int w = nodeAt(i + k - 1);
+        rowW[k] = rowOf(w);
+        const int e_w = dfAt(i + k) - dfAt(i + k - 1);  // c(x_{i+k-1}, x_{i+k})
+        remk[k] = TGA_LDG(rowP + i + k) - e_prev - e_w;
+    }
+    for (int j = lane; j <= L; j += 32) {
+        const int aj = j == 0 ? d.n + 1 + r : d.seq[st + j];
+        const int df_j = j == 0 ? 0 : d.brec[aj].distf;
+        const int e_j = dfAt(j + 1) - df_j;                // c(x_j, x_{j+1})
+        const int cij = TGA_LDG(rowI + j);
+        for (int k = 1; k <= 3; ++k) {
+            const int op = k == 1 ? 0 : k + 2;
+            if (!(mask & (1u << op)) || i + k - 1 > L) continue;
+            if (j >= i - 1 && j <= i + k - 1) continue;
+            const int delta = remk[k] + cij + TGA_LDG(rowW[k] + j + 1) - e_j;
+            TGA_TRY(delta, (unsigned)op * W2 + (unsigned)xi * W + (unsigned)aj);
+        }
+        if (j > i) {
+            const int cpj = TGA_LDG(rowP + j), ci_j1 = TGA_LDG(rowI + j + 1);
+            if (mask & 2u) {
+                int delta;
+                if (j == i + 1) {
+                    delta = cpj + ci_j1 - e_prev - e_j;
+                } else {
+                    const int e_jm = df_j - dfAt(j - 1);     // c(x_{j-1}, x_j)
+                    delta = cpj + TGA_LDG(rowN + j) + TGA_LDG(rowI + j - 1) + ci_j1 - e_prev - e_next - e_jm - e_j;
+                }
+                const unsigned xj = (unsigned)aj;
+                TGA_TRY(delta, W2 + min((unsigned)xi, xj) * W + max((unsigned)xi, xj));
+            }
+            if (mask & 4u) {
+                const int delta = cpj + ci_j1 - e_prev - e_j;
+                TGA_TRY(delta, 2u * W2 + (unsigned)xi * W + (unsigned)aj);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // apply (one block)
 
@@ -1006,13 +1078,14 @@ __device__ void apply_block(const Dev &d, const tga_move *ext, cudaGraphConditio
     }
 }
 
-// Permute the changed columns of rows x0, x0+xs, ... of the position-ordered
-// copy (whole block; sv holds Wp ints).
-__device__ void band_rows(const Dev &d, int x0, int xs, int *sv) {
+// Permute the changed columns of rows x0, x0+xs, ... (below x_end) of the
+// position-ordered copy (whole block; sv holds Wp ints).
+__device__ void band_rows(const Dev &d, int x0, int xs, int *sv, int x_end) {
     const int K = *(volatile int *)&d.ctl->chg_count;
     if (K == 0) return;
     const int2 *chg = d.chg;
-    for (int x = x0; x <= d.n; x += xs) {
+    if (x_end > d.n + 1) x_end = d.n + 1;
+    for (int x = x0; x < x_end; x += xs) {
         int *row = d.pcol + (size_t)x * d.ldp + kColOff;
         for (int e = threadIdx.x; e < K; e += blockDim.x) sv[e] = row[chg[e].y];
         __syncthreads();

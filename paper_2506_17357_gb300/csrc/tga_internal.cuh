@@ -65,7 +65,10 @@ struct Control {
     int maxL, maxLoad;                        // longest route and heaviest load (range check)
     int maxc, maxl, maxs, maxd, maxe, built;
     int last_op, last_a, last_b, last_delta;
-    int next_chunk, done_chunks, finished, pad;   // batched descent: chunk scheduling of this job
+    // batched descent: chunk scheduling of this job (evaluation phase, then
+    // the column-permutation phase of the applied move)
+    int next_chunk, done_chunks, finished, band_next;
+    int band_done, pad2[3];
 };
 
 // Everything a kernel needs, passed by value.
@@ -186,9 +189,13 @@ __host__ __device__ inline long long candidate_count(long long n, long long m, u
 
 // Batched descent (tga_batch.cu): one persistent launch over many contexts.
 constexpr int kBatchThreads = 256;            // 8 warps: 256-column inter tiles
+constexpr int kBandRowsPerChunk = 256;
+constexpr long long kChunkPairs = 1LL << 17;  // target candidate pairs per evaluation chunk
 struct BatchJob {
     Dev d;
-    int tr, nrt, nct, nchunks;                // tile rows; row/column tiles; chunks per step
+    int tr, nrt, nct, nchunks;                // tile rows; row/column tiles; evaluation chunks per step
+    int nband, ninter;                        // column-permutation chunks; inter-route chunks
+    const int *chunk_t0;                      // [ninter+1] first row tile of each inter-route chunk
 };
 struct BatchState {
     int build_next, jobs_done, status, pad;

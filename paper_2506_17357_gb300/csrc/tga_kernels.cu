@@ -79,6 +79,16 @@ __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d) {
     block_min_to(key, &d.ctl->best_key);
 }
 
+__global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d) {
+    if (*(volatile int *)&d.ctl->done) return;
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int best = kBestInit;
+    unsigned bidx = 0xffffffffu;
+    intra_cvrp_position(d, p, threadIdx.x & 31, best, bidx);
+    const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
+    block_min_to(key, &d.ctl->best_key);
+}
+
 __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaGraphConditionalHandle cond,
                                                int use_cond) {
     apply_block(d, ext, cond, use_cond);
@@ -86,7 +96,7 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
 
 __global__ void __launch_bounds__(256) k_band(Dev d) {
     extern __shared__ int sv[];
-    band_rows(d, blockIdx.x, gridDim.x, sv);
+    band_rows(d, blockIdx.x, gridDim.x, sv, d.n + 1);
 }
 
 __global__ void k_finalize(Dev d, tga_move *out) {
@@ -171,9 +181,14 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
 }
 
 void launch_intra(const Dev &d, cudaStream_t s) {
-    const int nb = (d.m + kIntraWarps - 1) / kIntraWarps;
-    if (d.has_tw) k_eval_intra<true><<<nb, kIntraWarps * 32, 0, s>>>(d);
-    else k_eval_intra<false><<<nb, kIntraWarps * 32, 0, s>>>(d);
+    if (d.has_tw) {
+        const int nb = (d.m + kIntraWarps - 1) / kIntraWarps;
+        k_eval_intra<true><<<nb, kIntraWarps * 32, 0, s>>>(d);
+    } else {
+        // CVRP: one warp per position (moved customer), 8 warps per block
+        const int nb = (d.Wp - 1 + 7) / 8;
+        k_eval_intra_cvrp<<<nb, 256, 0, s>>>(d);
+    }
 }
 
 void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s) {
