@@ -392,6 +392,59 @@ def bench_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_serve(args):
+    """Serving workload: a seeded Poisson stream of jobs (sizes log-uniform in
+    [100, 5000], 70% CVRP / 30% VRPTW) through the continuous-batching server
+    (memory budget 1 GiB, up to 32 slots) against the one-at-a-time path on the
+    same arrivals.  The arrival rate is set from the measured one-at-a-time
+    capacity mu1: 0.8 mu1 (both keep up; latency differs) and 2 mu1 (the
+    one-at-a-time queue grows)."""
+    import torch
+    from paper_2506_17357_gb300 import serving as S
+    torch.cuda.set_device(0)
+    count = args.serve_jobs
+    sizes, kinds = I.serving_sizes(count, seed=5)
+    reqs = []
+    for j in range(count):
+        inst, sol = I.serving_job(j, int(sizes[j]), bool(kinds[j]), seed=5)
+        reqs.append(S.Request(j, 0.0, inst, sol, I.mask_for(inst)))
+    pinned = {r.rid: S._Pinned(torch, r) for r in reqs}
+    budget = 1 << 30
+
+    def run(slots, arrivals):
+        rs = [S.Request(r.rid, float(a), r.inst, r.sol, r.op_mask) for r, a in zip(reqs, arrivals)]
+        srv = S.Server(budget_bytes=budget, max_slots=slots, keep_solutions=False)
+        return S.summarize(srv.serve(rs, pinned=pinned)), srv
+
+    for _ in range(max(1, args.warmup)):
+        S.Server(budget_bytes=budget, max_slots=4, keep_solutions=False).serve(
+            [S.Request(r.rid, 0.0, r.inst, r.sol, r.op_mask) for r in reqs[:6]], pinned=pinned)
+    zero = np.zeros(count)
+    cap1, _ = run(1, zero)
+    capN, _ = run(32, zero)
+    mu1 = cap1["jobs_per_s"]
+    sweep = {}
+    with ClockSampler(0) as clk:
+        for mult in (0.8, 2.0):
+            arr = I.poisson_arrivals(count, mult * mu1, seed=5)
+            one, _ = run(1, arr)
+            cont, _ = run(32, arr)
+            sweep[str(mult)] = {"rate_jobs_per_s": mult * mu1, "one_at_a_time": one, "continuous": cont}
+    clocks = clk.summary()
+    head = sweep["2.0"]["continuous"]
+    line = {"metric": "served jobs/s", "value": head["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1,
+            "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * head["makespan_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "p50_latency_ms": head["p50_latency_ms"], "p99_latency_ms": head["p99_latency_ms"],
+            "saturated_capacity_jobs_per_s": {"one_at_a_time": mu1, "continuous": capN["jobs_per_s"]},
+            "sweep": sweep,
+            "config": {"workload": "serve", "jobs": count, "sizes": "log-uniform [100, 5000]",
+                       "mix": "70% CVRP / 30% VRPTW", "budget_bytes": budget, "max_slots": 32,
+                       "arrivals": "seeded Poisson at 0.8x and 2x the one-at-a-time capacity"},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(args, seconds=15.0):
     """The oracle's concatenation evaluator (plain single-threaded C) on the
     host: best-improvement steps of the same workload from the same initial
@@ -447,7 +500,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tga", choices=["tga", "reference"])
-    ap.add_argument("--workload", default="vrptw1000", choices=sorted(WORKLOADS) + ["batch256"])
+    ap.add_argument("--workload", default="vrptw1000", choices=sorted(WORKLOADS) + ["batch256", "serve"])
+    ap.add_argument("--serve-jobs", type=int, default=120)
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -457,6 +511,8 @@ def main():
         bench_reference(args)
     elif args.workload == "batch256":
         bench_batch(args)
+    elif args.workload == "serve":
+        bench_serve(args)
     else:
         bench_gpu(args)
 

@@ -164,6 +164,20 @@ int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_h
  * rows_out: n entries (may be NULL).  Leaves the contexts to be rebuilt. */
 int tga_batch_autotune(tga_ctx **ctxs, int n, int32_t *rows_out);
 
+/* As tga_descend, but only enqueues the work on the context's stream and
+ * returns at once (no synchronisation).  Poll with tga_query; read results
+ * with tga_get_stats once done. */
+int tga_descend_async(tga_ctx *ctx, int64_t max_steps);
+
+/* *done_out = 1 when all work enqueued on the context's stream has
+ * finished, 0 while some is pending.  Never blocks. */
+int tga_query(tga_ctx *ctx, int32_t *done_out);
+
+/* Device bytes a context for n customers and m routes allocates (its
+ * workspace only; the caller's instance and solution arrays come on top).
+ * Host-only arithmetic, for admission control by memory budget. */
+size_t tga_workspace_bytes(int32_t n_customers, int32_t n_routes);
+
 /* Wait for the context's stream and report the device status. */
 int tga_sync(tga_ctx *ctx);
 

@@ -24,6 +24,7 @@ struct tga_ctx {
     // inter-route tiles
     int tile_rows = 0, tile_warps = 0, ntiles = 0;
     int2 *tiles = nullptr;
+    std::vector<int2> tiles_host;      // kept alive for the asynchronous upload
     // descent graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -61,17 +62,24 @@ int set_tiles(tga_ctx *c, int rows, int warps) {
     const int Wa = c->d.Wp - 1;   // anchor positions
     const int TC = warps * 32;
     const int nrt = (Wa + rows - 1) / rows, nct = (Wa + TC - 1) / TC;
-    std::vector<int2> t;
+    std::vector<int2> &t = c->tiles_host;
+    t.clear();
     t.reserve((size_t)nrt * nct / 2 + nrt + 8);
     for (int I = 0; I < nrt; ++I)
         for (int J = 0; J < nct; ++J)
             if ((long long)(J + 1) * TC - 1 > (long long)I * rows) t.push_back(make_int2(I, J));
-    if (c->tiles) cudaFree(c->tiles);
+    // stream-ordered allocation: no device-wide synchronisation, so other
+    // contexts' work keeps running while this one is set up or torn down
+    if (c->tiles) cudaFreeAsync(c->tiles, c->stream);
     c->tiles = nullptr;
     c->ntiles = (int)t.size();
     if (!t.empty()) {
-        if (cudaMalloc(&c->tiles, t.size() * sizeof(int2)) != cudaSuccess) return TGA_ERR_NOMEM;
-        if (cudaMemcpy(c->tiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+        if (cudaMallocAsync((void **)&c->tiles, t.size() * sizeof(int2), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return TGA_ERR_NOMEM;
+        }
+        if (cudaMemcpyAsync(c->tiles, t.data(), t.size() * sizeof(int2), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess)
             return TGA_ERR_CUDA;
     }
     c->tile_rows = rows;
@@ -139,7 +147,8 @@ int build_graph(tga_ctx *c) {
 int read_control(tga_ctx *c, Control *out) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return TGA_ERR_CUDA;
-    e = cudaMemcpy(out, c->d.ctl, sizeof(Control), cudaMemcpyDeviceToHost);
+    e = cudaMemcpyAsync(out, c->d.ctl, sizeof(Control), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return cuda_err(e);
 }
 
@@ -336,7 +345,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     const size_t o_intra = take(sizeof(int) * 10 * (size_t)(d.Wp + m));
     const size_t o_pcol = take(sizeof(int) * (size_t)(n + 1) * (size_t)d.ldp);
     c->ws_bytes = off;
-    if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
+    if (cudaMallocAsync(&c->ws, c->ws_bytes, c->stream) != cudaSuccess) {
         cudaGetLastError();
         tga_destroy(c);
         return TGA_ERR_NOMEM;
@@ -461,6 +470,31 @@ int tga_batch_autotune(tga_ctx **ctxs, int n, int32_t *rows_out) {
     // the tuning evaluations leave finished contexts behind: rebuild on next use
     for (int i = 0; i < n; ++i) ctxs[i]->built = false;
     return rc;
+}
+
+int tga_descend_async(tga_ctx *c, int64_t max_steps) {
+    if (!c || max_steps < 0) return TGA_ERR_INVALID;
+    return descend_launch(c, max_steps);
+}
+
+int tga_query(tga_ctx *c, int32_t *done_out) {
+    if (!c || !done_out) return TGA_ERR_INVALID;
+    const cudaError_t e = cudaStreamQuery(c->stream);
+    if (e == cudaSuccess) { *done_out = 1; return TGA_OK; }
+    if (e == cudaErrorNotReady) { cudaGetLastError(); *done_out = 0; return TGA_OK; }
+    return TGA_ERR_CUDA;
+}
+
+size_t tga_workspace_bytes(int32_t n_customers, int32_t n_routes) {
+    if (n_customers < 1 || n_routes < 1) return 0;
+    const size_t n = (size_t)n_customers, m = (size_t)n_routes, W = n + 1 + m, Wp = n + m + 1;
+    const size_t ldp = align_up(Wp, kMaxTileCols) + 16;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { off = align_up(off + bytes, 256); };
+    take(sizeof(Control)); take(4 * Wp); take(4 * (W + 1)); take(sizeof(BRec) * (W + 1));
+    take(sizeof(ERec) * (W + 1)); take(sizeof(RouteRec) * m); take(8 * Wp); take(4 * Wp); take(4 * Wp);
+    take(4 * Wp); take(4 * (n + 1)); take(4 * 10 * (Wp + m)); take(4 * (n + 1) * ldp);
+    return off;
 }
 
 int tga_sync(tga_ctx *c) {
@@ -589,8 +623,9 @@ int tga_destroy(tga_ctx *c) {
     if (!c) return TGA_ERR_INVALID;
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graph(c);
-    if (c->tiles) cudaFree(c->tiles);
-    if (c->ws) cudaFree(c->ws);
+    if (c->tiles) cudaFreeAsync(c->tiles, c->stream);
+    if (c->ws) cudaFreeAsync(c->ws, c->stream);
+    if (c->tiles || c->ws) cudaStreamSynchronize(c->stream);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->cap2) cudaStreamDestroy(c->cap2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);

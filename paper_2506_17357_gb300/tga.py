@@ -73,6 +73,9 @@ EXPORTS = [
     ("tga_descend_batch", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int64,
                                          ctypes.POINTER(tga_stats)]),
     ("tga_batch_autotune", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
+    ("tga_descend_async", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("tga_query", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    ("tga_workspace_bytes", ctypes.c_size_t, [ctypes.c_int32, ctypes.c_int32]),
     ("tga_sync", ctypes.c_int, [_P]),
     ("tga_get_stats", ctypes.c_int, [_P, ctypes.POINTER(tga_stats)]),
     ("tga_set_move_log", ctypes.c_int, [_P, _P, ctypes.c_int64]),
@@ -149,6 +152,20 @@ def tga_batch_autotune(ctxs):
     rows = (ctypes.c_int32 * len(ctxs))()
     _check(_lib().tga_batch_autotune(arr, len(ctxs), rows), "tga_batch_autotune")
     return list(rows)
+
+
+def tga_descend_async(ctx: int, max_steps: int = (1 << 62)):
+    _check(_lib().tga_descend_async(_P(ctx), max_steps), "tga_descend_async")
+
+
+def tga_query(ctx: int) -> bool:
+    done = ctypes.c_int32()
+    _check(_lib().tga_query(_P(ctx), ctypes.byref(done)), "tga_query")
+    return bool(done.value)
+
+
+def tga_workspace_bytes(n: int, m: int) -> int:
+    return int(_lib().tga_workspace_bytes(n, m))
 
 
 def tga_sync(ctx: int):
