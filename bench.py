@@ -166,6 +166,21 @@ def dist_env():
     return ws, rank, local
 
 
+def only_descent(args):
+    """One build + descent of the workload and nothing else (no timing): the
+    command profilers run to list the per-step kernel launches."""
+    import torch
+    from paper_2506_17357_gb300 import tga as T
+    desc, make, mask = WORKLOADS[args.workload]
+    inst, sol = make(args.seed)
+    ls = T.LocalSearch(inst, sol, mask).build()
+    st = ls.descend()
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": args.workload, "steps": st["steps"], "evaluations": st["evaluations"],
+                      "final_cost": st["final_cost"], "status": st["status"]}))
+    ls.close()
+
+
 def bench_gpu(args):
     import torch
     import torch.distributed as dist
@@ -502,12 +517,16 @@ def main():
     ap.add_argument("--impl", default="tga", choices=["tga", "reference"])
     ap.add_argument("--workload", default="vrptw1000", choices=sorted(WORKLOADS) + ["batch256", "serve"])
     ap.add_argument("--serve-jobs", type=int, default=120)
+    ap.add_argument("--only-descent", action="store_true",
+                    help="run one descent of the workload without timing (for profiler launch lists)")
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.only_descent:
+        only_descent(args)
+    elif args.impl == "reference":
         bench_reference(args)
     elif args.workload == "batch256":
         bench_batch(args)

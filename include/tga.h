@@ -189,11 +189,19 @@ int tga_get_stats(tga_ctx *ctx, tga_stats *out_host);
  * (NULL disables).  Used to compare whole trajectories. */
 int tga_set_move_log(tga_ctx *ctx, uint64_t *log_dev, int64_t capacity);
 
-/* Choose the inter-route tile shape: rows per tile (16, 32 or 64) and warps
- * per block (2, 4 or 8; 32 columns each); 0, 0 runs the built-in autotuner
- * (times every shape on the current state).  Call after tga_build_attrs. */
+/* Choose the inter-route tile shape: rows per tile (8, 16, 32 or 64) and
+ * warps per block (2, 4 or 8; 32 columns each); 0, 0 runs the built-in
+ * autotuner (times every shape, including row-split ones, on the current
+ * state).  Call after tga_build_attrs. */
 int tga_set_tile(tga_ctx *ctx, int32_t rows, int32_t warps);
 int tga_get_tile(tga_ctx *ctx, int32_t *rows, int32_t *warps);
+
+/* Full tile shape: rows per tile (8/16/32/64), column warps (2/4/8: 32
+ * columns each) and a row split (1/2/4 warps share one column slice and
+ * divide its rows; col_warps * row_split <= 8).  tga_set_tile(ctx, 0, 0)
+ * autotunes over these shapes. */
+int tga_set_tile_shape(tga_ctx *ctx, int32_t rows, int32_t col_warps, int32_t row_split);
+int tga_get_tile_shape(tga_ctx *ctx, int32_t *rows, int32_t *col_warps, int32_t *row_split);
 
 /* Time the inter-route evaluation kernel alone on the current state:
  * `reps` launches bracketed by CUDA events on the context's stream; writes the

@@ -74,8 +74,8 @@ __device__ void run_chunk(const BatchJob &J, int c, int *smem, int &best, unsign
             long long j0 = ((long long)I * TR + 1 + TC - 1) / TC - 1;
             if (j0 < 0) j0 = 0;
             for (int Jc = (int)j0; Jc < J.nct; ++Jc) {
-                if (OR) inter_tile<TW, true>(d, I * TR, Jc * TC, TR, smem, best, bidx);
-                else inter_tile<TW, false>(d, I * TR, Jc * TC, TR, smem, best, bidx);
+                if (OR) inter_tile<TW, true>(d, I * TR, Jc * TC, TR, 1, smem, best, bidx);
+                else inter_tile<TW, false>(d, I * TR, Jc * TC, TR, 1, smem, best, bidx);
             }
         }
         if (J.ninter > 1) return;

@@ -22,7 +22,7 @@ struct tga_ctx {
     int device = 0;
     bool built = false;
     // inter-route tiles
-    int tile_rows = 0, tile_warps = 0, ntiles = 0;
+    int tile_rows = 0, tile_warps = 0, tile_rs = 1, ntiles = 0;
     int2 *tiles = nullptr;
     std::vector<int2> tiles_host;      // kept alive for the asynchronous upload
     // descent graph
@@ -56,8 +56,9 @@ void drop_graph(tga_ctx *c) {
     c->graph_ready = false;
 }
 
-int set_tiles(tga_ctx *c, int rows, int warps) {
-    if (!(rows == 16 || rows == 32 || rows == 64) || !(warps == 2 || warps == 4 || warps == 8))
+int set_tiles(tga_ctx *c, int rows, int warps, int rs = 1) {
+    if (!(rows == 8 || rows == 16 || rows == 32 || rows == 64) || !(warps == 2 || warps == 4 || warps == 8) ||
+        !(rs == 1 || rs == 2 || rs == 4) || warps * rs > 8 || rows % rs != 0)
         return TGA_ERR_INVALID;
     const int Wa = c->d.Wp - 1;   // anchor positions
     const int TC = warps * 32;
@@ -84,6 +85,7 @@ int set_tiles(tga_ctx *c, int rows, int warps) {
     }
     c->tile_rows = rows;
     c->tile_warps = warps;
+    c->tile_rs = rs;
     drop_graph(c);
     return TGA_OK;
 }
@@ -96,7 +98,7 @@ void default_tiles(tga_ctx *c) {
 }
 
 int step_once(tga_ctx *c, unsigned long long cond, int use_cond, cudaStream_t s) {
-    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, s);
+    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, s, c->tile_rs);
     launch_apply(c->d, nullptr, cond, use_cond, s);
     launch_band(c->d, s);
     return check_launch();
@@ -122,7 +124,7 @@ int build_graph(tga_ctx *c) {
             // branches; both fold into the same packed best key
             cudaEventRecord(c->ev_fork, c->cap);
             cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
-            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap);
+            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap, c->tile_rs);
             launch_intra(c->d, c->cap2);
             cudaEventRecord(c->ev_join, c->cap2);
             cudaStreamWaitEvent(c->cap, c->ev_join, 0);
@@ -387,7 +389,7 @@ int tga_eval_best_move(tga_ctx *c, tga_move *out_dev) {
     if (!c->built) return TGA_ERR_STATE;
     if (!c->tiles && c->d.Wp > 2) default_tiles(c);
     launch_begin(c->d, 1, c->stream);
-    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);
+    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
     launch_finalize(c->d, out_dev, c->stream);
     return check_launch();
 }
@@ -527,31 +529,48 @@ int tga_set_tile(tga_ctx *c, int32_t rows, int32_t warps) {
     if (!c->built) return TGA_ERR_STATE;
     // autotune: time every shape on the current state (evaluation only; the
     // solution is not touched), keep the fastest.
-    static const int shapes[][2] = {{16, 2}, {32, 2}, {16, 4}, {32, 4}, {64, 4}, {32, 8}, {64, 8}};
+    static const int shapes[][3] = {{8, 2, 1},  {16, 2, 1}, {16, 2, 2}, {16, 2, 4}, {16, 4, 1}, {16, 4, 2},
+                                    {32, 2, 2}, {32, 2, 4}, {32, 4, 1}, {32, 4, 2}, {64, 4, 1}, {64, 4, 2},
+                                    {32, 8, 1}, {64, 8, 1}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float bestms = 1e30f;
-    int br = 32, bw = 4;
+    int br = 32, bw = 4, brs = 1;
     for (const auto &s : shapes) {
-        if (set_tiles(c, s[0], s[1]) != TGA_OK) continue;
+        if (set_tiles(c, s[0], s[1], s[2]) != TGA_OK) continue;
         launch_begin(c->d, 1, c->stream);
-        launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);
+        launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
         cudaEventRecord(e0, c->stream);
-        for (int k = 0; k < 3; ++k) launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);
+        for (int k = 0; k < 5; ++k)
+            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
         cudaEventRecord(e1, c->stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < bestms) { bestms = ms; br = s[0]; bw = s[1]; }
+        if (ms < bestms) { bestms = ms; br = s[0]; bw = s[1]; brs = s[2]; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // leave the context as it was before tuning (no pending key)
     cudaMemsetAsync(&c->d.ctl->best_key, 0xff, sizeof(unsigned long long), c->stream);
-    int rc = set_tiles(c, br, bw);
+    int rc = set_tiles(c, br, bw, brs);
     if (rc) return rc;
     return check_launch();
+}
+
+int tga_set_tile_shape(tga_ctx *c, int32_t rows, int32_t col_warps, int32_t row_split) {
+    if (!c) return TGA_ERR_INVALID;
+    return set_tiles(c, rows, col_warps, row_split);
+}
+
+int tga_get_tile_shape(tga_ctx *c, int32_t *rows, int32_t *col_warps, int32_t *row_split) {
+    if (!c || !rows || !col_warps || !row_split) return TGA_ERR_INVALID;
+    if (!c->tiles && c->built && c->d.Wp > 2) default_tiles(c);
+    *rows = c->tile_rows;
+    *col_warps = c->tile_warps;
+    *row_split = c->tile_rs;
+    return TGA_OK;
 }
 
 int tga_get_tile(tga_ctx *c, int32_t *rows, int32_t *warps) {
@@ -574,9 +593,9 @@ int tga_profile_inter(tga_ctx *c, int32_t reps, float *ms_per_launch) {
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TGA_ERR_CUDA;
     // the kernel returns immediately on a finished context: clear the flag
     cudaMemsetAsync(&c->d.ctl->done, 0, sizeof(int), c->stream);
-    launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);   // warm-up
+    launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);   // warm-up
     cudaEventRecord(e0, c->stream);
-    for (int k = 0; k < reps; ++k) launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream);
+    for (int k = 0; k < reps; ++k) launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
     cudaEventRecord(e1, c->stream);
     cudaEventSynchronize(e1);
     float ms = 0.f;

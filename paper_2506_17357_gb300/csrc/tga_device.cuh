@@ -391,12 +391,16 @@ __device__ void pcol_init_range(const Dev &d, long long t0, long long stride) {
     } while (0)
 
 // One tile of the inter-route pair triangle: rows p0..p0+TR-1, columns
-// q0..q0+32*NW-1 (NW = warps of the block).  Every thread folds its column's
-// candidates into (best, bidx); smem must hold inter_smem_bytes(TR, NW).
+// q0..q0+32*NWc-1 with NWc = warps / RS.  Warp w owns the 32 columns of slice
+// w % NWc and the rows of group w / NWc (TR/RS rows each).  Every thread folds
+// its column's candidates into (best, bidx); smem must hold
+// inter_smem_bytes(TR, NWc).
 template <bool TW, bool OR>
-__device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int *smem, int &best, unsigned &bidx) {
-    const int NW = blockDim.x >> 5, TC = NW * 32;
+__device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *smem, int &best, unsigned &bidx) {
+    const int NW = blockDim.x >> 5, NWc = NW / RS, TC = NWc * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cw = warp % NWc, rg = warp / NWc, rows_per = TR / RS;
+    const int i0 = rg * rows_per, i1 = i0 + rows_per;
     const int LDT = TC + 8;
     int *sT = smem;                                           // (TR+4) x LDT distances
     int4 *sR = reinterpret_cast<int4 *>(smem + (TR + 4) * LDT);   // TR row records
@@ -415,7 +419,7 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int *smem, int 
         const int a = (p < d.Wp) ? d.seq[p] : d.W;
         sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + (i & 7));
     }
-    const int q = q0 + warp * 32 + lane;
+    const int q = q0 + cw * 32 + lane;
     const int av = (q < d.Wp) ? d.seq[q] : d.W;
     const int4 *vr = reinterpret_cast<const int4 *>(d.erec + av);
     const int4 v0 = TGA_LDG(vr + 0), v1 = TGA_LDG(vr + 1), v2 = TGA_LDG(vr + 2);
@@ -435,14 +439,15 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int *smem, int 
 
     const int wL = d.wL, wT = d.wT;
     const unsigned W = (unsigned)d.W, W2 = W * W;
-    const int *col = sT + warp * 32 + lane + 4;
-    int tm10 = col[0];
-    int t0m1 = col[LDT - 1], t00 = col[LDT], t01 = col[LDT + 1];
-    int t10 = col[2 * LDT], t11 = col[2 * LDT + 1], t12 = col[2 * LDT + 2];
-    int t21 = col[3 * LDT + 1];
+    const int *col = sT + cw * 32 + lane + 4;
+    const int *c0 = col + i0 * LDT;                           // window at row i0
+    int tm10 = c0[0];
+    int t0m1 = c0[LDT - 1], t00 = c0[LDT], t01 = c0[LDT + 1];
+    int t10 = c0[2 * LDT], t11 = c0[2 * LDT + 1], t12 = c0[2 * LDT + 2];
+    int t21 = c0[3 * LDT + 1];
 
 #pragma unroll 1
-    for (int i = 0; i < TR; ++i) {
+    for (int i = i0; i < i1; ++i) {
         const int p = p0 + i;
         const int4 u0 = sR[i * 8 + 0], u1 = sR[i * 8 + 1], u2 = sR[i * 8 + 2];
         const int Uroute = u0.x, Ud = u0.y, Urem1 = u0.z, UK1 = u0.w;
@@ -582,8 +587,10 @@ struct RouteView {
 };
 
 template <bool TW>
+// kinds selects the sweeps this call runs: bit k-1 forward relocate/or-opt
+// of a run of k, bit 3 swap, bit 4 2-opt, bit 4+k backward run of k.
 __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, int baseDist, int baseTw,
-                             unsigned W, unsigned W2, int &best, unsigned &bidx) {
+                             unsigned W, unsigned W2, int &best, unsigned &bidx, unsigned kinds = 0xffu) {
     const int L = V.L;
     if (i >= 1) {
         // ---------------- moves that take the customer at element i forward
@@ -592,7 +599,7 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
         // relocate / or-opt of the run i..i+k-1 to after element j, j >= i+k
         for (int k = 1; k <= 3; ++k) {
             const int op = k == 1 ? 0 : k + 2;
-            if (!(mask & (1u << op)) || i + k - 1 > L) continue;
+            if (!(kinds & (1u << (k - 1))) || !(mask & (1u << op)) || i + k - 1 > L) continue;
             Seg run = V.seg(i, V.c(i, i + 1));
             for (int t = 1; t < k; ++t) run = seg_cat(run, V.seg(i + t, V.c(i + t, i + t + 1)));
             int tau = ptau, tw = ptwf, dist = pdist, last = i - 1;
@@ -618,7 +625,7 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
             }
         }
         // swap element i <-> element j, j > i
-        if (mask & 2u) {
+        if ((kinds & 8u) && (mask & 2u)) {
             Seg M{};
             for (int j = i + 1; j <= L; ++j) {
                 if (j > i + 2) M = seg_cat(M, V.seg(j - 1, V.c(j - 1, j)));
@@ -657,7 +664,7 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
             }
         }
         // 2-opt: reverse elements i..j, j > i
-        if (mask & 4u) {
+        if ((kinds & 16u) && (mask & 4u)) {
             Seg Rv = V.seg(i, 0);
             for (int j = i + 1; j <= L; ++j) {
                 Rv = seg_cat(V.seg(j, V.c(j, j - 1)), Rv);
@@ -679,7 +686,7 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
     const unsigned aj = (unsigned)V.anchor(j);
     for (int k = 1; k <= 3; ++k) {
         const int op = k == 1 ? 0 : k + 2;
-        if (!(mask & (1u << op)) || j + 2 + k - 1 > L) continue;
+        if (!(kinds & (1u << (4 + k))) || !(mask & (1u << op)) || j + 2 + k - 1 > L) continue;
         Seg M = V.seg(j + 1, V.c(j + 1, j + 2));
         for (int t = j + 2; t + k - 1 <= L; ++t) {
             if (t > j + 2) M = seg_cat(M, V.seg(t - 1, V.c(t - 1, t)));
@@ -753,6 +760,63 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
     for (int i = lane; i <= L; i += 32)
         intra_anchor<TW>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx);
     __syncwarp();
+}
+
+// Intra-route candidates of route r with a whole block: all warps stage the
+// route into S (kIntraSmemPerWarp ints), then warp w runs the sweep kinds
+// {w, w+nw, ...} of every anchor, so the serial sweeps of one anchor are
+// spread over the warps.
+template <bool TW>
+__device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsigned &bidx) {
+    const RouteRec R = d.rrec[r];
+    const int L = R.len;
+    if (L < 2) return;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    RouteView V;
+    V.d = &d; V.r = r; V.L = L; V.E = L + 2; V.st = R.start;
+    const int E = V.E;
+    const bool vecS = kIntraVec * E <= kIntraSmemPerWarp;
+    V.inS = vecS && kIntraVec * E + E * E <= kIntraSmemPerWarp;
+    int *base = vecS ? S : d.scr_intra + (R.start + r);
+    const int stride = vecS ? E : d.Wp + d.m;
+    int *node = base, *e = base + stride, *l = base + 2 * stride, *s = base + 3 * stride;
+    int *tau = base + 4 * stride, *twf = base + 5 * stride, *distf = base + 6 * stride;
+    int *Lg = base + 7 * stride, *twg = base + 8 * stride, *distg = base + 9 * stride;
+    V.node = node; V.e = e; V.l = l; V.s = s; V.tau = tau; V.twf = twf; V.distf = distf;
+    V.Lg = Lg; V.twg = twg; V.distg = distg;
+    for (int k = tid; k < E; k += nthr) {
+        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[V.st + k] : -1);
+        const int x = (k >= 1 && k <= L) ? a : 0;
+        node[k] = x;
+        if (TW) { e[k] = __ldg(d.early + x); l[k] = __ldg(d.late + x); s[k] = __ldg(d.service + x); }
+        else { e[k] = 0; l[k] = 0; s[k] = 0; }
+        if (a >= 0) {
+            const BRec b = d.brec[a];
+            tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
+            Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
+        } else {
+            tau[k] = 0; twf[k] = 0; distf[k] = 0; Lg[k] = 0; twg[k] = 0; distg[k] = 0;
+        }
+    }
+    __syncthreads();
+    if (V.inS) {
+        int *D = S + kIntraVec * E;
+        for (int t = tid; t < E * E; t += nthr) {
+            const int a = t / E, b = t - a * E;
+            D[t] = d.pcol[(size_t)node[a] * d.ldp + kColOff + V.st + b];
+        }
+        V.D = D;
+    } else {
+        V.D = nullptr;
+    }
+    __syncthreads();
+    unsigned kinds = 0;
+    for (int k = warp; k < 8; k += nw) kinds |= 1u << k;
+    const unsigned W = (unsigned)d.W, W2 = W * W;
+    const int wT = TW ? d.wT : 0;
+    for (int i = lane; i <= L; i += 32)
+        intra_anchor<TW>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, kinds);
 }
 
 // Intra-route candidates of a CVRP whose moved element is the customer at

@@ -209,9 +209,9 @@ int launch_batch(const BatchJob *jobs_dev, int njobs, BatchState *state_dev, lon
 void launch_check_instance(const Dev &d, cudaStream_t s);
 void launch_build(const Dev &d, cudaStream_t s);
 void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
-                 cudaStream_t s);
+                 cudaStream_t s, int rs = 1);
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
-                  cudaStream_t s);
+                  cudaStream_t s, int rs = 1);
 void launch_intra(const Dev &d, cudaStream_t s);
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond,
                   cudaStream_t s);

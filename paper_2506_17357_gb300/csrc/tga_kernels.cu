@@ -55,26 +55,25 @@ __global__ void k_pcol_init(Dev d) {
 }
 
 template <bool TW, bool OR>
-__global__ void __launch_bounds__(256) k_eval_inter(Dev d, const int2 *__restrict__ tiles, int TR) {
+__global__ void __launch_bounds__(256) k_eval_inter(Dev d, const int2 *__restrict__ tiles, int TR, int RS) {
     if (*(volatile int *)&d.ctl->done) return;
     extern __shared__ __align__(16) int smem[];
     const int2 tl = tiles[blockIdx.x];
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    inter_tile<TW, OR>(d, tl.x * TR, tl.y * (int)(blockDim.x), TR, smem, best, bidx);
+    inter_tile<TW, OR>(d, tl.x * TR, tl.y * (int)(blockDim.x / RS), TR, RS, smem, best, bidx);
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
 }
 
+// VRPTW intra-route moves: one block of kIntraWarps warps per route.
 template <bool TW>
 __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d) {
     if (*(volatile int *)&d.ctl->done) return;
-    __shared__ int smem[kIntraWarps * kIntraSmemPerWarp];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * kIntraWarps + warp;
+    __shared__ int smem[kIntraSmemPerWarp];
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    if (r < d.m) intra_route<TW>(d, r, lane, smem + warp * kIntraSmemPerWarp, best, bidx);
+    intra_route_block<TW>(d, blockIdx.x, smem, best, bidx);
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
 }
@@ -167,23 +166,23 @@ void launch_build(const Dev &d, cudaStream_t s) {
     k_pcol_init<<<(int)blocks, 256, 0, s>>>(d);
 }
 
-void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s) {
+void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs) {
     if (ntiles <= 0) return;
     const size_t sm = inter_smem_bytes(rows, warps);
     const bool orr = (d.op_mask & 48u) != 0;
+    const int nt = warps * 32 * rs;
     if (d.has_tw) {
-        if (orr) k_eval_inter<true, true><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
-        else k_eval_inter<true, false><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
+        if (orr) k_eval_inter<true, true><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs);
+        else k_eval_inter<true, false><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs);
     } else {
-        if (orr) k_eval_inter<false, true><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
-        else k_eval_inter<false, false><<<ntiles, warps * 32, sm, s>>>(d, tiles, rows);
+        if (orr) k_eval_inter<false, true><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs);
+        else k_eval_inter<false, false><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs);
     }
 }
 
 void launch_intra(const Dev &d, cudaStream_t s) {
     if (d.has_tw) {
-        const int nb = (d.m + kIntraWarps - 1) / kIntraWarps;
-        k_eval_intra<true><<<nb, kIntraWarps * 32, 0, s>>>(d);
+        k_eval_intra<true><<<d.m, kIntraWarps * 32, 0, s>>>(d);
     } else {
         // CVRP: one warp per position (moved customer), 8 warps per block
         const int nb = (d.Wp - 1 + 7) / 8;
@@ -191,8 +190,8 @@ void launch_intra(const Dev &d, cudaStream_t s) {
     }
 }
 
-void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s) {
-    launch_inter(d, tiles, ntiles, rows, warps, s);
+void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs) {
+    launch_inter(d, tiles, ntiles, rows, warps, s, rs);
     launch_intra(d, s);
 }
 

@@ -84,6 +84,9 @@ EXPORTS = [
     ("tga_eval_best_move_noalloc", ctypes.c_int, [ctypes.POINTER(tga_instance), ctypes.POINTER(tga_solution),
                                                   ctypes.c_uint32, _P, _P]),
     ("tga_profile_inter", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
+    ("tga_set_tile_shape", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    ("tga_get_tile_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
     ("tga_debug_read", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t)]),
     ("tga_destroy", ctypes.c_int, [_P]),
@@ -208,6 +211,17 @@ def tga_profile_inter(ctx: int, reps: int = 10) -> float:
     return ms.value
 
 
+def tga_set_tile_shape(ctx: int, rows: int, col_warps: int, row_split: int):
+    _check(_lib().tga_set_tile_shape(_P(ctx), rows, col_warps, row_split), "tga_set_tile_shape")
+
+
+def tga_get_tile_shape(ctx: int):
+    r, w, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().tga_get_tile_shape(_P(ctx), ctypes.byref(r), ctypes.byref(w), ctypes.byref(s)),
+           "tga_get_tile_shape")
+    return r.value, w.value, s.value
+
+
 def tga_debug_read(ctx: int, what: int) -> np.ndarray:
     """Copy an internal array (see include/tga.h) as raw int32 values."""
     size = ctypes.c_size_t()
@@ -318,9 +332,12 @@ class LocalSearch:
     def stats(self) -> dict:
         return tga_get_stats(self.ctx)
 
-    def set_tile(self, rows=0, warps=0):
-        tga_set_tile(self.ctx, rows, warps)
-        return tga_get_tile(self.ctx)
+    def set_tile(self, rows=0, warps=0, row_split=None):
+        if row_split is None:
+            tga_set_tile(self.ctx, rows, warps)
+        else:
+            tga_set_tile_shape(self.ctx, rows, warps, row_split)
+        return tga_get_tile_shape(self.ctx)
 
     def solution(self):
         self.stream.synchronize()

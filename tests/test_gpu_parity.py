@@ -132,7 +132,8 @@ def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None):
         ls.close()
 
 
-@pytest.mark.parametrize("tile", [None, (16, 2), (32, 4), (64, 8), (0, 0)])
+@pytest.mark.parametrize("tile", [None, (16, 2), (32, 4), (64, 8), (0, 0), (8, 2, 1), (16, 2, 2),
+                                  (32, 2, 4), (64, 4, 2)])
 def test_config1_full_trajectory(tile):
     inst, sol = I.config1(1)
     st, log, fin = _descend_gpu(inst, sol, I.MASK_CONFIG1, tile=tile)
