@@ -79,7 +79,7 @@ def algorithmic_ops(n, lens, mask, has_tw):
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("tga_kernels.cu", "tga_internal.cuh"):
+    for f in ("tga_kernels.cu", "tga_device.cuh", "tga_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2506_17357_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -127,7 +127,8 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)                                     # first sample lands before the region
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -174,9 +175,14 @@ def only_descent(args):
     desc, make, mask = WORKLOADS[args.workload]
     inst, sol = make(args.seed)
     ls = T.LocalSearch(inst, sol, mask).build()
-    st = ls.descend()
+    if args.tile:
+        tile = ls.set_tile(*[int(x) for x in args.tile.split(",")])
+    else:
+        tile = ls.set_tile(0, 0)                                   # autotune, as the timed bench does
+    st = ls.descend(max_steps=args.descent_steps) if args.descent_steps else ls.descend()
     torch.cuda.synchronize()
-    print(json.dumps({"workload": args.workload, "steps": st["steps"], "evaluations": st["evaluations"],
+    print(json.dumps({"workload": args.workload, "tile": list(tile), "steps": st["steps"],
+                      "evaluations": st["evaluations"],
                       "final_cost": st["final_cost"], "status": st["status"]}))
     ls.close()
 
@@ -196,7 +202,10 @@ def bench_gpu(args):
     inst, sol = make(seed)
     stream = torch.cuda.Stream(dev)
     ls = T.LocalSearch(inst, sol, mask, device=dev, stream=stream).build()
-    tile = ls.set_tile(0, 0)                                   # autotune on the initial state
+    if args.tile:                                              # pinned shape (profiler runs)
+        tile = ls.set_tile(*[int(x) for x in args.tile.split(",")])
+    else:
+        tile = ls.set_tile(0, 0)                               # autotune on the initial state
     torch.cuda.synchronize()
     tour0 = ls.tour.clone()
     rs0 = ls.route_start.clone()
@@ -512,13 +521,17 @@ def bench_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tga", choices=["tga", "reference"])
     ap.add_argument("--workload", default="vrptw1000", choices=sorted(WORKLOADS) + ["batch256", "serve"])
     ap.add_argument("--serve-jobs", type=int, default=120)
     ap.add_argument("--only-descent", action="store_true",
                     help="run one descent of the workload without timing (for profiler launch lists)")
+    ap.add_argument("--descent-steps", type=int, default=0,
+                    help="with --only-descent: stop after this many moves (0: run to the local optimum)")
+    ap.add_argument("--tile", default="",
+                    help="inter tile shape rows,warps,row_split (default: autotune on the initial state)")
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

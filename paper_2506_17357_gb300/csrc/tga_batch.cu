@@ -21,12 +21,6 @@ namespace tga {
 
 namespace {
 
-__device__ __forceinline__ long long now_ns() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 // Build one job with the whole block (positions, validation, attributes of
 // every route, the position-ordered distance copy), then arm its step limit.
 __device__ void build_job(const Dev &d, long long max_steps) {
@@ -95,6 +89,26 @@ __device__ void run_chunk(const BatchJob &J, int c, int *smem, int &best, unsign
     }
 }
 
+// A job is finished: write its solution back (when moves may have been
+// applied) and count it (whole block).
+__device__ void finish_job(const Dev &d, BatchState *B, bool write_solution) {
+    if (write_solution) sync_solution_range(d, threadIdx.x, blockDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        d.ctl->finished = 1;
+        __threadfence();
+        atomicAdd(&B->jobs_done, 1);
+    }
+}
+
+// Open the job's next evaluation (one thread).
+__device__ void release_eval(Control *C) {
+    C->done_chunks = 0;
+    __threadfence();
+    atomicExch(&C->next_chunk, 0);
+}
+
 }  // namespace
 
 __global__ void k_batch_init(const BatchJob *jobs, int njobs, BatchState *B) {
@@ -125,6 +139,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
     extern __shared__ __align__(16) int smem[];
     __shared__ __align__(16) BatchJob sJ;
     __shared__ int s_j, s_c, s_ph, s_last, s_stop;
+    __shared__ StepPlan sPlan;
     const int tid = threadIdx.x;
     const bool eval_only = mode != 0;
 
@@ -205,16 +220,19 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
         Control *C = J.d.ctl;
         if (ph == 1) {
             // column-permutation chunk of the move just applied
-            band_rows(J.d, c * kBandRowsPerChunk, 1, smem, (c + 1) * kBandRowsPerChunk);
+            load_plan(C, &sPlan);
+            __syncthreads();
+            band_plan_rows(J.d, sPlan, smem, c * kBandRowsPerChunk, (c + 1) * kBandRowsPerChunk, 0, 1);
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
-                if (atomicAdd(&C->band_done, 1) == J.nband - 1) {
-                    __threadfence();
-                    C->done_chunks = 0;
-                    __threadfence();
-                    atomicExch(&C->next_chunk, 0);          // release the next evaluation
-                }
+                s_last = atomicAdd(&C->band_done, 1) == J.nband - 1;
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                if (*(volatile int *)&C->done || C->steps >= C->step_limit) finish_job(J.d, B, true);
+                else if (tid == 0) release_eval(C);
             }
             __syncthreads();
             continue;
@@ -234,27 +252,27 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
             __threadfence();
             const Dev &d = J.d;
             if (!eval_only) {
-                apply_block(d, nullptr, 0, 0);
+                if (tid == 0) {
+                    decode_plan(d, nullptr, sPlan);
+                    C->plan = sPlan;
+                }
                 __syncthreads();
+                apply_plan_block(d, sPlan, smem, false, 0, 0);
             } else if (tid == 0) {
                 if (d.log && C->evals < d.log_cap) d.log[C->evals] = C->best_key;
                 C->evals += 1;
                 C->cand_total += C->cand_per_eval;
+                sPlan.act = 0;
             }
-            if (tid == 0) {
-                if (eval_only || C->done || C->steps >= C->step_limit) {
-                    C->finished = 1;
-                    __threadfence();
-                    atomicAdd(&B->jobs_done, 1);
-                } else if (C->chg_count == 0) {
-                    C->done_chunks = 0;
-                    __threadfence();
-                    atomicExch(&C->next_chunk, 0);
-                } else {
+            __syncthreads();
+            if (sPlan.act) {
+                if (tid == 0) {                        // release the permutation chunks
                     C->band_done = 0;
                     __threadfence();
-                    atomicExch(&C->band_next, 0);          // release the permutation chunks
+                    atomicExch(&C->band_next, 0);
                 }
+            } else {
+                finish_job(d, B, !eval_only);
             }
             __syncthreads();
         }
@@ -264,7 +282,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
 size_t batch_smem_bytes(int max_tr, int max_wp) {
     size_t a = inter_smem_bytes(max_tr, kBatchThreads / 32);
     const size_t b = (size_t)(kBatchThreads / 32) * kIntraSmemPerWarp * sizeof(int);
-    const size_t c = (size_t)max_wp * sizeof(int);
+    const size_t c = (size_t)band_smem_ints(max_wp, kBatchThreads / 32) * sizeof(int);
     if (b > a) a = b;
     if (c > a) a = c;
     return a;

@@ -100,7 +100,6 @@ void default_tiles(tga_ctx *c) {
 int step_once(tga_ctx *c, unsigned long long cond, int use_cond, cudaStream_t s) {
     launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, s, c->tile_rs);
     launch_apply(c->d, nullptr, cond, use_cond, s);
-    launch_band(c->d, s);
     return check_launch();
 }
 
@@ -129,7 +128,6 @@ int build_graph(tga_ctx *c) {
             cudaEventRecord(c->ev_join, c->cap2);
             cudaStreamWaitEvent(c->cap, c->ev_join, 0);
             launch_apply(c->d, nullptr, h, 1, c->cap);
-            launch_band(c->d, c->cap);
             cudaGraph_t outg = body;
             e = cudaStreamEndCapture(c->cap, &outg);
         }
@@ -171,12 +169,14 @@ int descend_launch(tga_ctx *c, int64_t max_steps) {
     }
     if (!c->tiles && c->d.Wp > 2) default_tiles(c);
     launch_begin(c->d, max_steps, c->stream);
+    if (max_steps == 0) return check_launch();       // the graph body runs at least once
     // TGA_GRAPH=0 launches the same per-step kernels from the host (for
     // profilers that do not trace kernels inside conditional graph bodies)
     const char *env = getenv("TGA_GRAPH");
     const bool use_graph = !(env && env[0] == '0');
     if (use_graph && build_graph(c) == TGA_OK) {
         if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return TGA_ERR_CUDA;
+        launch_sync_solution(c->d, c->stream);
         return check_launch();
     }
     // host-driven fallback: chunks of steps, stop when the device says done
@@ -193,7 +193,8 @@ int descend_launch(tga_ctx *c, int64_t max_steps) {
         if (rc) return rc;
         if (C.done) break;
     }
-    return TGA_OK;
+    launch_sync_solution(c->d, c->stream);
+    return check_launch();
 }
 
 int default_batch_tr(int Wp) { return Wp < 600 ? 16 : (Wp < 2000 ? 32 : 64); }
@@ -398,7 +399,7 @@ int tga_apply_move(tga_ctx *c, const tga_move *move_dev) {
     if (!c || !move_dev) return TGA_ERR_INVALID;
     if (!c->built) return TGA_ERR_STATE;
     launch_apply(c->d, move_dev, 0, 0, c->stream);
-    launch_band(c->d, c->stream);
+    launch_sync_solution(c->d, c->stream);
     return check_launch();
 }
 

@@ -351,6 +351,7 @@ __device__ void finish_block(const Dev &d) {
         C->maxL = maxL; C->maxLoad = maxLoad;
         C->steps = 0; C->evals = 0; C->cand_total = 0;
         C->done = 0; C->local_opt = 0; C->chg_count = 0;
+        C->plan_ready = 0; C->plan_done = 0;
         C->best_key = kNoKey;
         C->step_limit = 0x7fffffffffffffffLL;
         C->cand_per_eval = candidate_count(d.n, d.m, d.op_mask, l2, l1, lm2);
@@ -892,14 +893,14 @@ __device__ void intra_cvrp_position(const Dev &d, int p, int lane, int &best, un
 }
 
 // ---------------------------------------------------------------------------
-// apply (one block)
-
-struct MovePlan {
-    int op, a, b, delta;
-    int A, B, i, j, k;        // routes, 1-based indices (0 = depot), run length
-    int LA, LB, pA, pB;       // old lengths and depot positions
-    int nLA, nLB;             // new lengths
-};
+// apply (tensor update of Section 5.3.5)
+//
+// One launch per step.  CTA 0 decodes the best key into a StepPlan,
+// publishes it in Control, then rewrites the positions, the route offsets
+// and the attributes of the <= 2 touched routes.  Every other CTA waits for
+// the plan and permutes the changed columns of its rows of the
+// position-ordered distance copy, which CTA 0 never touches.  The batched
+// kernel runs the same two parts one after the other.
 
 // Old position of the anchor that sits at index t (1-based) of the new
 // route X (X is plan.A or plan.B).
@@ -942,220 +943,394 @@ __device__ __forceinline__ int new_src(const MovePlan &P, bool isA, int t) {
     return t <= P.j ? P.pB + t : P.pA + P.i + (t - P.j);
 }
 
-// Apply the best move (from *ext, or the context's packed best key) with the
-// whole block; at least 2 warps.
-__device__ void apply_block(const Dev &d, const tga_move *ext, cudaGraphConditionalHandle cond, int use_cond) {
-    Control *C = d.ctl;
-    __shared__ MovePlan P;
-    __shared__ int s_act, s_cnt;
-    __shared__ int s_lo, s_hi, s_delta_len, s_n1, s_n2, s_b1, s_b2;
-    __shared__ long long s_oldcost;
-    __shared__ int s_oldLA, s_oldLB, s_maxL, s_maxLoad;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        int act = 0;
-        if (!C->done || ext) {
-            unsigned long long key;
-            if (ext) {
-                key = ext->valid ? pack_key(ext->delta, ext->move_index) : kNoKey;
-            } else {
-                key = C->best_key;
-                if (d.log && C->evals < d.log_cap) d.log[C->evals] = key;
-                C->evals += 1;
-                C->cand_total += C->cand_per_eval;
-            }
-            C->best_key = kNoKey;
-            if (key == kNoKey || key_delta(key) >= 0) {
-                C->done = 1;
-                C->local_opt = 1;
-            } else {
-                const unsigned idx = (unsigned)(key & 0xffffffffu);
-                const unsigned W = (unsigned)d.W, W2 = W * W;
-                MovePlan pl;
-                pl.op = (int)(idx / W2);
-                pl.a = (int)((idx % W2) / W);
-                pl.b = (int)(idx % W);
-                pl.delta = key_delta(key);
-                bool ok = pl.op < 6 && ((d.op_mask >> pl.op) & 1u) && pl.a >= 1 && pl.b >= 1;
-                if (ok) {
-                    const BRec ba = d.brec[pl.a], bb = d.brec[pl.b];
-                    pl.A = ba.route; pl.B = bb.route; pl.i = ba.idx; pl.j = bb.idx;
-                    ok = pl.A >= 0 && pl.B >= 0;
-                    if (ok) {
-                        pl.LA = d.rrec[pl.A].len; pl.LB = d.rrec[pl.B].len;
-                        pl.pA = d.rrec[pl.A].start; pl.pB = d.rrec[pl.B].start;
-                    }
-                }
-                if (ok) {
-                    const int op = pl.op;
-                    pl.k = 1;
-                    if (op == 0 || op == 4 || op == 5) {
-                        pl.k = op == 0 ? 1 : op - 2;
-                        ok = pl.a <= d.n && pl.i + pl.k - 1 <= pl.LA &&
-                             !(pl.A == pl.B && pl.j >= pl.i - 1 && pl.j <= pl.i + pl.k - 1);
-                        pl.nLA = pl.A == pl.B ? pl.LA : pl.LA - pl.k;
-                        pl.nLB = pl.A == pl.B ? pl.LB : pl.LB + pl.k;
-                    } else if (op == 1) {
-                        ok = pl.a < pl.b && pl.b <= d.n;
-                        pl.nLA = pl.LA; pl.nLB = pl.LB;
-                        if (ok && pl.A == pl.B && pl.i > pl.j) { int t = pl.i; pl.i = pl.j; pl.j = t; }
-                    } else if (op == 2) {
-                        ok = pl.a <= d.n && pl.b <= d.n && pl.A == pl.B && pl.i < pl.j;
-                        pl.nLA = pl.LA; pl.nLB = pl.LB;
-                    } else {
-                        ok = pl.A < pl.B;
-                        pl.nLA = pl.i + pl.LB - pl.j;
-                        pl.nLB = pl.j + pl.LA - pl.i;
-                    }
-                }
-                if (!ok) {
-                    set_status(C, TGA_ERR_INVALID);
-                    C->done = 1;
-                } else {
-                    P = pl;
-                    act = 1;
-                    C->last_op = pl.op; C->last_a = pl.a; C->last_b = pl.b; C->last_delta = pl.delta;
-                    s_oldcost = (long long)d.rrec[pl.A].cost + (pl.A != pl.B ? d.rrec[pl.B].cost : 0);
-                    s_oldLA = pl.LA; s_oldLB = pl.LB;
-                    if (pl.A == pl.B) {
-                        s_lo = pl.A; s_hi = pl.A; s_delta_len = 0;
-                        s_b1 = pl.pA + 1; s_n1 = pl.LA; s_b2 = 0; s_n2 = 0;
-                    } else {
-                        const bool aLo = pl.A < pl.B;
-                        const int lo = aLo ? pl.A : pl.B, hi = aLo ? pl.B : pl.A;
-                        const int Llo = aLo ? pl.LA : pl.LB, nLlo = aLo ? pl.nLA : pl.nLB;
-                        const int plo = aLo ? pl.pA : pl.pB, phi = aLo ? pl.pB : pl.pA;
-                        const int Lhi = aLo ? pl.LB : pl.LA;
-                        s_lo = lo; s_hi = hi;
-                        s_delta_len = nLlo - Llo;
-                        if (s_delta_len != 0) {
-                            s_b1 = plo + 1; s_n1 = phi + Lhi - plo; s_b2 = 0; s_n2 = 0;
-                        } else {
-                            s_b1 = plo + 1; s_n1 = Llo; s_b2 = phi + 1; s_n2 = Lhi;
-                        }
-                    }
-                }
-            }
-        }
-        s_act = act;
-        s_cnt = 0;
-        s_maxL = 0;
-        s_maxLoad = 0;
+// u-th changed position of the plan.
+__device__ __forceinline__ int plan_pos(const StepPlan &S, int u) {
+    return u < S.n1 ? S.b1 + u : S.b2 + (u - S.n1);
+}
+
+// Old position of the anchor that lands at the changed position q.
+__device__ __forceinline__ int plan_src(const StepPlan &S, int q) {
+    const MovePlan &pl = S.mp;
+    if (pl.A == pl.B) return new_src(pl, true, q - pl.pA);
+    const bool aLo = pl.A < pl.B;
+    const int plo = aLo ? pl.pA : pl.pB, phi = aLo ? pl.pB : pl.pA;
+    const int nLlo = aLo ? pl.nLA : pl.nLB;
+    if (q <= plo + nLlo) return new_src(pl, aLo, q - plo);
+    if (q <= phi + S.dl) return q - S.dl;
+    return new_src(pl, !aLo, q - (phi + S.dl));
+}
+
+// The changed positions split into the rewritten customers of the touched
+// routes (positions qA0 + k for k < nA, then qB0 + k for k < nB) and the
+// block of old positions [s0, s1] that moves by dl (empty when s0 > s1).
+struct PlanParts {
+    int qA0, nA, qB0, nB, s0, s1, dl;
+};
+
+__device__ __forceinline__ PlanParts plan_parts(const StepPlan &S) {
+    const MovePlan &pl = S.mp;
+    PlanParts R;
+    R.dl = S.dl;
+    R.s0 = 1;
+    R.s1 = 0;
+    if (pl.A == pl.B) {
+        R.qA0 = pl.pA + 1; R.nA = pl.LA; R.qB0 = 0; R.nB = 0;
+        return R;
     }
-    __syncthreads();
-    if (s_act) {
-        const MovePlan pl = P;
-        const int dl = s_delta_len, lo = s_lo, hi = s_hi;
-        const int tot = s_n1 + s_n2;
-        const bool aLo = pl.A <= pl.B;
-        const int plo = aLo ? pl.pA : pl.pB, phi = aLo ? pl.pB : pl.pA;
-        const int nLlo = aLo ? pl.nLA : pl.nLB;
-        // pass 1: where does every changed position take its anchor from
-        for (int u = tid; u < tot; u += blockDim.x) {
-            const int q = u < s_n1 ? s_b1 + u : s_b2 + (u - s_n1);
-            int src, route;
-            if (pl.A == pl.B) {
-                src = new_src(pl, true, q - pl.pA);
-                route = pl.A;
-            } else if (q <= plo + nLlo) {
-                src = new_src(pl, lo == pl.A, q - plo);
-                route = lo;
-            } else if (q < phi + dl) {
-                src = q - dl;
-                route = d.brec[d.seq[src]].route;
-            } else if (q == phi + dl) {
-                src = phi;
-                route = hi;
-            } else {
-                src = new_src(pl, hi == pl.A, q - (phi + dl));
-                route = hi;
-            }
-            d.scr_src[u] = src;
-            d.scr_anchor[u] = d.seq[src];
-            d.scr_route[u] = route;
+    const bool aLo = pl.A < pl.B;
+    const int plo = aLo ? pl.pA : pl.pB, phi = aLo ? pl.pB : pl.pA;
+    const int Llo = aLo ? pl.LA : pl.LB, nLlo = aLo ? pl.nLA : pl.nLB, nLhi = aLo ? pl.nLB : pl.nLA;
+    R.qA0 = plo + 1; R.nA = nLlo;
+    R.qB0 = phi + S.dl + 1; R.nB = nLhi;
+    if (S.dl != 0) { R.s0 = plo + Llo + 1; R.s1 = phi; }
+    return R;
+}
+
+// Decode the step's move -- the evaluation's packed best key, or *ext --
+// into S (one thread).  S.act = 0 when there is nothing to apply: a local
+// optimum, a context that is done, or an invalid move (status set).
+__device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
+    Control *C = d.ctl;
+    S.act = 0;
+    if (C->done && !ext) return;
+    unsigned long long key;
+    if (ext) {
+        key = ext->valid ? pack_key(ext->delta, ext->move_index) : kNoKey;
+    } else {
+        key = C->best_key;
+        if (d.log && C->evals < d.log_cap) d.log[C->evals] = key;
+        C->evals += 1;
+        C->cand_total += C->cand_per_eval;
+    }
+    C->best_key = kNoKey;
+    if (key == kNoKey || key_delta(key) >= 0) {
+        C->done = 1;
+        C->local_opt = 1;
+        return;
+    }
+    const unsigned idx = (unsigned)(key & 0xffffffffu);
+    const unsigned W = (unsigned)d.W, W2 = W * W;
+    MovePlan pl;
+    pl.op = (int)(idx / W2);
+    pl.a = (int)((idx % W2) / W);
+    pl.b = (int)(idx % W);
+    pl.delta = key_delta(key);
+    bool ok = pl.op < 6 && ((d.op_mask >> pl.op) & 1u) && pl.a >= 1 && pl.b >= 1;
+    if (ok) {
+        const BRec ba = d.brec[pl.a], bb = d.brec[pl.b];
+        pl.A = ba.route; pl.B = bb.route; pl.i = ba.idx; pl.j = bb.idx;
+        ok = pl.A >= 0 && pl.B >= 0;
+        if (ok) {
+            pl.LA = d.rrec[pl.A].len; pl.LB = d.rrec[pl.B].len;
+            pl.pA = d.rrec[pl.A].start; pl.pB = d.rrec[pl.B].start;
         }
+    }
+    if (ok) {
+        const int op = pl.op;
+        pl.k = 1;
+        if (op == 0 || op == 4 || op == 5) {
+            pl.k = op == 0 ? 1 : op - 2;
+            ok = pl.a <= d.n && pl.i + pl.k - 1 <= pl.LA &&
+                 !(pl.A == pl.B && pl.j >= pl.i - 1 && pl.j <= pl.i + pl.k - 1);
+            pl.nLA = pl.A == pl.B ? pl.LA : pl.LA - pl.k;
+            pl.nLB = pl.A == pl.B ? pl.LB : pl.LB + pl.k;
+        } else if (op == 1) {
+            ok = pl.a < pl.b && pl.b <= d.n;
+            pl.nLA = pl.LA; pl.nLB = pl.LB;
+            if (ok && pl.A == pl.B && pl.i > pl.j) { int t = pl.i; pl.i = pl.j; pl.j = t; }
+        } else if (op == 2) {
+            ok = pl.a <= d.n && pl.b <= d.n && pl.A == pl.B && pl.i < pl.j;
+            pl.nLA = pl.LA; pl.nLB = pl.LB;
+        } else {
+            ok = pl.A < pl.B;
+            pl.nLA = pl.i + pl.LB - pl.j;
+            pl.nLB = pl.j + pl.LA - pl.i;
+        }
+    }
+    if (!ok) {
+        set_status(C, TGA_ERR_INVALID);
+        C->done = 1;
+        return;
+    }
+    S.mp = pl;
+    S.act = 1;
+    C->last_op = pl.op; C->last_a = pl.a; C->last_b = pl.b; C->last_delta = pl.delta;
+    S.oldcost = (long long)d.rrec[pl.A].cost + (pl.A != pl.B ? d.rrec[pl.B].cost : 0);
+    S.oldLA = pl.LA; S.oldLB = pl.LB;
+    if (pl.A == pl.B) {
+        S.lo = pl.A; S.hi = pl.A; S.dl = 0;
+        S.b1 = pl.pA + 1; S.n1 = pl.LA; S.b2 = 0; S.n2 = 0;
+    } else {
+        const bool aLo = pl.A < pl.B;
+        const int lo = aLo ? pl.A : pl.B, hi = aLo ? pl.B : pl.A;
+        const int Llo = aLo ? pl.LA : pl.LB, nLlo = aLo ? pl.nLA : pl.nLB;
+        const int plo = aLo ? pl.pA : pl.pB, phi = aLo ? pl.pB : pl.pA;
+        const int Lhi = aLo ? pl.LB : pl.LA;
+        S.lo = lo; S.hi = hi;
+        S.dl = nLlo - Llo;
+        if (S.dl != 0) {
+            S.b1 = plo + 1; S.n1 = phi + Lhi - plo; S.b2 = 0; S.n2 = 0;
+        } else {
+            S.b1 = plo + 1; S.n1 = Llo; S.b2 = phi + 1; S.n2 = Lhi;
+        }
+    }
+}
+
+// Rewrite positions, route offsets and the attributes of the touched routes
+// for plan S with the whole block (at least 3 warps); sbuf holds n1 + n2
+// ints.  Thread 0 then updates cost and counters and ends the step (done
+// flag, graph condition).  ext: the move came from the caller, whose delta
+// is not checked against the rebuilt routes.
+__device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, bool ext,
+                                 cudaGraphConditionalHandle cond, int use_cond) {
+    Control *C = d.ctl;
+    __shared__ int s_maxL, s_maxLoad;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    if (tid == 0) { s_maxL = 0; s_maxLoad = 0; }
+    if (S.act) {
+        const MovePlan pl = S.mp;
+        const int tot = S.n1 + S.n2;
+        // the anchor every changed position takes, all read before any write
+        for (int u = tid; u < tot; u += nthr) sbuf[u] = d.seq[plan_src(S, plan_pos(S, u))];
         __syncthreads();
-        // pass 2: write positions, tour, change list
-        for (int u = tid; u < tot; u += blockDim.x) {
-            const int q = u < s_n1 ? s_b1 + u : s_b2 + (u - s_n1);
-            const int a = d.scr_anchor[u], route = d.scr_route[u], src = d.scr_src[u];
+        for (int u = tid; u < tot; u += nthr) {
+            const int q = plan_pos(S, u), a = sbuf[u];
             d.seq[q] = a;
             d.pos_of[a] = q;
-            if (a <= d.n) d.tour[q - route - 1] = a;
-            if (src != q) {
-                const int slot = atomicAdd(&s_cnt, 1);
-                d.chg[slot] = make_int2(q, src);
-            }
         }
-        if (dl != 0) {
-            for (int r = lo + 1 + tid; r <= hi; r += blockDim.x) {
-                d.route_start[r] += dl;
-                d.rrec[r].start += dl;
-            }
-        }
-        __syncthreads();
+        if (S.dl != 0)
+            for (int r = S.lo + 1 + tid; r <= S.hi; r += nthr) d.rrec[r].start += S.dl;
         if (tid == 0) {
             d.rrec[pl.A].len = pl.nLA;
             if (pl.B != pl.A) d.rrec[pl.B].len = pl.nLB;
         }
         __syncthreads();
         const int warp = tid >> 5, lane = tid & 31;
-        if (warp == 0) rebuild_route(d, pl.A, lane);
-        if (warp == 1 && pl.B != pl.A) rebuild_route(d, pl.B, lane);
-        __syncthreads();
-        // exact longest route and heaviest load for the integer headroom check
-        int mL = 0, mLoad = 0;
-        for (int r = tid; r < d.m; r += blockDim.x) {
-            mL = max(mL, d.rrec[r].len);
-            mLoad = max(mLoad, d.rrec[r].load);
+        if (warp == 0) {
+            rebuild_route(d, pl.A, lane);
+        } else if (warp == 1) {
+            if (pl.B != pl.A) rebuild_route(d, pl.B, lane);
+        } else {
+            // meanwhile: longest route and heaviest load of the other routes
+            int mL = 0, mLoad = 0;
+            for (int r = tid - 64; r < d.m; r += nthr - 64) {
+                if (r == pl.A || r == pl.B) continue;
+                mL = max(mL, d.rrec[r].len);
+                mLoad = max(mLoad, d.rrec[r].load);
+            }
+            mL = __reduce_max_sync(0xffffffffu, mL);
+            mLoad = __reduce_max_sync(0xffffffffu, mLoad);
+            if (lane == 0) { atomicMax(&s_maxL, mL); atomicMax(&s_maxLoad, mLoad); }
         }
-        mL = __reduce_max_sync(0xffffffffu, mL);
-        mLoad = __reduce_max_sync(0xffffffffu, mLoad);
-        if (lane == 0) { atomicMax(&s_maxL, mL); atomicMax(&s_maxLoad, mLoad); }
         __syncthreads();
     }
     if (tid == 0) {
-        if (s_act) {
-            const MovePlan pl = P;
-            const long long newcost = (long long)d.rrec[pl.A].cost + (pl.A != pl.B ? d.rrec[pl.B].cost : 0);
-            const long long dact = newcost - s_oldcost;
+        if (S.act) {
+            const MovePlan &pl = S.mp;
+            const RouteRec RA = d.rrec[pl.A];
+            RouteRec RB = RA;
+            if (pl.B != pl.A) RB = d.rrec[pl.B];
+            const long long newcost = (long long)RA.cost + (pl.A != pl.B ? RB.cost : 0);
+            const long long dact = newcost - S.oldcost;
             if (!ext && dact != pl.delta) set_status(C, 7);
             C->cost += dact;
             C->steps += 1;
             if (pl.A != pl.B) {
                 auto sq = [](long long x) { return x * x; };
-                C->sumL2 += sq(pl.nLA) + sq(pl.nLB) - sq(s_oldLA) - sq(s_oldLB);
-                C->sumLm1 += max(pl.nLA - 1, 0) + max(pl.nLB - 1, 0) - max(s_oldLA - 1, 0) - max(s_oldLB - 1, 0);
-                C->sumLm2 += max(pl.nLA - 2, 0) + max(pl.nLB - 2, 0) - max(s_oldLA - 2, 0) - max(s_oldLB - 2, 0);
+                const int oA = S.oldLA, oB = S.oldLB;
+                C->sumL2 += sq(pl.nLA) + sq(pl.nLB) - sq(oA) - sq(oB);
+                C->sumLm1 += max(pl.nLA - 1, 0) + max(pl.nLB - 1, 0) - max(oA - 1, 0) - max(oB - 1, 0);
+                C->sumLm2 += max(pl.nLA - 2, 0) + max(pl.nLB - 2, 0) - max(oA - 2, 0) - max(oB - 2, 0);
                 C->cand_per_eval = candidate_count(d.n, d.m, d.op_mask, C->sumL2, C->sumLm1, C->sumLm2);
             }
-            C->maxL = s_maxL;
-            C->maxLoad = s_maxLoad;
+            C->maxL = max(s_maxL, max(RA.len, RB.len));
+            C->maxLoad = max(s_maxLoad, max(RA.load, RB.load));
             if (!range_ok(d, C)) { set_status(C, TGA_ERR_RANGE); C->done = 1; }
-            C->chg_count = s_cnt;
-        } else {
-            C->chg_count = 0;
         }
-        if (C->status != 0) C->done = 1;
+        // a stop (error or step limit) also ends host-launched descents
+        if (C->status != 0 || C->steps >= C->step_limit) C->done = 1;
         if (use_cond)
             cudaGraphSetConditional(cond, (!C->done && C->steps < C->step_limit) ? 1u : 0u);
     }
 }
 
-// Permute the changed columns of rows x0, x0+xs, ... (below x_end) of the
-// position-ordered copy (whole block; sv holds Wp ints).
-__device__ void band_rows(const Dev &d, int x0, int xs, int *sv, int x_end) {
-    const int K = *(volatile int *)&d.ctl->chg_count;
-    if (K == 0) return;
-    const int2 *chg = d.chg;
-    if (x_end > d.n + 1) x_end = d.n + 1;
-    for (int x = x0; x < x_end; x += xs) {
-        int *row = d.pcol + (size_t)x * d.ldp + kColOff;
-        for (int e = threadIdx.x; e < K; e += blockDim.x) sv[e] = row[chg[e].y];
+// row[t + dl] = row[t] for t in [s0, s1], one warp: passes of 8 x 32 values
+// whose loads all complete before their stores, walking against the shift
+// so that no pass reads a value an earlier pass wrote.
+__device__ __forceinline__ void shift_row_warp(int *row, int s0, int s1, int dl, int lane) {
+    constexpr int P = 8;
+    if (dl > 0) {
+        for (int hi = s1; hi >= s0; hi -= 32 * P) {
+            int v[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int t = hi - 32 * k - lane;
+                v[k] = t >= s0 ? row[t] : 0;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int t = hi - 32 * k - lane;
+                if (t >= s0) row[t + dl] = v[k];
+            }
+            __syncwarp();
+        }
+    } else {
+        for (int lo = s0; lo <= s1; lo += 32 * P) {
+            int v[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int t = lo + 32 * k + lane;
+                v[k] = t <= s1 ? row[t] : 0;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int t = lo + 32 * k + lane;
+                if (t <= s1) row[t + dl] = v[k];
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// The same with the whole block (passes of 4 x blockDim values).
+__device__ void shift_row_block(int *row, int s0, int s1, int dl) {
+    constexpr int P = 4;
+    const int nthr = blockDim.x, tid = threadIdx.x, step = P * nthr;
+    if (dl > 0) {
+        for (int hi = s1; hi >= s0; hi -= step) {
+            int v[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int t = hi - nthr * k - tid;
+                v[k] = t >= s0 ? row[t] : 0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int t = hi - nthr * k - tid;
+                if (t >= s0) row[t + dl] = v[k];
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int lo = s0; lo <= s1; lo += step) {
+            int v[P];
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int t = lo + nthr * k + tid;
+                v[k] = t <= s1 ? row[t] : 0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                const int t = lo + nthr * k + tid;
+                if (t <= s1) row[t + dl] = v[k];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+constexpr int kBandListMax = 4096;   // rewritten route elements listed in shared memory
+constexpr int kBandWarpBuf = 256;    // per-warp values of one row (route elements)
+
+// Shared memory (ints) the column permutation needs with nw warps.
+__host__ __device__ inline int band_smem_ints(int Wp, int nw) {
+    const int a = 2 * kBandListMax + nw * kBandWarpBuf;
+    return Wp > a ? Wp : a;
+}
+
+// Permute the columns of the position-ordered copy for plan S, rows
+// [row_lo, row_hi) shared among ncta CTAs of which this is number cta: a
+// warp per row while the rewritten route elements fit the per-warp buffer,
+// else a block per row.  Per row, the sources of the rewritten elements are
+// read first, then the block between the two routes shifts, then the
+// elements are written.  smem: band_smem_ints(Wp, warps) ints.
+__device__ void band_plan_rows(const Dev &d, const StepPlan &S, int *smem, int row_lo, int row_hi, int cta,
+                               int ncta) {
+    if (!S.act) return;
+    if (row_hi > d.n + 1) row_hi = d.n + 1;
+    const PlanParts P = plan_parts(S);
+    const int nL = P.nA + P.nB;
+    const bool shift = P.s0 <= P.s1;
+    const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    auto qk = [&](int k) { return k < P.nA ? P.qA0 + k : P.qB0 + (k - P.nA); };
+    __shared__ int s_cnt;
+    if (nL <= kBandListMax) {
+        int *sq = smem, *ss = smem + kBandListMax;
+        if (tid == 0) s_cnt = 0;
         __syncthreads();
-        for (int e = threadIdx.x; e < K; e += blockDim.x) row[chg[e].x] = sv[e];
+        for (int k = tid; k < nL; k += nthr) {
+            const int q = qk(k), src = plan_src(S, q);
+            if (src != q) {
+                const int e = atomicAdd(&s_cnt, 1);
+                sq[e] = q;
+                ss[e] = src;
+            }
+        }
+        __syncthreads();
+        const int K = s_cnt;
+        if (K <= kBandWarpBuf) {
+            int *wb = smem + 2 * kBandListMax + warp * kBandWarpBuf;
+            for (int x = row_lo + cta * nw + warp; x < row_hi; x += ncta * nw) {
+                int *row = d.pcol + (size_t)x * d.ldp + kColOff;
+                for (int e = lane; e < K; e += 32) wb[e] = row[ss[e]];
+                __syncwarp();
+                if (shift) shift_row_warp(row, P.s0, P.s1, P.dl, lane);
+                for (int e = lane; e < K; e += 32) row[sq[e]] = wb[e];
+                __syncwarp();
+            }
+            return;
+        }
+        __syncthreads();                 // the lists are overwritten below
+    }
+    // long routes: a block per row, sources recomputed per element
+    int *vb = smem;
+    for (int x = row_lo + cta; x < row_hi; x += ncta) {
+        int *row = d.pcol + (size_t)x * d.ldp + kColOff;
+        for (int k = tid; k < nL; k += nthr) vb[k] = row[plan_src(S, qk(k))];
+        __syncthreads();
+        if (shift) shift_row_block(row, P.s0, P.s1, P.dl);
+        for (int k = tid; k < nL; k += nthr) row[qk(k)] = vb[k];
         __syncthreads();
     }
+}
+
+// Write the caller's giant tour and route offsets from the device state
+// (positions, per-anchor routes, route start positions); grid-stride.
+__device__ void sync_solution_range(const Dev &d, long long t0, long long stride) {
+    for (long long q = t0; q < d.Wp - 1; q += stride) {
+        const int a = d.seq[q];
+        if (a >= 1 && a <= d.n) d.tour[q - d.brec[a].route - 1] = a;
+    }
+    for (long long r = t0; r <= d.m; r += stride)
+        d.route_start[r] = r < d.m ? d.rrec[r].start - (int)r : d.n;
+}
+
+__device__ __forceinline__ long long now_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait (one thread) until *flag != 0, at most limit_ns; false on timeout.
+__device__ bool wait_flag(const int *flag, long long limit_ns) {
+    const long long t0 = now_ns();
+    while (*(const volatile int *)flag == 0) {
+        if (now_ns() - t0 > limit_ns) return false;
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+// Copy the published plan into shared memory (whole block; L1 bypassed).
+__device__ void load_plan(const Control *C, StepPlan *dst) {
+    const volatile int *src = reinterpret_cast<const volatile int *>(&C->plan);
+    int *o = reinterpret_cast<int *>(dst);
+    for (int t = threadIdx.x; t < (int)(sizeof(StepPlan) / sizeof(int)); t += blockDim.x) o[t] = src[t];
 }
 
 

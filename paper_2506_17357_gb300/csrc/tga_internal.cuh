@@ -57,6 +57,29 @@ struct RouteRec {
     int start, len, load, dist, tw, cost, pad0, pad1;
 };
 
+// A decoded move.  Routes, indices, lengths and depot positions are the
+// ones before the move.
+struct MovePlan {
+    int op, a, b, delta;
+    int A, B, i, j, k;        // routes, 1-based indices (0 = depot), run length
+    int LA, LB, pA, pB;       // old lengths and depot positions
+    int nLA, nLB;             // new lengths
+};
+
+// What one step rewrites, decoded once by the applying CTA and published to
+// the CTAs that permute the columns of the position-ordered distance copy.
+// Positions [b1, b1+n1) and [b2, b2+n2) change; with two routes lo < hi
+// whose combined length is kept, every position strictly between them
+// (including the depot of hi) moves by dl = new length - old length of lo.
+struct StepPlan {
+    MovePlan mp;
+    int act;                  // 1: a move is applied this step
+    int lo, hi, dl;
+    int b1, n1, b2, n2;
+    int oldLA, oldLB;
+    long long oldcost;        // cost of routes A and B before the move
+};
+
 struct Control {
     unsigned long long best_key;              // min packed key of the running evaluation
     long long steps, evals, cand_total, cost, initial_cost, step_limit, cand_per_eval;
@@ -69,6 +92,10 @@ struct Control {
     // the column-permutation phase of the applied move)
     int next_chunk, done_chunks, finished, band_next;
     int band_done, pad2[3];
+    // single-instance apply: the plan of the running step, its publication
+    // flag, and the count of CTAs that finished the step's apply launch
+    StepPlan plan;
+    int plan_ready, plan_done, pad3[2];
 };
 
 // Everything a kernel needs, passed by value.
@@ -189,7 +216,7 @@ __host__ __device__ inline long long candidate_count(long long n, long long m, u
 
 // Batched descent (tga_batch.cu): one persistent launch over many contexts.
 constexpr int kBatchThreads = 256;            // 8 warps: 256-column inter tiles
-constexpr int kBandRowsPerChunk = 256;
+constexpr int kBandRowsPerChunk = 32;
 constexpr long long kChunkPairs = 1LL << 17;  // target candidate pairs per evaluation chunk
 struct BatchJob {
     Dev d;
@@ -215,7 +242,7 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
 void launch_intra(const Dev &d, cudaStream_t s);
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond,
                   cudaStream_t s);
-void launch_band(const Dev &d, cudaStream_t s);
+void launch_sync_solution(const Dev &d, cudaStream_t s);
 void launch_finalize(const Dev &d, tga_move *out, cudaStream_t s);
 void launch_begin(const Dev &d, long long max_steps, cudaStream_t s);
 size_t inter_smem_bytes(int rows, int warps);

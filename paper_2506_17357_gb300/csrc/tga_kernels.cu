@@ -16,11 +16,13 @@
 //   k_eval_intra   the same for intra-route candidates (route-based
 //                  extraction of Section 5.3.1), one thread per anchor
 //                  sweeping the other end of the move along its route.
-//   k_apply        Tensor update (Section 5.3.5) on the device: decode the
-//                  best key, rewrite the giant tour and positions, rebuild the
-//                  attributes of the <= 2 touched routes.
-//   k_band         keep the position-ordered distance copy in step with the
-//                  new positions (a permutation of the changed columns).
+//   k_apply        Tensor update (Section 5.3.5) on the device: CTA 0 decodes
+//                  the best key, rewrites the positions and rebuilds the
+//                  attributes of the <= 2 touched routes; the other CTAs keep
+//                  the position-ordered distance copy in step (a permutation
+//                  of the changed columns of every row).
+//   k_sync_solution  write the caller's giant tour and route offsets back
+//                  once a descent (or an applied move) is done.
 #include <cstdio>
 
 #define TGA_LDG(p) __ldg(p)
@@ -88,14 +90,48 @@ __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d) {
     block_min_to(key, &d.ctl->best_key);
 }
 
+// Apply: CTA 0 decodes and applies the move; CTAs 1.. permute the columns
+// of the position-ordered copy once the plan is published.  The last CTA to
+// finish re-arms the plan flag for the next step.
 __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaGraphConditionalHandle cond,
                                                int use_cond) {
-    apply_block(d, ext, cond, use_cond);
+    extern __shared__ __align__(16) int smem[];
+    __shared__ StepPlan sP;
+    __shared__ int s_ok;
+    Control *C = d.ctl;
+    const int tid = threadIdx.x;
+    if (blockIdx.x == 0) {
+        if (tid == 0) {
+            decode_plan(d, ext, sP);
+            C->plan = sP;
+            __threadfence();
+            atomicExch(&C->plan_ready, 1);
+        }
+        __syncthreads();
+        apply_plan_block(d, sP, smem, ext != nullptr, cond, use_cond);
+    } else {
+        if (tid == 0) {
+            s_ok = wait_flag(&C->plan_ready, 1000LL * 1000 * 1000);
+            if (!s_ok) set_status(C, TGA_ERR_TIMEOUT);
+        }
+        __syncthreads();
+        if (s_ok) load_plan(C, &sP);
+        else if (tid == 0) sP.act = 0;
+        __syncthreads();
+        band_plan_rows(d, sP, smem, 0, d.n + 1, blockIdx.x - 1, gridDim.x - 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&C->plan_done, 1) == (int)gridDim.x - 1) {
+            C->plan_done = 0;
+            C->plan_ready = 0;
+        }
+    }
 }
 
-__global__ void __launch_bounds__(256) k_band(Dev d) {
-    extern __shared__ int sv[];
-    band_rows(d, blockIdx.x, gridDim.x, sv, d.n + 1);
+__global__ void k_sync_solution(Dev d) {
+    sync_solution_range(d, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 __global__ void k_finalize(Dev d, tga_move *out) {
@@ -142,7 +178,7 @@ int setup_kernel_attrs(int max_band) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     (void)max_band;
     return e == cudaSuccess ? 0 : 1;
 }
@@ -195,13 +231,20 @@ void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warp
     launch_intra(d, s);
 }
 
-void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond, cudaStream_t s) {
-    k_apply<<<1, 512, 0, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond);
+int apply_grid(const Dev &d) {
+    const int rows = (d.n + 1 + 15) / 16;           // a warp per row, 16 warps per CTA
+    return 1 + (rows < 3 * 152 ? rows : 3 * 152);
 }
 
-void launch_band(const Dev &d, cudaStream_t s) {
-    int blocks = d.n + 1 < 152 * 8 ? d.n + 1 : 152 * 8;
-    k_band<<<blocks, 256, (size_t)d.Wp * sizeof(int), s>>>(d);
+void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond, cudaStream_t s) {
+    const size_t sm = (size_t)band_smem_ints(d.Wp, 16) * sizeof(int);
+    k_apply<<<apply_grid(d), 512, sm, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond);
+}
+
+void launch_sync_solution(const Dev &d, cudaStream_t s) {
+    int blocks = (d.Wp + 255) / 256;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    k_sync_solution<<<blocks, 256, 0, s>>>(d);
 }
 
 void launch_finalize(const Dev &d, tga_move *out, cudaStream_t s) { k_finalize<<<1, 1, 0, s>>>(d, out); }

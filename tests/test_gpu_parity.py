@@ -145,6 +145,30 @@ def test_config1_full_trajectory(tile):
     assert st["candidates"] == ocands
 
 
+@pytest.mark.parametrize("limit", [0, 1, 5, 63, 64, 65, None])
+def test_host_launched_descent_equals_graph(monkeypatch, limit):
+    """The host-launched per-step path (what profilers trace) runs the same
+    kernels as the device-driven graph loop: same move log, same solution,
+    and an exact stop at the step limit."""
+    inst = I.vrptw(300, 4)
+    sol = I.random_split_solution(inst, I.solution_seed(4))
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("TGA_GRAPH", mode)
+        ls = LocalSearch(inst, sol, I.MASK_ALL, log_capacity=1 << 16).build()
+        try:
+            st = ls.descend() if limit is None else ls.descend(max_steps=limit)
+            out[mode] = (st, ls.move_log(), ls.solution())
+        finally:
+            ls.close()
+    (sg, lg, (tg, rg)), (sh, lh, (th, rh)) = out["1"], out["0"]
+    if limit is not None:
+        assert sg["steps"] <= limit and (sg["local_optimum"] == 1 or sg["steps"] == limit)
+    for k in ("steps", "evaluations", "candidates", "final_cost", "local_optimum", "status"):
+        assert sg[k] == sh[k], k
+    assert np.array_equal(lg, lh) and np.array_equal(tg, th) and np.array_equal(rg, rh)
+
+
 @pytest.mark.parametrize("seed", [2, 3])
 def test_small_vrptw_full_trajectory(seed):
     inst = I.vrptw(200, seed)
