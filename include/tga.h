@@ -140,12 +140,44 @@ int tga_eval_best_move(tga_ctx *ctx, tga_move *out_dev);
  * local optimum.  A move that is not a candidate sets TGA_ERR_INVALID. */
 int tga_apply_move(tga_ctx *ctx, const tga_move *move_dev);
 
-/* Best-improvement descent: repeat evaluate + apply until no move has
- * delta < 0 or max_steps moves were applied in this call.  The loop runs on
- * the device as a CUDA graph with a conditional while node (no host round
- * trip per step).  Builds the attributes first if they were never built.
- * Synchronises the stream at the end and fills *out_host (may be NULL). */
+/* Best-improvement descent (appendix algorithm "Feasible and infeasible
+ * search"): repeat evaluate + apply until no move has delta < 0 or max_steps
+ * moves were applied in this call.  The loop runs on the device with no host
+ * round trip per step, along the path chosen by tga_set_descent_mode.
+ * Builds the attributes first if they were never built.  Synchronises the
+ * stream at the end and fills *out_host (may be NULL).  Every path gives the
+ * same moves, solution and counters bit for bit. */
 int tga_descend(tga_ctx *ctx, int64_t max_steps, tga_stats *out_host);
+
+/* Descent paths.
+ *  TGA_DESCENT_PERSISTENT  one cooperative launch for the whole descent: all
+ *      CTAs stay resident, evaluate their share of the step, meet at a grid
+ *      barrier, CTA 0 applies the move while the others permute distance
+ *      columns, and meet again (bounded waits: TGA_ERR_TIMEOUT after 5 s).
+ *      The launch claims every SM: do not run it concurrently with other
+ *      work that needs the GPU's SMs to make progress.
+ *  TGA_DESCENT_GRAPH  a CUDA graph whose conditional while node runs the
+ *      per-step kernels (evaluation branches, then apply) until the device
+ *      clears the condition; other streams' kernels interleave freely.
+ *  TGA_DESCENT_HOST  the same per-step kernels launched from the host in
+ *      chunks of 64 steps (for profilers that do not trace kernels inside
+ *      conditional graph bodies; also selected by the environment variable
+ *      TGA_GRAPH=0).
+ *  TGA_DESCENT_AUTO (default)  persistent for instances with
+ *      n + m + 1 < 4096 positions, else the graph; falls back to the graph
+ *      when the cooperative launch is refused. */
+enum {
+    TGA_DESCENT_AUTO = 0,
+    TGA_DESCENT_PERSISTENT = 1,
+    TGA_DESCENT_GRAPH = 2,
+    TGA_DESCENT_HOST = 3
+};
+int tga_set_descent_mode(tga_ctx *ctx, int32_t mode);
+
+/* The path the context's last descent took (TGA_DESCENT_*; AUTO if it never
+ * descended) and, for the persistent path, its grid size (grid_out may be
+ * NULL; 0 for the other paths). */
+int tga_get_descent_mode(tga_ctx *ctx, int32_t *last_used, int32_t *grid_out);
 
 /* Descend every context to a local optimum (at most max_steps moves each) in
  * ONE persistent launch on ctxs[0]'s stream (all contexts on one device).

@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "libtga.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The batched kernel reads job state that other SMs rewrite during the same
 # launch: its global loads must bypass the (non-coherent) L1.
-PER_FILE_FLAGS = {"tga_batch.cu": ["-Xptxas", "-dlcm=cg"]}
+PER_FILE_FLAGS = {"tga_batch.cu": ["-Xptxas", "-dlcm=cg"], "tga_persist.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def _nvcc() -> str:

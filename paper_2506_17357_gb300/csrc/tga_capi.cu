@@ -31,6 +31,10 @@ struct tga_ctx {
     bool graph_ready = false;
     bool graph_failed = false;
     int batch_tr = 0;                  // tile rows in batched descents (0: by size)
+    // descent path: requested mode and the one the last descent took
+    int mode = TGA_DESCENT_AUTO;
+    int last_mode = TGA_DESCENT_AUTO;
+    int persist_grid = 0;
 };
 
 namespace {
@@ -98,8 +102,9 @@ void default_tiles(tga_ctx *c) {
 }
 
 int step_once(tga_ctx *c, unsigned long long cond, int use_cond, cudaStream_t s) {
-    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, s, c->tile_rs);
-    launch_apply(c->d, nullptr, cond, use_cond, s);
+    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, s, c->tile_rs,
+                eval_blocks(c->d, c->ntiles));
+    launch_apply(c->d, nullptr, cond, use_cond, s, 1);
     return check_launch();
 }
 
@@ -123,11 +128,12 @@ int build_graph(tga_ctx *c) {
             // branches; both fold into the same packed best key
             cudaEventRecord(c->ev_fork, c->cap);
             cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
-            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap, c->tile_rs);
-            launch_intra(c->d, c->cap2);
+            const int tail = eval_blocks(c->d, c->ntiles);
+            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap, c->tile_rs, tail);
+            launch_intra(c->d, c->cap2, tail);
             cudaEventRecord(c->ev_join, c->cap2);
             cudaStreamWaitEvent(c->cap, c->ev_join, 0);
-            launch_apply(c->d, nullptr, h, 1, c->cap);
+            launch_apply(c->d, nullptr, h, 1, c->cap, 1);
             cudaGraph_t outg = body;
             e = cudaStreamEndCapture(c->cap, &outg);
         }
@@ -162,6 +168,19 @@ void fill_stats(const Control &C, tga_stats *s) {
     s->evaluations = C.evals;
 }
 
+// Instances below this many positions descend in one persistent launch when
+// the mode is automatic; larger ones run the per-step graph.
+constexpr int kPersistAutoMaxWp = 4096;
+
+// Persistent descent with the context's tile shape; the row split is raised
+// until a block has at least 4 warps (the tile list does not depend on it).
+int try_persist(tga_ctx *c) {
+    int rs = c->tile_rs;
+    while (c->tile_warps * 32 * rs < 128 && rs < 4 && c->tile_warps * rs * 2 <= 8 && c->tile_rows % (rs * 2) == 0)
+        rs *= 2;
+    return launch_persist(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, rs, c->stream, &c->persist_grid);
+}
+
 int descend_launch(tga_ctx *c, int64_t max_steps) {
     if (!c->built) {
         int rc = tga_build_attrs(c);
@@ -170,15 +189,29 @@ int descend_launch(tga_ctx *c, int64_t max_steps) {
     if (!c->tiles && c->d.Wp > 2) default_tiles(c);
     launch_begin(c->d, max_steps, c->stream);
     if (max_steps == 0) return check_launch();       // the graph body runs at least once
-    // TGA_GRAPH=0 launches the same per-step kernels from the host (for
-    // profilers that do not trace kernels inside conditional graph bodies)
+    int mode = c->mode;
+    // TGA_GRAPH=0 launches the per-step kernels from the host (for profilers
+    // that do not trace kernels inside conditional graph bodies)
     const char *env = getenv("TGA_GRAPH");
-    const bool use_graph = !(env && env[0] == '0');
-    if (use_graph && build_graph(c) == TGA_OK) {
+    if (env && env[0] == '0') mode = TGA_DESCENT_HOST;
+    const bool automatic = mode == TGA_DESCENT_AUTO;
+    if (automatic) mode = c->d.Wp < kPersistAutoMaxWp ? TGA_DESCENT_PERSISTENT : TGA_DESCENT_GRAPH;
+    if (mode == TGA_DESCENT_PERSISTENT) {
+        const int rc = try_persist(c);
+        if (rc == TGA_OK) {
+            c->last_mode = TGA_DESCENT_PERSISTENT;
+            return check_launch();
+        }
+        if (!automatic) return rc;
+        mode = TGA_DESCENT_GRAPH;
+    }
+    if (mode == TGA_DESCENT_GRAPH && build_graph(c) == TGA_OK) {
         if (cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) return TGA_ERR_CUDA;
         launch_sync_solution(c->d, c->stream);
+        c->last_mode = TGA_DESCENT_GRAPH;
         return check_launch();
     }
+    c->last_mode = TGA_DESCENT_HOST;
     // host-driven fallback: chunks of steps, stop when the device says done
     Control C;
     int64_t done_steps = 0;
@@ -558,6 +591,19 @@ int tga_set_tile(tga_ctx *c, int32_t rows, int32_t warps) {
     int rc = set_tiles(c, br, bw, brs);
     if (rc) return rc;
     return check_launch();
+}
+
+int tga_set_descent_mode(tga_ctx *c, int32_t mode) {
+    if (!c || mode < TGA_DESCENT_AUTO || mode > TGA_DESCENT_HOST) return TGA_ERR_INVALID;
+    c->mode = mode;
+    return TGA_OK;
+}
+
+int tga_get_descent_mode(tga_ctx *c, int32_t *last_used, int32_t *grid_out) {
+    if (!c || !last_used) return TGA_ERR_INVALID;
+    *last_used = c->last_mode;
+    if (grid_out) *grid_out = c->last_mode == TGA_DESCENT_PERSISTENT ? c->persist_grid : 0;
+    return TGA_OK;
 }
 
 int tga_set_tile_shape(tga_ctx *c, int32_t rows, int32_t col_warps, int32_t row_split) {

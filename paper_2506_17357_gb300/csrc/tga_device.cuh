@@ -213,14 +213,21 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
     }
 }
 
-__device__ bool range_ok(const Dev &d, const Control *C) {
-    if (C->maxc >= (1 << 24) || C->maxl >= (1 << 24) || C->maxe >= (1 << 24) ||
-        C->maxs >= (1 << 24) || C->maxd >= (1 << 24))
+// Integer headroom: a route built from two current routes plus three moved
+// customers must cost below 2^27 (bound from the longest route, heaviest load
+// and the largest distance, window and service).
+__device__ bool range_ok_vals(const Dev &d, int maxL, int maxLoad, int maxc, int maxl, int maxe, int maxs,
+                              int maxd) {
+    if (maxc >= (1 << 24) || maxl >= (1 << 24) || maxe >= (1 << 24) || maxs >= (1 << 24) || maxd >= (1 << 24))
         return false;
-    const long long L2 = 2LL * C->maxL + 4;
-    long long b = L2 * C->maxc + (long long)d.wL * (2LL * C->maxLoad + 3LL * C->maxd);
-    if (d.has_tw) b += (long long)d.wT * L2 * ((long long)C->maxl + C->maxs + C->maxc);
+    const long long L2 = 2LL * maxL + 4;
+    long long b = L2 * maxc + (long long)d.wL * (2LL * maxLoad + 3LL * maxd);
+    if (d.has_tw) b += (long long)d.wT * L2 * ((long long)maxl + maxs + maxc);
     return b < kRouteCostLim;
+}
+
+__device__ bool range_ok(const Dev &d, const Control *C) {
+    return range_ok_vals(d, C->maxL, C->maxLoad, C->maxc, C->maxl, C->maxe, C->maxs, C->maxd);
 }
 
 // ---------------------------------------------------------------------------
@@ -446,6 +453,7 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
     int t0m1 = c0[LDT - 1], t00 = c0[LDT], t01 = c0[LDT + 1];
     int t10 = c0[2 * LDT], t11 = c0[2 * LDT + 1], t12 = c0[2 * LDT + 2];
     int t21 = c0[3 * LDT + 1];
+    int wbest = __reduce_min_sync(0xffffffffu, best);
 
 #pragma unroll 1
     for (int i = i0; i < i1; ++i) {
@@ -527,7 +535,12 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
         int m = min(min(dR1, dR2), min(dS, dX));
         if (OR) m = min(m, min(min(dO2a, dO2b), min(dO3a, dO3b)));
         const bool skip = (Uroute == Vroute) | (p >= q);
-        if (!skip && m <= best) {
+        // Only a pair that can tie or beat the warp's best so far can hold the
+        // final argmin (every lane's best bounds the global minimum from
+        // above), so the packed keys are formed only then; filtering on the
+        // warp minimum rather than the lane's own keeps the whole warp off
+        // this path on almost every row.
+        if (!skip && m <= wbest) {
             const unsigned au = (unsigned)u2.w, avu = (unsigned)av;
             TGA_TRY(dR1, au * W + avu);
             TGA_TRY(dR2, avu * W + au);
@@ -540,6 +553,7 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
                 TGA_TRY(dO3b, 5u * W2 + avu * W + au);
             }
         }
+        wbest = __reduce_min_sync(0xffffffffu, best);
         // slide the stencil window one row down
         tm10 = t00;
         t0m1 = col[(i + 2) * LDT - 1];
@@ -986,6 +1000,147 @@ __device__ __forceinline__ PlanParts plan_parts(const StepPlan &S) {
     return R;
 }
 
+// Index into the plan's list of changed positions of position q (q must be
+// one of them).
+__device__ __forceinline__ int plan_u(const StepPlan &S, int q) {
+    return (q >= S.b1 && q < S.b1 + S.n1) ? q - S.b1 : S.n1 + (q - S.b2);
+}
+
+// Start-depot position of route A (isA) or B after the move.
+__device__ __forceinline__ int plan_new_start(const StepPlan &S, bool isA) {
+    const MovePlan &pl = S.mp;
+    if (pl.A == pl.B) return pl.pA;
+    const bool aLo = pl.A < pl.B;
+    const int plo = aLo ? pl.pA : pl.pB, phi = aLo ? pl.pB : pl.pA;
+    return (isA == aLo) ? plo : phi + S.dl;
+}
+
+__device__ __forceinline__ Seg seg_vals(int e, int l, int s, int load, int out) {
+    Seg x;
+    x.E = e; x.L = l; x.D = s; x.TW = 0; x.dist = 0; x.load = load; x.out = out;
+    return x;
+}
+
+// Rebuild route r after a move with one warp (all lanes call), for routes
+// with L + 2 <= 32 elements whose new customers are in shared memory:
+// customer t (1..L) is sbuf[plan_u(S, st + t)], st = the start-depot
+// position.  Produces exactly what rebuild_route does, but every global
+// read is issued in one round of independent loads -- node data, the edge
+// leaving each element and the bypass edges of the hoisted constants
+// (x- to x+, and x- to the element after runs of 2 and 3) -- followed by
+// the two concatenation scans (Section 4.3) in registers and the stores.
+// Lane 0 writes the route totals (load, dist, warp, cost) to tot[0..3].
+__device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int *sbuf, const StepPlan &S,
+                                   int lane, int *tot) {
+    const int E = L + 2;
+    const bool tw = d.has_tw != 0;
+    const int wTe = tw ? d.wT : 0;
+    const unsigned mask = d.op_mask;
+    const unsigned FULL = 0xffffffffu;
+    const int k = lane;
+    const bool valid = k < E;
+    const int x = (k >= 1 && k <= L) ? sbuf[plan_u(S, st + k)] : 0;   // node (depots are 0)
+    const int xn = __shfl_down_sync(FULL, x, 1), xm = __shfl_up_sync(FULL, x, 1);
+    const int x2 = __shfl_down_sync(FULL, x, 2), x3 = __shfl_down_sync(FULL, x, 3);
+    // ---- one round of loads
+    const int out = (valid && k + 1 < E) ? dmat(d, x, k + 1 <= L ? xn : 0) : 0;
+    const int dem = __ldg(d.demand + x);
+    const int ne = tw ? __ldg(d.early + x) : 0, nl = tw ? __ldg(d.late + x) : 0;
+    const int ns = tw ? __ldg(d.service + x) : 0;
+    const bool cust = k >= 1 && k <= L;
+    const int cmn = cust ? dmat(d, xm, k + 1 <= L ? xn : 0) : 0;
+    const int c2 = (cust && k + 1 <= L) ? dmat(d, xm, k + 2 <= L ? x2 : 0) : 0;
+    const int c3 = (cust && k + 2 <= L) ? dmat(d, xm, k + 3 <= L ? x3 : 0) : 0;
+    // ---- forward scan: prefix through element k
+    const Seg node = seg_vals(ne, nl, ns, dem, out);
+    Seg f = node;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        Seg o = shfl_seg_up(f, off);
+        if (lane >= off) f = seg_cat(o, f);
+    }
+    // ---- backward scan: elements k .. L+1
+    Seg g = node;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        Seg o = shfl_seg_down(g, off);
+        if (lane + off < E) g = seg_cat(g, o);
+    }
+    // route totals: the prefix of the end depot
+    const int Rload = __shfl_sync(FULL, f.load, E - 1);
+    const int Rdist = __shfl_sync(FULL, f.dist, E - 1);
+    const int Rtw = tw ? __shfl_sync(FULL, f.TW, E - 1) : 0;
+    const int Rcost = L == 0 ? 0 : Rdist + d.wL * max(Rload - d.Q, 0) + wTe * Rtw;
+    // own record: prefix through x, suffix after x (= backward scan at k+1)
+    const int tau = tw ? f.E + f.D - f.TW : 0, twf = tw ? f.TW : 0;
+    const int gL = __shfl_down_sync(FULL, g.L, 1), gTW = __shfl_down_sync(FULL, g.TW, 1);
+    const int gdist = __shfl_down_sync(FULL, g.dist, 1), gload = __shfl_down_sync(FULL, g.load, 1);
+    const int Lg = tw ? gL : 0, twg = tw ? gTW : 0;
+    // predecessor's prefix, and the suffixes after the last element of the
+    // runs x..x+1 and x..x+2 (the records of elements k+1 and k+2)
+    const int ptau = __shfl_up_sync(FULL, tau, 1), ptwf = __shfl_up_sync(FULL, twf, 1);
+    const int pdist = __shfl_up_sync(FULL, f.dist, 1);
+    const int w2L = __shfl_down_sync(FULL, Lg, 1), w2tw = __shfl_down_sync(FULL, twg, 1);
+    const int w2dist = __shfl_down_sync(FULL, gdist, 1);
+    const int w3L = __shfl_down_sync(FULL, Lg, 2), w3tw = __shfl_down_sync(FULL, twg, 2);
+    const int w3dist = __shfl_down_sync(FULL, gdist, 2);
+    // the runs x..x+1 and x..x+2
+    const Seg n1 = shfl_seg_down(node, 1), n2 = shfl_seg_down(node, 2);
+    const Seg run2 = seg_cat(node, n1), run3 = seg_cat(run2, n2);
+    if (k <= L) {
+        const int a = k == 0 ? d.n + 1 + r : x;
+        int4 *bp = reinterpret_cast<int4 *>(d.brec + a);
+        bp[0] = make_int4(x, r, k, 0);
+        bp[1] = make_int4(tau, twf, f.dist, f.load);
+        bp[2] = make_int4(Lg, twg, gdist, gload);
+        bp[3] = make_int4(0, 0, 0, 0);
+        const int Fc = f.dist + wTe * twf - Rcost;
+        const int Gc = gdist + wTe * twg;
+        int rem1 = kBig, K2 = kBig, LQd = 0, tauP = 0;
+        int C2 = kBig, ld2 = 0, E2 = 0, L2 = 0, Dm2 = 0;
+        int C3 = kBig, ld3 = 0, E3 = 0, L3 = 0, Dm3 = 0;
+        if (k >= 1) {
+            const int twr = tw ? ptwf + twg + max(ptau + cmn - Lg, 0) : 0;
+            const int c1 = pdist + cmn + gdist + d.wL * max(Rload - dem - d.Q, 0) + wTe * twr;
+            rem1 = c1 - Rcost + ((mask & 1u) ? 0 : kBig);
+            K2 = pdist + gdist + wTe * (ptwf + twg) - Rcost + ((mask & 2u) ? 0 : kBig);
+            LQd = Rload - dem - d.Q;
+            tauP = ptau;
+            if (k + 1 <= L && (mask & 16u)) {
+                const int twk = tw ? ptwf + w2tw + max(ptau + c2 - w2L, 0) : 0;
+                const int ck = pdist + c2 + w2dist + d.wL * max(Rload - run2.load - d.Q, 0) + wTe * twk - Rcost;
+                C2 = ck + run2.dist + wTe * (tw ? run2.TW : 0);
+                ld2 = run2.load;
+                if (tw) { E2 = run2.E; L2 = run2.L; Dm2 = run2.D - run2.TW; }
+            }
+            if (k + 2 <= L && (mask & 32u)) {
+                const int twk = tw ? ptwf + w3tw + max(ptau + c3 - w3L, 0) : 0;
+                const int ck = pdist + c3 + w3dist + d.wL * max(Rload - run3.load - d.Q, 0) + wTe * twk - Rcost;
+                C3 = ck + run3.dist + wTe * (tw ? run3.TW : 0);
+                ld3 = run3.load;
+                if (tw) { E3 = run3.E; L3 = run3.L; Dm3 = run3.D - run3.TW; }
+            }
+        }
+        int4 *ep = reinterpret_cast<int4 *>(d.erec + a);
+        ep[0] = make_int4(r, dem, rem1, Fc + Gc);
+        ep[1] = make_int4(Rload - d.Q, K2, LQd, Fc + ((mask & 8u) ? 0 : kBig));
+        ep[2] = make_int4(Gc, f.load, gload - d.Q, a);
+        ep[3] = make_int4(C2, ld2, C3, ld3);
+        ep[4] = make_int4(ne, nl, ns, tau);
+        ep[5] = make_int4(Lg, tauP, E2, L2);
+        ep[6] = make_int4(Dm2, E3, L3, Dm3);
+        ep[7] = make_int4(x, k, 0, 0);
+    }
+    if (lane == 0) {
+        RouteRec *R = d.rrec + r;
+        R->load = Rload;
+        R->dist = Rdist;
+        R->tw = Rtw;
+        R->cost = Rcost;
+        tot[0] = Rload; tot[1] = Rdist; tot[2] = Rtw; tot[3] = Rcost;
+    }
+}
+
 // Decode the step's move -- the evaluation's packed best key, or *ext --
 // into S (one thread).  S.act = 0 when there is nothing to apply: a local
 // optimum, a context that is done, or an invalid move (status set).
@@ -993,11 +1148,15 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
     Control *C = d.ctl;
     S.act = 0;
     if (C->done && !ext) return;
+    if (!ext && C->status != 0) {              // an error found during the last step ends the descent
+        C->done = 1;
+        return;
+    }
     unsigned long long key;
     if (ext) {
         key = ext->valid ? pack_key(ext->delta, ext->move_index) : kNoKey;
     } else {
-        key = C->best_key;
+        key = *(volatile unsigned long long *)&C->best_key;
         if (d.log && C->evals < d.log_cap) d.log[C->evals] = key;
         C->evals += 1;
         C->cand_total += C->cand_per_eval;
@@ -1078,13 +1237,20 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
 
 // Rewrite positions, route offsets and the attributes of the touched routes
 // for plan S with the whole block (at least 3 warps); sbuf holds n1 + n2
-// ints.  Thread 0 then updates cost and counters and ends the step (done
-// flag, graph condition).  ext: the move came from the caller, whose delta
-// is not checked against the rebuilt routes.
+// ints.  Warps 0 and 1 rebuild routes A and B -- from the new customers in
+// sbuf when a route fits one warp, else with the chunked scans -- while the
+// other warps find the longest route and heaviest load of the rest and one
+// thread prefetches the counters.  Thread 0 then updates cost and counters
+// and ends the step (done flag, graph condition).  ext: the move came from
+// the caller, whose delta is not checked against the rebuilt routes.
 __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, bool ext,
                                  cudaGraphConditionalHandle cond, int use_cond) {
     Control *C = d.ctl;
     __shared__ int s_maxL, s_maxLoad;
+    __shared__ int s_tot[2][4];
+    __shared__ int s_fast[2];
+    __shared__ long long s_cf[6];             // cost, steps, sumL2, sumLm1, sumLm2, step_limit
+    __shared__ int s_ci[6];                   // status, maxc, maxl, maxe, maxs, maxd
     const int tid = threadIdx.x, nthr = blockDim.x;
     if (tid == 0) { s_maxL = 0; s_maxLoad = 0; }
     if (S.act) {
@@ -1106,11 +1272,22 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
         }
         __syncthreads();
         const int warp = tid >> 5, lane = tid & 31;
-        if (warp == 0) {
-            rebuild_route(d, pl.A, lane);
-        } else if (warp == 1) {
-            if (pl.B != pl.A) rebuild_route(d, pl.B, lane);
+        if (warp <= 1) {
+            const bool isA = warp == 0;
+            if (isA || pl.B != pl.A) {
+                const int r = isA ? pl.A : pl.B, L = isA ? pl.nLA : pl.nLB;
+                const bool fast = L + 2 <= 32;
+                if (fast) rebuild_route_warp(d, r, plan_new_start(S, isA), L, sbuf, S, lane, s_tot[warp]);
+                else rebuild_route(d, r, lane);
+                if (lane == 0) s_fast[warp] = fast;
+            }
         } else {
+            if (tid == 64) {
+                s_cf[0] = C->cost; s_cf[1] = C->steps; s_cf[2] = C->sumL2;
+                s_cf[3] = C->sumLm1; s_cf[4] = C->sumLm2; s_cf[5] = C->step_limit;
+                s_ci[0] = C->status; s_ci[1] = C->maxc; s_ci[2] = C->maxl;
+                s_ci[3] = C->maxe; s_ci[4] = C->maxs; s_ci[5] = C->maxd;
+            }
             // meanwhile: longest route and heaviest load of the other routes
             int mL = 0, mLoad = 0;
             for (int r = tid - 64; r < d.m; r += nthr - 64) {
@@ -1127,30 +1304,48 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
     if (tid == 0) {
         if (S.act) {
             const MovePlan &pl = S.mp;
-            const RouteRec RA = d.rrec[pl.A];
-            RouteRec RB = RA;
-            if (pl.B != pl.A) RB = d.rrec[pl.B];
-            const long long newcost = (long long)RA.cost + (pl.A != pl.B ? RB.cost : 0);
+            const bool two = pl.B != pl.A;
+            int costA, loadA, costB = 0, loadB = 0;
+            if (s_fast[0]) { costA = s_tot[0][3]; loadA = s_tot[0][0]; }
+            else { costA = d.rrec[pl.A].cost; loadA = d.rrec[pl.A].load; }
+            if (two) {
+                if (s_fast[1]) { costB = s_tot[1][3]; loadB = s_tot[1][0]; }
+                else { costB = d.rrec[pl.B].cost; loadB = d.rrec[pl.B].load; }
+            }
+            const long long newcost = (long long)costA + costB;
             const long long dact = newcost - S.oldcost;
-            if (!ext && dact != pl.delta) set_status(C, 7);
-            C->cost += dact;
-            C->steps += 1;
-            if (pl.A != pl.B) {
+            int status = s_ci[0];
+            if (!ext && dact != pl.delta) { set_status(C, 7); status = 7; }
+            const long long cost = s_cf[0] + dact, steps = s_cf[1] + 1;
+            C->cost = cost;
+            C->steps = steps;
+            if (two) {
                 auto sq = [](long long x) { return x * x; };
                 const int oA = S.oldLA, oB = S.oldLB;
-                C->sumL2 += sq(pl.nLA) + sq(pl.nLB) - sq(oA) - sq(oB);
-                C->sumLm1 += max(pl.nLA - 1, 0) + max(pl.nLB - 1, 0) - max(oA - 1, 0) - max(oB - 1, 0);
-                C->sumLm2 += max(pl.nLA - 2, 0) + max(pl.nLB - 2, 0) - max(oA - 2, 0) - max(oB - 2, 0);
-                C->cand_per_eval = candidate_count(d.n, d.m, d.op_mask, C->sumL2, C->sumLm1, C->sumLm2);
+                const long long l2 = s_cf[2] + sq(pl.nLA) + sq(pl.nLB) - sq(oA) - sq(oB);
+                const long long l1 = s_cf[3] + max(pl.nLA - 1, 0) + max(pl.nLB - 1, 0) - max(oA - 1, 0) -
+                                     max(oB - 1, 0);
+                const long long lm2 = s_cf[4] + max(pl.nLA - 2, 0) + max(pl.nLB - 2, 0) - max(oA - 2, 0) -
+                                      max(oB - 2, 0);
+                C->sumL2 = l2; C->sumLm1 = l1; C->sumLm2 = lm2;
+                C->cand_per_eval = candidate_count(d.n, d.m, d.op_mask, l2, l1, lm2);
             }
-            C->maxL = max(s_maxL, max(RA.len, RB.len));
-            C->maxLoad = max(s_maxLoad, max(RA.load, RB.load));
-            if (!range_ok(d, C)) { set_status(C, TGA_ERR_RANGE); C->done = 1; }
+            const int maxL = max(s_maxL, max(pl.nLA, two ? pl.nLB : 0));
+            const int maxLoad = max(s_maxLoad, max(loadA, two ? loadB : 0));
+            C->maxL = maxL;
+            C->maxLoad = maxLoad;
+            if (!range_ok_vals(d, maxL, maxLoad, s_ci[1], s_ci[2], s_ci[3], s_ci[4], s_ci[5])) {
+                set_status(C, TGA_ERR_RANGE);
+                status = TGA_ERR_RANGE;
+            }
+            if (status != 0 || steps >= s_cf[5]) C->done = 1;
+            if (use_cond) cudaGraphSetConditional(cond, (status == 0 && steps < s_cf[5]) ? 1u : 0u);
+        } else {
+            // a stop (error or step limit) also ends host-launched descents
+            if (C->status != 0 || C->steps >= C->step_limit) C->done = 1;
+            if (use_cond)
+                cudaGraphSetConditional(cond, (!C->done && C->steps < C->step_limit) ? 1u : 0u);
         }
-        // a stop (error or step limit) also ends host-launched descents
-        if (C->status != 0 || C->steps >= C->step_limit) C->done = 1;
-        if (use_cond)
-            cudaGraphSetConditional(cond, (!C->done && C->steps < C->step_limit) ? 1u : 0u);
     }
 }
 
@@ -1331,6 +1526,22 @@ __device__ void load_plan(const Control *C, StepPlan *dst) {
     const volatile int *src = reinterpret_cast<const volatile int *>(&C->plan);
     int *o = reinterpret_cast<int *>(dst);
     for (int t = threadIdx.x; t < (int)(sizeof(StepPlan) / sizeof(int)); t += blockDim.x) o[t] = src[t];
+}
+
+// Last-block-done tail of a descent step's evaluation (thread 0 of every CTA
+// of the step's evaluation launches, after its key is folded in): the CTA
+// that finishes last decodes the best key into the step's plan, read by the
+// apply launch that follows on the stream.  The count re-arms itself.
+__device__ void eval_tail(const Dev &d, int total) {
+    Control *C = d.ctl;
+    __threadfence();
+    if (atomicAdd(&C->eval_done, 1) != total - 1) return;
+    __threadfence();
+    C->eval_done = 0;
+    StepPlan P;
+    decode_plan(d, nullptr, P);
+    C->plan = P;
+    C->plan_ready = 1;
 }
 
 

@@ -96,6 +96,11 @@ struct Control {
     // flag, and the count of CTAs that finished the step's apply launch
     StepPlan plan;
     int plan_ready, plan_done, pad3[2];
+    // persistent descent: grid-barrier arrivals (only grows within a launch)
+    // and the step whose plan was last published; CTAs of the running
+    // evaluation that have finished (the last one decodes the step's plan)
+    unsigned long long bar_count;
+    int plan_seq, eval_done;
 };
 
 // Everything a kernel needs, passed by value.
@@ -235,16 +240,26 @@ int launch_batch(const BatchJob *jobs_dev, int njobs, BatchState *state_dev, lon
 // Kernel entry points (tga_kernels.cu).
 void launch_check_instance(const Dev &d, cudaStream_t s);
 void launch_build(const Dev &d, cudaStream_t s);
+// tail > 0: the evaluation of a descent step whose inter- and intra-route
+// launches have `tail` CTAs in total (eval_blocks); the last CTA to finish
+// decodes the step's plan for the apply launch that follows.
 void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
-                 cudaStream_t s, int rs = 1);
+                 cudaStream_t s, int rs = 1, int tail = 0);
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
-                  cudaStream_t s, int rs = 1);
-void launch_intra(const Dev &d, cudaStream_t s);
+                  cudaStream_t s, int rs = 1, int tail = 0);
+void launch_intra(const Dev &d, cudaStream_t s, int tail = 0);
+int eval_blocks(const Dev &d, int ntiles);
+// pre = 1: apply the plan decoded by the evaluation's last CTA (descent
+// steps); else decode *ext (or the best key) in the launch itself.
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond,
-                  cudaStream_t s);
+                  cudaStream_t s, int pre = 0);
 void launch_sync_solution(const Dev &d, cudaStream_t s);
 void launch_finalize(const Dev &d, tga_move *out, cudaStream_t s);
 void launch_begin(const Dev &d, long long max_steps, cudaStream_t s);
+// Persistent single-instance descent (tga_persist.cu): one cooperative
+// launch; returns TGA_OK or an error code (nothing launched on error).
+int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, int rs, cudaStream_t s,
+                   int *grid_out);
 size_t inter_smem_bytes(int rows, int warps);
 int setup_kernel_attrs(int max_band);
 

@@ -56,8 +56,10 @@ __global__ void k_pcol_init(Dev d) {
     pcol_init_range(d, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
+// tail > 0: a descent step's evaluation (see eval_tail); every launch of
+// the step's evaluation returns at once on a finished descent.
 template <bool TW, bool OR>
-__global__ void __launch_bounds__(256) k_eval_inter(Dev d, const int2 *__restrict__ tiles, int TR, int RS) {
+__global__ void __launch_bounds__(256) k_eval_inter(Dev d, const int2 *__restrict__ tiles, int TR, int RS, int tail) {
     if (*(volatile int *)&d.ctl->done) return;
     extern __shared__ __align__(16) int smem[];
     const int2 tl = tiles[blockIdx.x];
@@ -66,11 +68,12 @@ __global__ void __launch_bounds__(256) k_eval_inter(Dev d, const int2 *__restric
     inter_tile<TW, OR>(d, tl.x * TR, tl.y * (int)(blockDim.x / RS), TR, RS, smem, best, bidx);
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
+    if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
 // VRPTW intra-route moves: one block of kIntraWarps warps per route.
 template <bool TW>
-__global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d) {
+__global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d, int tail) {
     if (*(volatile int *)&d.ctl->done) return;
     __shared__ int smem[kIntraSmemPerWarp];
     int best = kBestInit;
@@ -78,9 +81,10 @@ __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d) {
     intra_route_block<TW>(d, blockIdx.x, smem, best, bidx);
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
+    if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
-__global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d) {
+__global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d, int tail) {
     if (*(volatile int *)&d.ctl->done) return;
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int best = kBestInit;
@@ -88,19 +92,31 @@ __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d) {
     intra_cvrp_position(d, p, threadIdx.x & 31, best, bidx);
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
+    if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
-// Apply: CTA 0 decodes and applies the move; CTAs 1.. permute the columns
-// of the position-ordered copy once the plan is published.  The last CTA to
-// finish re-arms the plan flag for the next step.
+// Apply.  pre = 1 (descent steps): every CTA loads the plan the evaluation's
+// last CTA decoded (no plan: the descent is over, nothing to do); CTA 0
+// applies it and CTAs 1.. permute the columns of the position-ordered copy.
+// pre = 0: CTA 0 decodes *ext (or the best key) and publishes the plan while
+// the other CTAs wait for it.  The last CTA to finish re-arms the plan flag
+// for the next step.
 __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaGraphConditionalHandle cond,
-                                               int use_cond) {
+                                               int use_cond, int pre) {
     extern __shared__ __align__(16) int smem[];
     __shared__ StepPlan sP;
     __shared__ int s_ok;
     Control *C = d.ctl;
     const int tid = threadIdx.x;
-    if (blockIdx.x == 0) {
+    if (pre) {
+        if (tid == 0) s_ok = *(volatile int *)&C->plan_ready;
+        load_plan(C, &sP);                       // same round trip as the flag
+        __syncthreads();
+        if (!s_ok && tid == 0) sP.act = 0;
+        __syncthreads();
+        if (blockIdx.x == 0) apply_plan_block(d, sP, smem, false, cond, use_cond);
+        else band_plan_rows(d, sP, smem, 0, d.n + 1, blockIdx.x - 1, gridDim.x - 1);
+    } else if (blockIdx.x == 0) {
         if (tid == 0) {
             decode_plan(d, ext, sP);
             C->plan = sP;
@@ -155,6 +171,11 @@ __global__ void k_finalize(Dev d, tga_move *out) {
 
 __global__ void k_begin(Dev d, long long max_steps) {
     Control *C = d.ctl;
+    C->bar_count = 0;
+    C->plan_seq = 0;
+    C->eval_done = 0;
+    C->plan_ready = 0;
+    C->plan_done = 0;
     if (C->status != 0 || !C->built) { C->done = 1; return; }
     C->done = 0;
     C->local_opt = 0;
@@ -202,33 +223,35 @@ void launch_build(const Dev &d, cudaStream_t s) {
     k_pcol_init<<<(int)blocks, 256, 0, s>>>(d);
 }
 
-void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs) {
+void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs,
+                  int tail) {
     if (ntiles <= 0) return;
     const size_t sm = inter_smem_bytes(rows, warps);
     const bool orr = (d.op_mask & 48u) != 0;
     const int nt = warps * 32 * rs;
     if (d.has_tw) {
-        if (orr) k_eval_inter<true, true><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs);
-        else k_eval_inter<true, false><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs);
+        if (orr) k_eval_inter<true, true><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs, tail);
+        else k_eval_inter<true, false><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs, tail);
     } else {
-        if (orr) k_eval_inter<false, true><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs);
-        else k_eval_inter<false, false><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs);
+        if (orr) k_eval_inter<false, true><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs, tail);
+        else k_eval_inter<false, false><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs, tail);
     }
 }
 
-void launch_intra(const Dev &d, cudaStream_t s) {
-    if (d.has_tw) {
-        k_eval_intra<true><<<d.m, kIntraWarps * 32, 0, s>>>(d);
-    } else {
-        // CVRP: one warp per position (moved customer), 8 warps per block
-        const int nb = (d.Wp - 1 + 7) / 8;
-        k_eval_intra_cvrp<<<nb, 256, 0, s>>>(d);
-    }
+// VRPTW: one block per route; CVRP: one warp per moved position, 8 per block.
+int intra_blocks(const Dev &d) { return d.has_tw ? d.m : (d.Wp - 1 + 7) / 8; }
+
+int eval_blocks(const Dev &d, int ntiles) { return (ntiles > 0 ? ntiles : 0) + intra_blocks(d); }
+
+void launch_intra(const Dev &d, cudaStream_t s, int tail) {
+    if (d.has_tw) k_eval_intra<true><<<intra_blocks(d), kIntraWarps * 32, 0, s>>>(d, tail);
+    else k_eval_intra_cvrp<<<intra_blocks(d), 256, 0, s>>>(d, tail);
 }
 
-void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs) {
-    launch_inter(d, tiles, ntiles, rows, warps, s, rs);
-    launch_intra(d, s);
+void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs,
+                 int tail) {
+    launch_inter(d, tiles, ntiles, rows, warps, s, rs, tail);
+    launch_intra(d, s, tail);
 }
 
 int apply_grid(const Dev &d) {
@@ -236,9 +259,10 @@ int apply_grid(const Dev &d) {
     return 1 + (rows < 3 * 152 ? rows : 3 * 152);
 }
 
-void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond, cudaStream_t s) {
+void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond, cudaStream_t s,
+                  int pre) {
     const size_t sm = (size_t)band_smem_ints(d.Wp, 16) * sizeof(int);
-    k_apply<<<apply_grid(d), 512, sm, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond);
+    k_apply<<<apply_grid(d), 512, sm, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond, pre);
 }
 
 void launch_sync_solution(const Dev &d, cudaStream_t s) {

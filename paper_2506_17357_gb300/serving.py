@@ -4,11 +4,13 @@ Requests (an instance plus an initial solution) arrive over time.  A request
 is admitted as soon as a slot is free and its device footprint fits the
 memory budget; admission copies its (pinned) host arrays to the device on
 the slot's own CUDA stream, builds the attributes and enqueues the whole
-descent (tga_descend_async: a CUDA graph with a device-driven loop).  Jobs
-admitted while others run overlap on the GPU; finished jobs are retired (a
-device-to-host read of the final solution and counters), which frees their
-slot and budget for the next arrivals.  ``max_slots=1`` is the
-one-at-a-time plain path: one job on the GPU at a time, in arrival order.
+descent (tga_descend_async: a CUDA graph with a device-driven loop, so
+kernels of different jobs interleave on the SMs).  Jobs admitted while others
+run overlap on the GPU; finished jobs are retired (a device-to-host read of
+the final solution and counters), which frees their slot and budget for the
+next arrivals.  ``max_slots=1`` is the one-at-a-time plain path: one job on
+the GPU at a time, in arrival order, each descending along the library's
+default (fastest single-job) path, which may claim every SM.
 
 Admission is first-come first-served: a request that does not fit waits at
 the head of the queue (no reordering, so no starvation).  Results do not
@@ -80,7 +82,8 @@ class _Pinned:
 
 
 class _Job:
-    def __init__(self, torch, device, stream, req: Request, pinned: _Pinned, log_capacity: int):
+    def __init__(self, torch, device, stream, req: Request, pinned: _Pinned, log_capacity: int,
+                 mode: int = T.DESCENT_AUTO):
         self.torch = torch
         self.req = req
         self.stream = stream
@@ -101,6 +104,7 @@ class _Job:
         self.ctx = T.tga_create(self.c_inst, self.c_sol, req.op_mask, stream.cuda_stream)
         if self.log is not None:
             T.tga_set_move_log(self.ctx, self.log.data_ptr(), log_capacity)
+        T.tga_set_descent_mode(self.ctx, mode)
         T.tga_build_attrs(self.ctx)
         T.tga_descend_async(self.ctx)
 
@@ -182,8 +186,10 @@ class Server:
                 queue.popleft()
                 slot = free.pop()
                 adm = time.perf_counter() - t0
-                active[slot] = (_Job(torch, self.device, self.streams[slot], r, pinned[r.rid], self.log_capacity),
-                                adm, need)
+                # a persistent descent claims every SM: concurrent jobs use the graph path
+                mode = T.DESCENT_AUTO if self.max_slots == 1 else T.DESCENT_GRAPH
+                active[slot] = (_Job(torch, self.device, self.streams[slot], r, pinned[r.rid], self.log_capacity,
+                                     mode), adm, need)
                 used += need
             if not queue and active:
                 time.sleep(self.poll_s)

@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libtga.so")
 
 TGA_OK, TGA_ERR_INVALID, TGA_ERR_RANGE, TGA_ERR_NOMEM, TGA_ERR_CUDA = 0, 1, 2, 3, 4
 TGA_ERR_TIMEOUT, TGA_ERR_STATE = 5, 6
+DESCENT_AUTO, DESCENT_PERSISTENT, DESCENT_GRAPH, DESCENT_HOST = 0, 1, 2, 3
+DESCENT_NAMES = {0: "auto", 1: "persistent", 2: "graph", 3: "host"}
 NO_MOVE_KEY = (1 << 64) - 1
 
 
@@ -84,6 +86,8 @@ EXPORTS = [
     ("tga_eval_best_move_noalloc", ctypes.c_int, [ctypes.POINTER(tga_instance), ctypes.POINTER(tga_solution),
                                                   ctypes.c_uint32, _P, _P]),
     ("tga_profile_inter", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
+    ("tga_set_descent_mode", ctypes.c_int, [_P, ctypes.c_int32]),
+    ("tga_get_descent_mode", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("tga_set_tile_shape", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     ("tga_get_tile_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32)]),
@@ -211,6 +215,17 @@ def tga_profile_inter(ctx: int, reps: int = 10) -> float:
     return ms.value
 
 
+def tga_set_descent_mode(ctx: int, mode: int):
+    _check(_lib().tga_set_descent_mode(_P(ctx), mode), "tga_set_descent_mode")
+
+
+def tga_get_descent_mode(ctx: int):
+    """(path of the last descent as a DESCENT_* value, persistent grid size or 0)."""
+    m, g = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().tga_get_descent_mode(_P(ctx), ctypes.byref(m), ctypes.byref(g)), "tga_get_descent_mode")
+    return m.value, g.value
+
+
 def tga_set_tile_shape(ctx: int, rows: int, col_warps: int, row_split: int):
     _check(_lib().tga_set_tile_shape(_P(ctx), rows, col_warps, row_split), "tga_set_tile_shape")
 
@@ -328,6 +343,13 @@ class LocalSearch:
 
     def descend(self, max_steps: int = (1 << 62)) -> dict:
         return tga_descend(self.ctx, max_steps)
+
+    def set_descent_mode(self, mode: int):
+        tga_set_descent_mode(self.ctx, mode)
+        return self
+
+    def descent_mode(self):
+        return tga_get_descent_mode(self.ctx)
 
     def stats(self) -> dict:
         return tga_get_stats(self.ctx)

@@ -119,11 +119,13 @@ def test_integer_headroom_is_enforced():
     ls.close()
 
 
-def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None):
+def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None, mode=None):
     ls = LocalSearch(inst, sol, mask, log_capacity=cap).build()
     try:
         if tile is not None:
             ls.set_tile(*tile)
+        if mode is not None:
+            ls.set_descent_mode(mode)
         st = ls.descend()
         log = ls.move_log()
         tour, rs = ls.solution()
@@ -132,11 +134,12 @@ def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None):
         ls.close()
 
 
+@pytest.mark.parametrize("mode", [0, 2])       # automatic (persistent at this size), graph
 @pytest.mark.parametrize("tile", [None, (16, 2), (32, 4), (64, 8), (0, 0), (8, 2, 1), (16, 2, 2),
                                   (32, 2, 4), (64, 4, 2)])
-def test_config1_full_trajectory(tile):
+def test_config1_full_trajectory(tile, mode):
     inst, sol = I.config1(1)
-    st, log, fin = _descend_gpu(inst, sol, I.MASK_CONFIG1, tile=tile)
+    st, log, fin = _descend_gpu(inst, sol, I.MASK_CONFIG1, tile=tile, mode=mode)
     ofin, steps, olog, ocands = O.descend(inst, sol, I.MASK_CONFIG1, "def")
     assert st["status"] == 0 and st["local_optimum"] == 1
     assert st["steps"] == steps and np.array_equal(log, olog)
@@ -145,28 +148,62 @@ def test_config1_full_trajectory(tile):
     assert st["candidates"] == ocands
 
 
+@pytest.mark.parametrize("kind", ["vrptw", "cvrp"])
 @pytest.mark.parametrize("limit", [0, 1, 5, 63, 64, 65, None])
-def test_host_launched_descent_equals_graph(monkeypatch, limit):
-    """The host-launched per-step path (what profilers trace) runs the same
-    kernels as the device-driven graph loop: same move log, same solution,
-    and an exact stop at the step limit."""
-    inst = I.vrptw(300, 4)
+def test_descent_paths_agree(kind, limit):
+    """The persistent launch, the graph loop and the host-launched per-step
+    path (what profilers trace) give the same move log, solution and
+    counters, and stop exactly at the step limit."""
+    from paper_2506_17357_gb300 import tga as T
+    if kind == "vrptw":
+        inst = I.vrptw(300, 4)
+        mask = I.MASK_ALL
+    else:
+        inst = I.cvrp_uniform(400, 6)
+        mask = I.MASK_CONFIG3
     sol = I.random_split_solution(inst, I.solution_seed(4))
     out = {}
-    for mode in ("1", "0"):
-        monkeypatch.setenv("TGA_GRAPH", mode)
-        ls = LocalSearch(inst, sol, I.MASK_ALL, log_capacity=1 << 16).build()
+    for mode in (T.DESCENT_GRAPH, T.DESCENT_HOST, T.DESCENT_PERSISTENT):
+        ls = LocalSearch(inst, sol, mask, log_capacity=1 << 16).build()
         try:
+            ls.set_descent_mode(mode)
             st = ls.descend() if limit is None else ls.descend(max_steps=limit)
+            if limit != 0:
+                assert ls.descent_mode()[0] == mode
             out[mode] = (st, ls.move_log(), ls.solution())
         finally:
             ls.close()
-    (sg, lg, (tg, rg)), (sh, lh, (th, rh)) = out["1"], out["0"]
+    sg, lg, (tg, rg) = out[T.DESCENT_GRAPH]
     if limit is not None:
         assert sg["steps"] <= limit and (sg["local_optimum"] == 1 or sg["steps"] == limit)
-    for k in ("steps", "evaluations", "candidates", "final_cost", "local_optimum", "status"):
-        assert sg[k] == sh[k], k
-    assert np.array_equal(lg, lh) and np.array_equal(tg, th) and np.array_equal(rg, rh)
+    else:
+        assert sg["local_optimum"] == 1
+    for mode in (T.DESCENT_HOST, T.DESCENT_PERSISTENT):
+        sh, lh, (th, rh) = out[mode]
+        for k in ("steps", "evaluations", "candidates", "final_cost", "local_optimum", "status"):
+            assert sg[k] == sh[k], (mode, k)
+        assert np.array_equal(lg, lh) and np.array_equal(tg, th) and np.array_equal(rg, rh), mode
+
+
+def test_persistent_descent_resumes_and_reports_its_grid():
+    """A persistent descent stopped by the step limit resumes where it stopped
+    (second call) and reaches the same local optimum as one uninterrupted call."""
+    from paper_2506_17357_gb300 import tga as T
+    inst, sol = I.config1(3)
+    ref = _descend_gpu(inst, sol, I.MASK_CONFIG1, mode=T.DESCENT_GRAPH)
+    ls = LocalSearch(inst, sol, I.MASK_CONFIG1, log_capacity=1 << 12).build()
+    try:
+        ls.set_descent_mode(T.DESCENT_PERSISTENT)
+        a = ls.descend(max_steps=7)
+        mode, grid = ls.descent_mode()
+        assert mode == T.DESCENT_PERSISTENT and grid >= 1
+        assert a["steps"] == min(7, ref[0]["steps"])
+        b = ls.descend()
+        assert b["steps"] == ref[0]["steps"] and b["final_cost"] == ref[0]["final_cost"]
+        tour, rs = ls.solution()
+        assert np.array_equal(tour, ref[2].tour) and np.array_equal(rs, ref[2].route_start)
+    finally:
+        ls.close()
 
 
 @pytest.mark.parametrize("seed", [2, 3])
