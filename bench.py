@@ -47,8 +47,8 @@ WORKLOADS = {
 # Integer operations per inter-route candidate, counted from the delta
 # expressions (adds/subs, min/max, multiplies, plus one compare for the
 # running argmin).  Index: op rank.  CVRP and VRPTW (time-warp terms added).
-OPS_CVRP = {0: 8, 1: 13, 3: 13, 4: 8, 5: 8}
-OPS_TW = {0: 20, 1: 36, 3: 22, 4: 20, 5: 20}
+OPS_CVRP = {0: 8, 1: 13, 2: 6, 3: 13, 4: 8, 5: 8}
+OPS_TW = {0: 20, 1: 36, 2: 22, 3: 22, 4: 20, 5: 20}
 
 
 def inter_candidates(n, lens, mask):
@@ -76,25 +76,33 @@ def algorithmic_ops(n, lens, mask, has_tw):
     return sum(table[op] * c for op, c in inter_candidates(n, lens, mask).items())
 
 
+def descent_ops(op_candidates, has_tw):
+    """Integer operations of every candidate evaluated (per-operator totals
+    from the device counters, weighted by the per-candidate counts above)."""
+    table = OPS_TW if has_tw else OPS_CVRP
+    return sum(table[op] * c for op, c in enumerate(op_candidates))
+
+
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("tga_kernels.cu", "tga_device.cuh", "tga_internal.cuh"):
+    for f in ("tga_kernels.cu", "tga_persist.cu", "tga_device.cuh", "tga_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2506_17357_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload):
-    """DRAM bytes per inter-kernel launch from the committed ncu summary, or
-    None when the kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "k_eval_inter_traffic.json")
+def measured_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (profiles/dram_traffic.json), or None when the kernel sources
+    changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    ent = rec.get(workload)
+    ent = rec.get(kernel, {}).get(workload)
     if not ent or ent.get("source_hash") != kernel_source_hash():
         return None
     return ent.get("dram_bytes_per_launch")
@@ -258,9 +266,13 @@ def bench_gpu(args):
     value = c_all / t_max
     tlo_ms = 1e3 * total / args.steps
     evals = stats["evaluations"]
+    mode_used, grid = T.tga_get_descent_mode(ls.ctx)
+    persistent = mode_used == T.DESCENT_PERSISTENT
     # gpu launches per descent: build (check, positions, perm, routes, finish,
-    # pcol init) + begin + 4 per evaluation (inter, intra, apply, band)
-    launches_per_step = 6 + 1 + 4 * evals
+    # pcol init) + begin, then one persistent launch, or 3 per evaluation
+    # (inter, intra, apply) + the write-back of the solution
+    launches_per_step = 6 + 1 + (1 if persistent else 3 * evals + 1)
+    op_cands = T.tga_get_op_candidates(ls.ctx)
 
     # ---- end to end through the public API with host buffers
     e2e_times = []
@@ -278,31 +290,65 @@ def bench_gpu(args):
         assert st["candidates"] == stats["candidates"]
     e2e_value = stats["candidates"] * len(e2e_times) / sum(e2e_times)
 
-    # ---- roofline of the dominant kernel (inter-route evaluation), timed live
-    # with CUDA events on the context's stream at states along the trajectory
+    # ---- roofline of the dominant kernel, timed live with CUDA events on the
+    # context's stream.  Persistent path: the one launch that runs the whole
+    # descent (k_persist); its algorithmic work is every candidate evaluated,
+    # per operator.  Graph path: the inter-route evaluation kernel at states
+    # along the trajectory.
     peaks, peak_src = load_peaks()
     sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = 152 * 4 * 32 * sm_mhz_max * 1e6              # INT32 lane-ops/s at issue peak
-    restore()
-    T.tga_build_attrs(ls.ctx)
-    total_ops = 0.0
-    total_ms = 0.0
-    probes = 5
-    n_steps = steps[-1]
-    for j in range(probes):
-        ms = T.tga_profile_inter(ls.ctx, reps=20)
-        tour_h, rs_h = ls.solution()
-        lens = np.diff(rs_h)
-        total_ops += algorithmic_ops(inst.n, lens, mask, inst.has_tw)
-        total_ms += ms
-        if j + 1 < probes:
-            T.tga_descend(ls.ctx, max_steps=max(1, n_steps // (probes - 1)))
-    achieved = total_ops / (total_ms / 1e3)
-    roof = {"bound": "alu", "kernel": "k_eval_inter", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-            "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops,
-            "peak_source": f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz_max:.0f} MHz (issue peak)",
-            "ms_per_launch": total_ms / probes, "ops_per_launch": total_ops / probes,
-            "traffic": measured_traffic(args.workload), "kernel_source_hash": kernel_source_hash()}
+    peak_desc = f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz_max:.0f} MHz (issue peak)"
+
+    def inter_kernel_roof():
+        restore()
+        T.tga_build_attrs(ls.ctx)
+        total_ops = total_ms = 0.0
+        probes = 5
+        n_steps = steps[-1]
+        for j in range(probes):
+            ms = T.tga_profile_inter(ls.ctx, reps=20)
+            tour_h, rs_h = ls.solution()
+            lens = np.diff(rs_h)
+            total_ops += algorithmic_ops(inst.n, lens, mask, inst.has_tw)
+            total_ms += ms
+            if j + 1 < probes:
+                T.tga_descend(ls.ctx, max_steps=max(1, n_steps // (probes - 1)))
+        achieved = total_ops / (total_ms / 1e3)
+        return {"bound": "alu", "kernel": "k_eval_inter", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops, "peak_source": peak_desc,
+                "ms_per_launch": total_ms / probes, "ops_per_launch": total_ops / probes,
+                "work": "inter-route candidates of the state (per-candidate integer ops x candidates), "
+                        "mean over 5 states along the trajectory",
+                "traffic": measured_traffic(args.workload, "k_eval_inter"),
+                "kernel_source_hash": kernel_source_hash()}
+
+    inter_roof = inter_kernel_roof()
+    if persistent:
+        kms = []
+        for _ in range(3):
+            restore()
+            T.tga_build_attrs(ls.ctx)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            T.tga_descend_async(ls.ctx)
+            e1.record(stream)
+            e1.synchronize()
+            kms.append(e0.elapsed_time(e1))
+        ops = descent_ops(op_cands, inst.has_tw)
+        ms = float(np.mean(kms))
+        achieved = ops / (ms / 1e3)
+        roof = {"bound": "alu", "kernel": "k_persist", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops, "peak_source": peak_desc,
+                "ms_per_launch": ms, "ops_per_launch": ops, "grid": grid,
+                "work": "every candidate of every evaluation of the descent (per-operator device counters "
+                        "x per-candidate integer ops); one launch = one whole descent",
+                "traffic": measured_traffic(args.workload, "k_persist"),
+                "kernel_source_hash": kernel_source_hash(),
+                "inter_kernel": {k: inter_roof[k] for k in ("kernel", "achieved", "frac", "ms_per_launch",
+                                                             "ops_per_launch", "traffic")}}
+    else:
+        roof = inter_roof
     ls.close()
 
     if ws > 1:
@@ -321,7 +367,9 @@ def bench_gpu(args):
         "final_cost": stats["final_cost"],
         "config": {"workload": args.workload, "desc": desc, "instance_seed": args.seed,
                    "op_mask": mask, "tile_rows_warps": list(tile), "parallelism": f"replicas x{ws}",
+                   "descent_path": T.DESCENT_NAMES[mode_used],
                    "l2": "flushed between timed steps (512 MB write)"},
+        "candidates_per_operator": op_cands,
         "e2e": {"value": e2e_value, "unit": "candidate moves/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "time_to_local_optimum_ms": 1e3 * float(np.mean(e2e_times))},
         "gpu_launches": int(launches_per_step * args.steps),

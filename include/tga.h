@@ -216,6 +216,13 @@ int tga_sync(tga_ctx *ctx);
 /* Synchronise and copy the counters (steps, candidates, costs, status). */
 int tga_get_stats(tga_ctx *ctx, tga_stats *out_host);
 
+/* Synchronise and copy the candidate moves evaluated per operator rank
+ * (out_host[6]: relocate, swap, 2-opt, 2-opt*, or-opt 2, or-opt 3), summed
+ * over all evaluations since tga_build_attrs; their sum is
+ * tga_stats.candidates.  Used to count the algorithmic work of a descent
+ * per operator (the per-operator breakdown of the paper's Section 6.6). */
+int tga_get_op_candidates(tga_ctx *ctx, int64_t *out_host);
+
 /* Record one packed key ((uint32)(delta + 2^31) << 32 | idx) per
  * evaluation into a caller-owned DEVICE buffer of `capacity` entries
  * (NULL disables).  Used to compare whole trajectories. */

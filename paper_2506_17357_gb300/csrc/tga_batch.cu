@@ -260,8 +260,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
                 apply_plan_block(d, sPlan, smem, false, 0, 0);
             } else if (tid == 0) {
                 if (d.log && C->evals < d.log_cap) d.log[C->evals] = C->best_key;
-                C->evals += 1;
-                C->cand_total += C->cand_per_eval;
+                count_evaluation(d, C);
                 sPlan.act = 0;
             }
             __syncthreads();

@@ -549,6 +549,15 @@ int tga_get_stats(tga_ctx *c, tga_stats *out_host) {
     return TGA_OK;
 }
 
+int tga_get_op_candidates(tga_ctx *c, int64_t *out_host) {
+    if (!c || !out_host) return TGA_ERR_INVALID;
+    Control C;
+    int rc = read_control(c, &C);
+    if (rc) return rc;
+    for (int op = 0; op < 6; ++op) out_host[op] = C.cand_op[op];
+    return TGA_OK;
+}
+
 int tga_set_move_log(tga_ctx *c, uint64_t *log_dev, int64_t capacity) {
     if (!c || capacity < 0) return TGA_ERR_INVALID;
     c->d.log = (unsigned long long *)log_dev;

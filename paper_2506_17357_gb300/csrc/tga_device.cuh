@@ -156,6 +156,8 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
         const BRec b = d.brec[a];
         ERec e;
         e.route = r; e.anchor = a; e.node = x; e.idx = k; e.pad0 = 0; e.pad1 = 0;
+        d.brec[a].rlen = L;
+        d.brec[a].rcost = R.cost;
         e.d = __ldg(d.demand + x);
         e.e = tw ? __ldg(d.early + x) : 0;
         e.l = tw ? __ldg(d.late + x) : 0;
@@ -357,6 +359,7 @@ __device__ void finish_block(const Dev &d) {
         C->sumL2 = l2; C->sumLm1 = l1; C->sumLm2 = lm2;
         C->maxL = maxL; C->maxLoad = maxLoad;
         C->steps = 0; C->evals = 0; C->cand_total = 0;
+        for (int op = 0; op < 6; ++op) C->cand_op[op] = 0;
         C->done = 0; C->local_opt = 0; C->chg_count = 0;
         C->plan_ready = 0; C->plan_done = 0;
         C->best_key = kNoKey;
@@ -397,6 +400,27 @@ __device__ void pcol_init_range(const Dev &d, long long t0, long long stride) {
         const unsigned _i = (ix);                                          \
         if (_d < best || (_d == best && _i < bidx)) { best = _d; bidx = _i; } \
     } while (0)
+
+// Tile number bid of the inter-route pair triangle, in the order of the
+// host's tile list: row tiles I = 0.. (TR rows each), and in row tile I the
+// column tiles J = floor(I/g) .. nct-1 (g = TC/TR, an integer: the first
+// column tile holding a pair p < q).  The number of tiles before row tile I
+// has a closed form, so I is found by binary search with no memory access.
+__device__ __forceinline__ int2 tile_of(int bid, int Wp, int TR, int TC) {
+    const int Wa = Wp - 1;
+    const int nrt = (Wa + TR - 1) / TR, nct = (Wa + TC - 1) / TC, g = TC / TR;
+    auto before = [&](int I) -> long long {
+        const long long q = I / g, r = I - q * g;
+        return (long long)I * nct - ((long long)g * q * (q - 1) / 2 + r * q);
+    };
+    int lo = 0, hi = nrt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (before(mid) <= bid) lo = mid;
+        else hi = mid - 1;
+    }
+    return make_int2(lo, lo / g + (int)(bid - before(lo)));
+}
 
 // One tile of the inter-route pair triangle: rows p0..p0+TR-1, columns
 // q0..q0+32*NWc-1 with NWc = warps / RS.  Warp w owns the 32 columns of slice
@@ -834,6 +858,177 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
         intra_anchor<TW>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, kinds);
 }
 
+// ---------------------------------------------------------------------------
+// Intra-route candidates of a time-window route from subsequence tables.
+//
+// The route's attribute matrix of Section 4.2 -- the time-window data
+// (E, L, D - T_V, T_V) of every subsequence x_i..x_j of customers, forward
+// (F) and reversed (R, for 2-opt) -- is built in shared memory, one thread
+// per row i extending its row by the concatenation operator of Section 4.3.
+// Every intra-route candidate is then an O(1) concatenation of the prefix
+// before the move, at most three table entries or single customers, and the
+// suffix after it (route-based extraction, Section 5.3.1), so the threads of
+// the block take the (i, j) pairs of the route independently: the critical
+// path is one row of the table instead of a sweep per anchor.  Routes longer
+// than kTabMaxL customers fall back to intra_route_block.
+
+constexpr int kTabMaxL = 40;
+constexpr int kTabEntries = kTabMaxL * (kTabMaxL + 1) / 2;
+// shared ints: per-element arrays, the distance block and both int4 tables
+constexpr int kIntraTabSmemInts =
+    ((kIntraVec * (kTabMaxL + 2) + (kTabMaxL + 2) * (kTabMaxL + 2) + 3) / 4) * 4 + 2 * 4 * kTabEntries;
+
+// Entry (i, j), 1 <= i <= j <= L, of a packed upper-triangular table.
+__device__ __forceinline__ int tri_at(int i, int j, int L) {
+    return (i - 1) * L - ((i - 1) * (i - 2)) / 2 + (j - i);
+}
+
+// a (+) b for time-window data {E, L, D - T_V, T_V} with travel time t
+// between them (the concatenation of Section 4.3 in the difference form).
+__device__ __forceinline__ int4 tw_cat(const int4 a, const int4 b, int t) {
+    const int dt = a.z + t;
+    const int dw = max(b.x - dt - a.y, 0);
+    const int dv = max(a.x + dt - b.y, 0);
+    return make_int4(max(b.x - dt, a.x) - dw, min(b.y - dt, a.y) + dv, a.z + t + dw - dv + b.z, a.w + dv + b.w);
+}
+
+// Departure time and warp after entering segment g at arrival time a.
+__device__ __forceinline__ int tw_enter(int a, const int4 g, int &warp) {
+    const int w = max(a - g.y, 0);
+    warp += w + g.w;
+    return max(a, g.x) - w + g.z;
+}
+
+__device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsigned &bidx) {
+    const RouteRec R = d.rrec[r];
+    const int L = R.len;
+    if (L < 2) return;
+    if (L > kTabMaxL) {
+        intra_route_block<true>(d, r, S, best, bidx);
+        return;
+    }
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int E = L + 2, st = R.start;
+    int *node = S, *e = S + E, *l = S + 2 * E, *s = S + 3 * E, *tau = S + 4 * E, *twf = S + 5 * E;
+    int *distf = S + 6 * E, *Lg = S + 7 * E, *twg = S + 8 * E, *distg = S + 9 * E;
+    int *D = S + kIntraVec * E;                                   // E x E distances
+    int4 *Ft = reinterpret_cast<int4 *>(S + ((kIntraVec * E + E * E + 3) / 4) * 4);
+    int4 *Rt = Ft + L * (L + 1) / 2;
+    // ---- staging: element records, and the distance block from the
+    // position-ordered copy (row of element a, columns st .. st+E-1), both
+    // issued right after the positions are known
+    for (int k = tid; k < E; k += nthr) {
+        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[st + k] : -1);
+        const int x = (k >= 1 && k <= L) ? a : 0;
+        node[k] = x;
+        e[k] = __ldg(d.early + x); l[k] = __ldg(d.late + x); s[k] = __ldg(d.service + x);
+        if (a >= 0) {
+            const BRec b = d.brec[a];
+            tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
+            Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
+        } else {
+            tau[k] = 0; twf[k] = 0; distf[k] = 0; Lg[k] = 0; twg[k] = 0; distg[k] = 0;
+        }
+    }
+#pragma unroll 4
+    for (int t = tid; t < E * E; t += nthr) {
+        const int a = t / E, b = t - a * E;
+        const int x = (a >= 1 && a <= L) ? d.seq[st + a] : 0;
+        D[t] = TGA_LDG(d.pcol + (size_t)x * d.ldp + kColOff + st + b);
+    }
+    __syncthreads();
+    // ---- tables: thread c < L extends forward row i = c+1, thread L + c the
+    // reversed row (x_j .. x_i, entered from x_j)
+    for (int c = tid; c < 2 * L; c += nthr) {
+        const bool rev = c >= L;
+        const int i = (rev ? c - L : c) + 1;
+        int4 *T = rev ? Rt : Ft;
+        int4 cur = make_int4(e[i], l[i], s[i], 0);
+        T[tri_at(i, i, L)] = cur;
+        for (int j = i + 1; j <= L; ++j) {
+            const int4 nx = make_int4(e[j], l[j], s[j], 0);
+            cur = rev ? tw_cat(nx, cur, D[j * E + j - 1]) : tw_cat(cur, nx, D[(j - 1) * E + j]);
+            T[tri_at(i, j, L)] = cur;
+        }
+    }
+    __syncthreads();
+    // ---- candidates: pair (i, j), 0 <= i < j <= L, one pair per thread
+    const unsigned mask = d.op_mask;
+    const unsigned W = (unsigned)d.W, W2 = W * W;
+    const int wT = d.wT, baseDist = R.dist, baseTw = R.tw;
+    const int L1 = L + 1;
+    const unsigned adep = (unsigned)(d.n + 1 + r);
+    for (int t = tid; t < L1 * L1; t += nthr) {
+        const int i = t / L1, j = t - i * L1;
+        if (j <= i) continue;
+        if (i >= 1) {
+            const unsigned xi = (unsigned)node[i], xj = (unsigned)node[j];
+            const int ptau = tau[i - 1], ptwf = twf[i - 1], pdist = distf[i - 1];
+            // relocate (k = 1) / or-opt (k = 2, 3): run x_i..x_{i+k-1} to
+            // just after x_j, j >= i+k: prefix(i-1) + (i+k..j) + run + suffix(j)
+#pragma unroll
+            for (int k = 1; k <= 3; ++k) {
+                const int op = k == 1 ? 0 : k + 2;
+                if (!(mask & (1u << op)) || j < i + k) continue;
+                const int c0 = D[(i - 1) * E + i + k];
+                int tw = ptwf;
+                const int tm = tw_enter(ptau + c0, Ft[tri_at(i + k, j, L)], tw);
+                const int cA = D[j * E + i], cB = D[(i + k - 1) * E + j + 1];
+                const int tr = tw_enter(tm + cA, Ft[tri_at(i, i + k - 1, L)], tw);
+                const int w2 = max(tr + cB - Lg[j], 0);
+                const int dist = pdist + c0 + (distf[j] - distf[i + k]) + cA + (distf[i + k - 1] - distf[i]) + cB +
+                                 distg[j];
+                TGA_TRY(dist - baseDist + wT * (tw + w2 + twg[j] - baseTw), (unsigned)op * W2 + xi * W + xj);
+            }
+            // swap x_i <-> x_j
+            if (mask & 2u) {
+                const int ca = D[(i - 1) * E + j];
+                int tw = ptwf;
+                int tx = tw_enter(ptau + ca, make_int4(e[j], l[j], s[j], 0), tw);
+                int dist = pdist + ca + distg[j];
+                int last = j;
+                if (j > i + 1) {
+                    const int cb = D[j * E + i + 1];
+                    tx = tw_enter(tx + cb, Ft[tri_at(i + 1, j - 1, L)], tw);
+                    dist += cb + (distf[j - 1] - distf[i + 1]);
+                    last = j - 1;
+                }
+                const int cc = D[last * E + i], cd = D[i * E + j + 1];
+                tx = tw_enter(tx + cc, make_int4(e[i], l[i], s[i], 0), tw);
+                const int w4 = max(tx + cd - Lg[j], 0);
+                TGA_TRY(dist + cc + cd - baseDist + wT * (tw + w4 + twg[j] - baseTw),
+                        W2 + min(xi, xj) * W + max(xi, xj));
+            }
+            // 2-opt: reverse x_i..x_j
+            if (mask & 4u) {
+                const int ca = D[(i - 1) * E + j], cb = D[i * E + j + 1];
+                int tw = ptwf;
+                const int tx = tw_enter(ptau + ca, Rt[tri_at(i, j, L)], tw);
+                const int w2 = max(tx + cb - Lg[j], 0);
+                TGA_TRY(pdist + ca + (distf[j] - distf[i]) + cb + distg[j] - baseDist +
+                            wT * (tw + w2 + twg[j] - baseTw),
+                        2u * W2 + xi * W + xj);
+            }
+        }
+        // the run x_j..x_{j+k-1} moves back to just after element i (j >= i+2):
+        // prefix(i) + run + (i+1..j-1) + suffix(j+k-1)
+        const unsigned ai = i == 0 ? adep : (unsigned)node[i];
+#pragma unroll
+        for (int k = 1; k <= 3; ++k) {
+            const int op = k == 1 ? 0 : k + 2;
+            const int w = j + k - 1;
+            if (!(mask & (1u << op)) || j < i + 2 || w > L) continue;
+            const int ca = D[i * E + j], cb = D[w * E + i + 1], cc = D[(j - 1) * E + j + k];
+            int tw = twf[i];
+            int tx = tw_enter(tau[i] + ca, Ft[tri_at(j, w, L)], tw);
+            tx = tw_enter(tx + cb, Ft[tri_at(i + 1, j - 1, L)], tw);
+            const int w3 = max(tx + cc - Lg[w], 0);
+            const int dist = distf[i] + ca + (distf[w] - distf[j]) + cb + (distf[j - 1] - distf[i + 1]) + cc + distg[w];
+            TGA_TRY(dist - baseDist + wT * (tw + w3 + twg[w] - baseTw), (unsigned)op * W2 + (unsigned)node[j] * W + ai);
+        }
+    }
+}
+
 // Intra-route candidates of a CVRP whose moved element is the customer at
 // position p, with one warp (all lanes call): every delta is an O(1) edge
 // formula (loads do not change inside a route), lanes take the other end j
@@ -1090,10 +1285,10 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
     if (k <= L) {
         const int a = k == 0 ? d.n + 1 + r : x;
         int4 *bp = reinterpret_cast<int4 *>(d.brec + a);
-        bp[0] = make_int4(x, r, k, 0);
+        bp[0] = make_int4(x, r, k, L);
         bp[1] = make_int4(tau, twf, f.dist, f.load);
         bp[2] = make_int4(Lg, twg, gdist, gload);
-        bp[3] = make_int4(0, 0, 0, 0);
+        bp[3] = make_int4(Rcost, 0, 0, 0);
         const int Fc = f.dist + wTe * twf - Rcost;
         const int Gc = gdist + wTe * twg;
         int rem1 = kBig, K2 = kBig, LQd = 0, tauP = 0;
@@ -1158,8 +1353,7 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
     } else {
         key = *(volatile unsigned long long *)&C->best_key;
         if (d.log && C->evals < d.log_cap) d.log[C->evals] = key;
-        C->evals += 1;
-        C->cand_total += C->cand_per_eval;
+        count_evaluation(d, C);
     }
     C->best_key = kNoKey;
     if (key == kNoKey || key_delta(key) >= 0) {
@@ -1175,14 +1369,17 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
     pl.b = (int)(idx % W);
     pl.delta = key_delta(key);
     bool ok = pl.op < 6 && ((d.op_mask >> pl.op) & 1u) && pl.a >= 1 && pl.b >= 1;
+    int costA = 0, costB = 0;
     if (ok) {
+        // one round trip: the anchors' records carry route, index, route
+        // length and cost; the start depot sits idx positions before the anchor
         const BRec ba = d.brec[pl.a], bb = d.brec[pl.b];
+        const int qa = d.pos_of[pl.a], qb = d.pos_of[pl.b];
         pl.A = ba.route; pl.B = bb.route; pl.i = ba.idx; pl.j = bb.idx;
+        pl.LA = ba.rlen; pl.LB = bb.rlen;
+        pl.pA = qa - ba.idx; pl.pB = qb - bb.idx;
+        costA = ba.rcost; costB = bb.rcost;
         ok = pl.A >= 0 && pl.B >= 0;
-        if (ok) {
-            pl.LA = d.rrec[pl.A].len; pl.LB = d.rrec[pl.B].len;
-            pl.pA = d.rrec[pl.A].start; pl.pB = d.rrec[pl.B].start;
-        }
     }
     if (ok) {
         const int op = pl.op;
@@ -1214,7 +1411,7 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
     S.mp = pl;
     S.act = 1;
     C->last_op = pl.op; C->last_a = pl.a; C->last_b = pl.b; C->last_delta = pl.delta;
-    S.oldcost = (long long)d.rrec[pl.A].cost + (pl.A != pl.B ? d.rrec[pl.B].cost : 0);
+    S.oldcost = (long long)costA + (pl.A != pl.B ? costB : 0);
     S.oldLA = pl.LA; S.oldLB = pl.LB;
     if (pl.A == pl.B) {
         S.lo = pl.A; S.hi = pl.A; S.dl = 0;
@@ -1428,7 +1625,7 @@ __device__ void shift_row_block(int *row, int s0, int s1, int dl) {
     }
 }
 
-constexpr int kBandListMax = 4096;   // rewritten route elements listed in shared memory
+constexpr int kBandListMax = 1024;   // rewritten route elements listed in shared memory
 constexpr int kBandWarpBuf = 256;    // per-warp values of one row (route elements)
 
 // Shared memory (ints) the column permutation needs with nw warps.

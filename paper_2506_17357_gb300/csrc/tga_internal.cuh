@@ -34,10 +34,10 @@ constexpr int kMaxW = 26754;                  // 6 * W^2 < 2^32
 
 // Per-anchor base attributes (prefix through x, suffix after x).
 struct __align__(16) BRec {
-    int node, route, idx, pad0;               // idx: 0 for the start depot, 1..L customers
+    int node, route, idx, rlen;               // idx: 0 for the start depot, 1..L customers; rlen = L
     int tau, twf, distf, loadf;               // prefix: departure time after x, warp, distance, load
     int Lg, twg, distg, loadg;                // suffix after x: latest arrival (T_L), warp, distance, load
-    int pad1, pad2, pad3, pad4;
+    int rcost, pad2, pad3, pad4;              // cost of the route
 };
 
 // Per-anchor hoisted constants of the inter-route candidate expressions.
@@ -101,6 +101,8 @@ struct Control {
     // evaluation that have finished (the last one decodes the step's plan)
     unsigned long long bar_count;
     int plan_seq, eval_done;
+    int plan_cta, pad5[3];                    // persistent descent: the CTA applying the step
+    long long cand_op[6];                     // candidates evaluated per operator rank, all evaluations
 };
 
 // Everything a kernel needs, passed by value.
@@ -204,19 +206,37 @@ __device__ inline void block_min_to(unsigned long long key, unsigned long long *
     }
 }
 
-// Candidates of one evaluation from the route-length sums (closed form).
+// Candidates of one evaluation per operator rank from the route-length sums
+// (closed form; 0 for disabled operators).
+__host__ __device__ inline long long op_candidates(int op, long long n, long long m, unsigned mask,
+                                                   long long sumL2, long long sumLm1, long long sumLm2) {
+    if (!(mask & (1u << op))) return 0;
+    const long long A = n + m;
+    switch (op) {
+        case 0: return n * (A - 2);
+        case 1: return n * (n - 1) / 2;
+        case 2: return (sumL2 - n) / 2;
+        case 3: return (A * A - (sumL2 + 2 * n + m)) / 2;
+        case 4: return sumLm1 * (A - 3);
+        default: return sumLm2 * (A - 4);
+    }
+}
+
 __host__ __device__ inline long long candidate_count(long long n, long long m, unsigned mask,
                                                      long long sumL2, long long sumLm1,
                                                      long long sumLm2) {
-    const long long A = n + m;
     long long c = 0;
-    if (mask & 1u) c += n * (A - 2);
-    if (mask & 2u) c += n * (n - 1) / 2;
-    if (mask & 4u) c += (sumL2 - n) / 2;
-    if (mask & 8u) c += (A * A - (sumL2 + 2 * n + m)) / 2;
-    if (mask & 16u) c += sumLm1 * (A - 3);
-    if (mask & 32u) c += sumLm2 * (A - 4);
+    for (int op = 0; op < 6; ++op) c += op_candidates(op, n, m, mask, sumL2, sumLm1, sumLm2);
     return c;
+}
+
+// Count one evaluation of the current state (evaluation counter, candidate
+// totals, per operator).
+__device__ inline void count_evaluation(const Dev &d, Control *C) {
+    C->evals += 1;
+    C->cand_total += C->cand_per_eval;
+    for (int op = 0; op < 6; ++op)
+        C->cand_op[op] += op_candidates(op, d.n, d.m, d.op_mask, C->sumL2, C->sumLm1, C->sumLm2);
 }
 
 // Batched descent (tga_batch.cu): one persistent launch over many contexts.

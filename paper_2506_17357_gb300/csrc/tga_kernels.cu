@@ -58,38 +58,45 @@ __global__ void k_pcol_init(Dev d) {
 
 // tail > 0: a descent step's evaluation (see eval_tail); every launch of
 // the step's evaluation returns at once on a finished descent.
+// The finished-descent flag is loaded first but tested only before the key
+// is folded in, so its round trip overlaps the staging loads (a launch on a
+// finished descent does its work and discards it).
 template <bool TW, bool OR>
-__global__ void __launch_bounds__(256) k_eval_inter(Dev d, const int2 *__restrict__ tiles, int TR, int RS, int tail) {
-    if (*(volatile int *)&d.ctl->done) return;
+__global__ void __launch_bounds__(256) k_eval_inter(Dev d, int TR, int RS, int tail) {
+    const int done = *(volatile int *)&d.ctl->done;
     extern __shared__ __align__(16) int smem[];
-    const int2 tl = tiles[blockIdx.x];
+    const int TC = (int)blockDim.x / RS;
+    const int2 tl = tile_of(blockIdx.x, d.Wp, TR, TC);
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    inter_tile<TW, OR>(d, tl.x * TR, tl.y * (int)(blockDim.x / RS), TR, RS, smem, best, bidx);
+    inter_tile<TW, OR>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
+    if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
     if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
-// VRPTW intra-route moves: one block of kIntraWarps warps per route.
-template <bool TW>
+// VRPTW intra-route moves: one block of kIntraWarps warps per route
+// (subsequence tables in kIntraTabSmemInts ints of dynamic shared memory).
 __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d, int tail) {
-    if (*(volatile int *)&d.ctl->done) return;
-    __shared__ int smem[kIntraSmemPerWarp];
+    const int done = *(volatile int *)&d.ctl->done;
+    extern __shared__ __align__(16) int smem[];
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    intra_route_block<TW>(d, blockIdx.x, smem, best, bidx);
+    intra_route_table(d, blockIdx.x, smem, best, bidx);
+    if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
     if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
 __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d, int tail) {
-    if (*(volatile int *)&d.ctl->done) return;
+    const int done = *(volatile int *)&d.ctl->done;
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
     intra_cvrp_position(d, p, threadIdx.x & 31, best, bidx);
+    if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
     if (tail && threadIdx.x == 0) eval_tail(d, tail);
@@ -155,8 +162,7 @@ __global__ void k_finalize(Dev d, tga_move *out) {
     const unsigned long long key = C->best_key;
     C->best_key = kNoKey;
     if (d.log && C->evals < d.log_cap) d.log[C->evals] = key;
-    C->evals += 1;
-    C->cand_total += C->cand_per_eval;
+    count_evaluation(d, C);
     tga_move m;
     if (key == kNoKey) {
         m.delta = 0; m.move_index = 0; m.op = -1; m.a = 0; m.b = 0; m.valid = 0;
@@ -230,11 +236,11 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
     const bool orr = (d.op_mask & 48u) != 0;
     const int nt = warps * 32 * rs;
     if (d.has_tw) {
-        if (orr) k_eval_inter<true, true><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs, tail);
-        else k_eval_inter<true, false><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs, tail);
+        if (orr) k_eval_inter<true, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
+        else k_eval_inter<true, false><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
     } else {
-        if (orr) k_eval_inter<false, true><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs, tail);
-        else k_eval_inter<false, false><<<ntiles, nt, sm, s>>>(d, tiles, rows, rs, tail);
+        if (orr) k_eval_inter<false, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
+        else k_eval_inter<false, false><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
     }
 }
 
@@ -244,7 +250,7 @@ int intra_blocks(const Dev &d) { return d.has_tw ? d.m : (d.Wp - 1 + 7) / 8; }
 int eval_blocks(const Dev &d, int ntiles) { return (ntiles > 0 ? ntiles : 0) + intra_blocks(d); }
 
 void launch_intra(const Dev &d, cudaStream_t s, int tail) {
-    if (d.has_tw) k_eval_intra<true><<<intra_blocks(d), kIntraWarps * 32, 0, s>>>(d, tail);
+    if (d.has_tw) k_eval_intra<<<intra_blocks(d), kIntraWarps * 32, kIntraTabSmemInts * sizeof(int), s>>>(d, tail);
     else k_eval_intra_cvrp<<<intra_blocks(d), 256, 0, s>>>(d, tail);
 }
 

@@ -15,9 +15,9 @@
 //   decode       the last CTA to finish decodes the key into the step's plan
 //                and publishes it; every other CTA waits for the publication
 //                (this wait is the step's first synchronisation point);
-//   update       CTA 0 applies the move (Section 5.3.5, rewriting positions
-//                and the <= 2 touched routes); the other CTAs permute the
-//                columns of the position-ordered distance copy;
+//   update       the decoding CTA applies the move (Section 5.3.5, rewriting
+//                positions and the <= 2 touched routes); the other CTAs
+//                permute the columns of the position-ordered distance copy;
 //   barrier      then the next step, until the move is not improving or the
 //                step limit is reached; finally every CTA writes its share of
 //                the caller's giant tour back.
@@ -73,12 +73,12 @@ __device__ bool wait_seq(const int *seq, int want, long long limit_ns) {
 // ntiles inter-route tiles (TR rows x 32 * warps / RS columns each) and
 // nintra intra-route items: one route per item with time windows, else
 // blockDim/32 moved positions per item (one warp each).
-template <bool TW, bool OR>
-__global__ void __launch_bounds__(256) k_persist(Dev d, const int2 *__restrict__ tiles, int ntiles, int TR, int RS,
-                                                 int nintra, long long limit_ns) {
+template <bool TW, bool OR, int NT>
+__global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const int2 *__restrict__ tiles, int ntiles,
+                                                                   int TR, int RS, int nintra, long long limit_ns) {
     extern __shared__ __align__(16) int smem[];
     __shared__ StepPlan sP;
-    __shared__ int s_go, s_ok;
+    __shared__ int s_go, s_ok, s_app;
     Control *C = d.ctl;
     const int tid = threadIdx.x, G = gridDim.x, cta = blockIdx.x;
     const int nw = blockDim.x >> 5, warp = tid >> 5, lane = tid & 31;
@@ -93,21 +93,23 @@ __global__ void __launch_bounds__(256) k_persist(Dev d, const int2 *__restrict__
         // ---- evaluation (every CTA)
         int best = kBestInit;
         unsigned bidx = 0xffffffffu;
+        // intra-route items first: their dependent loads take longest
         for (int t = cta; t < items; t += G) {
-            if (t < ntiles) {
-                const int2 tl = tiles[t];
+            if (t >= nintra) {
+                const int2 tl = tile_of(t - nintra, d.Wp, TR, TC);
                 inter_tile<TW, OR>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
             } else if (TW) {
                 __syncthreads();                       // smem of the previous item is free
-                intra_route_block<true>(d, t - ntiles, smem, best, bidx);
+                intra_route_table(d, t, smem, best, bidx);
             } else {
-                intra_cvrp_position(d, (t - ntiles) * nw + warp, lane, best, bidx);
+                intra_cvrp_position(d, t * nw + warp, lane, best, bidx);
             }
         }
         const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
         block_min_to(key, &C->best_key);
-        // ---- the last CTA to finish decodes and publishes the plan; it
-        // stands in for a barrier: every CTA waits for the publication
+        // ---- the last CTA to finish decodes and publishes the plan, then
+        // applies it itself; every other CTA waits for the publication (this
+        // wait stands in for a barrier) and permutes distance columns
         if (tid == 0) {
             __threadfence();
             s_ok = 0;
@@ -116,26 +118,29 @@ __global__ void __launch_bounds__(256) k_persist(Dev d, const int2 *__restrict__
                 C->eval_done = 0;
                 decode_plan(d, nullptr, sP);
                 C->plan = sP;
+                C->plan_cta = cta;
                 __threadfence();
                 atomicExch(&C->plan_seq, step);
                 s_ok = 1;
+                s_app = cta;
             } else {
                 s_ok = wait_seq(&C->plan_seq, step, limit_ns) ? 2 : 0;
+                if (s_ok) s_app = *(volatile int *)&C->plan_cta;
             }
         }
         __syncthreads();
         if (!s_ok) { ok = false; break; }
         if (s_ok == 2) load_plan(C, &sP);
         __syncthreads();
-        // ---- update: CTA 0 applies, the others permute distance columns
-        if (cta == 0) {
+        // ---- update
+        if (s_ok == 1) {
             apply_plan_block(d, sP, smem, false, 0, 0);
             if (G == 1) {
                 __syncthreads();
                 band_plan_rows(d, sP, smem, 0, d.n + 1, 0, 1);
             }
         } else {
-            band_plan_rows(d, sP, smem, 0, d.n + 1, cta - 1, G - 1);
+            band_plan_rows(d, sP, smem, 0, d.n + 1, cta < s_app ? cta : cta - 1, G - 1);
         }
         target += G;
         if (!grid_barrier(&C->bar_count, target, limit_ns)) { ok = false; break; }
@@ -154,9 +159,13 @@ namespace {
 
 using PersistFn = void (*)(Dev, const int2 *, int, int, int, int, long long);
 
-PersistFn persist_fn(bool tw, bool orr) {
-    if (tw) return orr ? k_persist<true, true> : k_persist<true, false>;
-    return orr ? k_persist<false, true> : k_persist<false, false>;
+PersistFn persist_fn(bool tw, bool orr, int nt) {
+    if (nt == 128) {
+        if (tw) return orr ? k_persist<true, true, 128> : k_persist<true, false, 128>;
+        return orr ? k_persist<false, true, 128> : k_persist<false, false, 128>;
+    }
+    if (tw) return orr ? k_persist<true, true, 256> : k_persist<true, false, 256>;
+    return orr ? k_persist<false, true, 256> : k_persist<false, false, 256>;
 }
 
 }  // namespace
@@ -164,16 +173,16 @@ PersistFn persist_fn(bool tw, bool orr) {
 int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, int rs, cudaStream_t s,
                    int *grid_out) {
     const int nt = warps * 32 * rs;
-    if (ntiles <= 0 || nt < 96 || nt > 256) return TGA_ERR_INVALID;   // apply needs >= 3 warps
+    if (ntiles <= 0 || (nt != 128 && nt != 256)) return TGA_ERR_INVALID;   // apply needs >= 3 warps
     const int nw = nt / 32;
     const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0;
     const int nintra = tw ? d.m : (d.Wp - 1 + nw - 1) / nw;
     size_t sm = inter_smem_bytes(rows, warps);
     const size_t band = (size_t)band_smem_ints(d.Wp, nw) * sizeof(int);
     if (band > sm) sm = band;
-    if (tw && (size_t)kIntraSmemPerWarp * sizeof(int) > sm) sm = (size_t)kIntraSmemPerWarp * sizeof(int);
+    if (tw && (size_t)kIntraTabSmemInts * sizeof(int) > sm) sm = (size_t)kIntraTabSmemInts * sizeof(int);
     if (sm > 200 * 1024) return TGA_ERR_RANGE;
-    PersistFn fn = persist_fn(tw, orr);
+    PersistFn fn = persist_fn(tw, orr, nt);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
         cudaGetLastError();
         return TGA_ERR_CUDA;

@@ -81,6 +81,7 @@ EXPORTS = [
     ("tga_sync", ctypes.c_int, [_P]),
     ("tga_get_stats", ctypes.c_int, [_P, ctypes.POINTER(tga_stats)]),
     ("tga_set_move_log", ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    ("tga_get_op_candidates", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     ("tga_set_tile", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tga_get_tile", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("tga_eval_best_move_noalloc", ctypes.c_int, [ctypes.POINTER(tga_instance), ctypes.POINTER(tga_solution),
@@ -183,6 +184,13 @@ def tga_get_stats(ctx: int) -> dict:
     st = tga_stats()
     _check(_lib().tga_get_stats(_P(ctx), ctypes.byref(st)), "tga_get_stats")
     return st.as_dict()
+
+
+def tga_get_op_candidates(ctx: int):
+    """Candidates evaluated per operator rank (6 ints) over all evaluations."""
+    out = (ctypes.c_int64 * 6)()
+    _check(_lib().tga_get_op_candidates(_P(ctx), out), "tga_get_op_candidates")
+    return [int(v) for v in out]
 
 
 def tga_set_move_log(ctx: int, log_dev_ptr: int, capacity: int):
