@@ -163,8 +163,9 @@ int tga_descend(tga_ctx *ctx, int64_t max_steps, tga_stats *out_host);
  *      chunks of 64 steps (for profilers that do not trace kernels inside
  *      conditional graph bodies; also selected by the environment variable
  *      TGA_GRAPH=0).
- *  TGA_DESCENT_AUTO (default)  persistent for instances with
- *      n + m + 1 < 4096 positions, else the graph; falls back to the graph
+ *  TGA_DESCENT_AUTO (default)  the path tga_set_tile(ctx, 0, 0) measured
+ *      fastest; before any measurement, persistent for instances with
+ *      n + m + 1 < 4096 positions, else the graph.  Falls back to the graph
  *      when the cooperative launch is refused. */
 enum {
     TGA_DESCENT_AUTO = 0,
@@ -231,7 +232,12 @@ int tga_set_move_log(tga_ctx *ctx, uint64_t *log_dev, int64_t capacity);
 /* Choose the inter-route tile shape: rows per tile (8, 16, 32 or 64) and
  * warps per block (2, 4 or 8; 32 columns each); 0, 0 runs the built-in
  * autotuner (times every shape, including row-split ones, on the current
- * state).  Call after tga_build_attrs. */
+ * state).  Call after tga_build_attrs.  With the descent mode
+ * TGA_DESCENT_AUTO the autotuner then also times 24-step descents from the
+ * current solution along the graph path and along the persistent path under
+ * each of its block shapes, and the automatic mode keeps the fastest; the
+ * caller's solution is restored and the attributes rebuilt (counters reset),
+ * so the context is left as a fresh tga_build_attrs would leave it. */
 int tga_set_tile(tga_ctx *ctx, int32_t rows, int32_t warps);
 int tga_get_tile(tga_ctx *ctx, int32_t *rows, int32_t *warps);
 

@@ -35,6 +35,11 @@ struct tga_ctx {
     int mode = TGA_DESCENT_AUTO;
     int last_mode = TGA_DESCENT_AUTO;
     int persist_grid = 0;
+    // measured choice for the automatic mode (0: not measured, size rule)
+    // and the persistent path's tile shape (0: derived from the inter tile)
+    int auto_choice = 0;
+    int ptile_rows = 0, ptile_warps = 0, ptile_rs = 0;
+    int *saved = nullptr;              // workspace copy of the caller's solution (tuning)
 };
 
 namespace {
@@ -174,7 +179,23 @@ constexpr int kPersistAutoMaxWp = 4096;
 
 // Persistent descent with the context's tile shape; the row split is raised
 // until a block has at least 4 warps (the tile list does not depend on it).
+long long count_tiles(int Wp, int rows, int TC) {
+    const long long Wa = Wp - 1, nrt = (Wa + rows - 1) / rows, nct = (Wa + TC - 1) / TC;
+    long long t = 0;
+    for (long long I = 0; I < nrt; ++I) {
+        const long long j0 = (I * rows) / TC;
+        t += nct > j0 ? nct - j0 : 0;
+    }
+    return t;
+}
+
+int persist_shape(int rows, int warps, int rs, const Dev &d, cudaStream_t s, int *grid) {
+    return launch_persist(d, nullptr, (int)count_tiles(d.Wp, rows, warps * 32), rows, warps, rs, s, grid);
+}
+
 int try_persist(tga_ctx *c) {
+    if (c->ptile_rows)
+        return persist_shape(c->ptile_rows, c->ptile_warps, c->ptile_rs, c->d, c->stream, &c->persist_grid);
     int rs = c->tile_rs;
     while (c->tile_warps * 32 * rs < 128 && rs < 4 && c->tile_warps * rs * 2 <= 8 && c->tile_rows % (rs * 2) == 0)
         rs *= 2;
@@ -195,7 +216,9 @@ int descend_launch(tga_ctx *c, int64_t max_steps) {
     const char *env = getenv("TGA_GRAPH");
     if (env && env[0] == '0') mode = TGA_DESCENT_HOST;
     const bool automatic = mode == TGA_DESCENT_AUTO;
-    if (automatic) mode = c->d.Wp < kPersistAutoMaxWp ? TGA_DESCENT_PERSISTENT : TGA_DESCENT_GRAPH;
+    if (automatic)
+        mode = c->auto_choice ? c->auto_choice
+                              : (c->d.Wp < kPersistAutoMaxWp ? TGA_DESCENT_PERSISTENT : TGA_DESCENT_GRAPH);
     if (mode == TGA_DESCENT_PERSISTENT) {
         const int rc = try_persist(c);
         if (rc == TGA_OK) {
@@ -379,6 +402,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     const size_t o_ss = take(sizeof(int) * (size_t)d.Wp);
     const size_t o_seen = take(sizeof(int) * (size_t)(n + 1));
     const size_t o_intra = take(sizeof(int) * 10 * (size_t)(d.Wp + m));
+    const size_t o_saved = take(sizeof(int) * (size_t)(n + m + 1));
     const size_t o_pcol = take(sizeof(int) * (size_t)(n + 1) * (size_t)d.ldp);
     c->ws_bytes = off;
     if (cudaMallocAsync(&c->ws, c->ws_bytes, c->stream) != cudaSuccess) {
@@ -400,6 +424,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.seen = (int *)(base + o_seen);
     d.scr_intra = (int *)(base + o_intra);
     d.pcol = (int *)(base + o_pcol);
+    c->saved = (int *)(base + o_saved);
     if (cudaMemsetAsync(d.ctl, 0, sizeof(Control), c->stream) != cudaSuccess ||
         setup_kernel_attrs(d.Wp) != 0) {
         tga_destroy(c);
@@ -529,7 +554,7 @@ size_t tga_workspace_bytes(int32_t n_customers, int32_t n_routes) {
     auto take = [&](size_t bytes) { off = align_up(off + bytes, 256); };
     take(sizeof(Control)); take(4 * Wp); take(4 * (W + 1)); take(sizeof(BRec) * (W + 1));
     take(sizeof(ERec) * (W + 1)); take(sizeof(RouteRec) * m); take(8 * Wp); take(4 * Wp); take(4 * Wp);
-    take(4 * Wp); take(4 * (n + 1)); take(4 * 10 * (Wp + m)); take(4 * (n + 1) * ldp);
+    take(4 * Wp); take(4 * (n + 1)); take(4 * 10 * (Wp + m)); take(4 * (n + m + 1)); take(4 * (n + 1) * ldp);
     return off;
 }
 
@@ -566,6 +591,73 @@ int tga_set_move_log(tga_ctx *c, uint64_t *log_dev, int64_t capacity) {
     return TGA_OK;
 }
 
+// Time `steps` steps of a descent from the saved solution along one path
+// (persistent with the given shape, or the graph); milliseconds per
+// evaluation, or a negative value if the path cannot run.
+static float time_path(tga_ctx *c, int steps, bool persistent, int rows, int warps, int rs, cudaEvent_t e0,
+                cudaEvent_t e1) {
+    const size_t n = (size_t)c->d.n, m = (size_t)c->d.m;
+    cudaMemcpyAsync(c->d.tour, c->saved, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->d.route_start, c->saved + n, sizeof(int) * (m + 1), cudaMemcpyDeviceToDevice, c->stream);
+    if (tga_build_attrs(c) != TGA_OK) return -1.f;
+    launch_begin(c->d, steps, c->stream);
+    cudaEventRecord(e0, c->stream);
+    int rc = TGA_OK;
+    if (persistent) {
+        int grid = 0;
+        rc = persist_shape(rows, warps, rs, c->d, c->stream, &grid);
+    } else {
+        rc = build_graph(c);
+        if (!rc && cudaGraphLaunch(c->gexec, c->stream) != cudaSuccess) rc = TGA_ERR_CUDA;
+    }
+    cudaEventRecord(e1, c->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.f;
+    Control C;
+    if (rc || read_control(c, &C) || C.status || C.evals < 1) return -1.f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / (float)C.evals;
+}
+
+// Measured choice of the automatic descent path: short descents from the
+// current solution along the graph path (the tuned inter tile) and the
+// persistent path under each block shape of 128 or 256 threads; the fastest
+// per evaluation wins.  The caller's solution is restored and the
+// attributes rebuilt afterwards.
+static int tune_descent(tga_ctx *c, cudaEvent_t e0, cudaEvent_t e1) {
+    static const int pshapes[][3] = {{8, 2, 2},  {16, 2, 2}, {16, 4, 1}, {16, 4, 2}, {16, 2, 4},
+                                     {32, 2, 2}, {32, 4, 1}, {32, 4, 2}, {32, 8, 1}, {64, 4, 1}, {64, 8, 1}};
+    const int steps = 24;
+    const size_t n = (size_t)c->d.n, m = (size_t)c->d.m;
+    cudaMemcpyAsync(c->saved, c->d.tour, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->saved + n, c->d.route_start, sizeof(int) * (m + 1), cudaMemcpyDeviceToDevice, c->stream);
+    unsigned long long *log = c->d.log;
+    const long long cap = c->d.log_cap;
+    c->d.log = nullptr;                                  // tuning descents are not recorded
+    c->d.log_cap = 0;
+    drop_graph(c);
+    float best = time_path(c, steps, false, 0, 0, 0, e0, e1);
+    int choice = best > 0.f ? TGA_DESCENT_GRAPH : 0;
+    int br = 0, bw = 0, brs = 0;
+    for (const auto &p : pshapes) {
+        const float ms = time_path(c, steps, true, p[0], p[1], p[2], e0, e1);
+        if (ms > 0.f && (choice == 0 || ms < best)) {
+            best = ms;
+            choice = TGA_DESCENT_PERSISTENT;
+            br = p[0]; bw = p[1]; brs = p[2];
+        }
+    }
+    cudaGetLastError();
+    c->d.log = log;
+    c->d.log_cap = cap;
+    drop_graph(c);
+    c->auto_choice = choice;
+    c->ptile_rows = br; c->ptile_warps = bw; c->ptile_rs = brs;
+    cudaMemcpyAsync(c->d.tour, c->saved, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->d.route_start, c->saved + n, sizeof(int) * (m + 1), cudaMemcpyDeviceToDevice, c->stream);
+    return tga_build_attrs(c);
+}
+
 int tga_set_tile(tga_ctx *c, int32_t rows, int32_t warps) {
     if (!c) return TGA_ERR_INVALID;
     if (rows != 0 || warps != 0) return set_tiles(c, rows, warps);
@@ -593,11 +685,12 @@ int tga_set_tile(tga_ctx *c, int32_t rows, int32_t warps) {
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < bestms) { bestms = ms; br = s[0]; bw = s[1]; brs = s[2]; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     // leave the context as it was before tuning (no pending key)
     cudaMemsetAsync(&c->d.ctl->best_key, 0xff, sizeof(unsigned long long), c->stream);
     int rc = set_tiles(c, br, bw, brs);
+    if (!rc && c->mode == TGA_DESCENT_AUTO) rc = tune_descent(c, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     if (rc) return rc;
     return check_launch();
 }
