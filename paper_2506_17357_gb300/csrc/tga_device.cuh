@@ -565,17 +565,21 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
         // warp minimum rather than the lane's own keeps the whole warp off
         // this path on almost every row.
         if (!skip && m <= wbest) {
+            // the pair's best candidate: the first, in move-index order, whose
+            // delta is the minimum m (op rank first; within relocate and the
+            // or-opts the move of the lower anchor id first)
             const unsigned au = (unsigned)u2.w, avu = (unsigned)av;
-            TGA_TRY(dR1, au * W + avu);
-            TGA_TRY(dR2, avu * W + au);
-            TGA_TRY(dS, W2 + min(au, avu) * W + max(au, avu));
-            TGA_TRY(dX, 3u * W2 + (Uroute < Vroute ? au * W + avu : avu * W + au));
-            if (OR) {
-                TGA_TRY(dO2a, 4u * W2 + au * W + avu);
-                TGA_TRY(dO2b, 4u * W2 + avu * W + au);
-                TGA_TRY(dO3a, 5u * W2 + au * W + avu);
-                TGA_TRY(dO3b, 5u * W2 + avu * W + au);
-            }
+            const bool uf = au < avu;
+            const unsigned lo = uf ? au : avu, hi = uf ? avu : au;
+            unsigned op = 5, A = hi, B = lo;
+            if ((uf ? dR1 : dR2) == m) { op = 0; A = lo; B = hi; }
+            else if ((uf ? dR2 : dR1) == m) { op = 0; A = hi; B = lo; }
+            else if (dS == m) { op = 1; A = lo; B = hi; }
+            else if (dX == m) { op = 3; A = Uroute < Vroute ? au : avu; B = Uroute < Vroute ? avu : au; }
+            else if (OR && (uf ? dO2a : dO2b) == m) { op = 4; A = lo; B = hi; }
+            else if (OR && (uf ? dO2b : dO2a) == m) { op = 4; A = hi; B = lo; }
+            else if (OR && (uf ? dO3a : dO3b) == m) { op = 5; A = lo; B = hi; }
+            TGA_TRY(m, op * W2 + A * W + B);
         }
         wbest = __reduce_min_sync(0xffffffffu, best);
         // slide the stencil window one row down
