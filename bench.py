@@ -273,6 +273,7 @@ def bench_gpu(args):
     # (inter, intra, apply) + the write-back of the solution
     launches_per_step = 6 + 1 + (1 if persistent else 3 * evals + 1)
     op_cands = T.tga_get_op_candidates(ls.ctx)
+    pshape = T.tga_get_persistent_shape(ls.ctx)
 
     # ---- end to end through the public API with host buffers
     e2e_times = []
@@ -368,6 +369,7 @@ def bench_gpu(args):
         "config": {"workload": args.workload, "desc": desc, "instance_seed": args.seed,
                    "op_mask": mask, "tile_rows_warps": list(tile), "parallelism": f"replicas x{ws}",
                    "descent_path": T.DESCENT_NAMES[mode_used],
+                   "persistent_tile": list(pshape) if persistent else None,
                    "l2": "flushed between timed steps (512 MB write)"},
         "candidates_per_operator": op_cands,
         "e2e": {"value": e2e_value, "unit": "candidate moves/s", "h2d_bytes_per_step": int(h2d),

@@ -180,6 +180,11 @@ int tga_set_descent_mode(tga_ctx *ctx, int32_t mode);
  * NULL; 0 for the other paths). */
 int tga_get_descent_mode(tga_ctx *ctx, int32_t *last_used, int32_t *grid_out);
 
+/* The tile shape the persistent path uses (rows, column warps, row split):
+ * the one the autotuner measured fastest, else the inter-route tile with the
+ * row split raised to at least 4 warps per block. */
+int tga_get_persistent_shape(tga_ctx *ctx, int32_t *rows, int32_t *col_warps, int32_t *row_split);
+
 /* Descend every context to a local optimum (at most max_steps moves each) in
  * ONE persistent launch on ctxs[0]'s stream (all contexts on one device).
  * Each context is (re)built from its caller solution inside the launch.

@@ -708,6 +708,20 @@ int tga_get_descent_mode(tga_ctx *c, int32_t *last_used, int32_t *grid_out) {
     return TGA_OK;
 }
 
+int tga_get_persistent_shape(tga_ctx *c, int32_t *rows, int32_t *col_warps, int32_t *row_split) {
+    if (!c || !rows || !col_warps || !row_split) return TGA_ERR_INVALID;
+    if (c->ptile_rows) {
+        *rows = c->ptile_rows; *col_warps = c->ptile_warps; *row_split = c->ptile_rs;
+        return TGA_OK;
+    }
+    if (!c->tiles && c->built && c->d.Wp > 2) default_tiles(c);
+    int rs = c->tile_rs;
+    while (c->tile_warps * 32 * rs < 128 && rs < 4 && c->tile_warps * rs * 2 <= 8 && c->tile_rows % (rs * 2) == 0)
+        rs *= 2;
+    *rows = c->tile_rows; *col_warps = c->tile_warps; *row_split = rs;
+    return TGA_OK;
+}
+
 int tga_set_tile_shape(tga_ctx *c, int32_t rows, int32_t col_warps, int32_t row_split) {
     if (!c) return TGA_ERR_INVALID;
     return set_tiles(c, rows, col_warps, row_split);

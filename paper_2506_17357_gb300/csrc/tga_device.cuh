@@ -28,6 +28,33 @@ __device__ __forceinline__ void set_status(Control *C, int code) {
     atomicCAS(&C->status, 0, code);
 }
 
+// GPU-scope release/acquire operations (PTX memory model) for the hand-offs
+// between CTAs: lighter than a sequentially consistent fence around a
+// relaxed atomic.  A release by thread 0 after __syncthreads publishes the
+// whole block's earlier writes; an acquire by thread 0 followed by
+// __syncthreads orders the whole block's later reads.
+__device__ __forceinline__ int atom_add_acq_rel(int *p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void red_add_release(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ Seg shfl_seg_up(const Seg &s, int off) {
     Seg o;
     o.E = __shfl_up_sync(0xffffffffu, s.E, off);
@@ -1735,9 +1762,8 @@ __device__ void load_plan(const Control *C, StepPlan *dst) {
 // apply launch that follows on the stream.  The count re-arms itself.
 __device__ void eval_tail(const Dev &d, int total) {
     Control *C = d.ctl;
-    __threadfence();
-    if (atomicAdd(&C->eval_done, 1) != total - 1) return;
-    __threadfence();
+    // release: this CTA's key is folded in; acquire: so are all the others'
+    if (atom_add_acq_rel(&C->eval_done, 1) != total - 1) return;
     C->eval_done = 0;
     StepPlan P;
     decode_plan(d, nullptr, P);

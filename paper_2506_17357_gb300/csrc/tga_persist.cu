@@ -41,30 +41,27 @@ __device__ bool grid_barrier(unsigned long long *count, unsigned long long targe
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(count, 1ull);
+        red_add_release(count, 1ull);                  // publishes the block's writes
         int ok = 1;
-        if (*(volatile unsigned long long *)count < target) {
+        if (ld_acquire(count) < target) {
             const long long t0 = now_ns();
-            while (*(volatile unsigned long long *)count < target) {
+            while (ld_acquire(count) < target) {
                 if (now_ns() - t0 > limit_ns) { ok = 0; break; }
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
 }
 
-// Wait (one thread) until *seq == want, at most limit_ns.
+// Wait (one thread) until *seq == want, at most limit_ns (acquire).
 __device__ bool wait_seq(const int *seq, int want, long long limit_ns) {
-    if (*(const volatile int *)seq != want) {
+    if (ld_acquire(seq) != want) {
         const long long t0 = now_ns();
-        while (*(const volatile int *)seq != want)
+        while (ld_acquire(seq) != want)
             if (now_ns() - t0 > limit_ns) return false;
     }
-    __threadfence();
     return true;
 }
 
@@ -111,16 +108,14 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const 
         // applies it itself; every other CTA waits for the publication (this
         // wait stands in for a barrier) and permutes distance columns
         if (tid == 0) {
-            __threadfence();
             s_ok = 0;
-            if (atomicAdd(&C->eval_done, 1) == G - 1) {
-                __threadfence();
+            // release: this CTA's key is folded in; acquire: so are all the others'
+            if (atom_add_acq_rel(&C->eval_done, 1) == G - 1) {
                 C->eval_done = 0;
                 decode_plan(d, nullptr, sP);
                 C->plan = sP;
                 C->plan_cta = cta;
-                __threadfence();
-                atomicExch(&C->plan_seq, step);
+                st_release(&C->plan_seq, step);        // publishes the plan
                 s_ok = 1;
                 s_app = cta;
             } else {

@@ -89,6 +89,8 @@ EXPORTS = [
     ("tga_profile_inter", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     ("tga_set_descent_mode", ctypes.c_int, [_P, ctypes.c_int32]),
     ("tga_get_descent_mode", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    ("tga_get_persistent_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                                ctypes.POINTER(ctypes.c_int32)]),
     ("tga_set_tile_shape", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     ("tga_get_tile_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32)]),
@@ -232,6 +234,13 @@ def tga_get_descent_mode(ctx: int):
     m, g = ctypes.c_int32(), ctypes.c_int32()
     _check(_lib().tga_get_descent_mode(_P(ctx), ctypes.byref(m), ctypes.byref(g)), "tga_get_descent_mode")
     return m.value, g.value
+
+
+def tga_get_persistent_shape(ctx: int):
+    r, w, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib().tga_get_persistent_shape(_P(ctx), ctypes.byref(r), ctypes.byref(w), ctypes.byref(s)),
+           "tga_get_persistent_shape")
+    return r.value, w.value, s.value
 
 
 def tga_set_tile_shape(ctx: int, rows: int, col_warps: int, row_split: int):
