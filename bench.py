@@ -195,6 +195,65 @@ def only_descent(args):
     ls.close()
 
 
+OP_NAMES = ["relocate", "swap", "2-opt", "2-opt*", "or-opt-2", "or-opt-3"]
+
+
+def breakdown(inst, sol, mask, dev, stream, reps=20, step_count=200):
+    """Per-operator and per-step GPU times of the workload, outside the timed
+    region (the paper's per-operator and key-step analyses, Sections 6.6 and
+    6.7).  Per operator: one neighbourhood evaluation with only that operator
+    enabled (tga_eval_best_move, per-step kernels, autotuned inter tile) on the
+    initial solution.  Per step: evaluation and update times of the first
+    steps of the descent through tga_eval_best_move / tga_apply_move."""
+    import torch
+    from paper_2506_17357_gb300 import tga as T
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    per_op = {}
+    for op in range(6):
+        if not (mask >> op) & 1:
+            continue
+        ls = T.LocalSearch(inst, sol, 1 << op, device=dev, stream=stream).build()
+        ls.set_descent_mode(T.DESCENT_GRAPH)
+        ls.set_tile(0, 0)
+        T.tga_eval_best_move(ls.ctx, ls.move.data_ptr())
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            T.tga_eval_best_move(ls.ctx, ls.move.data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        us = 1e3 * e0.elapsed_time(e1) / reps
+        st = ls.stats()
+        cands = st["candidates"] / max(1, st["evaluations"])
+        per_op[OP_NAMES[op]] = {"us_per_evaluation": us, "candidates": int(cands),
+                                "candidates_per_s": cands / (us * 1e-6)}
+        ls.close()
+    ls = T.LocalSearch(inst, sol, mask, device=dev, stream=stream).build()
+    ls.set_descent_mode(T.DESCENT_GRAPH)
+    ls.set_tile(0, 0)
+    ev, up = [], []
+    for _ in range(step_count):
+        e0.record(stream)
+        T.tga_eval_best_move(ls.ctx, ls.move.data_ptr())
+        e1.record(stream)
+        ls.apply_current_move()
+        e2.record(stream)
+        e2.synchronize()
+        ev.append(1e3 * e0.elapsed_time(e1))
+        up.append(1e3 * e1.elapsed_time(e2))
+        mv = ls.move.cpu().numpy()
+        if not mv[5] or mv[0] >= 0:
+            break
+    ls.close()
+    return {"per_operator": per_op,
+            "per_step": {"steps": len(ev), "evaluation_us_median": float(np.median(ev)),
+                         "update_us_median": float(np.median(up)),
+                         "path": "per-step kernels launched one call at a time (eval: begin + inter + intra + "
+                                 "finalize; update: apply of the caller-given move + write-back)"}}
+
+
 def bench_gpu(args):
     import torch
     import torch.distributed as dist
@@ -351,6 +410,7 @@ def bench_gpu(args):
     else:
         roof = inter_roof
     ls.close()
+    brk = breakdown(inst, sol, mask, dev, stream) if rank == 0 else None
 
     if ws > 1:
         dist.barrier()
@@ -377,6 +437,7 @@ def bench_gpu(args):
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "roofline": roof,
+        "breakdown": brk,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, seconds=args.cpu_seconds)
@@ -519,7 +580,7 @@ def bench_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(args, seconds=15.0):
+def cpu_baseline(args, seconds=15.0, per_op_seconds=1.0):
     """The oracle's concatenation evaluator (plain single-threaded C) on the
     host: best-improvement steps of the same workload from the same initial
     solution, as many as fit in ``seconds``."""
@@ -538,9 +599,23 @@ def cpu_baseline(args, seconds=15.0):
             break
         cur = O.apply_move(inst, cur, bm["op"], bm["a"], bm["b"])
     dt = time.perf_counter() - t0
+    # per operator: the oracle's evaluation of the initial solution with only
+    # that operator enabled (about a second each)
+    per_op = {}
+    for op in range(6):
+        if not (mask >> op) & 1 or per_op_seconds <= 0:
+            continue
+        t1 = time.perf_counter()
+        reps = c1 = 0
+        while time.perf_counter() - t1 < per_op_seconds:
+            c1 += O.best_move(inst, sol, 1 << op, "concat")["candidates"]
+            reps += 1
+        d1 = time.perf_counter() - t1
+        per_op[OP_NAMES[op]] = {"ms_per_evaluation": 1e3 * d1 / reps, "candidates_per_s": c1 / d1}
     return {"value": cands / dt, "unit": "candidate moves/s", "cores": 1, "kind": "oracle",
             "sample": f"first {k} best-improvement evaluations of {args.workload} seed {args.seed} "
-                      f"(concatenation evaluator), {dt:.1f} s"}
+                      f"(concatenation evaluator), {dt:.1f} s",
+            "per_operator": per_op}
 
 
 def bench_reference(args):
@@ -550,11 +625,11 @@ def bench_reference(args):
     desc, make, mask = WORKLOADS[args.workload]
     per = max(2.0, args.cpu_seconds / max(1, args.steps))
     for _ in range(args.warmup):
-        cpu_baseline(args, seconds=min(per, 2.0))
+        cpu_baseline(args, seconds=min(per, 2.0), per_op_seconds=0.0)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args, seconds=per))
+        vals.append(cpu_baseline(args, seconds=per, per_op_seconds=0.0))
     dt = time.perf_counter() - t0
     value = float(np.mean([v["value"] for v in vals]))
     line = {"impl": "reference", "metric": "move evals/s", "value": value, "unit": "candidate moves/s",
