@@ -21,6 +21,10 @@ Functions and the passages they follow:
   operator; must agree exactly with "def".
 * ``descend``: the feasible/infeasible search loop of the appendix algorithm
   with best improvement: accept iff delta < 0, stop at a local optimum.
+* ``granular=nbr`` (every evaluating function): the edge-based extraction of
+  Section 5.3.1 with a granular mask given as the theta nearest customers of
+  each customer (rows of ``nbr``); the kept candidates are listed in
+  ``tga_oracle.h``.
 """
 from __future__ import annotations
 
@@ -45,7 +49,8 @@ class _Inst(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("capacity", ctypes.c_int32),
                 ("has_tw", ctypes.c_int32), ("w_load", ctypes.c_int32), ("w_tw", ctypes.c_int32),
                 ("dist", ctypes.c_void_p), ("demand", ctypes.c_void_p), ("service", ctypes.c_void_p),
-                ("early", ctypes.c_void_p), ("late", ctypes.c_void_p)]
+                ("early", ctypes.c_void_p), ("late", ctypes.c_void_p),
+                ("theta", ctypes.c_int32), ("nbr", ctypes.c_void_p)]
 
 
 class _Move(ctypes.Structure):
@@ -108,23 +113,28 @@ class OracleInstance:
     """Host copy of an instance laid out for the C oracle.  ``inst`` is any
     object with the fields of ``instances.Instance``."""
 
-    def __init__(self, inst, n_routes: int):
+    def __init__(self, inst, n_routes: int, granular=None):
         self.n = int(inst.n)
         self.m = int(n_routes)
         self._arrs = [_c32(inst.dist).reshape(-1), _c32(inst.demand), _c32(inst.service),
                       _c32(inst.tw_early), _c32(inst.tw_late)]
         d, dem, svc, e, l = self._arrs
+        theta, nbr_ptr = 0, None
+        if granular is not None:
+            self._nbr = _c32(granular)
+            assert self._nbr.ndim == 2 and self._nbr.shape[0] == self.n + 1
+            theta, nbr_ptr = int(self._nbr.shape[1]), self._nbr.ctypes.data
         self.c = _Inst(self.n, self.m, int(inst.capacity), int(bool(inst.has_tw)), int(inst.w_load),
                        int(inst.w_tw), d.ctypes.data, dem.ctypes.data, svc.ctypes.data,
-                       e.ctypes.data, l.ctypes.data)
+                       e.ctypes.data, l.ctypes.data, theta, nbr_ptr)
         self.W = self.n + 1 + self.m
 
     def ref(self):
         return ctypes.byref(self.c)
 
 
-def _oi(inst, sol) -> OracleInstance:
-    return OracleInstance(inst, int(np.asarray(sol.route_start).shape[0]) - 1)
+def _oi(inst, sol, granular=None) -> OracleInstance:
+    return OracleInstance(inst, int(np.asarray(sol.route_start).shape[0]) - 1, granular)
 
 
 def route_cost(inst, nodes, n_routes: int = 1) -> int:
@@ -151,15 +161,15 @@ def check_solution(inst, sol) -> int:
     return int(_load().orc_check_solution(oi.ref(), t.ctypes.data, rs.ctypes.data))
 
 
-def count_candidates(inst, sol, op_mask: int) -> int:
-    oi = _oi(inst, sol)
+def count_candidates(inst, sol, op_mask: int, granular=None) -> int:
+    oi = _oi(inst, sol, granular)
     t, rs = _c32(sol.tour), _c32(sol.route_start)
     return int(_load().orc_count_candidates(oi.ref(), t.ctypes.data, rs.ctypes.data, op_mask))
 
 
-def best_move(inst, sol, op_mask: int, method: str = "def"):
+def best_move(inst, sol, op_mask: int, method: str = "def", granular=None):
     """Returns dict(found, delta, idx, op, a, b, key, candidates)."""
-    oi = _oi(inst, sol)
+    oi = _oi(inst, sol, granular)
     t, rs = _c32(sol.tour), _c32(sol.route_start)
     mv = _Move()
     nc = ctypes.c_int64(0)
@@ -184,11 +194,11 @@ def unpack_key(key: int):
     return (int(key) >> 32) - (1 << 31), int(key) & 0xFFFFFFFF
 
 
-def list_moves(inst, sol, op_mask: int, method: str = "def"):
+def list_moves(inst, sol, op_mask: int, method: str = "def", granular=None):
     """All candidates as (idx array uint64, delta array int64)."""
-    oi = _oi(inst, sol)
+    oi = _oi(inst, sol, granular)
     t, rs = _c32(sol.tour), _c32(sol.route_start)
-    cnt = count_candidates(inst, sol, op_mask)
+    cnt = count_candidates(inst, sol, op_mask, granular)
     idx = np.zeros(max(cnt, 1), dtype=np.uint64)
     dl = np.zeros(max(cnt, 1), dtype=np.int64)
     got = _load().orc_list_moves(oi.ref(), t.ctypes.data, rs.ctypes.data, op_mask, METHODS[method],
@@ -211,10 +221,10 @@ def apply_move(inst, sol, op: int, a: int, b: int):
 
 
 def descend(inst, sol, op_mask: int, method: str = "def", max_steps: int = 1 << 62,
-            log_cap: int = 1 << 20):
+            log_cap: int = 1 << 20, granular=None):
     """Best-improvement descent on a copy of ``sol``.
     Returns (final solution, steps, key log (uint64 array), candidates)."""
-    oi = _oi(inst, sol)
+    oi = _oi(inst, sol, granular)
     new = sol.copy()
     new.tour = _c32(new.tour).copy()
     new.route_start = _c32(new.route_start).copy()

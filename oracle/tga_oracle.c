@@ -404,9 +404,29 @@ typedef struct {
     int count_only;
 } scan_t;
 
+/* Granular mask of the edge-based extraction (see tga_oracle.h). */
+static int in_mask(const orc_inst *in, int32_t x, int32_t y)
+{
+    for (int32_t k = 0; k < in->theta; ++k)
+        if (in->nbr[(int64_t)x * in->theta + k] == y) return 1;
+    return 0;
+}
+
+static int granular_kept(const orc_inst *in, const view_t *v, int32_t op, int32_t a, int32_t b)
+{
+    const int32_t n = v->n;
+    if (op == 2 || v->route_of[a] == v->route_of[b]) return 1;     /* intra-route */
+    if (op == 0 || op == 4 || op == 5) return b > n || in_mask(in, a, b);
+    if (op == 1) return in_mask(in, a, b) || in_mask(in, b, a);
+    if (a > n && b > n) return 0;                                    /* 2-opt* */
+    if (a > n || b > n) return 1;
+    return in_mask(in, a, b) || in_mask(in, b, a);
+}
+
 static void visit(scan_t *s, int32_t op, int32_t a, int32_t b)
 {
     const view_t *v = s->v;
+    if (s->in->theta > 0 && !granular_kept(s->in, v, op, a, b)) return;
     s->count++;
     if (s->count_only) return;
     int64_t d;

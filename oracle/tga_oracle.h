@@ -30,10 +30,22 @@
 extern "C" {
 #endif
 
+/* theta > 0 restricts the neighbourhood to the edge-based extraction of
+ * Section 5.3.1 with a granular mask: nbr[x*theta + k] (k < theta) are the
+ * customers y with M[x][y] = 1 for customer x (row 0 unused).  Intra-route
+ * candidates are always evaluated (route-based extraction); an inter-route
+ * candidate (op, a, b) is kept when
+ *   relocate / or-opt (the run starting at a moves after b): b is a start
+ *     depot, or M[a][b];
+ *   swap: M[a][b] or M[b][a];
+ *   2-opt*: exactly one of a, b is a start depot, or M[a][b] or M[b][a].
+ * theta = 0: the full neighbourhood (node-based extraction). */
 typedef struct {
     int32_t n, m, capacity, has_tw, w_load, w_tw;
     const int32_t *dist;                 /* (n+1)*(n+1), row-major */
     const int32_t *demand, *service, *early, *late;   /* n+1 each */
+    int32_t theta;
+    const int32_t *nbr;                  /* (n+1)*theta, or NULL when theta = 0 */
 } orc_inst;
 
 typedef struct {

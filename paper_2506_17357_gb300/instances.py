@@ -267,6 +267,24 @@ def random_split_solution(inst: Instance, seed: int) -> Solution:
     return Solution(np.asarray(perm, dtype=np.int32), np.asarray(starts, dtype=np.int32))
 
 
+def granular_neighbors(inst: Instance, theta: int) -> np.ndarray:
+    """Granular mask of the edge-based extraction (Section 5.3.1; neighbour
+    lists in the manner of Vidal et al. 2013): row x (customers 1..n) holds
+    the theta customers y != x with the smallest (c(x, y), y); row 0 is unused
+    (zeros).  An input, like the distance matrix: both evaluators read it."""
+    n = int(inst.n)
+    if not 1 <= theta <= n - 1:
+        raise ValueError(f"theta must be in [1, n-1], got {theta}")
+    d = np.asarray(inst.dist, dtype=np.int64)
+    out = np.zeros((n + 1, theta), dtype=np.int32)
+    ids = np.arange(1, n + 1, dtype=np.int64)
+    for x in range(1, n + 1):
+        key = d[x, 1:] * (n + 2) + ids            # distance first, then the smaller id
+        key[x - 1] = np.iinfo(np.int64).max       # not its own neighbour
+        out[x] = ids[np.argsort(key, kind="stable")[:theta]]
+    return out
+
+
 def solution_seed(instance_seed: int) -> int:
     return instance_seed + 1_000_000
 

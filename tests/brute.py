@@ -45,16 +45,40 @@ def _locate(routes, x):
     raise KeyError(x)
 
 
-def brute_moves(inst, routes, mask):
-    """dict move_index -> delta over the whole candidate set."""
+def brute_moves(inst, routes, mask, nbr=None):
+    """dict move_index -> delta over the whole candidate set.  ``nbr``: the
+    granular mask of the edge-based extraction (Section 5.3.1) as neighbour
+    rows; an inter-route candidate is kept by the rule of the edge-based
+    reading (relocate/or-opt: destination a start depot or in the moved
+    customer's row; swap: either in the other's row; 2-opt*: one start depot,
+    or either in the other's row), intra-route candidates always."""
     n, m = inst.n, len(routes)
     W = n + 1 + m
     base = total_cost(inst, routes)
     depot_anchor = {n + 1 + r: r for r in range(m)}
     anchors = list(range(1, n + 1)) + list(depot_anchor)
     out = {}
+    near = None if nbr is None else {x: set(int(y) for y in nbr[x]) for x in range(1, n + 1)}
+
+    def route_of(x):
+        return depot_anchor[x] if x in depot_anchor else _locate(routes, x)[0]
+
+    def kept(op, a, b):
+        if near is None or op == 2 or route_of(a) == route_of(b):
+            return True
+        if op in (0, 4, 5):
+            return b in depot_anchor or b in near[a]
+        if op == 1:
+            return b in near[a] or a in near[b]
+        if a in depot_anchor and b in depot_anchor:
+            return False
+        if a in depot_anchor or b in depot_anchor:
+            return True
+        return b in near[a] or a in near[b]
 
     def record(op, a, b, new_routes):
+        if not kept(op, a, b):
+            return
         idx = op * W * W + a * W + b
         assert idx not in out
         out[idx] = total_cost(inst, new_routes) - base

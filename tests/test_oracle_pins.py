@@ -306,3 +306,59 @@ def test_apply_rejects_non_candidates():
         O.apply_move(inst, sol, 0, u, pred)         # v == pred(u)
     with pytest.raises(ValueError):
         O.apply_move(inst, sol, 1, 5, 5)            # swap needs a < b
+
+
+# ----------------------------------------------------------------------------
+# edge-based extraction with a granular mask (Section 5.3.1)
+
+def test_granular_neighbors_are_the_nearest_customers():
+    inst = I.vrptw(40, 8)
+    nbr = I.granular_neighbors(inst, 6)
+    assert nbr.shape == (41, 6) and (nbr[0] == 0).all()
+    for x in range(1, 41):
+        order = sorted((int(inst.dist[x][y]), y) for y in range(1, 41) if y != x)
+        assert nbr[x].tolist() == [y for _, y in order[:6]]
+
+
+@pytest.mark.parametrize("kind", ["cvrp", "vrptw"])
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("theta", [1, 2, 4])
+def test_granular_candidate_sets_against_brute_force(kind, seed, theta):
+    """The kept candidates and their deltas equal the brute force restricted by
+    an independent Python statement of the same mask rule."""
+    n = 6 + seed % 3
+    inst, sol = _tiny(kind, n, 700 + seed, m_extra_empty=1)
+    nbr = I.granular_neighbors(inst, theta)
+    expect = brute_moves(inst, sol.routes(), I.MASK_ALL, nbr)
+    for method in ("def", "concat"):
+        idx, dl = O.list_moves(inst, sol, I.MASK_ALL, method, granular=nbr)
+        assert dict(zip(idx.tolist(), dl.tolist())) == expect, method
+        assert O.count_candidates(inst, sol, I.MASK_ALL, granular=nbr) == len(expect)
+    bm = O.best_move(inst, sol, I.MASK_ALL, "def", granular=nbr)
+    assert (bm["delta"], bm["idx"]) == min((d, i) for i, d in expect.items())
+
+
+def test_granular_full_mask_is_the_node_based_set():
+    """With every other customer in every row, the edge-based set is the full
+    node-based set minus the 2-opt* exchanges of two whole routes."""
+    inst, sol = _tiny("vrptw", 8, 31, m_extra_empty=1)
+    n, m = inst.n, sol.n_routes
+    W = n + 1 + m
+    full_idx, full_dl = O.list_moves(inst, sol, I.MASK_ALL, "def")
+    g_idx, g_dl = O.list_moves(inst, sol, I.MASK_ALL, "def", granular=I.granular_neighbors(inst, n - 1))
+    full = {int(i): int(d) for i, d in zip(full_idx, full_dl)
+            if not (i // (W * W) == 3 and (i % (W * W)) // W > n and i % W > n)}
+    assert {int(i): int(d) for i, d in zip(g_idx, g_dl)} == full
+
+
+def test_granular_descent_definition_equals_concatenation():
+    inst = I.vrptw(35, 12)
+    inst.capacity = 90
+    sol = I.random_split_solution(inst, 13)
+    nbr = I.granular_neighbors(inst, 5)
+    f1, s1, l1, c1 = O.descend(inst, sol, I.MASK_ALL, "def", granular=nbr)
+    f2, s2, l2, c2 = O.descend(inst, sol, I.MASK_ALL, "concat", granular=nbr)
+    assert s1 == s2 > 0 and (l1 == l2).all() and c1 == c2
+    assert (f1.tour == f2.tour).all() and O.check_solution(inst, f1) == 0
+    # the restricted descent stops at a local optimum of the restricted set
+    assert O.best_move(inst, f1, I.MASK_ALL, "def", granular=nbr)["delta"] >= 0
