@@ -267,8 +267,9 @@ def bench_gpu(args):
     desc, make, mask = WORKLOADS[args.workload]
     seed = args.seed + rank
     inst, sol = make(seed)
+    nbr = I.granular_neighbors(inst, args.granular) if args.granular else None
     stream = torch.cuda.Stream(dev)
-    ls = T.LocalSearch(inst, sol, mask, device=dev, stream=stream).build()
+    ls = T.LocalSearch(inst, sol, mask, device=dev, stream=stream, granular=nbr).build()
     if args.tile:                                              # pinned shape (profiler runs)
         tile = ls.set_tile(*[int(x) for x in args.tile.split(",")])
     else:
@@ -360,6 +361,22 @@ def bench_gpu(args):
     peak_ops = 152 * 4 * 32 * sm_mhz_max * 1e6              # INT32 lane-ops/s at issue peak
     peak_desc = f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz_max:.0f} MHz (issue peak)"
 
+    def kept_inter_ops():
+        """Edge-based extraction: integer ops of the inter-route candidates the
+        mask keeps in the current state (one evaluation's per-operator
+        counts minus the closed-form intra-route counts)."""
+        before = T.tga_get_op_candidates(ls.ctx)
+        T.tga_eval_best_move(ls.ctx, ls.move.data_ptr())
+        after = T.tga_get_op_candidates(ls.ctx)
+        tour_h, rs_h = ls.solution()
+        L = np.diff(rs_h).astype(np.int64)
+        intra = [int((L * (L - 1)).sum()), int((L * (L - 1) // 2).sum()), int((L * (L - 1) // 2).sum()), 0,
+                 int((np.maximum(L - 1, 0) * np.maximum(L - 2, 0)).sum()),
+                 int((np.maximum(L - 2, 0) * np.maximum(L - 3, 0)).sum())]
+        table = OPS_TW if inst.has_tw else OPS_CVRP
+        return sum(table[op] * (after[op] - before[op] - (intra[op] if (mask >> op) & 1 else 0))
+                   for op in range(6))
+
     def inter_kernel_roof():
         restore()
         T.tga_build_attrs(ls.ctx)
@@ -368,19 +385,24 @@ def bench_gpu(args):
         n_steps = steps[-1]
         for j in range(probes):
             ms = T.tga_profile_inter(ls.ctx, reps=20)
-            tour_h, rs_h = ls.solution()
-            lens = np.diff(rs_h)
-            total_ops += algorithmic_ops(inst.n, lens, mask, inst.has_tw)
+            if args.granular:
+                total_ops += kept_inter_ops()
+            else:
+                tour_h, rs_h = ls.solution()
+                lens = np.diff(rs_h)
+                total_ops += algorithmic_ops(inst.n, lens, mask, inst.has_tw)
             total_ms += ms
             if j + 1 < probes:
                 T.tga_descend(ls.ctx, max_steps=max(1, n_steps // (probes - 1)))
         achieved = total_ops / (total_ms / 1e3)
-        return {"bound": "alu", "kernel": "k_eval_inter", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+        kname = "k_eval_edges" if args.granular else "k_eval_inter"
+        return {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops, "peak_source": peak_desc,
                 "ms_per_launch": total_ms / probes, "ops_per_launch": total_ops / probes,
                 "work": "inter-route candidates of the state (per-candidate integer ops x candidates), "
                         "mean over 5 states along the trajectory",
-                "traffic": measured_traffic(args.workload, "k_eval_inter"),
+                "traffic": measured_traffic(args.workload + (f"-granular{args.granular}" if args.granular else ""),
+                                            kname),
                 "kernel_source_hash": kernel_source_hash()}
 
     inter_roof = inter_kernel_roof()
@@ -410,7 +432,7 @@ def bench_gpu(args):
     else:
         roof = inter_roof
     ls.close()
-    brk = breakdown(inst, sol, mask, dev, stream) if rank == 0 else None
+    brk = breakdown(inst, sol, mask, dev, stream) if rank == 0 and not args.granular else None
 
     if ws > 1:
         dist.barrier()
@@ -429,6 +451,8 @@ def bench_gpu(args):
         "config": {"workload": args.workload, "desc": desc, "instance_seed": args.seed,
                    "op_mask": mask, "tile_rows_warps": list(tile), "parallelism": f"replicas x{ws}",
                    "descent_path": T.DESCENT_NAMES[mode_used],
+                   "extraction": (f"edge-based, granular mask of the {args.granular} nearest customers"
+                                  if args.granular else "node-based, full neighbourhood"),
                    "persistent_tile": list(pshape) if persistent else None,
                    "l2": "flushed between timed steps (512 MB write)"},
         "candidates_per_operator": op_cands,
@@ -587,12 +611,14 @@ def cpu_baseline(args, seconds=15.0, per_op_seconds=1.0):
     import oracle as O
     desc, make, mask = WORKLOADS[args.workload]
     inst, sol = make(args.seed)
+    theta = getattr(args, "granular", 0)
+    nbr = I.granular_neighbors(inst, theta) if theta else None
     cur = sol
     t0 = time.perf_counter()
     cands = 0
     k = 0
     while time.perf_counter() - t0 < seconds:
-        bm = O.best_move(inst, cur, mask, "concat")
+        bm = O.best_move(inst, cur, mask, "concat", granular=nbr)
         cands += bm["candidates"]
         k += 1
         if not bm["found"] or bm["delta"] >= 0:
@@ -608,13 +634,13 @@ def cpu_baseline(args, seconds=15.0, per_op_seconds=1.0):
         t1 = time.perf_counter()
         reps = c1 = 0
         while time.perf_counter() - t1 < per_op_seconds:
-            c1 += O.best_move(inst, sol, 1 << op, "concat")["candidates"]
+            c1 += O.best_move(inst, sol, 1 << op, "concat", granular=nbr)["candidates"]
             reps += 1
         d1 = time.perf_counter() - t1
         per_op[OP_NAMES[op]] = {"ms_per_evaluation": 1e3 * d1 / reps, "candidates_per_s": c1 / d1}
     return {"value": cands / dt, "unit": "candidate moves/s", "cores": 1, "kind": "oracle",
             "sample": f"first {k} best-improvement evaluations of {args.workload} seed {args.seed} "
-                      f"(concatenation evaluator), {dt:.1f} s",
+                      f"(concatenation evaluator{', granular mask theta=%d' % theta if theta else ''}), {dt:.1f} s",
             "per_operator": per_op}
 
 
@@ -657,6 +683,8 @@ def main():
                     help="with --only-descent: stop after this many moves (0: run to the local optimum)")
     ap.add_argument("--tile", default="",
                     help="inter tile shape rows,warps,row_split (default: autotune on the initial state)")
+    ap.add_argument("--granular", type=int, default=0,
+                    help="edge-based extraction with the THETA nearest customers per customer (0: full neighbourhood)")
     ap.add_argument("--batch-jobs", type=int, default=256)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -278,6 +278,25 @@ int tga_profile_inter(tga_ctx *ctx, int32_t reps, float *ms_per_launch);
 int tga_eval_best_move_noalloc(const tga_instance *inst, const tga_solution *sol, uint32_t op_mask,
                                tga_stream_t stream, tga_move *out_dev);
 
+/* Edge-based extraction (Section 5.3.1, "edge-based extraction", the
+ * paper's ETGA): restrict the inter-route candidates of every evaluation to
+ * the node pairs of a granular mask M, given as theta > 0 entries per
+ * customer: nbr_dev[x*theta + k], k < theta, are the customers y with
+ * M[x][y] = 1 (DEVICE memory, (n+1)*theta int32, row 0 ignored, caller-owned
+ * and valid until the mask is replaced or the context destroyed).  Intra-route
+ * candidates are always evaluated.  An inter-route candidate (op, a, b) is
+ * kept when: relocate / or-opt (the run starting at a moves after b): b is a
+ * start depot, or M[a][b]; swap: M[a][b] or M[b][a]; 2-opt*: exactly one of
+ * a, b is a start depot, or M[a][b] or M[b][a].  Candidate counts
+ * (tga_stats.candidates, tga_get_op_candidates) count the kept candidates.
+ * theta = 0 restores the full neighbourhood.  Entries that are not another
+ * customer, or theta > n-1, give TGA_ERR_INVALID.  The edge-based extraction
+ * runs on the graph and host-launched descent paths (the persistent path
+ * returns TGA_ERR_STATE and the automatic mode takes the graph);
+ * tga_descend_batch refuses such contexts (TGA_ERR_STATE).  Synchronises the
+ * context's stream. */
+int tga_set_granular(tga_ctx *ctx, const int32_t *nbr_dev, int32_t theta);
+
 /* Diagnostic: synchronise and copy one internal array to host memory.
  * what: 0 control block, 1 positions (int32 anchor per position), 2 anchor
  * positions, 3 base attributes (64 B per anchor), 4 hoisted constants

@@ -40,6 +40,7 @@ struct tga_ctx {
     int auto_choice = 0;
     int ptile_rows = 0, ptile_warps = 0, ptile_rs = 0;
     int *saved = nullptr;              // workspace copy of the caller's solution (tuning)
+    void *granular = nullptr;          // reverse-entry flags of the mask rows + a check word
 };
 
 namespace {
@@ -478,6 +479,7 @@ int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_h
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return TGA_ERR_INVALID;
         if (ctxs[i]->device != ctxs[0]->device) return TGA_ERR_INVALID;
+        if (ctxs[i]->d.theta > 0) return TGA_ERR_STATE;      // the batched kernel has no edge-based path
     }
     int first = run_batch(ctxs, n, max_steps, 0, nullptr);
     for (int i = 0; i < n; ++i) {
@@ -801,9 +803,44 @@ int tga_debug_read(tga_ctx *c, int32_t what, void *host_dst, size_t bytes, size_
     return TGA_OK;
 }
 
+int tga_set_granular(tga_ctx *c, const int32_t *nbr_dev, int32_t theta) {
+    if (!c || theta < 0) return TGA_ERR_INVALID;
+    if (theta > 0 && (!nbr_dev || theta > c->d.n - 1)) return TGA_ERR_INVALID;
+    if (c->granular) cudaFreeAsync(c->granular, c->stream);
+    c->granular = nullptr;
+    c->d.theta = 0; c->d.nbr = nullptr; c->d.nbr_rev = nullptr;
+    drop_graph(c);
+    c->auto_choice = 0;
+    if (theta == 0) return check_launch();
+    const size_t flags = align_up((size_t)(c->d.n + 1) * (size_t)theta, 256);
+    if (cudaMallocAsync(&c->granular, flags + 256, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        c->granular = nullptr;
+        return TGA_ERR_NOMEM;
+    }
+    unsigned char *rev = (unsigned char *)c->granular;
+    int *bad = (int *)(rev + flags);
+    Dev g = c->d;
+    g.theta = theta; g.nbr = nbr_dev;
+    int h_bad = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) { launch_granular_setup(g, rev, bad, c->stream); e = cudaGetLastError(); }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess || h_bad) {
+        cudaFreeAsync(c->granular, c->stream);
+        c->granular = nullptr;
+        return e != cudaSuccess ? TGA_ERR_CUDA : TGA_ERR_INVALID;
+    }
+    c->d.theta = theta; c->d.nbr = nbr_dev; c->d.nbr_rev = rev;
+    return TGA_OK;
+}
+
 int tga_destroy(tga_ctx *c) {
     if (!c) return TGA_ERR_INVALID;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->granular) cudaFreeAsync(c->granular, c->stream);
+    c->granular = nullptr;
     drop_graph(c);
     if (c->tiles) cudaFreeAsync(c->tiles, c->stream);
     if (c->ws) cudaFreeAsync(c->ws, c->stream);

@@ -348,9 +348,9 @@ __device__ __forceinline__ void check_perm_one(const Dev &d, int x) {
 
 __device__ void finish_block(const Dev &d) {
     Control *C = d.ctl;
-    __shared__ long long s_cost[32], s_l2[32], s_l1[32], s_lm2[32];
+    __shared__ long long s_cost[32], s_l2[32], s_l1[32], s_lm2[32], s_q1[32], s_q2[32];
     __shared__ int s_maxL[32], s_maxLoad[32];
-    long long cost = 0, l2 = 0, l1 = 0, lm2 = 0;
+    long long cost = 0, l2 = 0, l1 = 0, lm2 = 0, q1 = 0, q2 = 0;
     int maxL = 0, maxLoad = 0;
     if (C->status == 0) {
         for (int r = threadIdx.x; r < d.m; r += blockDim.x) {
@@ -359,6 +359,8 @@ __device__ void finish_block(const Dev &d) {
             l2 += (long long)R.len * R.len;
             l1 += max(R.len - 1, 0);
             lm2 += max(R.len - 2, 0);
+            q1 += (long long)max(R.len - 1, 0) * max(R.len - 1, 0);
+            q2 += (long long)max(R.len - 2, 0) * max(R.len - 2, 0);
             maxL = max(maxL, R.len);
             maxLoad = max(maxLoad, R.load);
         }
@@ -368,22 +370,28 @@ __device__ void finish_block(const Dev &d) {
         l2 += __shfl_xor_sync(0xffffffffu, l2, off);
         l1 += __shfl_xor_sync(0xffffffffu, l1, off);
         lm2 += __shfl_xor_sync(0xffffffffu, lm2, off);
+        q1 += __shfl_xor_sync(0xffffffffu, q1, off);
+        q2 += __shfl_xor_sync(0xffffffffu, q2, off);
         maxL = max(maxL, __shfl_xor_sync(0xffffffffu, maxL, off));
         maxLoad = max(maxLoad, __shfl_xor_sync(0xffffffffu, maxLoad, off));
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) {
         s_cost[warp] = cost; s_l2[warp] = l2; s_l1[warp] = l1; s_lm2[warp] = lm2;
+        s_q1[warp] = q1; s_q2[warp] = q2;
         s_maxL[warp] = maxL; s_maxLoad[warp] = maxLoad;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int w = 1; w < nw; ++w) {
             cost += s_cost[w]; l2 += s_l2[w]; l1 += s_l1[w]; lm2 += s_lm2[w];
+            q1 += s_q1[w]; q2 += s_q2[w];
             maxL = max(maxL, s_maxL[w]); maxLoad = max(maxLoad, s_maxLoad[w]);
         }
         C->cost = cost; C->initial_cost = cost;
         C->sumL2 = l2; C->sumLm1 = l1; C->sumLm2 = lm2;
+        C->sumLm1sq = q1; C->sumLm2sq = q2;
+        for (int op = 0; op < 6; ++op) C->gcount[op] = 0;
         C->maxL = maxL; C->maxLoad = maxLoad;
         C->steps = 0; C->evals = 0; C->cand_total = 0;
         for (int op = 0; op < 6; ++op) C->cand_op[op] = 0;
@@ -619,6 +627,112 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
         t12 = col[(i + 3) * LDT + 2];
         t21 = col[(i + 4) * LDT + 1];
     }
+}
+
+// ---------------------------------------------------------------------------
+// inter-route evaluation, edge-based extraction (Section 5.3.1): the
+// candidates of one directed mask edge u -> v (v a customer in u's mask row)
+// or of u and the start depot v of another route, with the expressions of
+// inter_tile and the stencil distances gathered from the matrix by the
+// positional index.  Kept per edge: u (and its runs of 2 and 3) moved after
+// v; swap and 2-opt* on a customer edge once per unordered pair (rev: the
+// reverse entry exists, so only the edge with u < v takes them); 2-opt* of u
+// with a start depot.  Intra-route pairs are left to the route kernels.
+// Returns a bit mask of the operator ranks evaluated (one candidate each).
+template <bool TW, bool OR>
+__device__ unsigned edge_candidates(const Dev &d, int u, int v, bool rev, int &best, unsigned &bidx) {
+    const unsigned mask = d.op_mask;
+    const int4 *ur = reinterpret_cast<const int4 *>(d.erec + u);
+    const int4 *vr = reinterpret_cast<const int4 *>(d.erec + v);
+    const int4 u0 = TGA_LDG(ur + 0), u1 = TGA_LDG(ur + 1), u2 = TGA_LDG(ur + 2);
+    const int4 v0 = TGA_LDG(vr + 0), v1 = TGA_LDG(vr + 1), v2 = TGA_LDG(vr + 2);
+    int4 u3 = make_int4(0, 0, 0, 0), u4 = u3, u5 = u3, u6 = u3, v4 = u3, v5 = u3;
+    if (OR) u3 = TGA_LDG(ur + 3);
+    if (TW) { u4 = TGA_LDG(ur + 4); u5 = TGA_LDG(ur + 5); v4 = TGA_LDG(vr + 4); v5 = TGA_LDG(vr + 5); }
+    if (TW && OR) u6 = TGA_LDG(ur + 6);
+    const int pu = TGA_LDG(d.pos_of + u), pv = TGA_LDG(d.pos_of + v);
+    const int Uroute = u0.x, Vroute = v0.x;
+    unsigned evaluated = 0;
+    if (Uroute != Vroute) {
+        const bool vcust = v <= d.n;
+        // neighbours in the giant sequence (the next route's start depot stands
+        // for the end depot; past the sentinel, the depot)
+        auto nd = [&](int p) { return (p >= 0 && p < d.Wp) ? node_of(TGA_LDG(d.seq + p), d.n) : 0; };
+        const int xu = u, xv = vcust ? v : 0;
+        const int um = nd(pu - 1), up = nd(pu + 1), upp = nd(pu + 2);
+        const int vm = vcust ? nd(pv - 1) : 0, vp = nd(pv + 1), vpp = nd(pv + 2);
+        const int t00 = dmat(d, xu, xv), t01 = dmat(d, xu, vp), t10 = dmat(d, up, xv), t11 = dmat(d, up, vp);
+        const int t21 = dmat(d, upp, vp), t12 = dmat(d, up, vpp), tm10 = dmat(d, um, xv), t0m1 = dmat(d, xu, vm);
+        const int wL = d.wL, wT = d.wT;
+        const unsigned W = (unsigned)d.W, W2 = W * W;
+        const int Ud = u0.y, Urem1 = u0.z, UK2 = u1.y, ULQd = u1.z, UFc = u1.w;
+        const int UGc = u2.x, Uloadf = u2.y, UloadgQ = u2.z;
+        const int Vd = v0.y, VK1 = v0.w, VLQ = v1.x, VK2 = v1.y, VLQd = v1.z, VFc = v1.w;
+        const int VGc = v2.x, Vloadf = v2.y, VloadgQ = v2.z;
+        const int Ue = u4.x, Ul = u4.y, Us = u4.z, Utau = u4.w, ULg = u5.x, UtauP = u5.y;
+        const int Ve = v4.x, Vl = v4.y, Vs = v4.z, Vtau = v4.w, VLg = v5.x, VtauP = v5.y;
+        const unsigned au = (unsigned)u, av = (unsigned)v;
+        // u moved after v
+        if ((mask & 1u) && Urem1 < (kBig >> 1)) {
+            int dl = Urem1 + VK1 + t00 + t01 + wL * max(VLQ + Ud, 0);
+            if (TW) {
+                const int a1 = Vtau + t00, w1 = max(a1 - Ul, 0);
+                const int a2 = max(a1, Ue) - w1 + Us + t01, w2 = max(a2 - VLg, 0);
+                dl += wT * (w1 + w2);
+            }
+            evaluated |= 1u;
+            TGA_TRY(dl, au * W + av);
+        }
+        // the runs of 2 and 3 starting at u moved after v
+        if (OR) {
+            const int UC2 = u3.x, Uld2 = u3.y, UC3 = u3.z, Uld3 = u3.w;
+            if (UC2 < (kBig >> 1)) {
+                int dl = UC2 + VK1 + t00 + t11 + wL * max(VLQ + Uld2, 0);
+                if (TW) {
+                    const int UE2 = u5.z, UL2 = u5.w, UDm2 = u6.x;
+                    const int a1 = Vtau + t00, w1 = max(a1 - UL2, 0);
+                    const int a2 = max(a1, UE2) - w1 + UDm2 + t11, w2 = max(a2 - VLg, 0);
+                    dl += wT * (w1 + w2);
+                }
+                evaluated |= 16u;
+                TGA_TRY(dl, 4u * W2 + au * W + av);
+            }
+            if (UC3 < (kBig >> 1)) {
+                int dl = UC3 + VK1 + t00 + t21 + wL * max(VLQ + Uld3, 0);
+                if (TW) {
+                    const int UE3 = u6.y, UL3 = u6.z, UDm3 = u6.w;
+                    const int a1 = Vtau + t00, w1 = max(a1 - UL3, 0);
+                    const int a2 = max(a1, UE3) - w1 + UDm3 + t21, w2 = max(a2 - VLg, 0);
+                    dl += wT * (w1 + w2);
+                }
+                evaluated |= 32u;
+                TGA_TRY(dl, 5u * W2 + au * W + av);
+            }
+        }
+        const bool pair_once = vcust && (!rev || au < av);
+        // swap u <-> v
+        if ((mask & 2u) && pair_once) {
+            int dl = UK2 + VK2 + tm10 + t10 + t0m1 + t01 + wL * (max(ULQd + Vd, 0) + max(VLQd + Ud, 0));
+            if (TW) {
+                const int a1 = UtauP + tm10, w1 = max(a1 - Vl, 0);
+                const int a2 = max(a1, Ve) - w1 + Vs + t10, w2 = max(a2 - ULg, 0);
+                const int b1 = VtauP + t0m1, x1 = max(b1 - Ul, 0);
+                const int b2 = max(b1, Ue) - x1 + Us + t01, x2 = max(b2 - VLg, 0);
+                dl += wT * (w1 + w2 + x1 + x2);
+            }
+            evaluated |= 2u;
+            TGA_TRY(dl, W2 + min(au, av) * W + max(au, av));
+        }
+        // 2-opt*: head(u) + tail after v, head(v) + tail after u
+        if ((mask & 8u) && (pair_once || !vcust)) {
+            int dl = UFc + VGc + VFc + UGc + t01 + t10 +
+                     wL * (max(Uloadf + VloadgQ, 0) + max(Vloadf + UloadgQ, 0));
+            if (TW) dl += wT * (max(Utau + t01 - VLg, 0) + max(Vtau + t10 - ULg, 0));
+            evaluated |= 8u;
+            TGA_TRY(dl, 3u * W2 + (Uroute < Vroute ? au * W + av : av * W + au));
+        }
+    }
+    return evaluated;
 }
 
 // ---------------------------------------------------------------------------
@@ -1557,6 +1671,9 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
                                       max(oB - 2, 0);
                 C->sumL2 = l2; C->sumLm1 = l1; C->sumLm2 = lm2;
                 C->cand_per_eval = candidate_count(d.n, d.m, d.op_mask, l2, l1, lm2);
+                auto sqp = [&](int x) { return x > 0 ? (long long)x * x : 0LL; };
+                C->sumLm1sq += sqp(pl.nLA - 1) + sqp(pl.nLB - 1) - sqp(oA - 1) - sqp(oB - 1);
+                C->sumLm2sq += sqp(pl.nLA - 2) + sqp(pl.nLB - 2) - sqp(oA - 2) - sqp(oB - 2);
             }
             const int maxL = max(s_maxL, max(pl.nLA, two ? pl.nLB : 0));
             const int maxLoad = max(s_maxLoad, max(loadA, two ? loadB : 0));

@@ -103,6 +103,11 @@ struct Control {
     int plan_seq, eval_done;
     int plan_cta, pad5[3];                    // persistent descent: the CTA applying the step
     long long cand_op[6];                     // candidates evaluated per operator rank, all evaluations
+    // edge-based extraction: sum max(0,L-1)^2, sum max(0,L-2)^2 (intra-route
+    // or-opt counts) and the inter-route candidates the running evaluation
+    // kept, per operator rank
+    long long sumLm1sq, sumLm2sq;
+    unsigned long long gcount[6];
 };
 
 // Everything a kernel needs, passed by value.
@@ -127,6 +132,11 @@ struct Dev {
     int *scr_src;             // [Wp]
     int *seen;                // [n+1] permutation check scratch
     int *scr_intra;           // [10 * (Wp+m)] per-element arrays of routes too long for shared memory
+    // edge-based extraction (theta > 0): granular mask rows nbr[x*theta + k]
+    // and, per entry, whether the reverse entry exists (x in the row of nbr[x*theta+k])
+    int theta;
+    const int *nbr;
+    const unsigned char *nbr_rev;
 };
 
 __host__ __device__ inline int node_of(int anchor, int n) { return anchor <= n ? anchor : 0; }
@@ -230,10 +240,39 @@ __host__ __device__ inline long long candidate_count(long long n, long long m, u
     return c;
 }
 
+// Intra-route candidates of one evaluation per operator rank (closed form):
+// a route of L customers has L(L-1) relocate and L(L-1)/2 swap and 2-opt
+// candidates, (L-1)(L-2) or-opt-2 and (L-2)(L-3) or-opt-3 candidates.
+__host__ __device__ inline long long intra_candidates(int op, long long n, unsigned mask, long long sumL2,
+                                                      long long sumLm1, long long sumLm2, long long sumLm1sq,
+                                                      long long sumLm2sq) {
+    if (!(mask & (1u << op))) return 0;
+    switch (op) {
+        case 0: return sumL2 - n;
+        case 1: case 2: return (sumL2 - n) / 2;
+        case 3: return 0;
+        case 4: return sumLm1sq - sumLm1;
+        default: return sumLm2sq - sumLm2;
+    }
+}
+
 // Count one evaluation of the current state (evaluation counter, candidate
-// totals, per operator).
+// totals, per operator).  Edge-based extraction: the closed-form intra-route
+// candidates plus the inter-route ones the evaluation kernel counted.
 __device__ inline void count_evaluation(const Dev &d, Control *C) {
     C->evals += 1;
+    if (d.theta > 0) {
+        long long tot = 0;
+        for (int op = 0; op < 6; ++op) {
+            const long long c = intra_candidates(op, d.n, d.op_mask, C->sumL2, C->sumLm1, C->sumLm2,
+                                                 C->sumLm1sq, C->sumLm2sq) + (long long)C->gcount[op];
+            C->cand_op[op] += c;
+            tot += c;
+            C->gcount[op] = 0;
+        }
+        C->cand_total += tot;
+        return;
+    }
     C->cand_total += C->cand_per_eval;
     for (int op = 0; op < 6; ++op)
         C->cand_op[op] += op_candidates(op, d.n, d.m, d.op_mask, C->sumL2, C->sumLm1, C->sumLm2);
@@ -280,6 +319,9 @@ void launch_begin(const Dev &d, long long max_steps, cudaStream_t s);
 // launch; returns TGA_OK or an error code (nothing launched on error).
 int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, int rs, cudaStream_t s,
                    int *grid_out);
+// Edge-based extraction: validate the mask rows and mark reverse entries;
+// *bad_dev (device int) is set when an entry is not another customer.
+void launch_granular_setup(const Dev &d, unsigned char *rev, int *bad_dev, cudaStream_t s);
 size_t inter_smem_bytes(int rows, int warps);
 int setup_kernel_attrs(int max_band);
 

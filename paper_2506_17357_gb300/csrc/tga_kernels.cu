@@ -76,6 +76,56 @@ __global__ void __launch_bounds__(256) k_eval_inter(Dev d, int TR, int RS, int t
     if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
+// Edge-based extraction: one thread per kept pair (u, v), u a customer and
+// v one of the theta entries of u's mask row or one of the m start depots.
+// The per-operator candidate counts are folded into the control block before
+// the key, so the evaluation's last CTA sees them.
+template <bool TW, bool OR>
+__global__ void __launch_bounds__(256) k_eval_edges(Dev d, int tail) {
+    const int done = *(volatile int *)&d.ctl->done;
+    const int per = d.theta + d.m;
+    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int best = kBestInit;
+    unsigned bidx = 0xffffffffu;
+    unsigned evaluated = 0;                   // bit op: this thread evaluated an op-rank candidate
+    if (item < (long long)d.n * per) {
+        const int u = (int)(item / per) + 1, col = (int)(item - (long long)(u - 1) * per);
+        int v = d.n + 1 + (col - d.theta);
+        bool rev = false;
+        if (col < d.theta) {
+            const size_t e = (size_t)u * d.theta + col;
+            v = __ldg(d.nbr + e);
+            rev = __ldg(d.nbr_rev + e) != 0;
+        }
+        evaluated = edge_candidates<TW, OR>(d, u, v, rev, best, bidx);
+    }
+    if (done) return;
+    for (int op = 0; op < 6; ++op) {
+        const unsigned c = __popc(__ballot_sync(0xffffffffu, (evaluated >> op) & 1u));
+        if ((threadIdx.x & 31) == 0 && c) atomicAdd(&d.ctl->gcount[op], (unsigned long long)c);
+    }
+    const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
+    block_min_to(key, &d.ctl->best_key);
+    if (tail && threadIdx.x == 0) eval_tail(d, tail);
+}
+
+// Mask rows of the edge-based extraction: every entry must be another
+// customer; rev marks entries whose reverse entry exists.
+__global__ void k_granular_setup(Dev d, unsigned char *rev, int *bad) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)d.n * d.theta) return;
+    const int u = (int)(t / d.theta) + 1;
+    const int v = d.nbr[(size_t)u * d.theta + (t - (long long)(u - 1) * d.theta)];
+    unsigned char r = 0;
+    if (v < 1 || v > d.n || v == u) {
+        atomicExch(bad, 1);
+    } else {
+        for (int k = 0; k < d.theta; ++k)
+            if (d.nbr[(size_t)v * d.theta + k] == u) r = 1;
+    }
+    rev[(size_t)u * d.theta + (t - (long long)(u - 1) * d.theta)] = r;
+}
+
 // VRPTW intra-route moves: one block of kIntraWarps warps per route
 // (subsequence tables in kIntraTabSmemInts ints of dynamic shared memory).
 __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d, int tail) {
@@ -182,6 +232,7 @@ __global__ void k_begin(Dev d, long long max_steps) {
     C->eval_done = 0;
     C->plan_ready = 0;
     C->plan_done = 0;
+    for (int op = 0; op < 6; ++op) C->gcount[op] = 0;
     if (C->status != 0 || !C->built) { C->done = 1; return; }
     C->done = 0;
     C->local_opt = 0;
@@ -229,8 +280,22 @@ void launch_build(const Dev &d, cudaStream_t s) {
     k_pcol_init<<<(int)blocks, 256, 0, s>>>(d);
 }
 
+long long edge_items(const Dev &d) { return (long long)d.n * (d.theta + d.m); }
+
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs,
                   int tail) {
+    if (d.theta > 0) {          // edge-based extraction
+        const int blocks = (int)((edge_items(d) + 255) / 256);
+        const bool orr = (d.op_mask & 48u) != 0;
+        if (d.has_tw) {
+            if (orr) k_eval_edges<true, true><<<blocks, 256, 0, s>>>(d, tail);
+            else k_eval_edges<true, false><<<blocks, 256, 0, s>>>(d, tail);
+        } else {
+            if (orr) k_eval_edges<false, true><<<blocks, 256, 0, s>>>(d, tail);
+            else k_eval_edges<false, false><<<blocks, 256, 0, s>>>(d, tail);
+        }
+        return;
+    }
     if (ntiles <= 0) return;
     const size_t sm = inter_smem_bytes(rows, warps);
     const bool orr = (d.op_mask & 48u) != 0;
@@ -247,7 +312,16 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
 // VRPTW: one block per route; CVRP: one warp per moved position, 8 per block.
 int intra_blocks(const Dev &d) { return d.has_tw ? d.m : (d.Wp - 1 + 7) / 8; }
 
-int eval_blocks(const Dev &d, int ntiles) { return (ntiles > 0 ? ntiles : 0) + intra_blocks(d); }
+int eval_blocks(const Dev &d, int ntiles) {
+    if (d.theta > 0) return (int)((edge_items(d) + 255) / 256) + intra_blocks(d);
+    return (ntiles > 0 ? ntiles : 0) + intra_blocks(d);
+}
+
+void launch_granular_setup(const Dev &d, unsigned char *rev, int *bad_dev, cudaStream_t s) {
+    const long long t = (long long)d.n * d.theta;
+    if (t <= 0) return;
+    k_granular_setup<<<(int)((t + 255) / 256), 256, 0, s>>>(d, rev, bad_dev);
+}
 
 void launch_intra(const Dev &d, cudaStream_t s, int tail) {
     if (d.has_tw) k_eval_intra<<<intra_blocks(d), kIntraWarps * 32, kIntraTabSmemInts * sizeof(int), s>>>(d, tail);

@@ -168,6 +168,7 @@ PersistFn persist_fn(bool tw, bool orr, int nt) {
 int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, int rs, cudaStream_t s,
                    int *grid_out) {
     const int nt = warps * 32 * rs;
+    if (d.theta > 0) return TGA_ERR_STATE;                // edge-based extraction: per-step path only
     if (ntiles <= 0 || (nt != 128 && nt != 256)) return TGA_ERR_INVALID;   // apply needs >= 3 warps
     const int nw = nt / 32;
     const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0;

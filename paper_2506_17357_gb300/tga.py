@@ -81,6 +81,7 @@ EXPORTS = [
     ("tga_sync", ctypes.c_int, [_P]),
     ("tga_get_stats", ctypes.c_int, [_P, ctypes.POINTER(tga_stats)]),
     ("tga_set_move_log", ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    ("tga_set_granular", ctypes.c_int, [_P, _P, ctypes.c_int32]),
     ("tga_get_op_candidates", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     ("tga_set_tile", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tga_get_tile", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
@@ -195,6 +196,10 @@ def tga_get_op_candidates(ctx: int):
     return [int(v) for v in out]
 
 
+def tga_set_granular(ctx: int, nbr_dev_ptr: int, theta: int):
+    _check(_lib().tga_set_granular(_P(ctx), _P(nbr_dev_ptr or None), theta), "tga_set_granular")
+
+
 def tga_set_move_log(ctx: int, log_dev_ptr: int, capacity: int):
     _check(_lib().tga_set_move_log(_P(ctx), _P(log_dev_ptr or None), capacity), "tga_set_move_log")
 
@@ -282,7 +287,7 @@ class LocalSearch:
     (a torch.cuda.Stream or None for the current stream)."""
 
     def __init__(self, inst, sol, op_mask: int, device="cuda:0", stream=None, log_capacity: int = 0,
-                 pinned: bool = False):
+                 pinned: bool = False, granular=None):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -313,6 +318,12 @@ class LocalSearch:
         self.ctx = tga_create(self.c_inst, self.c_sol, self.op_mask, self.stream.cuda_stream)
         if self.log is not None:
             tga_set_move_log(self.ctx, self.log.data_ptr(), log_capacity)
+        self.nbr = None
+        if granular is not None:         # edge-based extraction: mask rows (n+1, theta)
+            nbr = np.ascontiguousarray(granular, dtype=np.int32)
+            with torch.cuda.stream(self.stream):
+                self.nbr = torch.from_numpy(nbr.reshape(-1)).to(self.device)
+            tga_set_granular(self.ctx, self.nbr.data_ptr(), int(nbr.shape[1]))
 
     # -- reuse the device buffers for another solution / instance of the same size
     def reload(self, inst=None, sol=None):
