@@ -182,7 +182,8 @@ def only_descent(args):
     from paper_2506_17357_gb300 import tga as T
     desc, make, mask = WORKLOADS[args.workload]
     inst, sol = make(args.seed)
-    ls = T.LocalSearch(inst, sol, mask).build()
+    nbr = I.granular_neighbors(inst, args.granular) if args.granular else None
+    ls = T.LocalSearch(inst, sol, mask, granular=nbr).build()
     if args.tile:
         tile = ls.set_tile(*[int(x) for x in args.tile.split(",")])
     else:
