@@ -397,10 +397,6 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     const size_t o_brec = take(sizeof(BRec) * (size_t)(W + 1));
     const size_t o_erec = take(sizeof(ERec) * (size_t)(W + 1));
     const size_t o_rrec = take(sizeof(RouteRec) * (size_t)m);
-    const size_t o_chg = take(sizeof(int2) * (size_t)d.Wp);
-    const size_t o_sa = take(sizeof(int) * (size_t)d.Wp);
-    const size_t o_sr = take(sizeof(int) * (size_t)d.Wp);
-    const size_t o_ss = take(sizeof(int) * (size_t)d.Wp);
     const size_t o_seen = take(sizeof(int) * (size_t)(n + 1));
     const size_t o_intra = take(sizeof(int) * 10 * (size_t)(d.Wp + m));
     const size_t o_saved = take(sizeof(int) * (size_t)(n + m + 1));
@@ -418,10 +414,6 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.brec = (BRec *)(base + o_brec);
     d.erec = (ERec *)(base + o_erec);
     d.rrec = (RouteRec *)(base + o_rrec);
-    d.chg = (int2 *)(base + o_chg);
-    d.scr_anchor = (int *)(base + o_sa);
-    d.scr_route = (int *)(base + o_sr);
-    d.scr_src = (int *)(base + o_ss);
     d.seen = (int *)(base + o_seen);
     d.scr_intra = (int *)(base + o_intra);
     d.pcol = (int *)(base + o_pcol);
@@ -555,8 +547,8 @@ size_t tga_workspace_bytes(int32_t n_customers, int32_t n_routes) {
     size_t off = 0;
     auto take = [&](size_t bytes) { off = align_up(off + bytes, 256); };
     take(sizeof(Control)); take(4 * Wp); take(4 * (W + 1)); take(sizeof(BRec) * (W + 1));
-    take(sizeof(ERec) * (W + 1)); take(sizeof(RouteRec) * m); take(8 * Wp); take(4 * Wp); take(4 * Wp);
-    take(4 * Wp); take(4 * (n + 1)); take(4 * 10 * (Wp + m)); take(4 * (n + m + 1)); take(4 * (n + 1) * ldp);
+    take(sizeof(ERec) * (W + 1)); take(sizeof(RouteRec) * m);
+    take(4 * (n + 1)); take(4 * 10 * (Wp + m)); take(4 * (n + m + 1)); take(4 * (n + 1) * ldp);
     return off;
 }
 

@@ -395,7 +395,7 @@ __device__ void finish_block(const Dev &d) {
         C->maxL = maxL; C->maxLoad = maxLoad;
         C->steps = 0; C->evals = 0; C->cand_total = 0;
         for (int op = 0; op < 6; ++op) C->cand_op[op] = 0;
-        C->done = 0; C->local_opt = 0; C->chg_count = 0;
+        C->done = 0; C->local_opt = 0;
         C->plan_ready = 0; C->plan_done = 0;
         C->best_key = kNoKey;
         C->step_limit = 0x7fffffffffffffffLL;

@@ -84,7 +84,7 @@ struct Control {
     unsigned long long best_key;              // min packed key of the running evaluation
     long long steps, evals, cand_total, cost, initial_cost, step_limit, cand_per_eval;
     long long sumL2, sumLm1, sumLm2;          // sum L^2, sum max(0,L-1), sum max(0,L-2)
-    int done, status, chg_count, local_opt;
+    int done, status, pad1, local_opt;
     int maxL, maxLoad;                        // longest route and heaviest load (range check)
     int maxc, maxl, maxs, maxd, maxe, built;
     int last_op, last_a, last_b, last_delta;
@@ -126,10 +126,6 @@ struct Dev {
     Control *ctl;
     unsigned long long *log;  // optional key log
     long long log_cap;
-    int2 *chg;                // [Wp] position changes (dst, src) of the last move
-    int *scr_anchor;          // [Wp] apply scratch
-    int *scr_route;           // [Wp]
-    int *scr_src;             // [Wp]
     int *seen;                // [n+1] permutation check scratch
     int *scr_intra;           // [10 * (Wp+m)] per-element arrays of routes too long for shared memory
     // edge-based extraction (theta > 0): granular mask rows nbr[x*theta + k]

@@ -49,10 +49,6 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
     const size_t o_brec = take(sizeof(BRec) * (W + 1));
     const size_t o_erec = take(sizeof(ERec) * (W + 1));
     const size_t o_rrec = take(sizeof(RouteRec) * m);
-    const size_t o_chg = take(sizeof(int2) * P);
-    const size_t o_sa = take(sizeof(int) * P);
-    const size_t o_sr = take(sizeof(int) * P);
-    const size_t o_ss = take(sizeof(int) * P);
     const size_t o_seen = take(sizeof(int) * (n + 1));
     const size_t o_intra = take(sizeof(int) * 10 * (P + m));
     const size_t o_tiles = take(sizeof(int2) * tiles_upper_bound(P));
@@ -64,10 +60,6 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
         d.brec = (BRec *)(base + o_brec);
         d.erec = (ERec *)(base + o_erec);
         d.rrec = (RouteRec *)(base + o_rrec);
-        d.chg = (int2 *)(base + o_chg);
-        d.scr_anchor = (int *)(base + o_sa);
-        d.scr_route = (int *)(base + o_sr);
-        d.scr_src = (int *)(base + o_ss);
         d.seen = (int *)(base + o_seen);
         d.scr_intra = (int *)(base + o_intra);
         d.pcol = (int *)(base + o_pcol);
@@ -81,8 +73,8 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
 constexpr size_t noalloc_max_bytes() {
     const size_t P = kNoAllocMaxPositions, N1 = P, M = P - 1, W1 = P + 1;
     return align256(sizeof(Control)) + align256(4 * P) + align256(4 * W1) + align256(sizeof(BRec) * W1) +
-           align256(sizeof(ERec) * W1) + align256(sizeof(RouteRec) * M) + align256(8 * P) +
-           3 * align256(4 * P) + align256(4 * N1) + align256(4 * 10 * (P + M)) +
+           align256(sizeof(ERec) * W1) + align256(sizeof(RouteRec) * M) + align256(4 * N1) +
+           align256(4 * 10 * (P + M)) +
            align256(sizeof(int2) * tiles_upper_bound(P)) + align256(4 * N1 * ldp_for(P));
 }
 
