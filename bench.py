@@ -168,6 +168,26 @@ class ClockSampler:
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_replicas(total_s, candidates, device):
+    """Whole-job figures of N independent replicas (one per rank): the
+    slowest rank's time and the candidates of all ranks.  Single process:
+    the inputs themselves."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_s), float(candidates)
+    t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(candidates)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
+def replica_seed(base_seed, rank):
+    """Instance seed of a rank's replica: every rank descends its own instance."""
+    return base_seed + rank
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -266,7 +286,7 @@ def bench_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     desc, make, mask = WORKLOADS[args.workload]
-    seed = args.seed + rank
+    seed = replica_seed(args.seed, rank)
     inst, sol = make(seed)
     nbr = I.granular_neighbors(inst, args.granular) if args.granular else None
     stream = torch.cuda.Stream(dev)
@@ -315,15 +335,7 @@ def bench_gpu(args):
         torch.cuda.synchronize()
     clocks = clk.summary()
     total = float(sum(times))
-    t_max = total
-    c_all = cands
-    if ws > 1:
-        t = torch.tensor([total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        c = torch.tensor([cands], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        c_all = float(c.item())
+    t_max, c_all = reduce_replicas(total, cands, dev)
     value = c_all / t_max
     tlo_ms = 1e3 * total / args.steps
     evals = stats["evaluations"]
