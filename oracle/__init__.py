@@ -11,7 +11,9 @@ Functions and the passages they follow:
 
 * ``route_cost`` / ``solution_cost``: Section 2 objective with the penalised
   load excess and the time-warp relaxation (Section 4.3.3), by forward
-  simulation.
+  simulation; with pickups (VRPSPDTW, an instance whose ``pickup`` is not
+  None) the load excess is that of the largest load on board
+  (``route_peak_load``).
 * ``best_move(method="def")``: the plain definition -- every candidate of
   relocate / swap / 2-opt / 2-opt* / or-opt (Section 4.1) is built by route
   surgery and costed from scratch; the smallest (delta, move index) wins
@@ -50,7 +52,7 @@ class _Inst(ctypes.Structure):
                 ("has_tw", ctypes.c_int32), ("w_load", ctypes.c_int32), ("w_tw", ctypes.c_int32),
                 ("dist", ctypes.c_void_p), ("demand", ctypes.c_void_p), ("service", ctypes.c_void_p),
                 ("early", ctypes.c_void_p), ("late", ctypes.c_void_p),
-                ("theta", ctypes.c_int32), ("nbr", ctypes.c_void_p)]
+                ("theta", ctypes.c_int32), ("nbr", ctypes.c_void_p), ("pickup", ctypes.c_void_p)]
 
 
 class _Move(ctypes.Structure):
@@ -76,6 +78,8 @@ def _load():
         P = ctypes.c_void_p
         lib.orc_route_cost.restype = ctypes.c_int64
         lib.orc_route_cost.argtypes = [ctypes.POINTER(_Inst), P, ctypes.c_int32]
+        lib.orc_route_peak_load.restype = ctypes.c_int64
+        lib.orc_route_peak_load.argtypes = [ctypes.POINTER(_Inst), P, ctypes.c_int32]
         lib.orc_route_warp.restype = ctypes.c_int64
         lib.orc_route_warp.argtypes = [ctypes.POINTER(_Inst), P, ctypes.c_int32]
         lib.orc_solution_cost.restype = ctypes.c_int64
@@ -124,9 +128,15 @@ class OracleInstance:
             self._nbr = _c32(granular)
             assert self._nbr.ndim == 2 and self._nbr.shape[0] == self.n + 1
             theta, nbr_ptr = int(self._nbr.shape[1]), self._nbr.ctypes.data
+        pick = getattr(inst, "pickup", None)
+        pick_ptr = None
+        if pick is not None:
+            self._pick = _c32(pick)
+            assert self._pick.shape == (self.n + 1,)
+            pick_ptr = self._pick.ctypes.data
         self.c = _Inst(self.n, self.m, int(inst.capacity), int(bool(inst.has_tw)), int(inst.w_load),
                        int(inst.w_tw), d.ctypes.data, dem.ctypes.data, svc.ctypes.data,
-                       e.ctypes.data, l.ctypes.data, theta, nbr_ptr)
+                       e.ctypes.data, l.ctypes.data, theta, nbr_ptr, pick_ptr)
         self.W = self.n + 1 + self.m
 
     def ref(self):
@@ -141,6 +151,13 @@ def route_cost(inst, nodes, n_routes: int = 1) -> int:
     oi = OracleInstance(inst, n_routes)
     a = _c32(nodes)
     return int(_load().orc_route_cost(oi.ref(), a.ctypes.data, a.shape[0]))
+
+
+def route_peak_load(inst, nodes) -> int:
+    """Largest load on board along the route (forward simulation)."""
+    oi = OracleInstance(inst, 1)
+    a = _c32(nodes)
+    return int(_load().orc_route_peak_load(oi.ref(), a.ctypes.data, a.shape[0]))
 
 
 def route_warp(inst, nodes) -> int:
@@ -237,9 +254,13 @@ def descend(inst, sol, op_mask: int, method: str = "def", max_steps: int = 1 << 
     return new, int(steps), log[:min(evals.value, log_cap)].copy(), int(cands.value)
 
 
+SEG_FIELDS = ("D", "LI", "LO", "LM", "TD", "TE", "TL", "TV", "first", "last")
+
+
 def seg_node(inst, v: int):
+    """Single-node segment as an int64 array with the fields SEG_FIELDS."""
     oi = OracleInstance(inst, 1)
-    out = np.zeros(8, dtype=np.int64)
+    out = np.zeros(10, dtype=np.int64)
     _load().orc_seg_node(oi.ref(), v, out.ctypes.data)
     return out
 
@@ -248,6 +269,6 @@ def seg_concat(inst, s1, s2):
     oi = OracleInstance(inst, 1)
     a = np.ascontiguousarray(s1, dtype=np.int64)
     b = np.ascontiguousarray(s2, dtype=np.int64)
-    out = np.zeros(8, dtype=np.int64)
+    out = np.zeros(10, dtype=np.int64)
     _load().orc_seg_concat(oi.ref(), a.ctypes.data, b.ctypes.data, out.ctypes.data)
     return out

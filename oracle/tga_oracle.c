@@ -6,6 +6,8 @@
  * Problem and objective: Section 2 of the paper (routes R_i = (v0, ..., v0),
  * distance objective, capacity and time windows), with the penalised
  * objective  cost(R) = dist(R) + w_load * max(0, load(R) - Q) + w_tw * warp(R)
+ * where load(R) is the largest load on board (the total delivery when the
+ * instance has no pickups; with pickups, Section 2's VRPSPDTW)
  * that a feasible/infeasible search uses (Appendix, Algorithm "Feasible and
  * infeasible search").  The fleet is fixed, so the vehicle term of the
  * Section 2 objective is a constant and is left out.
@@ -57,15 +59,29 @@ int64_t orc_route_warp(const orc_inst *in, const int32_t *nodes, int32_t len)
     return warp;
 }
 
+/* Largest load on board (Section 2: the vehicle leaves the depot carrying
+ * the deliveries of all its customers, then drops d_x and collects p_x at
+ * each customer in turn); without pickups the load only falls, so the
+ * largest load is the total delivery at departure. */
+int64_t orc_route_peak_load(const orc_inst *in, const int32_t *nodes, int32_t len)
+{
+    int64_t load = 0;
+    for (int32_t k = 0; k < len; ++k) load += in->demand[nodes[k]];
+    if (!in->pickup) return load;
+    int64_t peak = load;
+    for (int32_t k = 0; k < len; ++k) {
+        load += in->pickup[nodes[k]] - in->demand[nodes[k]];
+        if (load > peak) peak = load;
+    }
+    return peak;
+}
+
 int64_t orc_route_cost(const orc_inst *in, const int32_t *nodes, int32_t len)
 {
     if (len == 0) return 0;
     int64_t d = DIST(in, 0, nodes[0]) + DIST(in, nodes[len - 1], 0);
-    int64_t load = 0;
-    for (int32_t k = 0; k < len; ++k) {
-        load += in->demand[nodes[k]];
-        if (k + 1 < len) d += DIST(in, nodes[k], nodes[k + 1]);
-    }
+    for (int32_t k = 0; k + 1 < len; ++k) d += DIST(in, nodes[k], nodes[k + 1]);
+    const int64_t load = orc_route_peak_load(in, nodes, len);
     int64_t cost = d + (int64_t)in->w_load * max64(0, load - in->capacity);
     if (in->has_tw) cost += (int64_t)in->w_tw * orc_route_warp(in, nodes, len);
     return cost;
@@ -240,28 +256,35 @@ static int64_t delta_def(const orc_inst *in, const view_t *v, const moved_t *mv)
 /* ------------------------------------------------------------------------ */
 /* Sequence concatenation (Sections 4.2-4.3).                                */
 
-typedef struct { int64_t D, LM, TD, TE, TL, TV; } seg_t;
+typedef struct { int64_t D, LI, LO, LM, TD, TE, TL, TV; } seg_t;
 
 static seg_t seg_of_node(const orc_inst *in, int32_t x)
 {
     seg_t s;
-    s.D = 0; s.LM = in->demand[x]; s.TD = in->service[x];
+    const int64_t p = in->pickup ? in->pickup[x] : 0;
+    s.D = 0;
+    s.LI = in->demand[x]; s.LO = p; s.LM = max64(s.LI, p);
+    s.TD = in->service[x];
     s.TE = in->early[x]; s.TL = in->late[x]; s.TV = 0;
     return s;
 }
 
 /* sigma1 (+) sigma2 with travel t between last(sigma1) and first(sigma2).
- * Distance and load rules as printed.  For the time fields the offset
+ * Distance and load rules as printed (Section 4.3.1-4.3.2): with pickups the
+ * incoming, outgoing and largest loads L_I, L_O, L_M; without them the
+ * simplified rule in which L_M is additive.  For the time fields the offset
  * Delta_t = T_D(s1) - T_V(s1) + t: the printed extra "T_W(s1)" term names
  * no attribute (waiting is already inside T_D), so it is read as absent. */
-static seg_t concat(seg_t a, seg_t b, int64_t t)
+static seg_t concat(const orc_inst *in, seg_t a, seg_t b, int64_t t)
 {
     seg_t s;
     int64_t dt = a.TD - a.TV + t;
     int64_t dw = max64(b.TE - dt - a.TL, 0);
     int64_t dv = max64(a.TE + dt - b.TL, 0);
     s.D = a.D + t + b.D;
-    s.LM = a.LM + b.LM;
+    s.LI = a.LI + b.LI;
+    s.LO = a.LO + b.LO;
+    s.LM = in->pickup ? max64(a.LM + b.LI, a.LO + b.LM) : a.LM + b.LM;
     s.TD = a.TD + t + dw + b.TD;
     s.TE = max64(b.TE - dt, a.TE) - dw;
     s.TL = min64(b.TL - dt, a.TL) + dv;
@@ -269,17 +292,24 @@ static seg_t concat(seg_t a, seg_t b, int64_t t)
     return s;
 }
 
+static void seg_out(const seg_t *s, int64_t first, int64_t last, int64_t *o)
+{
+    o[0] = s->D; o[1] = s->LI; o[2] = s->LO; o[3] = s->LM;
+    o[4] = s->TD; o[5] = s->TE; o[6] = s->TL; o[7] = s->TV; o[8] = first; o[9] = last;
+}
+
 void orc_seg_node(const orc_inst *in, int32_t v, int64_t *o)
 {
     seg_t s = seg_of_node(in, v);
-    o[0] = s.D; o[1] = s.LM; o[2] = s.TD; o[3] = s.TE; o[4] = s.TL; o[5] = s.TV; o[6] = v; o[7] = v;
+    seg_out(&s, v, v, o);
 }
 
 void orc_seg_concat(const orc_inst *in, const int64_t *p, const int64_t *q, int64_t *o)
 {
-    seg_t a = {p[0], p[1], p[2], p[3], p[4], p[5]}, b = {q[0], q[1], q[2], q[3], q[4], q[5]};
-    seg_t s = concat(a, b, DIST(in, p[7], q[6]));
-    o[0] = s.D; o[1] = s.LM; o[2] = s.TD; o[3] = s.TE; o[4] = s.TL; o[5] = s.TV; o[6] = p[6]; o[7] = q[7];
+    seg_t a = {p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7]};
+    seg_t b = {q[0], q[1], q[2], q[3], q[4], q[5], q[6], q[7]};
+    seg_t s = concat(in, a, b, DIST(in, p[9], q[8]));
+    seg_out(&s, p[8], q[9], o);
 }
 
 /* Attribute matrix of one route: entry (i, j), 0 <= i <= j <= L+1, is the
@@ -302,11 +332,11 @@ static void amat_build(const orc_inst *in, amat_t *m, const int32_t *nodes, int3
     for (int32_t i = 0; i < P; ++i) {
         *AM(m, i, i) = seg_of_node(in, m->nd[i]);
         for (int32_t j = i + 1; j < P; ++j)
-            *AM(m, i, j) = concat(*AM(m, i, j - 1), seg_of_node(in, m->nd[j]), DIST(in, m->nd[j - 1], m->nd[j]));
+            *AM(m, i, j) = concat(in, *AM(m, i, j - 1), seg_of_node(in, m->nd[j]), DIST(in, m->nd[j - 1], m->nd[j]));
         if (need_rev) {
             *AR(m, i, i) = seg_of_node(in, m->nd[i]);
             for (int32_t j = i + 1; j < P; ++j)
-                *AR(m, i, j) = concat(seg_of_node(in, m->nd[j]), *AR(m, i, j - 1), DIST(in, m->nd[j], m->nd[j - 1]));
+                *AR(m, i, j) = concat(in, seg_of_node(in, m->nd[j]), *AR(m, i, j - 1), DIST(in, m->nd[j], m->nd[j - 1]));
         }
     }
 }
@@ -322,7 +352,7 @@ static piece_t pc_rv(const amat_t *m, int32_t i, int32_t j) { piece_t p = {*AR(m
 static int64_t chain_cost(const orc_inst *in, const piece_t *p, int32_t np_)
 {
     seg_t s = p[0].s;
-    for (int32_t k = 1; k < np_; ++k) s = concat(s, p[k].s, DIST(in, p[k - 1].last, p[k].first));
+    for (int32_t k = 1; k < np_; ++k) s = concat(in, s, p[k].s, DIST(in, p[k - 1].last, p[k].first));
     int64_t c = s.D + (int64_t)in->w_load * max64(0, s.LM - in->capacity);
     if (in->has_tw) c += (int64_t)in->w_tw * s.TV;
     return c;

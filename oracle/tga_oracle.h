@@ -10,8 +10,8 @@
  *                 and cost it by forward simulation (Section 2 objective with
  *                 the time-warp relaxation of Section 4.3.3).
  *   ORC_CONCAT -- the paper's sequence concatenation (Section 4.1-4.3): per
- *                 route attribute matrices (Section 4.2) holding D, L_M, T_D,
- *                 T_E, T_L, T_V for every subsequence, and each neighbour's
+ *                 route attribute matrices (Section 4.2) holding D, L_I, L_O,
+ *                 L_M, T_D, T_E, T_L, T_V for every subsequence, and each neighbour's
  *                 route attributes obtained by the concatenation operator.
  * Both return the lexicographically smallest (delta, move index).
  *
@@ -40,12 +40,18 @@ extern "C" {
  *   swap: M[a][b] or M[b][a];
  *   2-opt*: exactly one of a, b is a start depot, or M[a][b] or M[b][a].
  * theta = 0: the full neighbourhood (node-based extraction). */
+/* pickup: NULL for the CVRP and VRPTW; for the VRPSPDTW the pickup
+ * quantity p_x of every node (n+1 entries, p_0 = 0).  A vehicle leaves the
+ * depot with every delivery of its route on board, drops d_x and collects
+ * p_x at each customer; the capacity term uses the largest load on board
+ * (Section 4.3.2, attributes L_I, L_O, L_M). */
 typedef struct {
     int32_t n, m, capacity, has_tw, w_load, w_tw;
     const int32_t *dist;                 /* (n+1)*(n+1), row-major */
     const int32_t *demand, *service, *early, *late;   /* n+1 each */
     int32_t theta;
     const int32_t *nbr;                  /* (n+1)*theta, or NULL when theta = 0 */
+    const int32_t *pickup;               /* n+1, or NULL */
 } orc_inst;
 
 typedef struct {
@@ -58,6 +64,8 @@ typedef struct {
 enum { ORC_DEF = 0, ORC_CONCAT = 1 };
 
 int64_t orc_route_cost(const orc_inst *in, const int32_t *nodes, int32_t len);
+/* Largest load on board along the route (the total delivery without pickups). */
+int64_t orc_route_peak_load(const orc_inst *in, const int32_t *nodes, int32_t len);
 int64_t orc_route_warp(const orc_inst *in, const int32_t *nodes, int32_t len);
 int64_t orc_solution_cost(const orc_inst *in, const int32_t *tour, const int32_t *route_start);
 int     orc_check_solution(const orc_inst *in, const int32_t *tour, const int32_t *route_start);
@@ -74,7 +82,7 @@ int64_t orc_descend(const orc_inst *in, int32_t *tour, int32_t *route_start, uin
                     int method, int64_t max_steps, uint64_t *key_log, int64_t log_cap,
                     int64_t *cands_total, int64_t *n_evals);
 /* Concatenation of two segments (Section 4.3), exposed for property tests.
- * seg = {D, LM, TD, TE, TL, TV, first, last}. */
+ * seg = {D, LI, LO, LM, TD, TE, TL, TV, first, last}. */
 void    orc_seg_node(const orc_inst *in, int32_t v, int64_t *seg8);
 void    orc_seg_concat(const orc_inst *in, const int64_t *s1, const int64_t *s2, int64_t *out8);
 

@@ -24,6 +24,10 @@ Workload recipes (sizes and distributions of the five benchmark workloads):
   capacity 200, service time 10 (depot 0), depot window [0,10000]; window
   centre uniform in [c(0,i), 10000 - c(i,0) - 10], width uniform in
   [60,400]; e = centre - floor(w/2), l = e + w, both clipped to [0,10000].
+* ``vrpspdtw(n)``: the ``vrptw(n)`` recipe (same coordinates, deliveries,
+  windows and service times for a given seed) plus pickup quantities
+  uniform in [1,50] from their own stream (depot 0) -- the simultaneous
+  pickup and delivery variant of Section 2.
 * ``cvrp_clustered(n)``: depot uniform in [0,1000]^2; 50 cluster centres
   uniform in [0,1000]^2; each customer picks a centre uniformly and adds a
   zero-mean normal offset with sigma 40 per axis (Irwin-Hall sum of twelve
@@ -33,12 +37,15 @@ Workload recipes (sizes and distributions of the five benchmark workloads):
   square root (round to nearest; ties cannot occur for integer dx^2+dy^2).
 * Initial solution: a seeded Fisher-Yates permutation of the customers, split
   greedily into routes: a new route opens when the next customer's demand
-  would exceed the capacity.  Route count M is fixed from then on.
+  (or, with pickups, its delivery or its pickup) would take the route's
+  total delivery (or total pickup) above the capacity.  Route count M is
+  fixed from then on.
 """
 from __future__ import annotations
 
 import dataclasses
 import math
+from typing import Optional
 
 import numpy as np
 
@@ -52,6 +59,7 @@ _MASK64 = (1 << 64) - 1
 S_COORD, S_DEMAND, S_TW_CENTRE, S_TW_WIDTH = 1, 2, 3, 4
 S_CLUSTER_CENTRE, S_CLUSTER_PICK, S_GAUSS, S_PERM = 5, 6, 7, 8
 S_BATCH_SIZE, S_BATCH_KIND, S_ARRIVAL = 9, 10, 11
+S_PICKUP = 12
 
 HORIZON = 10000
 COORD_MAX = 1000
@@ -126,7 +134,7 @@ def rounded_euclidean(xy: np.ndarray) -> np.ndarray:
 
 
 def instance_from_arrays(name, dist, demand, capacity, service=None, tw_early=None,
-                         tw_late=None, coords=None, w_load=100, w_tw=100) -> "Instance":
+                         tw_late=None, coords=None, w_load=100, w_tw=100, pickup=None) -> "Instance":
     """Wrap explicit arrays (e.g. a hand-made example) as an Instance."""
     dist = np.ascontiguousarray(dist, dtype=np.int32)
     n1 = dist.shape[0]
@@ -135,8 +143,9 @@ def instance_from_arrays(name, dist, demand, capacity, service=None, tw_early=No
     e = np.zeros(n1, np.int32) if tw_early is None else np.asarray(tw_early, np.int32)
     l = np.full(n1, HORIZON, np.int32) if tw_late is None else np.asarray(tw_late, np.int32)
     xy = np.zeros((n1, 2), np.int32) if coords is None else np.asarray(coords, np.int32)
+    pk = None if pickup is None else np.asarray(pickup, np.int32)
     return Instance(name, n1 - 1, int(capacity), has_tw, xy, np.asarray(demand, np.int32),
-                    svc, e, l, dist, w_load, w_tw)
+                    svc, e, l, dist, w_load, w_tw, pk)
 
 
 @dataclasses.dataclass
@@ -154,9 +163,16 @@ class Instance:
     dist: np.ndarray            # (n+1, n+1) row-major
     w_load: int = 100
     w_tw: int = 100
+    pickup: Optional[np.ndarray] = None   # (n+1,), pickup[0] = 0; None: no pickups
+
+    @property
+    def has_pd(self) -> bool:
+        return self.pickup is not None
 
     @property
     def kind(self) -> str:
+        if self.pickup is not None:
+            return "vrpspdtw" if self.has_tw else "vrpspd"
         return "vrptw" if self.has_tw else "cvrp"
 
 
@@ -218,6 +234,16 @@ def vrptw(n: int, seed: int) -> Instance:
                     dem.astype(np.int32), svc, early, late, dist)
 
 
+def vrpspdtw(n: int, seed: int) -> Instance:
+    """VRPTW recipe plus pickups uniform in [1,50] (stream S_PICKUP)."""
+    base = vrptw(n, seed)
+    pk = np.zeros(n + 1, dtype=np.int64)
+    pk[1:] = uniform_int(splitmix64(seed, S_PICKUP, n), 1, 50)
+    base.name = f"vrpspdtw_n{n}_s{seed}"
+    base.pickup = pk.astype(np.int32)
+    return base
+
+
 def _round_half_away(x: np.ndarray) -> np.ndarray:
     return (np.sign(x) * np.floor(np.abs(x) + 0.5)).astype(np.int64)
 
@@ -254,13 +280,16 @@ def random_split_solution(inst: Instance, seed: int) -> Solution:
         for i, j in zip(bounds.tolist(), js):
             perm[i], perm[j] = perm[j], perm[i]
     starts = [0]
-    load = 0
+    load = pick = 0
+    pk = getattr(inst, "pickup", None)
     for t, c in enumerate(perm):
         d = int(inst.demand[c])
-        if t > 0 and load + d > inst.capacity:
+        p = 0 if pk is None else int(pk[c])
+        if t > 0 and (load + d > inst.capacity or pick + p > inst.capacity):
             starts.append(t)
-            load = 0
+            load = pick = 0
         load += d
+        pick += p
     starts.append(n)
     if n == 0:
         starts = [0, 0]
@@ -301,6 +330,13 @@ def config1(seed: int = 1):
 def config2(seed: int = 1):
     """VRPTW, 1000 customers; all five operators."""
     inst = vrptw(1000, seed)
+    return inst, random_split_solution(inst, solution_seed(seed))
+
+
+def config_spd(seed: int = 1, n: int = 1000):
+    """VRPSPDTW, 1000 customers (the VRPTW workload with pickups); all five
+    operators."""
+    inst = vrpspdtw(n, seed)
     return inst, random_split_solution(inst, solution_seed(seed))
 
 

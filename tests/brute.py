@@ -5,11 +5,22 @@ list surgery on a deep copy of the route list, and scored by recomputing the
 whole solution's cost from scratch with a fresh forward simulation.  Used only
 on tiny instances.
 
-Objective: Section 2 of the paper with the penalised capacity excess and the
-time-warp relaxation of Section 4.3.3 (weights w_load, w_tw).  Operators:
+Objective: Section 2 of the paper with the penalised capacity excess (of the
+largest load on board when the instance has pickups) and the time-warp
+relaxation of Section 4.3.3 (weights w_load, w_tw).  Operators:
 Section 4.1 (relocate, swap, 2-opt, 2-opt*) plus or-opt of 2-3 customers.
 """
 import copy
+
+
+def peak_load(inst, route):
+    """Largest load on board: after serving the first k customers the vehicle
+    carries the deliveries still owed to customers k+1.. plus the pickups of
+    customers 1..k (Section 2); k = 0 is the departure."""
+    pk = getattr(inst, "pickup", None)
+    d = [int(inst.demand[x]) for x in route]
+    p = [0 if pk is None else int(pk[x]) for x in route]
+    return max(sum(d[k:]) + sum(p[:k]) for k in range(len(route) + 1))
 
 
 def route_cost(inst, route):
@@ -18,7 +29,7 @@ def route_cost(inst, route):
     c = inst.dist
     seq = [0] + list(route) + [0]
     dist = sum(int(c[seq[k]][seq[k + 1]]) for k in range(len(seq) - 1))
-    load = sum(int(inst.demand[x]) for x in route)
+    load = peak_load(inst, route)
     cost = dist + inst.w_load * max(0, load - inst.capacity)
     if inst.has_tw:
         t = int(inst.tw_early[0])

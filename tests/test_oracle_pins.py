@@ -3,7 +3,8 @@
 * exhaustive rounding rule of the integer distances (number theory),
 * hand-worked examples under tests/golden/ (each cites its passage),
 * the paper's concatenation operator (Section 4.3) against the forward
-  simulation of the time-warp definition, and its associativity,
+  simulation of the time-warp definition and of the load on board, and its
+  associativity; special cases of the pickup-and-delivery load profile,
 * an independent pure-Python brute force over whole candidate sets,
 * closed-form candidate counts, textbook CVRP deltas, and geometry
   (2-opt on points in convex position ends in convex order),
@@ -44,9 +45,13 @@ def _sol(tour, rs):
 
 
 def _tiny(kind, n, seed, m_extra_empty=1):
-    inst = I.vrptw(n, seed) if kind == "vrptw" else I.cvrp_uniform(n, seed)
+    if kind in ("vrpspdtw", "vrpspd"):
+        inst = I.vrpspdtw(n, seed)
+        inst.has_tw = kind == "vrpspdtw"
+    else:
+        inst = I.vrptw(n, seed) if kind == "vrptw" else I.cvrp_uniform(n, seed)
     # a few multi-customer routes even at tiny n
-    inst.capacity = 100 if kind == "vrptw" else -(-int(inst.demand.sum()) // 3)
+    inst.capacity = 100 if kind != "cvrp" else -(-int(inst.demand.sum()) // 3)
     sol = I.random_split_solution(inst, seed + 11)
     rs = list(sol.route_start) + [n] * m_extra_empty   # trailing empty routes
     return inst, _sol(sol.tour, rs)
@@ -118,6 +123,51 @@ def test_hand_vrptw_warp():
 
 
 # ----------------------------------------------------------------------------
+def test_hand_vrpspd_load():
+    g = _golden("hand_vrpspd_load.json")
+    inst = I.instance_from_arrays("golden", np.array(g["dist"]), g["demand"], g["capacity"],
+                                  pickup=g["pickup"])
+    sol = _sol(g["tour"], g["route_start"])
+    ex = g["expected"]
+    for order, peak in ex["peak_loads"].items():
+        route = [int(x) for x in order.split(",")]
+        assert O.route_peak_load(inst, route) == peak
+        from tests.brute import peak_load
+        assert peak_load(inst, route) == peak
+    assert [O.route_cost(inst, r) for r in sol.routes()] == ex["route_costs"]
+    assert O.count_candidates(inst, sol, g["op_mask"]) == ex["n_candidates"]
+    for method in ("def", "concat"):
+        idx, dl = O.list_moves(inst, sol, g["op_mask"], method)
+        assert {str(i): d for i, d in zip(idx.tolist(), dl.tolist())} == ex["deltas"]
+        bm = O.best_move(inst, sol, g["op_mask"], method)
+        assert {k: bm[k] for k in ("delta", "idx", "op", "a", "b")} == ex["best"]
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_peak_load_special_cases(seed):
+    """Section 2 load profile: without pickups the largest load is the total
+    delivery at departure; with deliveries all zero it is the total pickup on
+    return; it always lies between max(sum d, sum p) and sum d + sum p; and
+    driving the route backwards with the roles of d and p exchanged gives the
+    same profile in reverse, so the same largest load."""
+    inst = I.vrpspdtw(30, 500 + seed)
+    no_pk = I.vrptw(30, 500 + seed)
+    only_pk = I.vrpspdtw(30, 500 + seed)
+    only_pk.demand = np.zeros_like(only_pk.demand)
+    swapped = I.vrpspdtw(30, 500 + seed)
+    swapped.demand, swapped.pickup = inst.pickup.copy(), inst.demand.copy()
+    rng = random.Random(seed)
+    for _ in range(100):
+        route = rng.sample(range(1, inst.n + 1), rng.randint(1, 15))
+        sd = sum(int(inst.demand[x]) for x in route)
+        sp = sum(int(inst.pickup[x]) for x in route)
+        peak = O.route_peak_load(inst, route)
+        assert O.route_peak_load(no_pk, route) == sd
+        assert O.route_peak_load(only_pk, route) == sp
+        assert max(sd, sp) <= peak <= sd + sp
+        assert O.route_peak_load(swapped, route[::-1]) == peak
+
+
 def _fold(inst, nodes):
     s = O.seg_node(inst, nodes[0])
     for x in nodes[1:]:
@@ -125,12 +175,15 @@ def _fold(inst, nodes):
     return s
 
 
+@pytest.mark.parametrize("kind", ["vrptw", "vrpspdtw"])
 @pytest.mark.parametrize("seed", range(6))
-def test_concat_equals_forward_simulation(seed):
+def test_concat_equals_forward_simulation(kind, seed):
     """Section 4.3: folding the concatenation operator over (0, route, 0)
-    gives the route's distance, load and time warp of the forward simulation
-    (travel time = distance, waiting allowed, late arrival warps back)."""
-    inst = I.vrptw(40, 100 + seed)
+    gives the route's distance, loads and time warp of the forward simulation
+    (travel time = distance, waiting allowed, late arrival warps back; the
+    largest load on board from the load profile of Section 2)."""
+    inst = I.vrptw(40, 100 + seed) if kind == "vrptw" else I.vrpspdtw(40, 100 + seed)
+    pk = inst.pickup if inst.pickup is not None else np.zeros_like(inst.demand)
     rng = random.Random(seed)
     for _ in range(200):
         L = rng.randint(1, 12)
@@ -139,13 +192,16 @@ def test_concat_equals_forward_simulation(seed):
         seq = [0] + route + [0]
         assert s[0] == sum(int(inst.dist[seq[k], seq[k + 1]]) for k in range(len(seq) - 1))
         assert s[1] == sum(int(inst.demand[x]) for x in route)
-        assert s[5] == O.route_warp(inst, route)
+        assert s[2] == sum(int(pk[x]) for x in route)
+        assert s[3] == O.route_peak_load(inst, route)
+        assert s[7] == O.route_warp(inst, route)
         assert py_route_cost(inst, route) == O.route_cost(inst, route)
 
 
+@pytest.mark.parametrize("kind", ["vrptw", "vrpspdtw"])
 @pytest.mark.parametrize("seed", range(4))
-def test_concat_associative(seed):
-    inst = I.vrptw(30, 200 + seed)
+def test_concat_associative(kind, seed):
+    inst = I.vrptw(30, 200 + seed) if kind == "vrptw" else I.vrpspdtw(30, 200 + seed)
     rng = random.Random(seed)
     for _ in range(300):
         nodes = rng.sample(range(0, inst.n + 1), rng.randint(3, 9))
@@ -158,7 +214,7 @@ def test_concat_associative(seed):
 
 
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["cvrp", "vrptw"])
+@pytest.mark.parametrize("kind", ["cvrp", "vrptw", "vrpspdtw", "vrpspd"])
 @pytest.mark.parametrize("seed", range(5))
 def test_candidate_sets_against_brute_force(kind, seed):
     """Every candidate (move index -> delta) equals a from-scratch recompute of
@@ -268,7 +324,8 @@ def test_two_opt_descent_reaches_convex_order():
 
 @pytest.mark.parametrize("kind,n,seed,mask", [
     ("cvrp", 25, 1, I.MASK_CONFIG1), ("vrptw", 30, 2, I.MASK_ALL),
-    ("cvrp", 40, 3, I.MASK_CONFIG3), ("vrptw", 45, 4, I.MASK_ALL)])
+    ("cvrp", 40, 3, I.MASK_CONFIG3), ("vrptw", 45, 4, I.MASK_ALL),
+    ("vrpspdtw", 35, 5, I.MASK_ALL), ("vrpspd", 30, 6, I.MASK_ALL)])
 def test_descent_invariants(kind, n, seed, mask):
     inst, sol = _tiny(kind, n, seed, m_extra_empty=1)
     c0 = O.solution_cost(inst, sol)
