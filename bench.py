@@ -42,13 +42,25 @@ WORKLOADS = {
     "cvrp100": ("CVRP 1 depot + 100 customers, relocate/swap/2-opt/2-opt*", I.config1, I.MASK_CONFIG1),
     "cvrp10000": ("clustered CVRP 1 depot + 10000 customers, relocate/swap/2-opt*/or-opt", I.config3,
                   I.MASK_CONFIG3),
+    "vrpspdtw1000": ("VRPSPDTW 1 depot + 1000 customers with pickups and deliveries, all five operators",
+                     I.config_spd, I.MASK_ALL),
 }
 
 # Integer operations per inter-route candidate, counted from the delta
 # expressions (adds/subs, min/max, multiplies, plus one compare for the
-# running argmin).  Index: op rank.  CVRP and VRPTW (time-warp terms added).
+# running argmin).  Index: op rank.  CVRP and VRPTW (time-warp terms added);
+# with pickups the load term of each new route is the three-way maximum of
+# the largest-load constants instead of one sum (relocate/or-opt +5, swap +8,
+# 2-opt* +4) and the intra-route 2-opt closes a load chain (+14).
 OPS_CVRP = {0: 8, 1: 13, 2: 6, 3: 13, 4: 8, 5: 8}
 OPS_TW = {0: 20, 1: 36, 2: 22, 3: 22, 4: 20, 5: 20}
+OPS_PD = {0: 25, 1: 44, 2: 36, 3: 26, 4: 25, 5: 25}
+
+
+def ops_table(inst):
+    if getattr(inst, "pickup", None) is not None:
+        return OPS_PD
+    return OPS_TW if inst.has_tw else OPS_CVRP
 
 
 def inter_candidates(n, lens, mask):
@@ -71,15 +83,13 @@ def inter_candidates(n, lens, mask):
     return out
 
 
-def algorithmic_ops(n, lens, mask, has_tw):
-    table = OPS_TW if has_tw else OPS_CVRP
+def algorithmic_ops(n, lens, mask, table):
     return sum(table[op] * c for op, c in inter_candidates(n, lens, mask).items())
 
 
-def descent_ops(op_candidates, has_tw):
+def descent_ops(op_candidates, table):
     """Integer operations of every candidate evaluated (per-operator totals
     from the device counters, weighted by the per-candidate counts above)."""
-    table = OPS_TW if has_tw else OPS_CVRP
     return sum(table[op] * c for op, c in enumerate(op_candidates))
 
 
@@ -386,7 +396,7 @@ def bench_gpu(args):
         intra = [int((L * (L - 1)).sum()), int((L * (L - 1) // 2).sum()), int((L * (L - 1) // 2).sum()), 0,
                  int((np.maximum(L - 1, 0) * np.maximum(L - 2, 0)).sum()),
                  int((np.maximum(L - 2, 0) * np.maximum(L - 3, 0)).sum())]
-        table = OPS_TW if inst.has_tw else OPS_CVRP
+        table = ops_table(inst)
         return sum(table[op] * (after[op] - before[op] - (intra[op] if (mask >> op) & 1 else 0))
                    for op in range(6))
 
@@ -403,7 +413,7 @@ def bench_gpu(args):
             else:
                 tour_h, rs_h = ls.solution()
                 lens = np.diff(rs_h)
-                total_ops += algorithmic_ops(inst.n, lens, mask, inst.has_tw)
+                total_ops += algorithmic_ops(inst.n, lens, mask, ops_table(inst))
             total_ms += ms
             if j + 1 < probes:
                 T.tga_descend(ls.ctx, max_steps=max(1, n_steps // (probes - 1)))
@@ -430,7 +440,7 @@ def bench_gpu(args):
             e1.record(stream)
             e1.synchronize()
             kms.append(e0.elapsed_time(e1))
-        ops = descent_ops(op_cands, inst.has_tw)
+        ops = descent_ops(op_cands, ops_table(inst))
         ms = float(np.mean(kms))
         achieved = ops / (ms / 1e3)
         roof = {"bound": "alu", "kernel": "k_persist", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,

@@ -70,7 +70,20 @@ enum {
 
 /* Problem data (Section 2).  has_tw = 0 is the CVRP: service, tw_early and
  * tw_late may then be NULL.  w_load / w_tw are the penalty weights of the
- * penalised objective; both must be >= 0. */
+ * penalised objective; both must be >= 0.
+ *
+ * pickup = NULL: no pickups (CVRP, VRPTW); the load term penalises the total
+ * delivery of a route above the capacity.  pickup != NULL: the VRP with
+ * simultaneous pickup and delivery and time windows (VRPSPDTW, Section 2;
+ * has_tw must be 1, else TGA_ERR_INVALID -- a VRPSPD without windows is
+ * passed with windows [0, horizon] and zero service times).  A vehicle
+ * leaves the depot with the deliveries of its whole route, drops demand[x]
+ * and collects pickup[x] at each customer, and the load term penalises the
+ * largest load on board above the capacity (attributes L_I, L_O, L_M of
+ * Section 4.3.2).  pickup[x] >= 0, pickup[0] = 0 (checked on the device by
+ * tga_build_attrs: TGA_ERR_INVALID).  Contexts with pickups run the
+ * single-instance paths (every descent mode, tga_eval_best_move_noalloc);
+ * tga_descend_batch and tga_set_granular refuse them with TGA_ERR_STATE. */
 typedef struct {
     int32_t n_customers;       /* n >= 1 */
     int32_t n_routes;          /* m >= 1 */
@@ -82,6 +95,7 @@ typedef struct {
     const int32_t *service;    /* device, n+1 (VRPTW), service[0] = 0 */
     const int32_t *tw_early;   /* device, n+1 (VRPTW), [0] = depot opening */
     const int32_t *tw_late;    /* device, n+1 (VRPTW), [0] = latest return */
+    const int32_t *pickup;     /* device, n+1, or NULL (see above) */
 } tga_instance;
 
 typedef struct {
@@ -193,13 +207,15 @@ int tga_get_persistent_shape(tga_ctx *ctx, int32_t *rows, int32_t *col_warps, in
  * job's last chunk applies its move, so large jobs spread over many SMs.
  * Idle CTAs poll under a 20 s limit (TGA_ERR_TIMEOUT).  Results per context
  * equal tga_descend's bit for bit.  Waits for completion.
- * out_host: n entries (may be NULL).  Returns the first error. */
+ * out_host: n entries (may be NULL).  Returns the first error.  Contexts with
+ * edge-based extraction or with pickups are refused (TGA_ERR_STATE). */
 int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_host);
 
 /* Autotune the batched tile rows (16/32/64) per size bucket (n+m+1 below 400,
  * 800, 1400, above): times evaluation-only batched launches of each bucket's
  * median context and keeps the fastest shape for the whole bucket.
- * rows_out: n entries (may be NULL).  Leaves the contexts to be rebuilt. */
+ * rows_out: n entries (may be NULL).  Leaves the contexts to be rebuilt.
+ * Refuses the same contexts as tga_descend_batch (TGA_ERR_STATE). */
 int tga_batch_autotune(tga_ctx **ctxs, int n, int32_t *rows_out);
 
 /* As tga_descend, but only enqueues the work on the context's stream and

@@ -36,7 +36,7 @@ __device__ void build_job(const Dev &d, long long max_steps) {
     __syncthreads();
     const int st = *(volatile int *)&d.ctl->status;
     if (st == 0)
-        for (int r = warp; r < d.m; r += nw) rebuild_route(d, r, lane);
+        for (int r = warp; r < d.m; r += nw) rebuild_route<false>(d, r, lane);
     __syncthreads();
     finish_block(d);
     __syncthreads();
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch(const BatchJob *__restr
                     C->plan = sPlan;
                 }
                 __syncthreads();
-                apply_plan_block(d, sPlan, smem, false, 0, 0);
+                apply_plan_block<false>(d, sPlan, smem, false, 0, 0);
             } else if (tid == 0) {
                 if (d.log && C->evals < d.log_cap) d.log[C->evals] = C->best_key;
                 count_evaluation(d, C);

@@ -258,6 +258,8 @@ int default_batch_tr(int Wp) { return Wp < 600 ? 16 : (Wp < 2000 ? 32 : 64); }
 
 // One persistent launch over all contexts (see tga_batch.cu).
 int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *tr_override) {
+    for (int i = 0; i < n; ++i)                  // no edge-based or pickup path in the batched kernel
+        if (ctxs[i]->d.theta > 0 || ctxs[i]->d.has_pd) return TGA_ERR_STATE;
     cudaStream_t s = ctxs[0]->stream;
     for (int i = 0; i < n; ++i)
         if (ctxs[i]->stream != s && cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return TGA_ERR_CUDA;
@@ -360,6 +362,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     if (op_mask == 0 || op_mask >= 64u) return TGA_ERR_INVALID;
     if (!inst->dist || !inst->demand || !sol->tour || !sol->route_start) return TGA_ERR_INVALID;
     if (inst->has_tw && (!inst->service || !inst->tw_early || !inst->tw_late)) return TGA_ERR_INVALID;
+    if (inst->pickup && !inst->has_tw) return TGA_ERR_INVALID;       // pickups come with time windows
     const long long W = n + 1 + m;
     if (W > kMaxW) return TGA_ERR_RANGE;
 
@@ -381,9 +384,11 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     Dev &d = c->d;
     d.n = (int)n; d.m = (int)m; d.W = (int)W; d.Wp = (int)(n + m + 1);
     d.Q = inst->capacity; d.wL = inst->w_load; d.wT = inst->w_tw; d.has_tw = inst->has_tw ? 1 : 0;
+    d.has_pd = inst->pickup ? 1 : 0;
     d.op_mask = op_mask;
     d.dist = inst->dist; d.demand = inst->demand;
     d.service = inst->service; d.early = inst->tw_early; d.late = inst->tw_late;
+    d.pickup = inst->pickup;
     d.tour = sol->tour; d.route_start = sol->route_start;
     d.ldp = (int)(align_up((size_t)d.Wp, kMaxTileCols) + 16);
     d.log = nullptr; d.log_cap = 0;
@@ -396,9 +401,10 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     const size_t o_pos = take(sizeof(int) * (size_t)(W + 1));
     const size_t o_brec = take(sizeof(BRec) * (size_t)(W + 1));
     const size_t o_erec = take(sizeof(ERec) * (size_t)(W + 1));
+    const size_t o_prec = take(d.has_pd ? sizeof(PRec) * (size_t)(W + 1) : 0);
     const size_t o_rrec = take(sizeof(RouteRec) * (size_t)m);
     const size_t o_seen = take(sizeof(int) * (size_t)(n + 1));
-    const size_t o_intra = take(sizeof(int) * 10 * (size_t)(d.Wp + m));
+    const size_t o_intra = take(sizeof(int) * kIntraVecPD * (size_t)(d.Wp + m));
     const size_t o_saved = take(sizeof(int) * (size_t)(n + m + 1));
     const size_t o_pcol = take(sizeof(int) * (size_t)(n + 1) * (size_t)d.ldp);
     c->ws_bytes = off;
@@ -413,6 +419,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.pos_of = (int *)(base + o_pos);
     d.brec = (BRec *)(base + o_brec);
     d.erec = (ERec *)(base + o_erec);
+    d.prec = d.has_pd ? (PRec *)(base + o_prec) : nullptr;
     d.rrec = (RouteRec *)(base + o_rrec);
     d.seen = (int *)(base + o_seen);
     d.scr_intra = (int *)(base + o_intra);
@@ -472,6 +479,7 @@ int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_h
         if (!ctxs[i]) return TGA_ERR_INVALID;
         if (ctxs[i]->device != ctxs[0]->device) return TGA_ERR_INVALID;
         if (ctxs[i]->d.theta > 0) return TGA_ERR_STATE;      // the batched kernel has no edge-based path
+        if (ctxs[i]->d.has_pd) return TGA_ERR_STATE;         // ... and no pickup path
     }
     int first = run_batch(ctxs, n, max_steps, 0, nullptr);
     for (int i = 0; i < n; ++i) {
@@ -798,6 +806,7 @@ int tga_debug_read(tga_ctx *c, int32_t what, void *host_dst, size_t bytes, size_
 int tga_set_granular(tga_ctx *c, const int32_t *nbr_dev, int32_t theta) {
     if (!c || theta < 0) return TGA_ERR_INVALID;
     if (theta > 0 && (!nbr_dev || theta > c->d.n - 1)) return TGA_ERR_INVALID;
+    if (theta > 0 && c->d.has_pd) return TGA_ERR_STATE;      // the edge-based kernel has no pickup path
     if (c->granular) cudaFreeAsync(c->granular, c->stream);
     c->granular = nullptr;
     c->d.theta = 0; c->d.nbr = nullptr; c->d.nbr_rev = nullptr;

@@ -91,6 +91,30 @@ __device__ __forceinline__ Seg shfl_seg_idx(const Seg &s, int src) {
     return o;
 }
 
+__device__ __forceinline__ Ld shfl_ld_up(const Ld &s, int off) {
+    Ld o;
+    o.i = __shfl_up_sync(0xffffffffu, s.i, off);
+    o.o = __shfl_up_sync(0xffffffffu, s.o, off);
+    o.m = __shfl_up_sync(0xffffffffu, s.m, off);
+    return o;
+}
+
+__device__ __forceinline__ Ld shfl_ld_down(const Ld &s, int off) {
+    Ld o;
+    o.i = __shfl_down_sync(0xffffffffu, s.i, off);
+    o.o = __shfl_down_sync(0xffffffffu, s.o, off);
+    o.m = __shfl_down_sync(0xffffffffu, s.m, off);
+    return o;
+}
+
+__device__ __forceinline__ Ld shfl_ld_idx(const Ld &s, int src) {
+    Ld o;
+    o.i = __shfl_sync(0xffffffffu, s.i, src);
+    o.o = __shfl_sync(0xffffffffu, s.o, src);
+    o.m = __shfl_sync(0xffffffffu, s.m, src);
+    return o;
+}
+
 __device__ __forceinline__ int route_node(const Dev &d, int start, int L, int k) {
     return (k <= 0 || k > L) ? 0 : d.seq[start + k];
 }
@@ -104,13 +128,17 @@ __device__ __forceinline__ int route_anchor(const Dev &d, int r, int start, int 
 // Forward inclusive scan gives the prefix F(x) of every anchor, backward
 // inclusive scan the suffix; the route's totals are the prefix of the end
 // depot.  Routes longer than 32 elements are scanned in chunks with a carry.
+// PD (pickups): the loads L_I, L_O, L_M (Section 4.3.2) are scanned beside.
+template <bool PD>
 __device__ void rebuild_route(const Dev &d, int r, int lane) {
     const RouteRec rr = d.rrec[r];
     const int st = rr.start, L = rr.len, E = L + 2;
     const bool tw = d.has_tw != 0;
+    constexpr bool pd = PD;
     const int wTe = tw ? d.wT : 0;
     // ---- forward scan: prefixes
     Seg carry{};
+    Ld lcarry{0, 0, 0};
     bool have = false;
     for (int base = 0; base < E; base += 32) {
         const int k = base + lane;
@@ -125,6 +153,16 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
             if (lane >= off) s = seg_cat(o, s);
         }
         if (have) s = seg_cat(carry, s);
+        Ld l{0, 0, 0};
+        if (pd) {
+            l = ld_node(d, x);
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const Ld o = shfl_ld_up(l, off);
+                if (lane >= off) l = ld_cat(o, l);
+            }
+            if (have) l = ld_cat(lcarry, l);
+        }
         if (valid) {
             if (k <= L) {
                 const int a = route_anchor(d, r, st, L, k);
@@ -134,16 +172,20 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
                 b->twf = tw ? s.TW : 0;
                 b->distf = s.dist;
                 b->loadf = s.load;
+                if (pd) { b->lof = l.o; b->lmf = l.m; }
             } else {
                 RouteRec *R = d.rrec + r;
                 const int twr = tw ? s.TW : 0;
+                const int lm = pd ? l.m : s.load;
                 R->load = s.load;
+                if (pd) { R->lo = l.o; R->lm = lm; }
                 R->dist = s.dist;
                 R->tw = twr;
-                R->cost = L == 0 ? 0 : s.dist + d.wL * max(s.load - d.Q, 0) + wTe * twr;
+                R->cost = L == 0 ? 0 : s.dist + d.wL * max(lm - d.Q, 0) + wTe * twr;
             }
         }
         carry = shfl_seg_idx(s, 31);
+        if (pd) lcarry = shfl_ld_idx(l, 31);
         have = true;
     }
     // ---- backward scan: suffix after each anchor
@@ -162,6 +204,16 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
             if (lane + off < 32 && k + off < E) s = seg_cat(s, o);
         }
         if (have && valid) s = seg_cat(s, carry);
+        Ld l{0, 0, 0};
+        if (pd) {
+            l = ld_node(d, x);
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const Ld o = shfl_ld_down(l, off);
+                if (lane + off < 32 && k + off < E) l = ld_cat(l, o);
+            }
+            if (have && valid) l = ld_cat(l, lcarry);
+        }
         if (valid && k >= 1) {
             const int a = route_anchor(d, r, st, L, k - 1);
             BRec *b = d.brec + a;
@@ -169,19 +221,23 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
             b->twg = tw ? s.TW : 0;
             b->distg = s.dist;
             b->loadg = s.load;
+            if (pd) b->lmg = l.m;
         }
         carry = shfl_seg_idx(s, 0);
+        if (pd) lcarry = shfl_ld_idx(l, 0);
         have = true;
     }
     __syncwarp();
     // ---- hoisted constants per anchor
     const RouteRec R = d.rrec[r];
     const unsigned mask = d.op_mask;
+    const int Q = d.Q;
     for (int k = lane; k <= L; k += 32) {
         const int a = route_anchor(d, r, st, L, k);
         const int x = k == 0 ? 0 : a;
         const BRec b = d.brec[a];
         ERec e;
+        PRec pr{};
         e.route = r; e.anchor = a; e.node = x; e.idx = k; e.pad0 = 0; e.pad1 = 0;
         d.brec[a].rlen = L;
         d.brec[a].rcost = R.cost;
@@ -196,11 +252,17 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
         e.K1 = Fc + Gc;
         e.Fc = Fc + ((mask & 8u) ? 0 : kBig);
         e.Gc = Gc;
-        e.LQ = R.load - d.Q;
+        e.LQ = R.load - Q;
         e.loadf = b.loadf;
-        e.loadgQ = b.loadg - d.Q;
+        e.loadgQ = b.loadg - Q;
         e.C2 = kBig; e.ld2 = 0; e.E2 = 0; e.L2 = 0; e.Dm2 = 0;
         e.C3 = kBig; e.ld3 = 0; e.E3 = 0; e.L3 = 0; e.Dm3 = 0;
+        if (pd) {
+            pr.pk = __ldg(d.pickup + x);
+            pr.mx = max(e.d, pr.pk);
+            pr.IA = b.lmf + b.loadg - Q; pr.IB = b.lof + b.loadg - Q; pr.IC = b.lof + b.lmg - Q;
+            pr.HM = b.lmf - Q; pr.HO = b.lof - Q; pr.TI = b.loadg; pr.TM = b.lmg;
+        }
         if (k == 0) {
             e.rem1 = kBig; e.K2 = kBig; e.LQd = 0; e.tauP = 0;
         } else {
@@ -209,42 +271,54 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
             const int xn = route_node(d, st, L, k + 1);
             const int cmn = dmat(d, xm, xn);
             const int twr = tw ? bp.twf + b.twg + max(bp.tau + cmn - b.Lg, 0) : 0;
-            const int c1 = bp.distf + cmn + b.distg + d.wL * max(R.load - e.d - d.Q, 0) + wTe * twr;
+            // load of the route without x: prefix through x- + suffix after x
+            const int lrem = pd ? max(bp.lmf + b.loadg, bp.lof + b.lmg) : R.load - e.d;
+            const int c1 = bp.distf + cmn + b.distg + d.wL * max(lrem - Q, 0) + wTe * twr;
             e.rem1 = c1 - R.cost + ((mask & 1u) ? 0 : kBig);
             e.K2 = bp.distf + b.distg + wTe * (bp.twf + b.twg) - R.cost + ((mask & 2u) ? 0 : kBig);
-            e.LQd = R.load - e.d - d.Q;
+            e.LQd = R.load - e.d - Q;
             e.tauP = bp.tau;
+            if (pd) {
+                pr.SA = bp.lmf + b.loadg - Q; pr.SB = bp.lof + b.loadg - Q; pr.SC = bp.lof + b.lmg - Q;
+            }
             for (int K = 2; K <= 3; ++K) {
                 if (k + K - 1 > L || !(mask & (1u << (K + 2)))) continue;
                 Seg run = seg_node(d, x, dmat(d, x, route_node(d, st, L, k + 1)));
+                Ld rl{0, 0, 0};
+                if (pd) rl = ld_node(d, x);
                 for (int t = 1; t < K; ++t) {
                     const int y = route_node(d, st, L, k + t);
                     run = seg_cat(run, seg_node(d, y, dmat(d, y, route_node(d, st, L, k + t + 1))));
+                    if (pd) rl = ld_cat(rl, ld_node(d, y));
                 }
                 const int w = route_node(d, st, L, k + K - 1);
                 const BRec bw = d.brec[w];
                 const int wn = route_node(d, st, L, k + K);
                 const int c2 = dmat(d, xm, wn);
                 const int twk = tw ? bp.twf + bw.twg + max(bp.tau + c2 - bw.Lg, 0) : 0;
-                const int ck = bp.distf + c2 + bw.distg + d.wL * max(R.load - run.load - d.Q, 0) +
-                               wTe * twk - R.cost;
+                const int lk = pd ? max(bp.lmf + bw.loadg, bp.lof + bw.lmg) : R.load - run.load;
+                const int ck = bp.distf + c2 + bw.distg + d.wL * max(lk - Q, 0) + wTe * twk - R.cost;
                 const int CK = ck + run.dist + wTe * (tw ? run.TW : 0);
                 if (K == 2) {
                     e.C2 = CK; e.ld2 = run.load;
                     e.E2 = tw ? run.E : 0; e.L2 = tw ? run.L : 0; e.Dm2 = tw ? run.D - run.TW : 0;
+                    pr.LO2 = rl.o; pr.LM2 = rl.m;
                 } else {
                     e.C3 = CK; e.ld3 = run.load;
                     e.E3 = tw ? run.E : 0; e.L3 = tw ? run.L : 0; e.Dm3 = tw ? run.D - run.TW : 0;
+                    pr.LO3 = rl.o; pr.LM3 = rl.m;
                 }
             }
         }
         d.erec[a] = e;
+        if (pd) d.prec[a] = pr;
     }
 }
 
 // Integer headroom: a route built from two current routes plus three moved
 // customers must cost below 2^27 (bound from the longest route, heaviest load
-// and the largest distance, window and service).
+// and the largest distance, window and service).  With pickups "load" is
+// delivery plus pickup, which bounds every load on board.
 __device__ bool range_ok_vals(const Dev &d, int maxL, int maxLoad, int maxc, int maxl, int maxe, int maxs,
                               int maxd) {
     if (maxc >= (1 << 24) || maxl >= (1 << 24) || maxe >= (1 << 24) || maxs >= (1 << 24) || maxd >= (1 << 24))
@@ -299,6 +373,11 @@ __device__ void check_instance_tiles(const Dev &d, int part, int nparts) {
         const int dm = d.demand[i];
         if (dm < 0 || (i == 0 && dm != 0)) bad = true;
         md = max(md, dm);
+        if (d.has_pd) {                        // range bound: delivery plus pickup
+            const int pk = d.pickup[i];
+            if (pk < 0 || (i == 0 && pk != 0)) bad = true;
+            md = max(md, dm + pk);
+        }
         if (d.has_tw) {
             const int e = d.early[i], l = d.late[i], sv = d.service[i];
             if (e < 0 || l < 0 || sv < 0 || (i == 0 && sv != 0)) bad = true;
@@ -362,7 +441,7 @@ __device__ void finish_block(const Dev &d) {
             q1 += (long long)max(R.len - 1, 0) * max(R.len - 1, 0);
             q2 += (long long)max(R.len - 2, 0) * max(R.len - 2, 0);
             maxL = max(maxL, R.len);
-            maxLoad = max(maxLoad, R.load);
+            maxLoad = max(maxLoad, d.has_pd ? R.load + R.lo : R.load);
         }
     }
     for (int off = 16; off > 0; off >>= 1) {
@@ -411,6 +490,7 @@ __device__ void finish_block(const Dev &d) {
         BRec b{};
         b.route = -1;
         d.brec[d.W] = b;
+        if (d.has_pd) d.prec[d.W] = PRec{};
     }
 }
 
@@ -461,16 +541,18 @@ __device__ __forceinline__ int2 tile_of(int bid, int Wp, int TR, int TC) {
 // q0..q0+32*NWc-1 with NWc = warps / RS.  Warp w owns the 32 columns of slice
 // w % NWc and the rows of group w / NWc (TR/RS rows each).  Every thread folds
 // its column's candidates into (best, bidx); smem must hold
-// inter_smem_bytes(TR, NWc).
-template <bool TW, bool OR>
+// inter_smem_bytes(TR, NWc, PD).  PD: pickups (requires TW); every load
+// excess is that of the new route's largest load (PRec constants).
+template <bool TW, bool OR, bool PD = false>
 __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *smem, int &best, unsigned &bidx) {
+    constexpr int NG = PD ? 12 : 8;                           // int4 records per row
     const int NW = blockDim.x >> 5, NWc = NW / RS, TC = NWc * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cw = warp % NWc, rg = warp / NWc, rows_per = TR / RS;
     const int i0 = rg * rows_per, i1 = i0 + rows_per;
     const int LDT = TC + 8;
     int *sT = smem;                                           // (TR+4) x LDT distances
-    int4 *sR = reinterpret_cast<int4 *>(smem + (TR + 4) * LDT);   // TR row records
+    int4 *sR = reinterpret_cast<int4 *>(smem + (TR + 4) * LDT);   // TR row records (ERec, then PRec)
     __syncthreads();                                          // previous user of smem is done
 
     // Extraction: rows p0-1 .. p0+TR+2, positions q0-4 .. q0+TC+3
@@ -481,10 +563,20 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
         int4 *dst = reinterpret_cast<int4 *>(sT + rr * LDT);
         for (int c = lane; c < (LDT >> 2); c += 32) dst[c] = TGA_LDG(src + c);
     }
-    for (int i = threadIdx.x; i < TR * 8; i += blockDim.x) {
-        const int p = p0 + (i >> 3);
-        const int a = (p < d.Wp) ? d.seq[p] : d.W;
-        sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + (i & 7));
+    if (PD) {
+        for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
+            const int row = i / NG, g = i - row * NG;
+            const int p = p0 + row;
+            const int a = (p < d.Wp) ? d.seq[p] : d.W;
+            sR[i] = g < 8 ? TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + g)
+                          : TGA_LDG(reinterpret_cast<const int4 *>(d.prec + a) + (g - 8));
+        }
+    } else {
+        for (int i = threadIdx.x; i < TR * 8; i += blockDim.x) {
+            const int p = p0 + (i >> 3);
+            const int a = (p < d.Wp) ? d.seq[p] : d.W;
+            sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + (i & 7));
+        }
     }
     const int q = q0 + cw * 32 + lane;
     const int av = (q < d.Wp) ? d.seq[q] : d.W;
@@ -502,6 +594,12 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
     const int Ve = v4.x, Vl = v4.y, Vs = v4.z, Vtau = v4.w;
     const int VLg = v5.x, VtauP = v5.y, VE2 = v5.z, VL2 = v5.w;
     const int VDm2 = v6.x, VE3 = v6.y, VL3 = v6.z, VDm3 = v6.w;
+    int4 w0 = make_int4(0, 0, 0, 0), w1 = w0, w2 = w0, w3 = w0;
+    if (PD) {
+        const int4 *pr = reinterpret_cast<const int4 *>(d.prec + av);
+        w0 = TGA_LDG(pr + 0); w1 = TGA_LDG(pr + 1); w2 = TGA_LDG(pr + 2);
+        if (OR) w3 = TGA_LDG(pr + 3);
+    }
     __syncthreads();
 
     const int wL = d.wL, wT = d.wT;
@@ -517,7 +615,7 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
 #pragma unroll 1
     for (int i = i0; i < i1; ++i) {
         const int p = p0 + i;
-        const int4 u0 = sR[i * 8 + 0], u1 = sR[i * 8 + 1], u2 = sR[i * 8 + 2];
+        const int4 u0 = sR[i * NG + 0], u1 = sR[i * NG + 1], u2 = sR[i * NG + 2];
         const int Uroute = u0.x, Ud = u0.y, Urem1 = u0.z, UK1 = u0.w;
         const int ULQ = u1.x, UK2 = u1.y, ULQd = u1.z, UFc = u1.w;
         const int UGc = u2.x, Uloadf = u2.y, UloadgQ = u2.z;
@@ -525,26 +623,54 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
         //   c(u,v)=t00 c(u,v+)=t01 c(u+,v)=t10 c(u+,v+)=t11 c(u++,v+)=t21
         //   c(u+,v++)=t12 c(u-,v)=tm10 c(u,v-)=t0m1
         // relocate u -> after v, relocate v -> after u
-        int dR1 = Urem1 + VK1 + t00 + t01 + wL * max(VLQ + Ud, 0);
-        int dR2 = Vrem1 + UK1 + t00 + t10 + wL * max(ULQ + Vd, 0);
+        // (with pickups the load terms follow below)
+        int dR1 = Urem1 + VK1 + t00 + t01 + (PD ? 0 : wL * max(VLQ + Ud, 0));
+        int dR2 = Vrem1 + UK1 + t00 + t10 + (PD ? 0 : wL * max(ULQ + Vd, 0));
         // swap u <-> v
         int dS = UK2 + VK2 + tm10 + t10 + t0m1 + t01 +
-                 wL * (max(ULQd + Vd, 0) + max(VLQd + Ud, 0));
+                 (PD ? 0 : wL * (max(ULQd + Vd, 0) + max(VLQd + Ud, 0)));
         // 2-opt*: head(u)+tail after v, head(v)+tail after u
         int dX = UFc + VGc + VFc + UGc + t01 + t10 +
-                 wL * (max(Uloadf + VloadgQ, 0) + max(Vloadf + UloadgQ, 0));
+                 (PD ? 0 : wL * (max(Uloadf + VloadgQ, 0) + max(Vloadf + UloadgQ, 0)));
         int dO2a = 0, dO2b = 0, dO3a = 0, dO3b = 0;
         int4 u3 = make_int4(0, 0, 0, 0);
         if (OR) {
-            u3 = sR[i * 8 + 3];
+            u3 = sR[i * NG + 3];
             const int UC2 = u3.x, Uld2 = u3.y, UC3 = u3.z, Uld3 = u3.w;
-            dO2a = UC2 + VK1 + t00 + t11 + wL * max(VLQ + Uld2, 0);
-            dO2b = VC2 + UK1 + t00 + t11 + wL * max(ULQ + Vld2, 0);
-            dO3a = UC3 + VK1 + t00 + t21 + wL * max(VLQ + Uld3, 0);
-            dO3b = VC3 + UK1 + t00 + t12 + wL * max(ULQ + Vld3, 0);
+            dO2a = UC2 + VK1 + t00 + t11 + (PD ? 0 : wL * max(VLQ + Uld2, 0));
+            dO2b = VC2 + UK1 + t00 + t11 + (PD ? 0 : wL * max(ULQ + Vld2, 0));
+            dO3a = UC3 + VK1 + t00 + t21 + (PD ? 0 : wL * max(VLQ + Uld3, 0));
+            dO3b = VC3 + UK1 + t00 + t12 + (PD ? 0 : wL * max(ULQ + Vld3, 0));
+        }
+        if (PD) {
+            // largest loads of the new routes (Section 4.3.2) from the PRec
+            // constants: insertion after an anchor, a customer in place of
+            // another, and the 2-opt* recombinations
+            const int4 x0 = sR[i * NG + 8], x1 = sR[i * NG + 9], x2 = sR[i * NG + 10];
+            const int UIA = x0.x, UIB = x0.y, UIC = x0.z, Upk = x0.w;
+            const int USA = x1.x, USB = x1.y, USC = x1.z, Umx = x1.w;
+            const int UHM = x2.x, UHO = x2.y, UTI = x2.z, UTM = x2.w;
+            const int VIA = w0.x, VIB = w0.y, VIC = w0.z, Vpk = w0.w;
+            const int VSA = w1.x, VSB = w1.y, VSC = w1.z, Vmx = w1.w;
+            const int VHM = w2.x, VHO = w2.y, VTI = w2.z, VTM = w2.w;
+            dR1 += wL * max(max(max(VIA + Ud, VIB + Umx), VIC + Upk), 0);
+            dR2 += wL * max(max(max(UIA + Vd, UIB + Vmx), UIC + Vpk), 0);
+            dS += wL * (max(max(max(USA + Vd, USB + Vmx), USC + Vpk), 0) +
+                        max(max(max(VSA + Ud, VSB + Umx), VSC + Upk), 0));
+            dX += wL * (max(max(UHM + VTI, UHO + VTM), 0) + max(max(VHM + UTI, VHO + UTM), 0));
+            if (OR) {
+                const int4 x3 = sR[i * NG + 11];
+                const int ULO2 = x3.x, ULM2 = x3.y, ULO3 = x3.z, ULM3 = x3.w;
+                const int VLO2 = w3.x, VLM2 = w3.y, VLO3 = w3.z, VLM3 = w3.w;
+                const int Uld2 = u3.y, Uld3 = u3.w;
+                dO2a += wL * max(max(max(VIA + Uld2, VIB + ULM2), VIC + ULO2), 0);
+                dO2b += wL * max(max(max(UIA + Vld2, UIB + VLM2), UIC + VLO2), 0);
+                dO3a += wL * max(max(max(VIA + Uld3, VIB + ULM3), VIC + ULO3), 0);
+                dO3b += wL * max(max(max(UIA + Vld3, UIB + VLM3), UIC + VLO3), 0);
+            }
         }
         if (TW) {
-            const int4 u4 = sR[i * 8 + 4], u5 = sR[i * 8 + 5];
+            const int4 u4 = sR[i * NG + 4], u5 = sR[i * NG + 5];
             const int Ue = u4.x, Ul = u4.y, Us = u4.z, Utau = u4.w;
             const int ULg = u5.x, UtauP = u5.y;
             {   // u inserted between v and v+
@@ -567,7 +693,7 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
             dX += wT * (max(Utau + t01 - VLg, 0) + max(Vtau + t10 - ULg, 0));
             if (OR) {
                 const int UE2 = u5.z, UL2 = u5.w;
-                const int4 u6 = sR[i * 8 + 6];
+                const int4 u6 = sR[i * NG + 6];
                 const int UDm2 = u6.x, UE3 = u6.y, UL3 = u6.z, UDm3 = u6.w;
                 {
                     const int a1 = Vtau + t00, w1 = max(a1 - UL2, 0);
@@ -750,14 +876,23 @@ __device__ unsigned edge_candidates(const Dev &d, int u, int v, bool rev, int &b
 
 constexpr int kIntraWarps = 4;
 constexpr int kIntraSmemPerWarp = 2816;      // ints (11 KB)
-constexpr int kIntraVec = 10;                // staged per-element int arrays
 
 struct RouteView {
     const Dev *d;
     int r, L, E, st;
     bool inS;                 // distance block in shared memory
     const int *node, *e, *l, *s, *tau, *twf, *distf, *Lg, *twg, *distg;
+    // pickups: prefix L_I, L_O, L_M through element k; suffix L_I, L_M after it
+    const int *lif, *lof, *lmf, *lig, *lmg;
     const int *D;             // E x E (if inS)
+    // loads of the customer at element k (1..L)
+    __device__ __forceinline__ Ld ldn(int k) const {
+        Ld x;
+        x.i = lif[k] - lif[k - 1];
+        x.o = lof[k] - lof[k - 1];
+        x.m = max(x.i, x.o);
+        return x;
+    }
     __device__ __forceinline__ int c(int a, int b) const {
         if (inS) return D[a * E + b];
         return TGA_LDG(d->pcol + (size_t)node[a] * d->ldp + kColOff + st + b);
@@ -770,12 +905,18 @@ struct RouteView {
     }
 };
 
-template <bool TW>
 // kinds selects the sweeps this call runs: bit k-1 forward relocate/or-opt
 // of a run of k, bit 3 swap, bit 4 2-opt, bit 4+k backward run of k.
+// PD: pickups; each candidate adds the change of the load excess of the
+// route's largest load (basePen = the current excess), built by the same
+// incremental concatenations with the loads of Section 4.3.2.
+template <bool TW, bool PD = false>
 __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, int baseDist, int baseTw,
-                             unsigned W, unsigned W2, int &best, unsigned &bidx, unsigned kinds = 0xffu) {
+                             unsigned W, unsigned W2, int &best, unsigned &bidx, unsigned kinds = 0xffu,
+                             int Q = 0, int wL = 0, int basePen = 0) {
     const int L = V.L;
+    // load term of a new route whose largest load is LM
+    auto pen = [&](int LM) { return wL * (max(LM - Q, 0) - basePen); };
     if (i >= 1) {
         // ---------------- moves that take the customer at element i forward
         const unsigned xi = (unsigned)V.node[i];
@@ -786,6 +927,13 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
             if (!(kinds & (1u << (k - 1))) || !(mask & (1u << op)) || i + k - 1 > L) continue;
             Seg run = V.seg(i, V.c(i, i + 1));
             for (int t = 1; t < k; ++t) run = seg_cat(run, V.seg(i + t, V.c(i + t, i + t + 1)));
+            Ld runl{0, 0, 0};
+            int ao = 0, am = 0;                  // prefix through i-1, then the elements i+k..j
+            if (PD) {
+                runl = V.ldn(i);
+                for (int t = 1; t < k; ++t) runl = ld_cat(runl, V.ldn(i + t));
+                ao = V.lof[i - 1]; am = V.lmf[i - 1];
+            }
             int tau = ptau, tw = ptwf, dist = pdist, last = i - 1;
             for (int j = i + k; j <= L; ++j) {
                 const int c1 = V.c(last, j);
@@ -805,15 +953,23 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
                     const int w2 = max(a2 - V.Lg[j], 0);
                     delta += wT * (tw + w1 + run.TW + w2 + V.twg[j] - baseTw);
                 }
+                if (PD) {
+                    const Ld nj = V.ldn(j);
+                    am = max(am + nj.i, ao + nj.m);
+                    ao += nj.o;
+                    delta += pen(ld_close(ao, am, runl, V.lig[j], V.lmg[j]));
+                }
                 TGA_TRY(delta, (unsigned)op * W2 + xi * W + (unsigned)V.node[j]);
             }
         }
         // swap element i <-> element j, j > i
         if ((kinds & 8u) && (mask & 2u)) {
             Seg M{};
+            Ld Ml{0, 0, 0};
             for (int j = i + 1; j <= L; ++j) {
                 if (j > i + 2) M = seg_cat(M, V.seg(j - 1, V.c(j - 1, j)));
                 else if (j == i + 2) M = V.seg(i + 1, V.c(i + 1, j));
+                if (PD && j >= i + 2) Ml = j == i + 2 ? V.ldn(i + 1) : ld_cat(Ml, V.ldn(j - 1));
                 const bool hasM = j > i + 1;
                 const int ca = V.c(i - 1, j);
                 int dist = pdist + ca + V.distg[j];
@@ -843,6 +999,12 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
                     const int w4 = max(t2 + cd - V.Lg[j], 0);
                     delta += wT * (tw + w + w4 + V.twg[j] - baseTw);
                 }
+                if (PD) {   // prefix(i-1) + x_j + (i+1..j-1) + x_i + suffix(j)
+                    Ld g = V.ldn(j);
+                    if (hasM) g = ld_cat(g, Ml);
+                    g = ld_cat(g, V.ldn(i));
+                    delta += pen(ld_close(V.lof[i - 1], V.lmf[i - 1], g, V.lig[j], V.lmg[j]));
+                }
                 const unsigned xj = (unsigned)V.node[j];
                 TGA_TRY(delta, W2 + min(xi, xj) * W + max(xi, xj));
             }
@@ -850,6 +1012,8 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
         // 2-opt: reverse elements i..j, j > i
         if ((kinds & 16u) && (mask & 4u)) {
             Seg Rv = V.seg(i, 0);
+            Ld Rl{0, 0, 0};
+            if (PD) Rl = V.ldn(i);
             for (int j = i + 1; j <= L; ++j) {
                 Rv = seg_cat(V.seg(j, V.c(j, j - 1)), Rv);
                 const int ca = V.c(i - 1, j), cb = V.c(i, j + 1);
@@ -859,6 +1023,10 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
                     const int a2 = max(a1, Rv.E) - w1 + Rv.D - Rv.TW + cb;
                     const int w2 = max(a2 - V.Lg[j], 0);
                     delta += wT * (ptwf + w1 + Rv.TW + w2 + V.twg[j] - baseTw);
+                }
+                if (PD) {   // prefix(i-1) + reversed (i..j) + suffix(j)
+                    Rl = ld_cat(V.ldn(j), Rl);
+                    delta += pen(ld_close(V.lof[i - 1], V.lmf[i - 1], Rl, V.lig[j], V.lmg[j]));
                 }
                 TGA_TRY(delta, 2u * W2 + xi * W + (unsigned)V.node[j]);
             }
@@ -872,8 +1040,11 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
         const int op = k == 1 ? 0 : k + 2;
         if (!(kinds & (1u << (4 + k))) || !(mask & (1u << op)) || j + 2 + k - 1 > L) continue;
         Seg M = V.seg(j + 1, V.c(j + 1, j + 2));
+        Ld Ml{0, 0, 0};
+        if (PD) Ml = V.ldn(j + 1);
         for (int t = j + 2; t + k - 1 <= L; ++t) {
             if (t > j + 2) M = seg_cat(M, V.seg(t - 1, V.c(t - 1, t)));
+            if (PD && t > j + 2) Ml = ld_cat(Ml, V.ldn(t - 1));
             Seg run = V.seg(t, V.c(t, t + 1));
             for (int u = 1; u < k; ++u) run = seg_cat(run, V.seg(t + u, V.c(t + u, t + u + 1)));
             const int w = t + k - 1;
@@ -887,6 +1058,12 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
                 const int w3 = max(a3 - V.Lg[w], 0);
                 delta += wT * (V.twf[j] + w1 + run.TW + w2 + M.TW + w3 + V.twg[w] - baseTw);
             }
+            if (PD) {   // prefix(j) + run (t..w) + (j+1..t-1) + suffix(w)
+                Ld g = V.ldn(t);
+                for (int u = 1; u < k; ++u) g = ld_cat(g, V.ldn(t + u));
+                g = ld_cat(g, Ml);
+                delta += pen(ld_close(V.lof[j], V.lmf[j], g, V.lig[w], V.lmg[w]));
+            }
             TGA_TRY(delta, (unsigned)op * W2 + (unsigned)V.node[t] * W + aj);
         }
     }
@@ -894,7 +1071,7 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
 
 // Intra-route candidates of route r with one warp (all 32 lanes call);
 // S is this warp's kIntraSmemPerWarp ints of shared memory.
-template <bool TW>
+template <bool TW, bool PD = false>
 __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, unsigned &bidx) {
     const RouteRec R = d.rrec[r];
     const int L = R.len;
@@ -902,8 +1079,9 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
     RouteView V;
     V.d = &d; V.r = r; V.L = L; V.E = L + 2; V.st = R.start;
     const int E = V.E;
-    const bool vecS = kIntraVec * E <= kIntraSmemPerWarp;
-    V.inS = vecS && kIntraVec * E + E * E <= kIntraSmemPerWarp;
+    constexpr int NV = PD ? kIntraVecPD : kIntraVec;
+    const bool vecS = NV * E <= kIntraSmemPerWarp;
+    V.inS = vecS && NV * E + E * E <= kIntraSmemPerWarp;
     // per-element arrays: shared memory when they fit, else this
     // route's own slice [start+r, start+r+E) of the global scratch
     int *base = vecS ? S : d.scr_intra + (R.start + r);
@@ -913,6 +1091,9 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
     int *Lg = base + 7 * stride, *twg = base + 8 * stride, *distg = base + 9 * stride;
     V.node = node; V.e = e; V.l = l; V.s = s; V.tau = tau; V.twf = twf; V.distf = distf;
     V.Lg = Lg; V.twg = twg; V.distg = distg;
+    int *lif = base + 10 * stride, *lof = base + 11 * stride, *lmf = base + 12 * stride;
+    int *lig = base + 13 * stride, *lmg = base + 14 * stride;
+    V.lif = lif; V.lof = lof; V.lmf = lmf; V.lig = lig; V.lmg = lmg;
     for (int k = lane; k < E; k += 32) {
         const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[V.st + k] : -1);
         const int x = (k >= 1 && k <= L) ? a : 0;
@@ -923,13 +1104,15 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
             const BRec b = d.brec[a];
             tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
             Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
+            if (PD) { lif[k] = b.loadf; lof[k] = b.lof; lmf[k] = b.lmf; lig[k] = b.loadg; lmg[k] = b.lmg; }
         } else {
             tau[k] = 0; twf[k] = 0; distf[k] = 0; Lg[k] = 0; twg[k] = 0; distg[k] = 0;
+            if (PD) { lif[k] = 0; lof[k] = 0; lmf[k] = 0; lig[k] = 0; lmg[k] = 0; }
         }
     }
     __syncwarp();
     if (V.inS) {
-        int *D = S + kIntraVec * E;
+        int *D = S + NV * E;
         for (int t = lane; t < E * E; t += 32) {
             const int a = t / E, b = t - a * E;
             D[t] = d.pcol[(size_t)node[a] * d.ldp + kColOff + V.st + b];
@@ -942,7 +1125,8 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
     const unsigned W = (unsigned)d.W, W2 = W * W;
     const int wT = TW ? d.wT : 0;
     for (int i = lane; i <= L; i += 32)
-        intra_anchor<TW>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx);
+        intra_anchor<TW, PD>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, 0xffu, d.Q, d.wL,
+                              max(R.lm - d.Q, 0));
     __syncwarp();
 }
 
@@ -950,7 +1134,7 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
 // route into S (kIntraSmemPerWarp ints), then warp w runs the sweep kinds
 // {w, w+nw, ...} of every anchor, so the serial sweeps of one anchor are
 // spread over the warps.
-template <bool TW>
+template <bool TW, bool PD = false>
 __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsigned &bidx) {
     const RouteRec R = d.rrec[r];
     const int L = R.len;
@@ -960,8 +1144,9 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
     RouteView V;
     V.d = &d; V.r = r; V.L = L; V.E = L + 2; V.st = R.start;
     const int E = V.E;
-    const bool vecS = kIntraVec * E <= kIntraSmemPerWarp;
-    V.inS = vecS && kIntraVec * E + E * E <= kIntraSmemPerWarp;
+    constexpr int NV = PD ? kIntraVecPD : kIntraVec;
+    const bool vecS = NV * E <= kIntraSmemPerWarp;
+    V.inS = vecS && NV * E + E * E <= kIntraSmemPerWarp;
     int *base = vecS ? S : d.scr_intra + (R.start + r);
     const int stride = vecS ? E : d.Wp + d.m;
     int *node = base, *e = base + stride, *l = base + 2 * stride, *s = base + 3 * stride;
@@ -969,6 +1154,9 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
     int *Lg = base + 7 * stride, *twg = base + 8 * stride, *distg = base + 9 * stride;
     V.node = node; V.e = e; V.l = l; V.s = s; V.tau = tau; V.twf = twf; V.distf = distf;
     V.Lg = Lg; V.twg = twg; V.distg = distg;
+    int *lif = base + 10 * stride, *lof = base + 11 * stride, *lmf = base + 12 * stride;
+    int *lig = base + 13 * stride, *lmg = base + 14 * stride;
+    V.lif = lif; V.lof = lof; V.lmf = lmf; V.lig = lig; V.lmg = lmg;
     for (int k = tid; k < E; k += nthr) {
         const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[V.st + k] : -1);
         const int x = (k >= 1 && k <= L) ? a : 0;
@@ -979,13 +1167,15 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
             const BRec b = d.brec[a];
             tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
             Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
+            if (PD) { lif[k] = b.loadf; lof[k] = b.lof; lmf[k] = b.lmf; lig[k] = b.loadg; lmg[k] = b.lmg; }
         } else {
             tau[k] = 0; twf[k] = 0; distf[k] = 0; Lg[k] = 0; twg[k] = 0; distg[k] = 0;
+            if (PD) { lif[k] = 0; lof[k] = 0; lmf[k] = 0; lig[k] = 0; lmg[k] = 0; }
         }
     }
     __syncthreads();
     if (V.inS) {
-        int *D = S + kIntraVec * E;
+        int *D = S + NV * E;
         for (int t = tid; t < E * E; t += nthr) {
             const int a = t / E, b = t - a * E;
             D[t] = d.pcol[(size_t)node[a] * d.ldp + kColOff + V.st + b];
@@ -1000,7 +1190,8 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
     const unsigned W = (unsigned)d.W, W2 = W * W;
     const int wT = TW ? d.wT : 0;
     for (int i = lane; i <= L; i += 32)
-        intra_anchor<TW>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, kinds);
+        intra_anchor<TW, PD>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, kinds, d.Q, d.wL,
+                              max(R.lm - d.Q, 0));
 }
 
 // ---------------------------------------------------------------------------
@@ -1019,9 +1210,11 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
 
 constexpr int kTabMaxL = 40;
 constexpr int kTabEntries = kTabMaxL * (kTabMaxL + 1) / 2;
-// shared ints: per-element arrays, the distance block and both int4 tables
+// shared ints: per-element arrays, the distance block and both int4 tables;
+// with pickups also five load arrays and the forward and reversed L_M tables
 constexpr int kIntraTabSmemInts =
     ((kIntraVec * (kTabMaxL + 2) + (kTabMaxL + 2) * (kTabMaxL + 2) + 3) / 4) * 4 + 2 * 4 * kTabEntries;
+constexpr int kIntraTabSmemIntsPD = kIntraTabSmemInts + 5 * (kTabMaxL + 2) + 2 * kTabEntries;
 
 // Entry (i, j), 1 <= i <= j <= L, of a packed upper-triangular table.
 __device__ __forceinline__ int tri_at(int i, int j, int L) {
@@ -1044,12 +1237,13 @@ __device__ __forceinline__ int tw_enter(int a, const int4 g, int &warp) {
     return max(a, g.x) - w + g.z;
 }
 
+template <bool PD = false>
 __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsigned &bidx) {
     const RouteRec R = d.rrec[r];
     const int L = R.len;
     if (L < 2) return;
     if (L > kTabMaxL) {
-        intra_route_block<true>(d, r, S, best, bidx);
+        intra_route_block<true, PD>(d, r, S, best, bidx);
         return;
     }
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1059,6 +1253,11 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
     int *D = S + kIntraVec * E;                                   // E x E distances
     int4 *Ft = reinterpret_cast<int4 *>(S + ((kIntraVec * E + E * E + 3) / 4) * 4);
     int4 *Rt = Ft + L * (L + 1) / 2;
+    // pickups: prefix L_I, L_O, L_M through element k, suffix L_I, L_M after
+    // it, and the L_M of every subsequence forward (FtM) and reversed (RtM)
+    int *lif = reinterpret_cast<int *>(Rt + L * (L + 1) / 2);
+    int *lof = lif + E, *lmf = lif + 2 * E, *lig = lif + 3 * E, *lmg = lif + 4 * E;
+    int *FtM = lif + 5 * E, *RtM = FtM + L * (L + 1) / 2;
     // ---- staging: element records, and the distance block from the
     // position-ordered copy (row of element a, columns st .. st+E-1), both
     // issued right after the positions are known
@@ -1071,8 +1270,10 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
             const BRec b = d.brec[a];
             tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
             Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
+            if (PD) { lif[k] = b.loadf; lof[k] = b.lof; lmf[k] = b.lmf; lig[k] = b.loadg; lmg[k] = b.lmg; }
         } else {
             tau[k] = 0; twf[k] = 0; distf[k] = 0; Lg[k] = 0; twg[k] = 0; distg[k] = 0;
+            if (PD) { lif[k] = 0; lof[k] = 0; lmf[k] = 0; lig[k] = 0; lmg[k] = 0; }
         }
     }
 #pragma unroll 4
@@ -1095,8 +1296,31 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
             cur = rev ? tw_cat(nx, cur, D[j * E + j - 1]) : tw_cat(cur, nx, D[(j - 1) * E + j]);
             T[tri_at(i, j, L)] = cur;
         }
+        if (PD) {
+            int *TM = rev ? RtM : FtM;
+            auto nodeld = [&](int k) {
+                Ld x;
+                x.i = lif[k] - lif[k - 1]; x.o = lof[k] - lof[k - 1]; x.m = max(x.i, x.o);
+                return x;
+            };
+            Ld cl = nodeld(i);
+            TM[tri_at(i, i, L)] = cl.m;
+            for (int j = i + 1; j <= L; ++j) {
+                cl = rev ? ld_cat(nodeld(j), cl) : ld_cat(cl, nodeld(j));
+                TM[tri_at(i, j, L)] = cl.m;
+            }
+        }
     }
     __syncthreads();
+    // loads of the subsequence x_i..x_j (forward, or reversed when rev)
+    auto segld = [&](int i, int j, bool rev) {
+        Ld x;
+        x.i = lif[j] - lif[i - 1]; x.o = lof[j] - lof[i - 1];
+        x.m = (rev ? RtM : FtM)[tri_at(i, j, L)];
+        return x;
+    };
+    const int Q = d.Q, wL = d.wL, basePen = PD ? max(R.lm - Q, 0) : 0;
+    auto pen = [&](int LM) { return wL * (max(LM - Q, 0) - basePen); };
     // ---- candidates: pair (i, j), 0 <= i < j <= L, one pair per thread
     const unsigned mask = d.op_mask;
     const unsigned W = (unsigned)d.W, W2 = W * W;
@@ -1123,7 +1347,12 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
                 const int w2 = max(tr + cB - Lg[j], 0);
                 const int dist = pdist + c0 + (distf[j] - distf[i + k]) + cA + (distf[i + k - 1] - distf[i]) + cB +
                                  distg[j];
-                TGA_TRY(dist - baseDist + wT * (tw + w2 + twg[j] - baseTw), (unsigned)op * W2 + xi * W + xj);
+                int lp = 0;
+                if (PD) {   // prefix(i-1) + (i+k..j) + run + suffix(j)
+                    const Ld g = ld_cat(segld(i + k, j, false), segld(i, i + k - 1, false));
+                    lp = pen(ld_close(lof[i - 1], lmf[i - 1], g, lig[j], lmg[j]));
+                }
+                TGA_TRY(dist - baseDist + wT * (tw + w2 + twg[j] - baseTw) + lp, (unsigned)op * W2 + xi * W + xj);
             }
             // swap x_i <-> x_j
             if (mask & 2u) {
@@ -1141,7 +1370,14 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
                 const int cc = D[last * E + i], cd = D[i * E + j + 1];
                 tx = tw_enter(tx + cc, make_int4(e[i], l[i], s[i], 0), tw);
                 const int w4 = max(tx + cd - Lg[j], 0);
-                TGA_TRY(dist + cc + cd - baseDist + wT * (tw + w4 + twg[j] - baseTw),
+                int lp = 0;
+                if (PD) {   // prefix(i-1) + x_j + (i+1..j-1) + x_i + suffix(j)
+                    Ld g = segld(j, j, false);
+                    if (j > i + 1) g = ld_cat(g, segld(i + 1, j - 1, false));
+                    g = ld_cat(g, segld(i, i, false));
+                    lp = pen(ld_close(lof[i - 1], lmf[i - 1], g, lig[j], lmg[j]));
+                }
+                TGA_TRY(dist + cc + cd - baseDist + wT * (tw + w4 + twg[j] - baseTw) + lp,
                         W2 + min(xi, xj) * W + max(xi, xj));
             }
             // 2-opt: reverse x_i..x_j
@@ -1150,8 +1386,9 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
                 int tw = ptwf;
                 const int tx = tw_enter(ptau + ca, Rt[tri_at(i, j, L)], tw);
                 const int w2 = max(tx + cb - Lg[j], 0);
+                const int lp = PD ? pen(ld_close(lof[i - 1], lmf[i - 1], segld(i, j, true), lig[j], lmg[j])) : 0;
                 TGA_TRY(pdist + ca + (distf[j] - distf[i]) + cb + distg[j] - baseDist +
-                            wT * (tw + w2 + twg[j] - baseTw),
+                            wT * (tw + w2 + twg[j] - baseTw) + lp,
                         2u * W2 + xi * W + xj);
             }
         }
@@ -1169,7 +1406,13 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
             tx = tw_enter(tx + cb, Ft[tri_at(i + 1, j - 1, L)], tw);
             const int w3 = max(tx + cc - Lg[w], 0);
             const int dist = distf[i] + ca + (distf[w] - distf[j]) + cb + (distf[j - 1] - distf[i + 1]) + cc + distg[w];
-            TGA_TRY(dist - baseDist + wT * (tw + w3 + twg[w] - baseTw), (unsigned)op * W2 + (unsigned)node[j] * W + ai);
+            int lp = 0;
+            if (PD) {   // prefix(i) + run (j..w) + (i+1..j-1) + suffix(w)
+                const Ld g = ld_cat(segld(j, w, false), segld(i + 1, j - 1, false));
+                lp = pen(ld_close(lof[i], lmf[i], g, lig[w], lmg[w]));
+            }
+            TGA_TRY(dist - baseDist + wT * (tw + w3 + twg[w] - baseTw) + lp,
+                    (unsigned)op * W2 + (unsigned)node[j] * W + ai);
         }
     }
 }
@@ -1370,10 +1613,12 @@ __device__ __forceinline__ Seg seg_vals(int e, int l, int s, int load, int out) 
 // (x- to x+, and x- to the element after runs of 2 and 3) -- followed by
 // the two concatenation scans (Section 4.3) in registers and the stores.
 // Lane 0 writes the route totals (load, dist, warp, cost) to tot[0..3].
+template <bool PD>
 __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int *sbuf, const StepPlan &S,
                                    int lane, int *tot) {
     const int E = L + 2;
     const bool tw = d.has_tw != 0;
+    constexpr bool pd = PD;
     const int wTe = tw ? d.wT : 0;
     const unsigned mask = d.op_mask;
     const unsigned FULL = 0xffffffffu;
@@ -1406,11 +1651,27 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
         Seg o = shfl_seg_down(g, off);
         if (lane + off < E) g = seg_cat(g, o);
     }
+    // pickups: the same two scans of the loads (Section 4.3.2)
+    Ld ndl{0, 0, 0}, fl{0, 0, 0}, gl{0, 0, 0};
+    if (pd) {
+        ndl = ld_node(d, x);
+        fl = ndl;
+        gl = ndl;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const Ld o = shfl_ld_up(fl, off);
+            if (lane >= off) fl = ld_cat(o, fl);
+            const Ld p = shfl_ld_down(gl, off);
+            if (lane + off < E) gl = ld_cat(gl, p);
+        }
+    }
     // route totals: the prefix of the end depot
     const int Rload = __shfl_sync(FULL, f.load, E - 1);
     const int Rdist = __shfl_sync(FULL, f.dist, E - 1);
     const int Rtw = tw ? __shfl_sync(FULL, f.TW, E - 1) : 0;
-    const int Rcost = L == 0 ? 0 : Rdist + d.wL * max(Rload - d.Q, 0) + wTe * Rtw;
+    const int Rlo = pd ? __shfl_sync(FULL, fl.o, E - 1) : 0;
+    const int Rlm = pd ? __shfl_sync(FULL, fl.m, E - 1) : Rload;
+    const int Rcost = L == 0 ? 0 : Rdist + d.wL * max(Rlm - d.Q, 0) + wTe * Rtw;
     // own record: prefix through x, suffix after x (= backward scan at k+1)
     const int tau = tw ? f.E + f.D - f.TW : 0, twf = tw ? f.TW : 0;
     const int gL = __shfl_down_sync(FULL, g.L, 1), gTW = __shfl_down_sync(FULL, g.TW, 1);
@@ -1427,13 +1688,26 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
     // the runs x..x+1 and x..x+2
     const Seg n1 = shfl_seg_down(node, 1), n2 = shfl_seg_down(node, 2);
     const Seg run2 = seg_cat(node, n1), run3 = seg_cat(run2, n2);
+    // pickups: suffix loads after x, after x+1 and after x+2; prefix loads
+    // through x-; the loads of the runs
+    int glI = 0, glM = 0, w2I = 0, w2M = 0, w3I = 0, w3M = 0, plo = 0, plm = 0;
+    Ld r2l{0, 0, 0}, r3l{0, 0, 0};
+    if (pd) {
+        glI = __shfl_down_sync(FULL, gl.i, 1); glM = __shfl_down_sync(FULL, gl.m, 1);
+        w2I = __shfl_down_sync(FULL, glI, 1); w2M = __shfl_down_sync(FULL, glM, 1);
+        w3I = __shfl_down_sync(FULL, glI, 2); w3M = __shfl_down_sync(FULL, glM, 2);
+        plo = __shfl_up_sync(FULL, fl.o, 1); plm = __shfl_up_sync(FULL, fl.m, 1);
+        const Ld m1 = shfl_ld_down(ndl, 1), m2 = shfl_ld_down(ndl, 2);
+        r2l = ld_cat(ndl, m1);
+        r3l = ld_cat(r2l, m2);
+    }
     if (k <= L) {
         const int a = k == 0 ? d.n + 1 + r : x;
         int4 *bp = reinterpret_cast<int4 *>(d.brec + a);
         bp[0] = make_int4(x, r, k, L);
         bp[1] = make_int4(tau, twf, f.dist, f.load);
         bp[2] = make_int4(Lg, twg, gdist, gload);
-        bp[3] = make_int4(Rcost, 0, 0, 0);
+        bp[3] = make_int4(Rcost, fl.o, fl.m, glM);
         const int Fc = f.dist + wTe * twf - Rcost;
         const int Gc = gdist + wTe * twg;
         int rem1 = kBig, K2 = kBig, LQd = 0, tauP = 0;
@@ -1441,21 +1715,24 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
         int C3 = kBig, ld3 = 0, E3 = 0, L3 = 0, Dm3 = 0;
         if (k >= 1) {
             const int twr = tw ? ptwf + twg + max(ptau + cmn - Lg, 0) : 0;
-            const int c1 = pdist + cmn + gdist + d.wL * max(Rload - dem - d.Q, 0) + wTe * twr;
+            const int lrem = pd ? max(plm + glI, plo + glM) : Rload - dem;
+            const int c1 = pdist + cmn + gdist + d.wL * max(lrem - d.Q, 0) + wTe * twr;
             rem1 = c1 - Rcost + ((mask & 1u) ? 0 : kBig);
             K2 = pdist + gdist + wTe * (ptwf + twg) - Rcost + ((mask & 2u) ? 0 : kBig);
             LQd = Rload - dem - d.Q;
             tauP = ptau;
             if (k + 1 <= L && (mask & 16u)) {
                 const int twk = tw ? ptwf + w2tw + max(ptau + c2 - w2L, 0) : 0;
-                const int ck = pdist + c2 + w2dist + d.wL * max(Rload - run2.load - d.Q, 0) + wTe * twk - Rcost;
+                const int lk = pd ? max(plm + w2I, plo + w2M) : Rload - run2.load;
+                const int ck = pdist + c2 + w2dist + d.wL * max(lk - d.Q, 0) + wTe * twk - Rcost;
                 C2 = ck + run2.dist + wTe * (tw ? run2.TW : 0);
                 ld2 = run2.load;
                 if (tw) { E2 = run2.E; L2 = run2.L; Dm2 = run2.D - run2.TW; }
             }
             if (k + 2 <= L && (mask & 32u)) {
                 const int twk = tw ? ptwf + w3tw + max(ptau + c3 - w3L, 0) : 0;
-                const int ck = pdist + c3 + w3dist + d.wL * max(Rload - run3.load - d.Q, 0) + wTe * twk - Rcost;
+                const int lk = pd ? max(plm + w3I, plo + w3M) : Rload - run3.load;
+                const int ck = pdist + c3 + w3dist + d.wL * max(lk - d.Q, 0) + wTe * twk - Rcost;
                 C3 = ck + run3.dist + wTe * (tw ? run3.TW : 0);
                 ld3 = run3.load;
                 if (tw) { E3 = run3.E; L3 = run3.L; Dm3 = run3.D - run3.TW; }
@@ -1470,14 +1747,26 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
         ep[5] = make_int4(Lg, tauP, E2, L2);
         ep[6] = make_int4(Dm2, E3, L3, Dm3);
         ep[7] = make_int4(x, k, 0, 0);
+        if (pd) {
+            const int Q = d.Q;
+            const int pk = ndl.o;
+            int4 *pp = reinterpret_cast<int4 *>(d.prec + a);
+            pp[0] = make_int4(fl.m + glI - Q, fl.o + glI - Q, fl.o + glM - Q, pk);
+            pp[1] = k >= 1 ? make_int4(plm + glI - Q, plo + glI - Q, plo + glM - Q, max(dem, pk))
+                           : make_int4(0, 0, 0, max(dem, pk));
+            pp[2] = make_int4(fl.m - Q, fl.o - Q, glI, glM);
+            pp[3] = make_int4(C2 < kBig ? r2l.o : 0, C2 < kBig ? r2l.m : 0, C3 < kBig ? r3l.o : 0,
+                              C3 < kBig ? r3l.m : 0);
+        }
     }
     if (lane == 0) {
         RouteRec *R = d.rrec + r;
         R->load = Rload;
+        if (pd) { R->lo = Rlo; R->lm = Rlm; }
         R->dist = Rdist;
         R->tw = Rtw;
         R->cost = Rcost;
-        tot[0] = Rload; tot[1] = Rdist; tot[2] = Rtw; tot[3] = Rcost;
+        tot[0] = pd ? Rload + Rlo : Rload; tot[1] = Rdist; tot[2] = Rtw; tot[3] = Rcost;
     }
 }
 
@@ -1585,6 +1874,7 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
 // thread prefetches the counters.  Thread 0 then updates cost and counters
 // and ends the step (done flag, graph condition).  ext: the move came from
 // the caller, whose delta is not checked against the rebuilt routes.
+template <bool PD>
 __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, bool ext,
                                  cudaGraphConditionalHandle cond, int use_cond) {
     Control *C = d.ctl;
@@ -1619,8 +1909,8 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
             if (isA || pl.B != pl.A) {
                 const int r = isA ? pl.A : pl.B, L = isA ? pl.nLA : pl.nLB;
                 const bool fast = L + 2 <= 32;
-                if (fast) rebuild_route_warp(d, r, plan_new_start(S, isA), L, sbuf, S, lane, s_tot[warp]);
-                else rebuild_route(d, r, lane);
+                if (fast) rebuild_route_warp<PD>(d, r, plan_new_start(S, isA), L, sbuf, S, lane, s_tot[warp]);
+                else rebuild_route<PD>(d, r, lane);
                 if (lane == 0) s_fast[warp] = fast;
             }
         } else {
@@ -1635,7 +1925,8 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
             for (int r = tid - 64; r < d.m; r += nthr - 64) {
                 if (r == pl.A || r == pl.B) continue;
                 mL = max(mL, d.rrec[r].len);
-                mLoad = max(mLoad, d.rrec[r].load);
+                const RouteRec &Rr = d.rrec[r];
+                mLoad = max(mLoad, PD ? Rr.load + Rr.lo : Rr.load);
             }
             mL = __reduce_max_sync(0xffffffffu, mL);
             mLoad = __reduce_max_sync(0xffffffffu, mLoad);
@@ -1648,11 +1939,13 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
             const MovePlan &pl = S.mp;
             const bool two = pl.B != pl.A;
             int costA, loadA, costB = 0, loadB = 0;
+            // range load: the delivery total, plus the pickup total with pickups
+            auto rload = [&](int r) { return d.rrec[r].load + (PD ? d.rrec[r].lo : 0); };
             if (s_fast[0]) { costA = s_tot[0][3]; loadA = s_tot[0][0]; }
-            else { costA = d.rrec[pl.A].cost; loadA = d.rrec[pl.A].load; }
+            else { costA = d.rrec[pl.A].cost; loadA = rload(pl.A); }
             if (two) {
                 if (s_fast[1]) { costB = s_tot[1][3]; loadB = s_tot[1][0]; }
-                else { costB = d.rrec[pl.B].cost; loadB = d.rrec[pl.B].load; }
+                else { costB = d.rrec[pl.B].cost; loadB = rload(pl.B); }
             }
             const long long newcost = (long long)costA + costB;
             const long long dact = newcost - S.oldcost;

@@ -9,7 +9,8 @@
 //     node-based extraction (Section 5.3.1, Eqs. "node_based1/2");
 //   * per anchor the attributes of its prefix (start depot .. x) and of the
 //     suffix after it (x+ .. end depot): distance, load and the time-window
-//     attributes of Section 4.3.3 (T_D, T_E, T_L, T_V);
+//     attributes of Section 4.3.3 (T_D, T_E, T_L, T_V); with pickups also
+//     the outgoing and largest loads L_O, L_M of Section 4.3.2;
 //   * hoisted per-anchor constants that make every candidate an O(1)
 //     integer expression (ERec);
 //   * a copy of the distance matrix whose columns are in position order
@@ -31,13 +32,18 @@ constexpr unsigned long long kNoKey = ~0ull;
 constexpr int kColOff = 4;                    // pcol storage column of position q is q + 4
 constexpr int kMaxTileCols = 256;             // widest tile (8 warps x 32 columns)
 constexpr int kMaxW = 26754;                  // 6 * W^2 < 2^32
+constexpr int kIntraVec = 10;                 // per-element int arrays of an intra-route view
+constexpr int kIntraVecPD = 15;               // ... with the five load arrays of pickups
 
-// Per-anchor base attributes (prefix through x, suffix after x).
+// Per-anchor base attributes (prefix through x, suffix after x).  Loads:
+// loadf / loadg are the incoming loads L_I (total delivery) of the prefix
+// and the suffix; lof, lmf are the prefix's outgoing and largest loads and
+// lmg the suffix's largest load (Section 4.3.2; written only with pickups).
 struct __align__(16) BRec {
     int node, route, idx, rlen;               // idx: 0 for the start depot, 1..L customers; rlen = L
     int tau, twf, distf, loadf;               // prefix: departure time after x, warp, distance, load
     int Lg, twg, distg, loadg;                // suffix after x: latest arrival (T_L), warp, distance, load
-    int rcost, pad2, pad3, pad4;              // cost of the route
+    int rcost, lof, lmf, lmg;                 // cost of the route; pickup loads
 };
 
 // Per-anchor hoisted constants of the inter-route candidate expressions.
@@ -53,8 +59,24 @@ struct __align__(16) ERec {
     int node, idx, pad0, pad1;                // g7
 };
 
+// Per-anchor hoisted constants of the inter-route candidates with pickups
+// (P = prefix through x, S = suffix after x, P- = prefix through the
+// predecessor; every load excess is that of the largest load L_M of the
+// new route, Section 4.3.2).  A segment s inserted between x and x+ gives
+// the excess max(IA + L_I(s), IB + L_M(s), IC + L_O(s)); a customer y in
+// place of x gives max(SA + d_y, SB + max(d_y, p_y), SC + p_y); the 2-opt*
+// route head(x) + tail after z gives max(HM(x) + TI(z), HO(x) + TM(z)).
+struct __align__(16) PRec {
+    int IA, IB, IC, pk;                       // LM_P + LI_S - Q, LO_P + LI_S - Q, LO_P + LM_S - Q; p_x
+    int SA, SB, SC, mx;                       // the same with P-; max(d_x, p_x)
+    int HM, HO, TI, TM;                       // LM_P - Q, LO_P - Q, LI_S, LM_S
+    int LO2, LM2, LO3, LM3;                   // L_O, L_M of the runs of 2 and 3 starting at x
+};
+
+// load = total delivery (L_I); with pickups lo = total pickup (L_O) and lm
+// = the largest load on board (L_M), which the cost penalises
 struct RouteRec {
-    int start, len, load, dist, tw, cost, pad0, pad1;
+    int start, len, load, dist, tw, cost, lo, lm;
 };
 
 // A decoded move.  Routes, indices, lengths and depot positions are the
@@ -114,20 +136,23 @@ struct Control {
 struct Dev {
     int n, m, W, Wp, ldp;
     int Q, wL, wT, has_tw;
+    int has_pd;               // pickups (VRPSPDTW; requires has_tw)
     unsigned op_mask;
     const int *dist, *demand, *service, *early, *late;
+    const int *pickup;        // [n+1] or null
     int *tour, *route_start;
     int *seq;                 // [Wp]  anchor at each position (sentinel: W)
     int *pos_of;              // [W+1]
     BRec *brec;               // [W+1] (index W is the dummy record)
     ERec *erec;               // [W+1]
+    PRec *prec;               // [W+1] (pickups only)
     RouteRec *rrec;           // [m]
     int *pcol;                // [(n+1) * ldp]
     Control *ctl;
     unsigned long long *log;  // optional key log
     long long log_cap;
     int *seen;                // [n+1] permutation check scratch
-    int *scr_intra;           // [10 * (Wp+m)] per-element arrays of routes too long for shared memory
+    int *scr_intra;           // [kIntraVecPD * (Wp+m)] per-element arrays of routes too long for shared memory
     // edge-based extraction (theta > 0): granular mask rows nbr[x*theta + k]
     // and, per entry, whether the reverse entry exists (x in the row of nbr[x*theta+k])
     int theta;
@@ -178,6 +203,37 @@ __device__ __forceinline__ Seg seg_node(const Dev &d, int node, int out) {
     }
     s.TW = 0; s.dist = 0; s.load = __ldg(d.demand + node); s.out = out;
     return s;
+}
+
+// Loads of a segment with pickups (Section 4.3.2): incoming L_I (deliveries
+// on board when it starts), outgoing L_O (pickups on board when it ends) and
+// the largest load L_M.  {0, 0, 0} (a depot) is neutral on both sides
+// because L_M >= L_I and L_M >= L_O for every segment.
+struct Ld {
+    int i, o, m;
+};
+
+__device__ __forceinline__ Ld ld_cat(const Ld &a, const Ld &b) {
+    Ld s;
+    s.i = a.i + b.i;
+    s.o = a.o + b.o;
+    s.m = max(a.m + b.i, a.o + b.m);
+    return s;
+}
+
+__device__ __forceinline__ Ld ld_node(const Dev &d, int node) {
+    Ld s;
+    s.i = __ldg(d.demand + node);
+    s.o = __ldg(d.pickup + node);
+    s.m = max(s.i, s.o);
+    return s;
+}
+
+// Largest load of prefix (o, m) + segment g + suffix (si, sm): the new
+// route's L_M when the suffix's L_I and L_M are si and sm.
+__device__ __forceinline__ int ld_close(int o, int m, const Ld &g, int si, int sm) {
+    const int m1 = max(m + g.i, o + g.m);
+    return max(m1 + si, o + g.o + sm);
 }
 
 __device__ __forceinline__ unsigned long long pack_key(int delta, unsigned idx) {
@@ -318,7 +374,7 @@ int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int wa
 // Edge-based extraction: validate the mask rows and mark reverse entries;
 // *bad_dev (device int) is set when an entry is not another customer.
 void launch_granular_setup(const Dev &d, unsigned char *rev, int *bad_dev, cudaStream_t s);
-size_t inter_smem_bytes(int rows, int warps);
+size_t inter_smem_bytes(int rows, int warps, bool pd = false);
 int setup_kernel_attrs(int max_band);
 
 }  // namespace tga

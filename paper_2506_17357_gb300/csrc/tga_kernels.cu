@@ -47,7 +47,8 @@ __global__ void k_build_routes(Dev d) {
     if (d.ctl->status != 0) return;
     const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= d.m) return;
-    rebuild_route(d, r, threadIdx.x & 31);
+    if (d.has_pd) rebuild_route<true>(d, r, threadIdx.x & 31);
+    else rebuild_route<false>(d, r, threadIdx.x & 31);
 }
 
 __global__ void __launch_bounds__(1024) k_build_finish(Dev d) { finish_block(d); }
@@ -61,7 +62,7 @@ __global__ void k_pcol_init(Dev d) {
 // The finished-descent flag is loaded first but tested only before the key
 // is folded in, so its round trip overlaps the staging loads (a launch on a
 // finished descent does its work and discards it).
-template <bool TW, bool OR>
+template <bool TW, bool OR, bool PD = false>
 __global__ void __launch_bounds__(256) k_eval_inter(Dev d, int TR, int RS, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
     extern __shared__ __align__(16) int smem[];
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(256) k_eval_inter(Dev d, int TR, int RS, int t
     const int2 tl = tile_of(blockIdx.x, d.Wp, TR, TC);
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    inter_tile<TW, OR>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
+    inter_tile<TW, OR, PD>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
     if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
@@ -127,13 +128,15 @@ __global__ void k_granular_setup(Dev d, unsigned char *rev, int *bad) {
 }
 
 // VRPTW intra-route moves: one block of kIntraWarps warps per route
-// (subsequence tables in kIntraTabSmemInts ints of dynamic shared memory).
+// (subsequence tables in kIntraTabSmemInts ints of dynamic shared memory;
+// kIntraTabSmemIntsPD with pickups).
+template <bool PD>
 __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
     extern __shared__ __align__(16) int smem[];
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    intra_route_table(d, blockIdx.x, smem, best, bidx);
+    intra_route_table<PD>(d, blockIdx.x, smem, best, bidx);
     if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
@@ -158,6 +161,7 @@ __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d, int tail) {
 // pre = 0: CTA 0 decodes *ext (or the best key) and publishes the plan while
 // the other CTAs wait for it.  The last CTA to finish re-arms the plan flag
 // for the next step.
+template <bool PD>
 __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaGraphConditionalHandle cond,
                                                int use_cond, int pre) {
     extern __shared__ __align__(16) int smem[];
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
         __syncthreads();
         if (!s_ok && tid == 0) sP.act = 0;
         __syncthreads();
-        if (blockIdx.x == 0) apply_plan_block(d, sP, smem, false, cond, use_cond);
+        if (blockIdx.x == 0) apply_plan_block<PD>(d, sP, smem, false, cond, use_cond);
         else band_plan_rows(d, sP, smem, 0, d.n + 1, blockIdx.x - 1, gridDim.x - 1);
     } else if (blockIdx.x == 0) {
         if (tid == 0) {
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
             atomicExch(&C->plan_ready, 1);
         }
         __syncthreads();
-        apply_plan_block(d, sP, smem, ext != nullptr, cond, use_cond);
+        apply_plan_block<PD>(d, sP, smem, ext != nullptr, cond, use_cond);
     } else {
         if (tid == 0) {
             s_ok = wait_flag(&C->plan_ready, 1000LL * 1000 * 1000);
@@ -244,9 +248,9 @@ __global__ void k_begin(Dev d, long long max_steps) {
 // ---------------------------------------------------------------------------
 // host-side launchers
 
-size_t inter_smem_bytes(int rows, int warps) {
+size_t inter_smem_bytes(int rows, int warps, bool pd) {
     const int LDT = warps * 32 + 8;
-    return (size_t)(rows + 4) * LDT * sizeof(int) + (size_t)rows * sizeof(ERec);
+    return (size_t)(rows + 4) * LDT * sizeof(int) + (size_t)rows * (sizeof(ERec) + (pd ? sizeof(PRec) : 0));
 }
 
 int setup_kernel_attrs(int max_band) {
@@ -256,7 +260,12 @@ int setup_kernel_attrs(int max_band) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eval_inter<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eval_inter<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     (void)max_band;
     return e == cudaSuccess ? 0 : 1;
 }
@@ -297,10 +306,13 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
         return;
     }
     if (ntiles <= 0) return;
-    const size_t sm = inter_smem_bytes(rows, warps);
+    const size_t sm = inter_smem_bytes(rows, warps, d.has_pd != 0);
     const bool orr = (d.op_mask & 48u) != 0;
     const int nt = warps * 32 * rs;
-    if (d.has_tw) {
+    if (d.has_pd) {             // pickups come with time windows
+        if (orr) k_eval_inter<true, true, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
+        else k_eval_inter<true, false, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
+    } else if (d.has_tw) {
         if (orr) k_eval_inter<true, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
         else k_eval_inter<true, false><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
     } else {
@@ -324,7 +336,10 @@ void launch_granular_setup(const Dev &d, unsigned char *rev, int *bad_dev, cudaS
 }
 
 void launch_intra(const Dev &d, cudaStream_t s, int tail) {
-    if (d.has_tw) k_eval_intra<<<intra_blocks(d), kIntraWarps * 32, kIntraTabSmemInts * sizeof(int), s>>>(d, tail);
+    if (d.has_pd)
+        k_eval_intra<true><<<intra_blocks(d), kIntraWarps * 32, kIntraTabSmemIntsPD * sizeof(int), s>>>(d, tail);
+    else if (d.has_tw)
+        k_eval_intra<false><<<intra_blocks(d), kIntraWarps * 32, kIntraTabSmemInts * sizeof(int), s>>>(d, tail);
     else k_eval_intra_cvrp<<<intra_blocks(d), 256, 0, s>>>(d, tail);
 }
 
@@ -342,7 +357,8 @@ int apply_grid(const Dev &d) {
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond, cudaStream_t s,
                   int pre) {
     const size_t sm = (size_t)band_smem_ints(d.Wp, 16) * sizeof(int);
-    k_apply<<<apply_grid(d), 512, sm, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond, pre);
+    if (d.has_pd) k_apply<true><<<apply_grid(d), 512, sm, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond, pre);
+    else k_apply<false><<<apply_grid(d), 512, sm, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond, pre);
 }
 
 void launch_sync_solution(const Dev &d, cudaStream_t s) {

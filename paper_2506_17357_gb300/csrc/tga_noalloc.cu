@@ -48,9 +48,10 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
     const size_t o_pos = take(sizeof(int) * (W + 1));
     const size_t o_brec = take(sizeof(BRec) * (W + 1));
     const size_t o_erec = take(sizeof(ERec) * (W + 1));
+    const size_t o_prec = take(sizeof(PRec) * (W + 1));
     const size_t o_rrec = take(sizeof(RouteRec) * m);
     const size_t o_seen = take(sizeof(int) * (n + 1));
-    const size_t o_intra = take(sizeof(int) * 10 * (P + m));
+    const size_t o_intra = take(sizeof(int) * kIntraVecPD * (P + m));
     const size_t o_tiles = take(sizeof(int2) * tiles_upper_bound(P));
     const size_t o_pcol = take(sizeof(int) * (n + 1) * (size_t)d.ldp);
     if (base) {
@@ -59,6 +60,7 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
         d.pos_of = (int *)(base + o_pos);
         d.brec = (BRec *)(base + o_brec);
         d.erec = (ERec *)(base + o_erec);
+        d.prec = (PRec *)(base + o_prec);
         d.rrec = (RouteRec *)(base + o_rrec);
         d.seen = (int *)(base + o_seen);
         d.scr_intra = (int *)(base + o_intra);
@@ -73,8 +75,8 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
 constexpr size_t noalloc_max_bytes() {
     const size_t P = kNoAllocMaxPositions, N1 = P, M = P - 1, W1 = P + 1;
     return align256(sizeof(Control)) + align256(4 * P) + align256(4 * W1) + align256(sizeof(BRec) * W1) +
-           align256(sizeof(ERec) * W1) + align256(sizeof(RouteRec) * M) + align256(4 * N1) +
-           align256(4 * 10 * (P + M)) +
+           align256(sizeof(ERec) * W1) + align256(sizeof(PRec) * W1) + align256(sizeof(RouteRec) * M) +
+           align256(4 * N1) + align256(4 * kIntraVecPD * (P + M)) +
            align256(sizeof(int2) * tiles_upper_bound(P)) + align256(4 * N1 * ldp_for(P));
 }
 
@@ -133,6 +135,7 @@ extern "C" int tga_eval_best_move_noalloc(const tga_instance *inst, const tga_so
     if (op_mask == 0 || op_mask >= 64u) return TGA_ERR_INVALID;
     if (!inst->dist || !inst->demand || !sol->tour || !sol->route_start) return TGA_ERR_INVALID;
     if (inst->has_tw && (!inst->service || !inst->tw_early || !inst->tw_late)) return TGA_ERR_INVALID;
+    if (inst->pickup && !inst->has_tw) return TGA_ERR_INVALID;
     if (n + m + 1 > kNoAllocMaxPositions) return TGA_ERR_RANGE;
 
     Dev d{};
@@ -141,6 +144,8 @@ extern "C" int tga_eval_best_move_noalloc(const tga_instance *inst, const tga_so
     d.op_mask = op_mask;
     d.dist = inst->dist; d.demand = inst->demand;
     d.service = inst->service; d.early = inst->tw_early; d.late = inst->tw_late;
+    d.has_pd = inst->pickup ? 1 : 0;
+    d.pickup = inst->pickup;
     d.tour = sol->tour; d.route_start = sol->route_start;
     d.ldp = (int)ldp_for((size_t)d.Wp);
     d.log = nullptr; d.log_cap = 0;

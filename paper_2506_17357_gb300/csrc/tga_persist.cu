@@ -70,7 +70,8 @@ __device__ bool wait_seq(const int *seq, int want, long long limit_ns) {
 // ntiles inter-route tiles (TR rows x 32 * warps / RS columns each) and
 // nintra intra-route items: one route per item with time windows, else
 // blockDim/32 moved positions per item (one warp each).
-template <bool TW, bool OR, int NT>
+// PD: pickups (with time windows).
+template <bool TW, bool OR, int NT, bool PD>
 __global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const int2 *__restrict__ tiles, int ntiles,
                                                                    int TR, int RS, int nintra, long long limit_ns) {
     extern __shared__ __align__(16) int smem[];
@@ -94,10 +95,10 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const 
         for (int t = cta; t < items; t += G) {
             if (t >= nintra) {
                 const int2 tl = tile_of(t - nintra, d.Wp, TR, TC);
-                inter_tile<TW, OR>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
+                inter_tile<TW, OR, PD>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
             } else if (TW) {
                 __syncthreads();                       // smem of the previous item is free
-                intra_route_table(d, t, smem, best, bidx);
+                intra_route_table<PD>(d, t, smem, best, bidx);
             } else {
                 intra_cvrp_position(d, t * nw + warp, lane, best, bidx);
             }
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const 
         __syncthreads();
         // ---- update
         if (s_ok == 1) {
-            apply_plan_block(d, sP, smem, false, 0, 0);
+            apply_plan_block<PD>(d, sP, smem, false, 0, 0);
             if (G == 1) {
                 __syncthreads();
                 band_plan_rows(d, sP, smem, 0, d.n + 1, 0, 1);
@@ -154,13 +155,15 @@ namespace {
 
 using PersistFn = void (*)(Dev, const int2 *, int, int, int, int, long long);
 
-PersistFn persist_fn(bool tw, bool orr, int nt) {
+PersistFn persist_fn(bool tw, bool orr, int nt, bool pd) {
     if (nt == 128) {
-        if (tw) return orr ? k_persist<true, true, 128> : k_persist<true, false, 128>;
-        return orr ? k_persist<false, true, 128> : k_persist<false, false, 128>;
+        if (pd) return orr ? k_persist<true, true, 128, true> : k_persist<true, false, 128, true>;
+        if (tw) return orr ? k_persist<true, true, 128, false> : k_persist<true, false, 128, false>;
+        return orr ? k_persist<false, true, 128, false> : k_persist<false, false, 128, false>;
     }
-    if (tw) return orr ? k_persist<true, true, 256> : k_persist<true, false, 256>;
-    return orr ? k_persist<false, true, 256> : k_persist<false, false, 256>;
+    if (pd) return orr ? k_persist<true, true, 256, true> : k_persist<true, false, 256, true>;
+    if (tw) return orr ? k_persist<true, true, 256, false> : k_persist<true, false, 256, false>;
+    return orr ? k_persist<false, true, 256, false> : k_persist<false, false, 256, false>;
 }
 
 }  // namespace
@@ -171,14 +174,15 @@ int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int wa
     if (d.theta > 0) return TGA_ERR_STATE;                // edge-based extraction: per-step path only
     if (ntiles <= 0 || (nt != 128 && nt != 256)) return TGA_ERR_INVALID;   // apply needs >= 3 warps
     const int nw = nt / 32;
-    const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0;
+    const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0, pd = d.has_pd != 0;
     const int nintra = tw ? d.m : (d.Wp - 1 + nw - 1) / nw;
-    size_t sm = inter_smem_bytes(rows, warps);
+    size_t sm = inter_smem_bytes(rows, warps, pd);
     const size_t band = (size_t)band_smem_ints(d.Wp, nw) * sizeof(int);
     if (band > sm) sm = band;
-    if (tw && (size_t)kIntraTabSmemInts * sizeof(int) > sm) sm = (size_t)kIntraTabSmemInts * sizeof(int);
+    const size_t tab = (size_t)(pd ? kIntraTabSmemIntsPD : kIntraTabSmemInts) * sizeof(int);
+    if (tw && tab > sm) sm = tab;
     if (sm > 200 * 1024) return TGA_ERR_RANGE;
-    PersistFn fn = persist_fn(tw, orr, nt);
+    PersistFn fn = persist_fn(tw, orr, nt, pd);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
         cudaGetLastError();
         return TGA_ERR_CUDA;

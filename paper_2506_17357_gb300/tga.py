@@ -40,7 +40,7 @@ class tga_instance(ctypes.Structure):
                 ("w_load", ctypes.c_int32), ("w_tw", ctypes.c_int32),
                 ("dist", ctypes.c_void_p), ("demand", ctypes.c_void_p),
                 ("service", ctypes.c_void_p), ("tw_early", ctypes.c_void_p),
-                ("tw_late", ctypes.c_void_p)]
+                ("tw_late", ctypes.c_void_p), ("pickup", ctypes.c_void_p)]
 
 
 class tga_solution(ctypes.Structure):
@@ -300,11 +300,15 @@ class LocalSearch:
         with torch.cuda.stream(self.stream):
             host = [t(inst.dist).reshape(-1), t(inst.demand), t(inst.service), t(inst.tw_early),
                     t(inst.tw_late), t(sol.tour), t(sol.route_start)]
+            pk = getattr(inst, "pickup", None)
+            if pk is not None:                   # VRPSPDTW: pickup quantities
+                host.append(t(pk))
             if pinned:
                 host = [h.pin_memory() for h in host]
             dev = [h.to(self.device, non_blocking=pinned) for h in host]
             (self.dist, self.demand, self.service, self.early, self.late,
-             self.tour, self.route_start) = dev
+             self.tour, self.route_start) = dev[:7]
+            self.pickup = dev[7] if pk is not None else None
             self.move = torch.zeros(6, dtype=torch.int32, device=self.device)   # one tga_move
             self.log = (torch.full((log_capacity,), -1, dtype=torch.int64, device=self.device)
                         if log_capacity else None)
@@ -313,7 +317,8 @@ class LocalSearch:
                                    self.demand.data_ptr(),
                                    self.service.data_ptr() if inst.has_tw else None,
                                    self.early.data_ptr() if inst.has_tw else None,
-                                   self.late.data_ptr() if inst.has_tw else None)
+                                   self.late.data_ptr() if inst.has_tw else None,
+                                   self.pickup.data_ptr() if self.pickup is not None else None)
         self.c_sol = tga_solution(self.tour.data_ptr(), self.route_start.data_ptr())
         self.ctx = tga_create(self.c_inst, self.c_sol, self.op_mask, self.stream.cuda_stream)
         if self.log is not None:
@@ -335,6 +340,10 @@ class LocalSearch:
         if inst is not None:
             pairs += [(self.dist, inst.dist), (self.demand, inst.demand), (self.service, inst.service),
                       (self.early, inst.tw_early), (self.late, inst.tw_late)]
+            if (getattr(inst, "pickup", None) is None) != (self.pickup is None):
+                raise ValueError("reload cannot add or drop pickups")
+            if self.pickup is not None:
+                pairs.append((self.pickup, inst.pickup))
         if sol is not None:
             pairs += [(self.tour, sol.tour), (self.route_start, sol.route_start)]
         if not hasattr(self, "_pinned"):

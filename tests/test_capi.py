@@ -70,3 +70,9 @@ def test_create_rejects_bad_arguments_on_host(lib):
     inst = tga.tga_instance(10, 2, 10, 0, 100, 100, 1, 1, None, None, None)
     rc = tga._lib().tga_create(ctypes.byref(inst), ctypes.byref(sol), 0, None, ctypes.byref(out))
     assert rc == tga.TGA_ERR_INVALID      # empty operator mask
+    inst = tga.tga_instance(10, 2, 10, 0, 100, 100, 1, 1, None, None, None, 1)
+    rc = tga._lib().tga_create(ctypes.byref(inst), ctypes.byref(sol), 0x3F, None, ctypes.byref(out))
+    assert rc == tga.TGA_ERR_INVALID      # pickups without time windows
+    rc = tga._lib().tga_eval_best_move_noalloc(ctypes.byref(inst), ctypes.byref(sol), 0x3F, None,
+                                               ctypes.c_void_p(1))
+    assert rc == tga.TGA_ERR_INVALID
