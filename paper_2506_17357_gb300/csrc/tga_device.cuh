@@ -1,14 +1,18 @@
 // Block- and warp-level device functions of libtga, shared by the
-// single-instance kernels (tga_kernels.cu) and the persistent batched kernel
-// (tga_batch.cu).
+// single-instance kernels (tga_kernels.cu), the persistent single-instance
+// descent (tga_persist.cu) and the persistent batched kernel (tga_batch.cu).
 //
 // TGA_LDG(p) loads data that the search mutates (positions, attribute
-// records, the position-ordered distance copy).  The single-instance kernels
-// define it as __ldg: their state changes only between launches.  The
-// batched kernel, where several SMs read a job's state that another SM
-// rewrote during the same launch, defines it as a plain load and is compiled
-// with L1 caching of global loads disabled (-dlcm=cg), so every such read is
-// served by L2.
+// records, the position-ordered distance copy).  The per-step kernels define
+// it as __ldg: their state changes only between launches.  The persistent
+// kernels, where several SMs read state that another SM rewrote during the
+// same launch, define it as a plain load and are compiled with L1 caching of
+// global loads disabled (-dlcm=cg), so every such read is served by L2.
+//
+// Template flag PD (pickups, the VRPSPDTW; always with time windows): the
+// load term of a route is that of its largest load on board, evaluated from
+// the incoming / outgoing / largest loads of Section 4.3.2.  Without it the
+// code is the CVRP / VRPTW one, where loads simply add.
 #pragma once
 #ifndef TGA_LDG
 #error "define TGA_LDG before including tga_device.cuh"
@@ -864,6 +868,8 @@ __device__ unsigned edge_candidates(const Dev &d, int u, int v, bool rev, int &b
 // ---------------------------------------------------------------------------
 // intra-route evaluation
 //
+// Sweeps over a route (the batched kernel's intra-route evaluation, and the
+// fallback for time-window routes too long for the subsequence tables).
 // One warp per route.  The route's elements (0 = start depot, 1..L
 // customers, L+1 = end depot) are staged in shared memory with their node
 // data, the prefix/suffix attributes of every anchor, and -- when it fits --
@@ -1612,7 +1618,9 @@ __device__ __forceinline__ Seg seg_vals(int e, int l, int s, int load, int out) 
 // leaving each element and the bypass edges of the hoisted constants
 // (x- to x+, and x- to the element after runs of 2 and 3) -- followed by
 // the two concatenation scans (Section 4.3) in registers and the stores.
-// Lane 0 writes the route totals (load, dist, warp, cost) to tot[0..3].
+// Lane 0 writes the route totals (range load, dist, warp, cost) to
+// tot[0..3]; the range load is the delivery total, plus the pickup total
+// with pickups.
 template <bool PD>
 __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int *sbuf, const StepPlan &S,
                                    int lane, int *tot) {

@@ -13,9 +13,11 @@
 //                  argmin (Eq. "min_obj") is a per-thread running minimum
 //                  reduced by warp shuffles and one 64-bit atomicMin per
 //                  block over packed (delta, move index) keys.
-//   k_eval_intra   the same for intra-route candidates (route-based
-//                  extraction of Section 5.3.1), one thread per anchor
-//                  sweeping the other end of the move along its route.
+//   k_eval_intra   the same for intra-route candidates with time windows
+//                  (route-based extraction of Section 5.3.1): one CTA per
+//                  route builds the route's subsequence tables (Section 4.2)
+//                  in shared memory and takes the (i, j) pairs in parallel;
+//                  k_eval_intra_cvrp: one warp per moved CVRP customer.
 //   k_apply        Tensor update (Section 5.3.5) on the device: CTA 0 decodes
 //                  the best key, rewrites the positions and rebuilds the
 //                  attributes of the <= 2 touched routes; the other CTAs keep
