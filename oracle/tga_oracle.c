@@ -29,6 +29,12 @@
  *   op 4/5 or-opt  a = first of k = 2/3 consecutive customers of one route,
  *                  b = anchor outside the run, b != pred(a): move the run,
  *                  same orientation, to just after b.
+ *   op 6 swap(1,2) a = customer, b = first of two consecutive customers of
+ *                  one route, a not in that run: a takes the run's place and
+ *                  the run (same orientation) takes a's (Section 5.3.1 Swap
+ *                  with N1 = 1, N2 = 2; same or other route).
+ *   op 7 swap(2,2) a < b, each the first of two consecutive customers, the
+ *                  runs disjoint: the runs exchange places (N1 = N2 = 2).
  * The best move is the lexicographically smallest (delta, idx).
  */
 #include "tga_oracle.h"
@@ -242,6 +248,39 @@ static int build_move(const view_t *v, int32_t op, int32_t a, int32_t b, moved_t
         mv->nr = 2; mv->r[0] = A; mv->r[1] = B; mv->len[0] = la; mv->len[1] = lb;
         return 1;
     }
+    if (op == 6 || op == 7) {
+        /* run of k1 customers at a (k1 = 1 for op 6), run of 2 at b */
+        const int32_t k1 = (op == 6) ? 1 : 2;
+        if (!is_customer(v, a) || !is_customer(v, b)) return 0;
+        if (op == 7 && !(a < b)) return 0;
+        int32_t A = v->route_of[a], i = v->idx_of[a], LA = rlen(v, A);
+        int32_t B = v->route_of[b], j = v->idx_of[b], LB = rlen(v, B);
+        if (i + k1 > LA || j + 2 > LB) return 0;
+        const int32_t *ra = rnodes(v, A), *rb = rnodes(v, B);
+        if (A == B && !(i + k1 <= j || j + 2 <= i)) return 0;   /* the runs overlap */
+        int32_t *na = mv->buf[0], la = 0;
+        if (A != B) {
+            int32_t *nb = mv->buf[1], lb = 0;
+            cat(na, &la, ra, i);
+            cat(na, &la, rb + j, 2);
+            cat(na, &la, ra + i + k1, LA - i - k1);
+            cat(nb, &lb, rb, j);
+            cat(nb, &lb, ra + i, k1);
+            cat(nb, &lb, rb + j + 2, LB - j - 2);
+            mv->nr = 2; mv->r[0] = A; mv->r[1] = B; mv->len[0] = la; mv->len[1] = lb;
+            return 1;
+        }
+        /* one route: first run (x, length kx) before second run (y, length ky) */
+        int32_t x = i, kx = k1, y = j, ky = 2;
+        if (j < i) { x = j; kx = 2; y = i; ky = k1; }
+        cat(na, &la, ra, x);
+        cat(na, &la, ra + y, ky);
+        cat(na, &la, ra + x + kx, y - x - kx);
+        cat(na, &la, ra + x, kx);
+        cat(na, &la, ra + y + ky, LA - y - ky);
+        mv->nr = 1; mv->r[0] = A; mv->len[0] = la;
+        return 1;
+    }
     return 0;
 }
 
@@ -408,6 +447,26 @@ static int64_t delta_concat(const orc_inst *in, const view_t *v, const amat_t *a
         p[0] = pc_fw(ma, 0, i - 1); p[1] = pc_rv(ma, i, j); p[2] = pc_fw(ma, j + 1, ma->L + 1);
         return chain_cost(in, p, 3) - v->rcost[A];
     }
+    if (op == 6 || op == 7) {
+        const int32_t k1 = (op == 6) ? 1 : 2;
+        int32_t A = v->route_of[a], B = v->route_of[b];
+        int32_t i = v->idx_of[a] + 1, j = v->idx_of[b] + 1;     /* 1-based */
+        const amat_t *ma = &am[A], *mb = &am[B];
+        if (A != B) {
+            p[0] = pc_fw(ma, 0, i - 1); p[1] = pc_fw(mb, j, j + 1); p[2] = pc_fw(ma, i + k1, ma->L + 1);
+            q[0] = pc_fw(mb, 0, j - 1); q[1] = pc_fw(ma, i, i + k1 - 1); q[2] = pc_fw(mb, j + 2, mb->L + 1);
+            return chain_cost(in, p, 3) + chain_cost(in, q, 3) - v->rcost[A] - v->rcost[B];
+        }
+        int32_t x = i, kx = k1, y = j, ky = 2;
+        if (j < i) { x = j; kx = 2; y = i; ky = k1; }
+        int32_t np_ = 0;
+        p[np_++] = pc_fw(ma, 0, x - 1);
+        p[np_++] = pc_fw(ma, y, y + ky - 1);
+        if (y > x + kx) p[np_++] = pc_fw(ma, x + kx, y - 1);
+        p[np_++] = pc_fw(ma, x, x + kx - 1);
+        p[np_++] = pc_fw(ma, y + ky, ma->L + 1);
+        return chain_cost(in, p, np_) - v->rcost[A];
+    }
     /* op 3: 2-opt* */
     int32_t A = v->route_of[a], B = v->route_of[b];
     int32_t i = v->idx_of[a] + 1, j = v->idx_of[b] + 1;
@@ -447,7 +506,7 @@ static int granular_kept(const orc_inst *in, const view_t *v, int32_t op, int32_
     const int32_t n = v->n;
     if (op == 2 || v->route_of[a] == v->route_of[b]) return 1;     /* intra-route */
     if (op == 0 || op == 4 || op == 5) return b > n || in_mask(in, a, b);
-    if (op == 1) return in_mask(in, a, b) || in_mask(in, b, a);
+    if (op == 1 || op == 6 || op == 7) return in_mask(in, a, b) || in_mask(in, b, a);
     if (a > n && b > n) return 0;                                    /* 2-opt* */
     if (a > n || b > n) return 1;
     return in_mask(in, a, b) || in_mask(in, b, a);
@@ -479,7 +538,7 @@ static void scan_all(scan_t *s, uint32_t mask)
     const view_t *v = s->v;
     int32_t n = v->n, m = v->m;
     /* op 0 and or-opt: run starting at customer u, destination anchor b */
-    for (int32_t op = 0; op <= 5; ++op) {
+    for (int32_t op = 0; op <= 7; ++op) {
         if (!(mask & (1u << op))) continue;
         if (op == 0 || op == 4 || op == 5) {
             int32_t k = (op == 0) ? 1 : op - 2;
@@ -499,6 +558,21 @@ static void scan_all(scan_t *s, uint32_t mask)
         } else if (op == 1) {
             for (int32_t a = 1; a <= n; ++a)
                 for (int32_t b = a + 1; b <= n; ++b) visit(s, 1, a, b);
+        } else if (op == 6 || op == 7) {
+            /* b starts a run of 2; a is a single customer (op 6) or starts a
+             * run of 2 with a < b (op 7); the runs must not overlap */
+            const int32_t k1 = (op == 6) ? 1 : 2;
+            for (int32_t b = 1; b <= n; ++b) {
+                int32_t B = v->route_of[b], j = v->idx_of[b];
+                if (j + 2 > rlen(v, B)) continue;
+                for (int32_t a = 1; a <= n; ++a) {
+                    if (op == 7 && !(a < b)) continue;
+                    int32_t A = v->route_of[a], i = v->idx_of[a];
+                    if (i + k1 > rlen(v, A)) continue;
+                    if (A == B && !(i + k1 <= j || j + 2 <= i)) continue;
+                    visit(s, op, a, b);
+                }
+            }
         } else if (op == 2) {
             for (int32_t r = 0; r < m; ++r) {
                 const int32_t *rr = rnodes(v, r);

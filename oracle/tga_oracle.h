@@ -20,7 +20,8 @@
  * between two visits of depot 0.  Anchors: customers 1..n, and the start
  * depot of route r is anchor n+1+r; W = n+1+m.  Move index
  * idx = op*W*W + a*W + b with op ranks 0 relocate, 1 swap, 2 2-opt,
- * 3 2-opt*, 4 or-opt(2), 5 or-opt(3).
+ * 3 2-opt*, 4 or-opt(2), 5 or-opt(3), 6 swap of a customer with a run of
+ * two (a the customer, b the run's first), 7 swap of two runs of two (a < b).
  */
 #ifndef TGA_ORACLE_H
 #define TGA_ORACLE_H
@@ -37,7 +38,7 @@ extern "C" {
  * candidate (op, a, b) is kept when
  *   relocate / or-opt (the run starting at a moves after b): b is a start
  *     depot, or M[a][b];
- *   swap: M[a][b] or M[b][a];
+ *   swap (ranks 1, 6, 7): M[a][b] or M[b][a];
  *   2-opt*: exactly one of a, b is a start depot, or M[a][b] or M[b][a].
  * theta = 0: the full neighbourhood (node-based extraction). */
 /* pickup: NULL for the CVRP and VRPTW; for the VRPSPDTW the pickup

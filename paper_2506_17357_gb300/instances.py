@@ -348,7 +348,11 @@ def config3(seed: int = 1):
 
 # Operator ranks (move-index op field) and the per-workload operator masks.
 OP_RELOCATE, OP_SWAP, OP_2OPT, OP_2OPT_STAR, OP_OROPT2, OP_OROPT3 = range(6)
+# swaps with unequal or longer runs (Section 5.3.1 Swap with N1, N2 > 0): a
+# customer with a run of two (rank 6), two runs of two (rank 7)
+OP_SWAP12, OP_SWAP22 = 6, 7
 MASK_ALL = 0x3F
+MASK_EXT = 0xFF          # every rank, with the swaps of runs
 MASK_CONFIG1 = (1 << OP_RELOCATE) | (1 << OP_SWAP) | (1 << OP_2OPT) | (1 << OP_2OPT_STAR)
 MASK_CONFIG2 = MASK_ALL
 MASK_CONFIG3 = MASK_ALL & ~(1 << OP_2OPT)

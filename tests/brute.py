@@ -8,7 +8,9 @@ on tiny instances.
 Objective: Section 2 of the paper with the penalised capacity excess (of the
 largest load on board when the instance has pickups) and the time-warp
 relaxation of Section 4.3.3 (weights w_load, w_tw).  Operators:
-Section 4.1 (relocate, swap, 2-opt, 2-opt*) plus or-opt of 2-3 customers.
+Section 4.1 (relocate, swap, 2-opt, 2-opt*) plus or-opt of 2-3 customers,
+and the swaps of Section 5.3.1 with unequal or longer runs: a customer with a
+run of two, and two runs of two.
 """
 import copy
 
@@ -126,6 +128,39 @@ def brute_moves(inst, routes, mask, nbr=None):
                 rb, j = _locate(nr, b)
                 nr[ra][i], nr[rb][j] = b, a
                 record(1, a, b, nr)
+    # ops 6 / 7: a customer (6) or a run of two starting at a (7, a < b)
+    # exchanges places with the run of two starting at b; the runs stay in
+    # order and must not share a customer
+    for op, k1 in ((6, 1), (7, 2)):
+        if not mask >> op & 1:
+            continue
+        for b in range(1, n + 1):
+            rb, j = _locate(routes, b)
+            if j + 2 > len(routes[rb]):
+                continue
+            for a in range(1, n + 1):
+                if op == 7 and not a < b:
+                    continue
+                ra, i = _locate(routes, a)
+                if i + k1 > len(routes[ra]):
+                    continue
+                run_a = routes[ra][i:i + k1]
+                run_b = routes[rb][j:j + 2]
+                if set(run_a) & set(run_b):
+                    continue
+                nr = copy.deepcopy(routes)
+                if ra != rb:
+                    nr[ra][i:i + k1] = run_b
+                    nr[rb][j:j + 2] = run_a
+                else:
+                    # rebuild the route as a sequence of placeholders
+                    seq = list(routes[ra])
+                    first, second = (i, j) if i < j else (j, i)
+                    lf, ls = (k1, 2) if i < j else (2, k1)
+                    new = (seq[:first] + seq[second:second + ls] + seq[first + lf:second] +
+                           seq[first:first + lf] + seq[second + ls:])
+                    nr[ra] = new
+                record(op, a, b, nr)
     if mask >> 2 & 1:
         for r, route in enumerate(routes):
             for i in range(len(route)):

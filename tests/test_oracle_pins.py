@@ -214,6 +214,44 @@ def test_concat_associative(kind, seed):
 
 
 # ----------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["cvrp", "vrptw", "vrpspdtw"])
+@pytest.mark.parametrize("seed", range(5))
+def test_swaps_of_runs_against_brute_force(kind, seed):
+    """Ranks 6 and 7 (a customer with a run of two, two runs of two; Section
+    5.3.1 Swap with N1 = 1, 2 and N2 = 2): every candidate and delta equals the
+    independent Python statement of the exchange, in and across routes."""
+    n = 6 + seed % 4
+    inst, sol = _tiny(kind, n, 900 + seed, m_extra_empty=1)
+    expect = brute_moves(inst, sol.routes(), 64 | 128)
+    assert expect, "no run-swap candidates"
+    for method in ("def", "concat"):
+        idx, dl = O.list_moves(inst, sol, 64 | 128, method)
+        assert dict(zip(idx.tolist(), dl.tolist())) == expect, method
+    full = brute_moves(inst, sol.routes(), I.MASK_EXT)
+    bm = O.best_move(inst, sol, I.MASK_EXT, "concat")
+    assert (bm["delta"], bm["idx"]) == min((d, i) for i, d in full.items())
+
+
+def test_swap_of_runs_hand_example():
+    """One route (0, 1, 2, 3, 4, 0) on a line: node x at coordinate 10 x.
+    Exchanging customer 1 with the run (3, 4) gives (0, 3, 4, 2, 1, 0):
+    distance 30 + 10 + 20 + 10 + 10 = 80 instead of 80 for the straight
+    route, delta 0; exchanging the runs (1, 2) and (3, 4) gives
+    (0, 3, 4, 1, 2, 0): 30 + 10 + 30 + 10 + 20 = 100, delta +20."""
+    pts = np.array([[10 * x, 0] for x in range(5)], np.int64)
+    inst = I.instance_from_arrays("line", I.rounded_euclidean(pts), [0, 1, 1, 1, 1], 100)
+    sol = _sol([1, 2, 3, 4], [0, 4])
+    W = 4 + 1 + 1
+    idx, dl = O.list_moves(inst, sol, 64 | 128, "def")
+    got = dict(zip(idx.tolist(), dl.tolist()))
+    assert got[6 * W * W + 1 * W + 3] == 0
+    assert got[7 * W * W + 1 * W + 3] == 20
+    # customer 4 with the run (1, 2): (0, 4, 3, 1, 2, 0): 40 + 10 + 20 + 10 + 20 = 100
+    assert got[6 * W * W + 4 * W + 1] == 20
+    # candidates: runs (1,2), (2,3), (3,4); singles not in the run: 2 each -> 6; run pairs: (1,2)-(3,4) -> 1
+    assert len(got) == 7
+
+
 @pytest.mark.parametrize("kind", ["cvrp", "vrptw", "vrpspdtw", "vrpspd"])
 @pytest.mark.parametrize("seed", range(5))
 def test_candidate_sets_against_brute_force(kind, seed):
@@ -236,6 +274,11 @@ def _closed_form_count(n, lens, mask):
     m = len(lens)
     A = n + m
     c = 0
+    runs2 = sum(max(0, L - 1) for L in lens)          # runs of two consecutive customers
+    if mask & 64:           # a customer with a run of two it is not part of
+        c += runs2 * (n - 2)
+    if mask & 128:          # unordered pairs of runs of two that share no customer
+        c += runs2 * (runs2 - 1) // 2 - sum(max(0, L - 2) for L in lens)
     if mask & 1:
         c += n * (A - 2)
     if mask & 2:
@@ -251,7 +294,8 @@ def _closed_form_count(n, lens, mask):
     return c
 
 
-@pytest.mark.parametrize("mask", [1, 2, 4, 8, 16, 32, I.MASK_ALL, I.MASK_CONFIG1, I.MASK_CONFIG3])
+@pytest.mark.parametrize("mask", [1, 2, 4, 8, 16, 32, 64, 128, I.MASK_ALL, I.MASK_EXT, I.MASK_CONFIG1,
+                                  I.MASK_CONFIG3])
 def test_candidate_counts_closed_form(mask):
     for kind, n, seed in (("cvrp", 40, 1), ("vrptw", 60, 2), ("cvrp", 7, 3)):
         inst, sol = _tiny(kind, n, seed, m_extra_empty=2)
@@ -325,7 +369,8 @@ def test_two_opt_descent_reaches_convex_order():
 @pytest.mark.parametrize("kind,n,seed,mask", [
     ("cvrp", 25, 1, I.MASK_CONFIG1), ("vrptw", 30, 2, I.MASK_ALL),
     ("cvrp", 40, 3, I.MASK_CONFIG3), ("vrptw", 45, 4, I.MASK_ALL),
-    ("vrpspdtw", 35, 5, I.MASK_ALL), ("vrpspd", 30, 6, I.MASK_ALL)])
+    ("vrpspdtw", 35, 5, I.MASK_ALL), ("vrpspd", 30, 6, I.MASK_ALL),
+    ("cvrp", 30, 7, I.MASK_EXT), ("vrptw", 35, 8, I.MASK_EXT)])
 def test_descent_invariants(kind, n, seed, mask):
     inst, sol = _tiny(kind, n, seed, m_extra_empty=1)
     c0 = O.solution_cost(inst, sol)
