@@ -52,9 +52,12 @@ WORKLOADS = {
 # with pickups the load term of each new route is the three-way maximum of
 # the largest-load constants instead of one sum (relocate/or-opt +5, swap +8,
 # 2-opt* +4) and the intra-route 2-opt closes a load chain (+14).
-OPS_CVRP = {0: 8, 1: 13, 2: 6, 3: 13, 4: 8, 5: 8}
-OPS_TW = {0: 20, 1: 36, 2: 22, 3: 22, 4: 20, 5: 20}
-OPS_PD = {0: 25, 1: 44, 2: 36, 3: 26, 4: 25, 5: 25}
+# Ranks 6 and 7 (swaps of runs, --extended-swaps): two gap constants, two
+# inserted pieces and two load terms, plus two time-warp chains of a piece
+# each with time windows.
+OPS_CVRP = {0: 8, 1: 13, 2: 6, 3: 13, 4: 8, 5: 8, 6: 15, 7: 15}
+OPS_TW = {0: 20, 1: 36, 2: 22, 3: 22, 4: 20, 5: 20, 6: 39, 7: 39}
+OPS_PD = {0: 25, 1: 44, 2: 36, 3: 26, 4: 25, 5: 25, 6: 0, 7: 0}      # ranks 6, 7 have no pickup variant
 
 
 def ops_table(inst):
@@ -210,7 +213,7 @@ def only_descent(args):
     command profilers run to list the per-step kernel launches."""
     import torch
     from paper_2506_17357_gb300 import tga as T
-    desc, make, mask = WORKLOADS[args.workload]
+    desc, make, mask = workload(args)
     inst, sol = make(args.seed)
     nbr = I.granular_neighbors(inst, args.granular) if args.granular else None
     ls = T.LocalSearch(inst, sol, mask, granular=nbr).build()
@@ -220,13 +223,26 @@ def only_descent(args):
         tile = ls.set_tile(0, 0)                                   # autotune, as the timed bench does
     st = ls.descend(max_steps=args.descent_steps) if args.descent_steps else ls.descend()
     torch.cuda.synchronize()
-    print(json.dumps({"workload": args.workload, "tile": list(tile), "steps": st["steps"],
+    print(json.dumps({"workload": workload_name(args), "tile": list(tile), "steps": st["steps"],
                       "evaluations": st["evaluations"],
                       "final_cost": st["final_cost"], "status": st["status"]}))
     ls.close()
 
 
-OP_NAMES = ["relocate", "swap", "2-opt", "2-opt*", "or-opt-2", "or-opt-3"]
+OP_NAMES = ["relocate", "swap", "2-opt", "2-opt*", "or-opt-2", "or-opt-3", "swap-1-2", "swap-2-2"]
+
+
+def workload(args):
+    """(description, generator, operator mask) of the chosen workload;
+    --extended-swaps adds ranks 6 and 7 (swaps of runs) to its mask."""
+    desc, make, mask = WORKLOADS[args.workload]
+    if getattr(args, "extended_swaps", False):
+        desc, mask = desc + ", plus the swaps of runs (ranks 6, 7)", mask | I.MASK_EXT
+    return desc, make, mask
+
+
+def workload_name(args):
+    return args.workload + ("-xswap" if getattr(args, "extended_swaps", False) else "")
 
 
 def breakdown(inst, sol, mask, dev, stream, reps=20, step_count=200):
@@ -242,7 +258,7 @@ def breakdown(inst, sol, mask, dev, stream, reps=20, step_count=200):
     e1 = torch.cuda.Event(enable_timing=True)
     e2 = torch.cuda.Event(enable_timing=True)
     per_op = {}
-    for op in range(6):
+    for op in range(8):
         if not (mask >> op) & 1:
             continue
         ls = T.LocalSearch(inst, sol, 1 << op, device=dev, stream=stream).build()
@@ -295,7 +311,7 @@ def bench_gpu(args):
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    desc, make, mask = WORKLOADS[args.workload]
+    desc, make, mask = workload(args)
     seed = replica_seed(args.seed, rank)
     inst, sol = make(seed)
     nbr = I.granular_neighbors(inst, args.granular) if args.granular else None
@@ -398,7 +414,7 @@ def bench_gpu(args):
                  int((np.maximum(L - 2, 0) * np.maximum(L - 3, 0)).sum())]
         table = ops_table(inst)
         return sum(table[op] * (after[op] - before[op] - (intra[op] if (mask >> op) & 1 else 0))
-                   for op in range(6))
+                   for op in range(6))     # the edge-based extraction has no ranks 6, 7
 
     def inter_kernel_roof():
         restore()
@@ -424,7 +440,7 @@ def bench_gpu(args):
                 "ms_per_launch": total_ms / probes, "ops_per_launch": total_ops / probes,
                 "work": "inter-route candidates of the state (per-candidate integer ops x candidates), "
                         "mean over 5 states along the trajectory",
-                "traffic": measured_traffic(args.workload + (f"-granular{args.granular}" if args.granular else ""),
+                "traffic": measured_traffic(workload_name(args) + (f"-granular{args.granular}" if args.granular else ""),
                                             kname),
                 "kernel_source_hash": kernel_source_hash()}
 
@@ -448,7 +464,7 @@ def bench_gpu(args):
                 "ms_per_launch": ms, "ops_per_launch": ops, "grid": grid,
                 "work": "every candidate of every evaluation of the descent (per-operator device counters "
                         "x per-candidate integer ops); one launch = one whole descent",
-                "traffic": measured_traffic(args.workload, "k_persist"),
+                "traffic": measured_traffic(workload_name(args), "k_persist"),
                 "kernel_source_hash": kernel_source_hash(),
                 "inter_kernel": {k: inter_roof[k] for k in ("kernel", "achieved", "frac", "ms_per_launch",
                                                              "ops_per_launch", "traffic")}}
@@ -471,7 +487,7 @@ def bench_gpu(args):
         "time_to_local_optimum_ms": tlo_ms, "moves_applied": steps[-1], "evaluations": evals,
         "candidates_per_descent": stats["candidates"], "initial_cost": stats["initial_cost"],
         "final_cost": stats["final_cost"],
-        "config": {"workload": args.workload, "desc": desc, "instance_seed": args.seed,
+        "config": {"workload": workload_name(args), "desc": desc, "instance_seed": args.seed,
                    "op_mask": mask, "tile_rows_warps": list(tile), "parallelism": f"replicas x{ws}",
                    "descent_path": T.DESCENT_NAMES[mode_used],
                    "extraction": (f"edge-based, granular mask of the {args.granular} nearest customers"
@@ -632,7 +648,7 @@ def cpu_baseline(args, seconds=15.0, per_op_seconds=1.0):
     host: best-improvement steps of the same workload from the same initial
     solution, as many as fit in ``seconds``."""
     import oracle as O
-    desc, make, mask = WORKLOADS[args.workload]
+    desc, make, mask = workload(args)
     inst, sol = make(args.seed)
     theta = getattr(args, "granular", 0)
     nbr = I.granular_neighbors(inst, theta) if theta else None
@@ -651,7 +667,7 @@ def cpu_baseline(args, seconds=15.0, per_op_seconds=1.0):
     # per operator: the oracle's evaluation of the initial solution with only
     # that operator enabled (about a second each)
     per_op = {}
-    for op in range(6):
+    for op in range(8):
         if not (mask >> op) & 1 or per_op_seconds <= 0:
             continue
         t1 = time.perf_counter()
@@ -662,7 +678,7 @@ def cpu_baseline(args, seconds=15.0, per_op_seconds=1.0):
         d1 = time.perf_counter() - t1
         per_op[OP_NAMES[op]] = {"ms_per_evaluation": 1e3 * d1 / reps, "candidates_per_s": c1 / d1}
     return {"value": cands / dt, "unit": "candidate moves/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {k} best-improvement evaluations of {args.workload} seed {args.seed} "
+            "sample": f"first {k} best-improvement evaluations of {workload_name(args)} seed {args.seed} "
                       f"(concatenation evaluator{', granular mask theta=%d' % theta if theta else ''}), {dt:.1f} s",
             "per_operator": per_op}
 
@@ -671,7 +687,7 @@ def bench_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    desc, make, mask = WORKLOADS[args.workload]
+    desc, make, mask = workload(args)
     per = max(2.0, args.cpu_seconds / max(1, args.steps))
     for _ in range(args.warmup):
         cpu_baseline(args, seconds=min(per, 2.0), per_op_seconds=0.0)
@@ -684,7 +700,7 @@ def bench_reference(args):
     line = {"impl": "reference", "metric": "move evals/s", "value": value, "unit": "candidate moves/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": args.workload, "desc": desc, "instance_seed": args.seed,
+            "data": "synthetic", "config": {"workload": workload_name(args), "desc": desc, "instance_seed": args.seed,
                                             "op_mask": mask},
             "cpu_baseline": {"value": value, "unit": "candidate moves/s", "cores": 1, "kind": "oracle",
                              "sample": vals[-1]["sample"]},
@@ -706,6 +722,8 @@ def main():
                     help="with --only-descent: stop after this many moves (0: run to the local optimum)")
     ap.add_argument("--tile", default="",
                     help="inter tile shape rows,warps,row_split (default: autotune on the initial state)")
+    ap.add_argument("--extended-swaps", action="store_true",
+                    help="add op ranks 6, 7 (a customer with a run of two, two runs of two) to the workload")
     ap.add_argument("--granular", type=int, default=0,
                     help="edge-based extraction with the THETA nearest customers per customer (0: full neighbourhood)")
     ap.add_argument("--batch-jobs", type=int, default=256)

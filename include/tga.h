@@ -123,8 +123,19 @@ typedef struct {
 } tga_stats;
 
 /* Create a context for one instance + solution.
- *  op_mask: bit k enables op rank k (0x3F = all); must be non-zero and
- *  < 64.  Validates sizes on the host (TGA_ERR_INVALID / TGA_ERR_RANGE for
+ *  op_mask: bit k enables op rank k; must be non-zero and < 256.  Ranks:
+ *  0 relocate, 1 swap, 2 2-opt, 3 2-opt*, 4 / 5 or-opt of 2 / 3 customers
+ *  (0x3F = all of these), 6 a customer exchanged with a run of two
+ *  consecutive customers (a = the customer, b = the run's first), 7 two runs
+ *  of two exchanged (a < b, the runs' firsts) -- the Swap of Section 5.3.1
+ *  with run lengths N1, N2 in {1, 2}; in and across routes, runs keep their
+ *  orientation and must not share a customer.  Ranks 6 and 7 run on the
+ *  per-step descent paths (graph and host-launched; the persistent mode
+ *  refuses them with TGA_ERR_STATE and the automatic mode takes the graph),
+ *  need n + m + 1 <= 23170 (8 W^2 < 2^32), have no pickup variant (a
+ *  pickup instance with them: TGA_ERR_INVALID) and are refused by the
+ *  batched launch and the edge-based extraction (TGA_ERR_STATE).
+ *  Validates sizes on the host (TGA_ERR_INVALID / TGA_ERR_RANGE for
  *  W too large), allocates the context's device workspace (about
  *  4*(n+1)*(n+m+257) bytes for the position-ordered distance copy plus
  *  O(n+m)), and returns *out.  Nothing is computed until tga_build_attrs.
@@ -239,7 +250,8 @@ int tga_sync(tga_ctx *ctx);
 int tga_get_stats(tga_ctx *ctx, tga_stats *out_host);
 
 /* Synchronise and copy the candidate moves evaluated per operator rank
- * (out_host[6]: relocate, swap, 2-opt, 2-opt*, or-opt 2, or-opt 3), summed
+ * (out_host[8]: relocate, swap, 2-opt, 2-opt*, or-opt 2, or-opt 3, customer
+ * with a run of two, two runs of two), summed
  * over all evaluations since tga_build_attrs; their sum is
  * tga_stats.candidates.  Used to count the algorithmic work of a descent
  * per operator (the per-operator breakdown of the paper's Section 6.6). */

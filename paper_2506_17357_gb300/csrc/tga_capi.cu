@@ -137,6 +137,7 @@ int build_graph(tga_ctx *c) {
             const int tail = eval_blocks(c->d, c->ntiles);
             launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap, c->tile_rs, tail);
             launch_intra(c->d, c->cap2, tail);
+            launch_xswap(c->d, c->cap2, tail);
             cudaEventRecord(c->ev_join, c->cap2);
             cudaStreamWaitEvent(c->cap, c->ev_join, 0);
             launch_apply(c->d, nullptr, h, 1, c->cap, 1);
@@ -259,7 +260,7 @@ int default_batch_tr(int Wp) { return Wp < 600 ? 16 : (Wp < 2000 ? 32 : 64); }
 // One persistent launch over all contexts (see tga_batch.cu).
 int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *tr_override) {
     for (int i = 0; i < n; ++i)                  // no edge-based or pickup path in the batched kernel
-        if (ctxs[i]->d.theta > 0 || ctxs[i]->d.has_pd) return TGA_ERR_STATE;
+        if (ctxs[i]->d.theta > 0 || ctxs[i]->d.has_pd || (ctxs[i]->d.op_mask & kExtOps)) return TGA_ERR_STATE;
     cudaStream_t s = ctxs[0]->stream;
     for (int i = 0; i < n; ++i)
         if (ctxs[i]->stream != s && cudaStreamSynchronize(ctxs[i]->stream) != cudaSuccess) return TGA_ERR_CUDA;
@@ -359,12 +360,13 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     *out = nullptr;
     const long long n = inst->n_customers, m = inst->n_routes;
     if (n < 1 || m < 1 || inst->capacity < 0 || inst->w_load < 0 || inst->w_tw < 0) return TGA_ERR_INVALID;
-    if (op_mask == 0 || op_mask >= 64u) return TGA_ERR_INVALID;
+    if (op_mask == 0 || op_mask >= 256u) return TGA_ERR_INVALID;
     if (!inst->dist || !inst->demand || !sol->tour || !sol->route_start) return TGA_ERR_INVALID;
     if (inst->has_tw && (!inst->service || !inst->tw_early || !inst->tw_late)) return TGA_ERR_INVALID;
     if (inst->pickup && !inst->has_tw) return TGA_ERR_INVALID;       // pickups come with time windows
+    if (inst->pickup && (op_mask & kExtOps)) return TGA_ERR_INVALID;  // no pickup variant of the run swaps
     const long long W = n + 1 + m;
-    if (W > kMaxW) return TGA_ERR_RANGE;
+    if (W > ((op_mask & kExtOps) ? kMaxWExt : kMaxW)) return TGA_ERR_RANGE;
 
     tga_ctx *c = new (std::nothrow) tga_ctx();
     if (!c) return TGA_ERR_NOMEM;
@@ -402,6 +404,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     const size_t o_brec = take(sizeof(BRec) * (size_t)(W + 1));
     const size_t o_erec = take(sizeof(ERec) * (size_t)(W + 1));
     const size_t o_prec = take(d.has_pd ? sizeof(PRec) * (size_t)(W + 1) : 0);
+    const size_t o_xrec = take((op_mask & kExtOps) ? sizeof(XRec) * (size_t)(W + 1) : 0);
     const size_t o_rrec = take(sizeof(RouteRec) * (size_t)m);
     const size_t o_seen = take(sizeof(int) * (size_t)(n + 1));
     const size_t o_intra = take(sizeof(int) * kIntraVecPD * (size_t)(d.Wp + m));
@@ -420,6 +423,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.brec = (BRec *)(base + o_brec);
     d.erec = (ERec *)(base + o_erec);
     d.prec = d.has_pd ? (PRec *)(base + o_prec) : nullptr;
+    d.xrec = (op_mask & kExtOps) ? (XRec *)(base + o_xrec) : nullptr;
     d.rrec = (RouteRec *)(base + o_rrec);
     d.seen = (int *)(base + o_seen);
     d.scr_intra = (int *)(base + o_intra);
@@ -581,7 +585,7 @@ int tga_get_op_candidates(tga_ctx *c, int64_t *out_host) {
     Control C;
     int rc = read_control(c, &C);
     if (rc) return rc;
-    for (int op = 0; op < 6; ++op) out_host[op] = C.cand_op[op];
+    for (int op = 0; op < 8; ++op) out_host[op] = C.cand_op[op];
     return TGA_OK;
 }
 
@@ -807,6 +811,7 @@ int tga_set_granular(tga_ctx *c, const int32_t *nbr_dev, int32_t theta) {
     if (!c || theta < 0) return TGA_ERR_INVALID;
     if (theta > 0 && (!nbr_dev || theta > c->d.n - 1)) return TGA_ERR_INVALID;
     if (theta > 0 && c->d.has_pd) return TGA_ERR_STATE;      // the edge-based kernel has no pickup path
+    if (theta > 0 && (c->d.op_mask & kExtOps)) return TGA_ERR_STATE;   // ... and no swaps of runs
     if (c->granular) cudaFreeAsync(c->granular, c->stream);
     c->granular = nullptr;
     c->d.theta = 0; c->d.nbr = nullptr; c->d.nbr_rev = nullptr;

@@ -127,13 +127,41 @@ __device__ __forceinline__ int route_anchor(const Dev &d, int r, int start, int 
     return k == 0 ? d.n + 1 + r : route_node(d, start, L, k);
 }
 
+// Constants of the swaps of runs for the customer x at index k >= 1 of a
+// route (XRec): p* = the predecessor's prefix (distance, warp, departure),
+// g* = x's suffix after it, g1* = the suffix after x+ (has1: x+ is a
+// customer), run = the segment x, x+ (valid when has1), d1 = x+'s demand.
+__device__ __forceinline__ XRec make_xrec(int wTe, int Rcost, int Rload, int Q, int pdist, int ptwf, int ptau,
+                                          int gdist, int gtw, int gL, bool has1, int g1dist, int g1tw, int g1L,
+                                          const Seg &run, int d1, int e, int l, int sv, int dx) {
+    XRec x;
+    x.S1 = pdist + gdist + wTe * (ptwf + gtw) - Rcost;
+    x.tauP = ptau; x.Lg1 = gL; x.LQd1 = Rload - dx - Q;
+    if (has1) {
+        x.S2 = pdist + g1dist + wTe * (ptwf + g1tw) - Rcost;
+        x.Lg2 = g1L; x.LQd2 = Rload - dx - d1 - Q; x.ld2 = dx + d1;
+        x.E2 = run.E; x.L2 = run.L; x.Dm2 = run.D - run.TW; x.RC2 = run.dist + wTe * run.TW;
+    } else {
+        x.S2 = kBig; x.Lg2 = 0; x.LQd2 = 0; x.ld2 = 0; x.E2 = 0; x.L2 = 0; x.Dm2 = 0; x.RC2 = 0;
+    }
+    x.e = e; x.l = l; x.s = sv; x.d = dx;
+    return x;
+}
+
+__device__ __forceinline__ XRec xrec_none() {
+    XRec x{};
+    x.S1 = kBig; x.S2 = kBig;
+    return x;
+}
+
 // Rebuild every attribute of route r with one warp (all 32 lanes must call).
 // Elements of the route: 0 = start depot, 1..L customers, L+1 = end depot.
 // Forward inclusive scan gives the prefix F(x) of every anchor, backward
 // inclusive scan the suffix; the route's totals are the prefix of the end
 // depot.  Routes longer than 32 elements are scanned in chunks with a carry.
 // PD (pickups): the loads L_I, L_O, L_M (Section 4.3.2) are scanned beside.
-template <bool PD>
+// XS: also the constants of the swaps of runs (XRec).
+template <bool PD, bool XS = false>
 __device__ void rebuild_route(const Dev &d, int r, int lane) {
     const RouteRec rr = d.rrec[r];
     const int st = rr.start, L = rr.len, E = L + 2;
@@ -269,11 +297,25 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
         }
         if (k == 0) {
             e.rem1 = kBig; e.K2 = kBig; e.LQd = 0; e.tauP = 0;
+            if (XS) d.xrec[a] = xrec_none();
         } else {
             const int xm = route_node(d, st, L, k - 1);
             const BRec bp = d.brec[route_anchor(d, r, st, L, k - 1)];
             const int xn = route_node(d, st, L, k + 1);
             const int cmn = dmat(d, xm, xn);
+            if (XS) {
+                const bool has1 = k + 1 <= L;
+                Seg run{};
+                int d1 = 0, g1dist = 0, g1tw = 0, g1L = 0;
+                if (has1) {
+                    run = seg_cat(seg_node(d, x, dmat(d, x, xn)), seg_node(d, xn, 0));
+                    const BRec b1 = d.brec[xn];
+                    d1 = __ldg(d.demand + xn);
+                    g1dist = b1.distg; g1tw = b1.twg; g1L = b1.Lg;
+                }
+                d.xrec[a] = make_xrec(wTe, R.cost, R.load, Q, bp.distf, bp.twf, bp.tau, b.distg, b.twg, b.Lg, has1,
+                                      g1dist, g1tw, g1L, run, d1, e.e, e.l, e.s, e.d);
+            }
             const int twr = tw ? bp.twf + b.twg + max(bp.tau + cmn - b.Lg, 0) : 0;
             // load of the route without x: prefix through x- + suffix after x
             const int lrem = pd ? max(bp.lmf + b.loadg, bp.lof + b.lmg) : R.load - e.d;
@@ -477,7 +519,7 @@ __device__ void finish_block(const Dev &d) {
         for (int op = 0; op < 6; ++op) C->gcount[op] = 0;
         C->maxL = maxL; C->maxLoad = maxLoad;
         C->steps = 0; C->evals = 0; C->cand_total = 0;
-        for (int op = 0; op < 6; ++op) C->cand_op[op] = 0;
+        for (int op = 0; op < 8; ++op) C->cand_op[op] = 0;
         C->done = 0; C->local_opt = 0;
         C->plan_ready = 0; C->plan_done = 0;
         C->best_key = kNoKey;
@@ -495,6 +537,7 @@ __device__ void finish_block(const Dev &d) {
         b.route = -1;
         d.brec[d.W] = b;
         if (d.has_pd) d.prec[d.W] = PRec{};
+        if (d.op_mask & kExtOps) d.xrec[d.W] = xrec_none();
     }
 }
 
@@ -912,11 +955,12 @@ struct RouteView {
 };
 
 // kinds selects the sweeps this call runs: bit k-1 forward relocate/or-opt
-// of a run of k, bit 3 swap, bit 4 2-opt, bit 4+k backward run of k.
+// of a run of k, bit 3 swap, bit 4 2-opt, bit 4+k backward run of k, bit 8
+// the swaps of runs (XS).
 // PD: pickups; each candidate adds the change of the load excess of the
 // route's largest load (basePen = the current excess), built by the same
 // incremental concatenations with the loads of Section 4.3.2.
-template <bool TW, bool PD = false>
+template <bool TW, bool PD = false, bool XS = false>
 __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, int baseDist, int baseTw,
                              unsigned W, unsigned W2, int &best, unsigned &bidx, unsigned kinds = 0xffu,
                              int Q = 0, int wL = 0, int basePen = 0) {
@@ -1038,6 +1082,55 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
             }
         }
     }
+    // ---------------- swaps of runs starting at element i: the run
+    // i..i+kx-1 exchanges places with a later run y..y+ky-1 (y >= i+kx);
+    // the middle i+kx..y-1 grows with y
+    if (XS && (kinds & 256u) && i >= 1) {
+        auto enter = [&](int t, const Seg &g, int &warp) {
+            const int w = max(t - g.L, 0);
+            warp += w + g.TW;
+            return max(t, g.E) - w + g.D - g.TW;
+        };
+        const unsigned xi = (unsigned)V.node[i];
+        for (int v = 0; v < 3; ++v) {
+            const int kx = v == 0 ? 1 : 2, ky = v == 1 ? 1 : 2;
+            const unsigned op = (kx == 2 && ky == 2) ? 7u : 6u;
+            if (!(mask & (1u << op)) || i + kx - 1 > L) continue;
+            Seg rx = V.seg(i, V.c(i, i + 1));
+            if (kx == 2) rx = seg_cat(rx, V.seg(i + 1, 0));
+            Seg M{};
+            for (int y = i + kx; y + ky - 1 <= L; ++y) {
+                if (y == i + kx + 1) M = V.seg(i + kx, V.c(i + kx, y));
+                else if (y > i + kx + 1) M = seg_cat(M, V.seg(y - 1, V.c(y - 1, y)));
+                const bool hasM = y > i + kx;
+                const int last = y + ky - 1, xe = i + kx - 1;
+                Seg ry = V.seg(y, V.c(y, y + 1));
+                if (ky == 2) ry = seg_cat(ry, V.seg(y + 1, 0));
+                const int c1 = V.c(i - 1, y), c2 = V.c(last, hasM ? i + kx : i);
+                const int c4 = V.c(xe, last + 1);
+                int dist = V.distf[i - 1] + c1 + ry.dist + c2 + rx.dist + c4 + V.distg[last];
+                int c3 = 0;
+                if (hasM) {
+                    c3 = V.c(y - 1, i);
+                    dist += M.dist + c3;
+                }
+                int delta = dist - baseDist;
+                if (TW) {
+                    int warp = V.twf[i - 1];
+                    int t = enter(V.tau[i - 1] + c1, ry, warp);
+                    if (hasM) t = enter(t + c2, M, warp) + c3;
+                    else t += c2;
+                    t = enter(t, rx, warp);
+                    const int w4 = max(t + c4 - V.Lg[last], 0);
+                    delta += wT * (warp + w4 + V.twg[last] - baseTw);
+                }
+                const unsigned xy = (unsigned)V.node[y];
+                const unsigned a = kx == ky ? min(xi, xy) : (kx == 1 ? xi : xy);
+                const unsigned b = kx == ky ? max(xi, xy) : (kx == 1 ? xy : xi);
+                TGA_TRY(delta, op * W2 + a * W + b);
+            }
+        }
+    }
     // ---------------- moves whose destination is element j = i: the run
     // t..t+k-1, t >= j+2, moves back to just after element j.
     const int j = i;
@@ -1077,7 +1170,7 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
 
 // Intra-route candidates of route r with one warp (all 32 lanes call);
 // S is this warp's kIntraSmemPerWarp ints of shared memory.
-template <bool TW, bool PD = false>
+template <bool TW, bool PD = false, bool XS = false>
 __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, unsigned &bidx) {
     const RouteRec R = d.rrec[r];
     const int L = R.len;
@@ -1131,7 +1224,7 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
     const unsigned W = (unsigned)d.W, W2 = W * W;
     const int wT = TW ? d.wT : 0;
     for (int i = lane; i <= L; i += 32)
-        intra_anchor<TW, PD>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, 0xffu, d.Q, d.wL,
+        intra_anchor<TW, PD, XS>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, 0x1ffu, d.Q, d.wL,
                               max(R.lm - d.Q, 0));
     __syncwarp();
 }
@@ -1140,7 +1233,7 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
 // route into S (kIntraSmemPerWarp ints), then warp w runs the sweep kinds
 // {w, w+nw, ...} of every anchor, so the serial sweeps of one anchor are
 // spread over the warps.
-template <bool TW, bool PD = false>
+template <bool TW, bool PD = false, bool XS = false>
 __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsigned &bidx) {
     const RouteRec R = d.rrec[r];
     const int L = R.len;
@@ -1192,11 +1285,11 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
     }
     __syncthreads();
     unsigned kinds = 0;
-    for (int k = warp; k < 8; k += nw) kinds |= 1u << k;
+    for (int k = warp; k < (XS ? 9 : 8); k += nw) kinds |= 1u << k;
     const unsigned W = (unsigned)d.W, W2 = W * W;
     const int wT = TW ? d.wT : 0;
     for (int i = lane; i <= L; i += 32)
-        intra_anchor<TW, PD>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, kinds, d.Q, d.wL,
+        intra_anchor<TW, PD, XS>(V, i, d.op_mask, wT, R.dist, R.tw, W, W2, best, bidx, kinds, d.Q, d.wL,
                               max(R.lm - d.Q, 0));
 }
 
@@ -1243,13 +1336,14 @@ __device__ __forceinline__ int tw_enter(int a, const int4 g, int &warp) {
     return max(a, g.x) - w + g.z;
 }
 
-template <bool PD = false>
+// XS: also the swaps of runs inside the route (op ranks 6, 7).
+template <bool PD = false, bool XS = false>
 __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsigned &bidx) {
     const RouteRec R = d.rrec[r];
     const int L = R.len;
     if (L < 2) return;
     if (L > kTabMaxL) {
-        intra_route_block<true, PD>(d, r, S, best, bidx);
+        intra_route_block<true, PD, XS>(d, r, S, best, bidx);
         return;
     }
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1331,6 +1425,28 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
     const unsigned mask = d.op_mask;
     const unsigned W = (unsigned)d.W, W2 = W * W;
     const int wT = d.wT, baseDist = R.dist, baseTw = R.tw;
+    // exchange of the run x..x+kx-1 with the later run y..y+ky-1 (x + kx <= y):
+    // prefix(x-1) + (y..) + (x+kx..y-1) + (x..) + suffix(y+ky-1)
+    auto xchg = [&](int x, int kx, int y, int ky) {
+        const int last = y + ky - 1, xe = x + kx - 1;
+        const int c1 = D[(x - 1) * E + y];
+        int tw = twf[x - 1];
+        int tx = tw_enter(tau[x - 1] + c1, Ft[tri_at(y, last, L)], tw);
+        int dist = distf[x - 1] + c1 + (distf[last] - distf[y]);
+        int prev = last;
+        if (y > x + kx) {
+            const int c2 = D[last * E + x + kx];
+            tx = tw_enter(tx + c2, Ft[tri_at(x + kx, y - 1, L)], tw);
+            dist += c2 + (distf[y - 1] - distf[x + kx]);
+            prev = y - 1;
+        }
+        const int c3 = D[prev * E + x];
+        tx = tw_enter(tx + c3, Ft[tri_at(x, xe, L)], tw);
+        const int c4 = D[xe * E + last + 1];
+        const int w4 = max(tx + c4 - Lg[last], 0);
+        dist += c3 + (distf[xe] - distf[x]) + c4 + distg[last];
+        return dist - baseDist + wT * (tw + w4 + twg[last] - baseTw);
+    };
     const int L1 = L + 1;
     const unsigned adep = (unsigned)(d.n + 1 + r);
     for (int t = tid; t < L1 * L1; t += nthr) {
@@ -1386,6 +1502,15 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
                 TGA_TRY(dist + cc + cd - baseDist + wT * (tw + w4 + twg[j] - baseTw) + lp,
                         W2 + min(xi, xj) * W + max(xi, xj));
             }
+            if (XS) {
+                // a customer with a run of two, and two runs of two
+                if ((mask & 64u) && j + 1 <= L)          // x_i alone, the run x_j x_j+1
+                    TGA_TRY(xchg(i, 1, j, 2), 6u * W2 + xi * W + xj);
+                if ((mask & 64u) && i + 1 <= L && j >= i + 2)   // the run x_i x_i+1, x_j alone
+                    TGA_TRY(xchg(i, 2, j, 1), 6u * W2 + xj * W + xi);
+                if ((mask & 128u) && j >= i + 2 && j + 1 <= L)
+                    TGA_TRY(xchg(i, 2, j, 2), 7u * W2 + min(xi, xj) * W + max(xi, xj));
+            }
             // 2-opt: reverse x_i..x_j
             if (mask & 4u) {
                 const int ca = D[(i - 1) * E + j], cb = D[i * E + j + 1];
@@ -1430,6 +1555,9 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
 // position-ordered copy indexed by j, so a warp's loads are contiguous.
 //   relocate/or-opt run i..i+k-1 after j: rem_k + c(x_j,x_i) + c(x_{i+k-1},x_{j+1}) - c(x_j,x_{j+1})
 //   swap i<j (adjacent or not), 2-opt i<j (reversal of i..j).
+// XS: also the swaps of runs -- x_i alone with the run x_j x_j+1 (either
+// side), and the run x_i x_i+1 with a later run x_j x_j+1.
+template <bool XS = false>
 __device__ void intra_cvrp_position(const Dev &d, int p, int lane, int &best, unsigned &bidx) {
     if (p >= d.Wp - 1) return;
     const int ax = d.seq[p];
@@ -1492,6 +1620,43 @@ __device__ void intra_cvrp_position(const Dev &d, int p, int lane, int &best, un
                 TGA_TRY(delta, 2u * W2 + (unsigned)xi * W + (unsigned)aj);
             }
         }
+        if (XS && j >= 1) {
+            // e(k) = c(x_k, x_k+1), the route's edge leaving element k
+            auto edge = [&](int k) { return dfAt(k + 1) - dfAt(k); };
+            const unsigned xj = (unsigned)aj;
+            if ((mask & 64u) && j + 1 <= L) {
+                // x_i alone, the run x_j x_j+1
+                int delta = kBig;
+                if (j == i + 1) {            // (i-1) (i+1 i+2) (i) (i+3)
+                    delta = TGA_LDG(rowP + i + 1) + TGA_LDG(rowI + i + 2) + TGA_LDG(rowI + i + 3) - e_prev - e_next -
+                            edge(i + 2);
+                } else if (j >= i + 2) {     // (i-1) (j j+1) (i+1..j-1) (i) (j+2)
+                    delta = TGA_LDG(rowP + j) + TGA_LDG(rowN + j + 1) + TGA_LDG(rowI + j - 1) +
+                            TGA_LDG(rowI + j + 2) - e_prev - e_next - edge(j - 1) - edge(j + 1);
+                } else if (j == i - 2) {     // (i-3) (i) (i-2 i-1) (i+1)
+                    delta = TGA_LDG(rowI + i - 3) + TGA_LDG(rowI + i - 2) + TGA_LDG(rowP + i + 1) - edge(i - 3) -
+                            e_prev - e_next;
+                } else if (j <= i - 3) {     // (j-1) (i) (j+2..i-1) (j j+1) (i+1)
+                    delta = TGA_LDG(rowI + j - 1) + TGA_LDG(rowI + j + 2) + TGA_LDG(rowP + j) +
+                            TGA_LDG(rowN + j + 1) - edge(j - 1) - edge(j + 1) - e_prev - e_next;
+                }
+                if (delta < kBig) TGA_TRY(delta, 6u * W2 + (unsigned)xi * W + xj);
+            }
+            if ((mask & 128u) && i + 1 <= L && j >= i + 2 && j + 1 <= L) {
+                // the run x_i x_i+1 with the later run x_j x_j+1
+                const int *rowN2 = rowOf(nodeAt(i + 2));
+                const int e_i1 = edge(i + 1);        // c(x_i+1, x_i+2)
+                int delta;
+                if (j == i + 2) {            // (i-1) (i+2 i+3) (i i+1) (i+4)
+                    delta = TGA_LDG(rowP + i + 2) + TGA_LDG(rowI + i + 3) + TGA_LDG(rowN + i + 4) - e_prev - e_i1 -
+                            edge(i + 3);
+                } else {                     // (i-1) (j j+1) (i+2..j-1) (i i+1) (j+2)
+                    delta = TGA_LDG(rowP + j) + TGA_LDG(rowN2 + j + 1) + TGA_LDG(rowI + j - 1) +
+                            TGA_LDG(rowN + j + 2) - e_prev - e_i1 - edge(j - 1) - edge(j + 1);
+                }
+                TGA_TRY(delta, 7u * W2 + min((unsigned)xi, xj) * W + max((unsigned)xi, xj));
+            }
+        }
     }
 }
 
@@ -1528,8 +1693,27 @@ __device__ __forceinline__ int new_src(const MovePlan &P, bool isA, int t) {
             f = (t == P.i) ? P.j : (t == P.j ? P.i : t);
         } else if (op == 2) {
             f = (t >= P.i && t <= P.j) ? P.i + P.j - t : t;
+        } else if (op >= 6) {
+            // runs x (kx) before y (ky) exchange places; the middle keeps its order
+            const bool af = P.i < P.j;
+            const int x = af ? P.i : P.j, kx = af ? P.k : 2, y = af ? P.j : P.i, ky = af ? 2 : P.k;
+            if (t < x) f = t;
+            else if (t < x + ky) f = y + (t - x);
+            else if (t < y + ky - kx) f = x + kx + (t - x - ky);
+            else if (t < y + ky) f = x + (t - (y + ky - kx));
+            else f = t;
         }
         return P.pA + f;
+    }
+    if (op >= 6) {      // the run of k at a and the run of 2 at b exchange routes
+        if (isA) {
+            if (t < P.i) return P.pA + t;
+            if (t < P.i + 2) return P.pB + P.j + (t - P.i);
+            return P.pA + t - 2 + P.k;
+        }
+        if (t < P.j) return P.pB + t;
+        if (t < P.j + P.k) return P.pA + P.i + (t - P.j);
+        return P.pB + t - P.k + 2;
     }
     if (op == 0 || op == 4 || op == 5) {
         if (isA) return t < P.i ? P.pA + t : P.pA + t + P.k;
@@ -1621,7 +1805,7 @@ __device__ __forceinline__ Seg seg_vals(int e, int l, int s, int load, int out) 
 // Lane 0 writes the route totals (range load, dist, warp, cost) to
 // tot[0..3]; the range load is the delivery total, plus the pickup total
 // with pickups.
-template <bool PD>
+template <bool PD, bool XS = false>
 __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int *sbuf, const StepPlan &S,
                                    int lane, int *tot) {
     const int E = L + 2;
@@ -1696,6 +1880,7 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
     // the runs x..x+1 and x..x+2
     const Seg n1 = shfl_seg_down(node, 1), n2 = shfl_seg_down(node, 2);
     const Seg run2 = seg_cat(node, n1), run3 = seg_cat(run2, n2);
+    const int dnext = XS ? __shfl_down_sync(FULL, dem, 1) : 0;       // demand of x+
     // pickups: suffix loads after x, after x+1 and after x+2; prefix loads
     // through x-; the loads of the runs
     int glI = 0, glM = 0, w2I = 0, w2M = 0, w3I = 0, w3M = 0, plo = 0, plm = 0;
@@ -1755,6 +1940,11 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
         ep[5] = make_int4(Lg, tauP, E2, L2);
         ep[6] = make_int4(Dm2, E3, L3, Dm3);
         ep[7] = make_int4(x, k, 0, 0);
+        if (XS) {
+            d.xrec[a] = k == 0 ? xrec_none()
+                               : make_xrec(wTe, Rcost, Rload, d.Q, pdist, ptwf, ptau, gdist, twg, Lg, k + 1 <= L,
+                                           w2dist, w2tw, w2L, run2, dnext, ne, nl, ns, dem);
+        }
         if (pd) {
             const int Q = d.Q;
             const int pk = ndl.o;
@@ -1810,7 +2000,7 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
     pl.a = (int)((idx % W2) / W);
     pl.b = (int)(idx % W);
     pl.delta = key_delta(key);
-    bool ok = pl.op < 6 && ((d.op_mask >> pl.op) & 1u) && pl.a >= 1 && pl.b >= 1;
+    bool ok = pl.op < 8 && ((d.op_mask >> pl.op) & 1u) && pl.a >= 1 && pl.b >= 1;
     int costA = 0, costB = 0;
     if (ok) {
         // one round trip: the anchors' records carry route, index, route
@@ -1839,6 +2029,13 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
         } else if (op == 2) {
             ok = pl.a <= d.n && pl.b <= d.n && pl.A == pl.B && pl.i < pl.j;
             pl.nLA = pl.LA; pl.nLB = pl.LB;
+        } else if (op >= 6) {
+            // a run of k (1 or 2) at a and a run of 2 at b, disjoint
+            pl.k = op == 6 ? 1 : 2;
+            ok = pl.a <= d.n && pl.b <= d.n && (op == 6 || pl.a < pl.b) && pl.i + pl.k - 1 <= pl.LA &&
+                 pl.j + 1 <= pl.LB && (pl.A != pl.B || pl.i + pl.k <= pl.j || pl.j + 2 <= pl.i);
+            pl.nLA = pl.A == pl.B ? pl.LA : pl.LA - pl.k + 2;
+            pl.nLB = pl.A == pl.B ? pl.LB : pl.LB - 2 + pl.k;
         } else {
             ok = pl.A < pl.B;
             pl.nLA = pl.i + pl.LB - pl.j;
@@ -1882,7 +2079,7 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
 // thread prefetches the counters.  Thread 0 then updates cost and counters
 // and ends the step (done flag, graph condition).  ext: the move came from
 // the caller, whose delta is not checked against the rebuilt routes.
-template <bool PD>
+template <bool PD, bool XS = false>
 __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, bool ext,
                                  cudaGraphConditionalHandle cond, int use_cond) {
     Control *C = d.ctl;
@@ -1917,8 +2114,8 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
             if (isA || pl.B != pl.A) {
                 const int r = isA ? pl.A : pl.B, L = isA ? pl.nLA : pl.nLB;
                 const bool fast = L + 2 <= 32;
-                if (fast) rebuild_route_warp<PD>(d, r, plan_new_start(S, isA), L, sbuf, S, lane, s_tot[warp]);
-                else rebuild_route<PD>(d, r, lane);
+                if (fast) rebuild_route_warp<PD, XS>(d, r, plan_new_start(S, isA), L, sbuf, S, lane, s_tot[warp]);
+                else rebuild_route<PD, XS>(d, r, lane);
                 if (lane == 0) s_fast[warp] = fast;
             }
         } else {

@@ -32,6 +32,9 @@ constexpr unsigned long long kNoKey = ~0ull;
 constexpr int kColOff = 4;                    // pcol storage column of position q is q + 4
 constexpr int kMaxTileCols = 256;             // widest tile (8 warps x 32 columns)
 constexpr int kMaxW = 26754;                  // 6 * W^2 < 2^32
+constexpr int kMaxWExt = 23170;               // 8 * W^2 < 2^32 (swaps of runs enabled)
+constexpr unsigned kExtOps = 0xC0u;           // op ranks 6, 7: swaps of runs
+constexpr int kXswapRows = 16, kXswapThreads = 128;   // swaps of runs: rows per block, columns per block
 constexpr int kIntraVec = 10;                 // per-element int arrays of an intra-route view
 constexpr int kIntraVecPD = 15;               // ... with the five load arrays of pickups
 
@@ -71,6 +74,22 @@ struct __align__(16) PRec {
     int SA, SB, SC, mx;                       // the same with P-; max(d_x, p_x)
     int HM, HO, TI, TM;                       // LM_P - Q, LO_P - Q, LI_S, LM_S
     int LO2, LM2, LO3, LM3;                   // L_O, L_M of the runs of 2 and 3 starting at x
+};
+
+// Per-anchor constants of the swaps of runs (op ranks 6, 7: a customer with
+// a run of two, two runs of two; Section 5.3.1 Swap with N1, N2 in {1, 2}).
+// For customer x: the gap left by x alone (S1) or by the run x, x+ (S2) --
+// prefix distance and warp through the predecessor plus suffix after the
+// gap, minus the route cost (2^29 when the run does not exist) -- with the
+// departure time after the predecessor and the latest arrival and load
+// slack of the suffix; the run x, x+ as a time-window segment {E, L,
+// D - T_V} with RC2 = its distance + w_tw * its warp and its load; and the
+// node data of x.
+struct __align__(16) XRec {
+    int S1, tauP, Lg1, LQd1;                  // gap of x: removal constant, tau(x-), T_L after x, load - d_x - Q
+    int S2, Lg2, LQd2, ld2;                   // gap of the run: removal constant, T_L after x+, load - run - Q, run load
+    int E2, L2, Dm2, RC2;                     // the run as a segment; RC2 = dist + w_tw * warp
+    int e, l, s, d;                           // x's window, service and demand
 };
 
 // load = total delivery (L_I); with pickups lo = total pickup (L_O) and lm
@@ -124,7 +143,7 @@ struct Control {
     unsigned long long bar_count;
     int plan_seq, eval_done;
     int plan_cta, pad5[3];                    // persistent descent: the CTA applying the step
-    long long cand_op[6];                     // candidates evaluated per operator rank, all evaluations
+    long long cand_op[8];                     // candidates evaluated per operator rank, all evaluations
     // edge-based extraction: sum max(0,L-1)^2, sum max(0,L-2)^2 (intra-route
     // or-opt counts) and the inter-route candidates the running evaluation
     // kept, per operator rank
@@ -146,6 +165,7 @@ struct Dev {
     BRec *brec;               // [W+1] (index W is the dummy record)
     ERec *erec;               // [W+1]
     PRec *prec;               // [W+1] (pickups only)
+    XRec *xrec;               // [W+1] (swaps of runs only)
     RouteRec *rrec;           // [m]
     int *pcol;                // [(n+1) * ldp]
     Control *ctl;
@@ -280,7 +300,12 @@ __host__ __device__ inline long long op_candidates(int op, long long n, long lon
         case 2: return (sumL2 - n) / 2;
         case 3: return (A * A - (sumL2 + 2 * n + m)) / 2;
         case 4: return sumLm1 * (A - 3);
-        default: return sumLm2 * (A - 4);
+        case 5: return sumLm2 * (A - 4);
+        // runs of two: sumLm1 of them; a customer outside the run (n - 2 each),
+        // and pairs of runs minus the overlapping pairs (sumLm2: one per
+        // three consecutive customers)
+        case 6: return sumLm1 * (n - 2);
+        default: return sumLm1 * (sumLm1 - 1) / 2 - sumLm2;
     }
 }
 
@@ -288,7 +313,7 @@ __host__ __device__ inline long long candidate_count(long long n, long long m, u
                                                      long long sumL2, long long sumLm1,
                                                      long long sumLm2) {
     long long c = 0;
-    for (int op = 0; op < 6; ++op) c += op_candidates(op, n, m, mask, sumL2, sumLm1, sumLm2);
+    for (int op = 0; op < 8; ++op) c += op_candidates(op, n, m, mask, sumL2, sumLm1, sumLm2);
     return c;
 }
 
@@ -326,7 +351,7 @@ __device__ inline void count_evaluation(const Dev &d, Control *C) {
         return;
     }
     C->cand_total += C->cand_per_eval;
-    for (int op = 0; op < 6; ++op)
+    for (int op = 0; op < 8; ++op)
         C->cand_op[op] += op_candidates(op, d.n, d.m, d.op_mask, C->sumL2, C->sumLm1, C->sumLm2);
 }
 
@@ -359,6 +384,8 @@ void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warp
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
                   cudaStream_t s, int rs = 1, int tail = 0);
 void launch_intra(const Dev &d, cudaStream_t s, int tail = 0);
+// swaps of runs between routes (op ranks 6, 7; no-op unless enabled)
+void launch_xswap(const Dev &d, cudaStream_t s, int tail = 0);
 int eval_blocks(const Dev &d, int ntiles);
 // pre = 1: apply the plan decoded by the evaluation's last CTA (descent
 // steps); else decode *ext (or the best key) in the launch itself.

@@ -50,6 +50,7 @@ __global__ void k_build_routes(Dev d) {
     const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (r >= d.m) return;
     if (d.has_pd) rebuild_route<true>(d, r, threadIdx.x & 31);
+    else if (d.op_mask & kExtOps) rebuild_route<false, true>(d, r, threadIdx.x & 31);
     else rebuild_route<false>(d, r, threadIdx.x & 31);
 }
 
@@ -132,25 +133,26 @@ __global__ void k_granular_setup(Dev d, unsigned char *rev, int *bad) {
 // VRPTW intra-route moves: one block of kIntraWarps warps per route
 // (subsequence tables in kIntraTabSmemInts ints of dynamic shared memory;
 // kIntraTabSmemIntsPD with pickups).
-template <bool PD>
+template <bool PD, bool XS>
 __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
     extern __shared__ __align__(16) int smem[];
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    intra_route_table<PD>(d, blockIdx.x, smem, best, bidx);
+    intra_route_table<PD, XS>(d, blockIdx.x, smem, best, bidx);
     if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
     if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
+template <bool XS>
 __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
     const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    intra_cvrp_position(d, p, threadIdx.x & 31, best, bidx);
+    intra_cvrp_position<XS>(d, p, threadIdx.x & 31, best, bidx);
     if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d, int tail) {
 // pre = 0: CTA 0 decodes *ext (or the best key) and publishes the plan while
 // the other CTAs wait for it.  The last CTA to finish re-arms the plan flag
 // for the next step.
-template <bool PD>
+template <bool PD, bool XS>
 __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaGraphConditionalHandle cond,
                                                int use_cond, int pre) {
     extern __shared__ __align__(16) int smem[];
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
         __syncthreads();
         if (!s_ok && tid == 0) sP.act = 0;
         __syncthreads();
-        if (blockIdx.x == 0) apply_plan_block<PD>(d, sP, smem, false, cond, use_cond);
+        if (blockIdx.x == 0) apply_plan_block<PD, XS>(d, sP, smem, false, cond, use_cond);
         else band_plan_rows(d, sP, smem, 0, d.n + 1, blockIdx.x - 1, gridDim.x - 1);
     } else if (blockIdx.x == 0) {
         if (tid == 0) {
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
             atomicExch(&C->plan_ready, 1);
         }
         __syncthreads();
-        apply_plan_block<PD>(d, sP, smem, ext != nullptr, cond, use_cond);
+        apply_plan_block<PD, XS>(d, sP, smem, ext != nullptr, cond, use_cond);
     } else {
         if (tid == 0) {
             s_ok = wait_flag(&C->plan_ready, 1000LL * 1000 * 1000);
@@ -247,6 +249,97 @@ __global__ void k_begin(Dev d, long long max_steps) {
     C->step_limit = lim < C->steps ? 0x7fffffffffffffffLL : lim;
 }
 
+// Swaps of runs between routes (op ranks 6, 7; Section 5.3.1 Swap with
+// N1 in {1, 2}, N2 = 2).  The block stages kXswapRows rows (customer a at
+// position p: its XRec, route and the nodes at p-1 .. p+2); thread q holds
+// the column anchor b at position q.  For each row with a in another route
+// than b, with t(r, c) = c(node at p+r, node at q+c) read from the
+// position-ordered distance copy (contiguous over the threads):
+//   rank 6, a alone <-> the run b b+:
+//     route of a: prefix(a-) + (b b+) + suffix after a   links t(-1,0), t(1,1)
+//     route of b: prefix(b-) + a + suffix after b+        links t(0,-1), t(0,2)
+//   rank 7 (p < q), the runs a a+ <-> b b+:
+//     route of a: prefix(a-) + (b b+) + suffix after a+  links t(-1,0), t(2,1)
+//     route of b: prefix(b-) + (a a+) + suffix after b+  links t(0,-1), t(1,2)
+// Intra-route exchanges are evaluated by the route kernels.
+template <bool TW>
+__global__ void __launch_bounds__(kXswapThreads) k_eval_xswap(Dev d, int tail) {
+    const int done = *(volatile int *)&d.ctl->done;
+    __shared__ int s_node[kXswapRows + 3], s_anc[kXswapRows], s_rt[kXswapRows];
+    __shared__ XRec s_xr[kXswapRows];
+    const int ncb = (d.Wp + kXswapThreads - 1) / kXswapThreads;
+    const int rb = blockIdx.x / ncb, cb = blockIdx.x - rb * ncb;
+    const int p0 = rb * kXswapRows, tid = threadIdx.x;
+    if (tid < kXswapRows + 3) {
+        const int pp = p0 - 1 + tid;
+        s_node[tid] = (pp >= 0 && pp < d.Wp) ? node_of(d.seq[pp], d.n) : 0;
+    }
+    if (tid < kXswapRows) {
+        const int p = p0 + tid;
+        const int a = p < d.Wp ? d.seq[p] : d.W;
+        const bool cust = a >= 1 && a <= d.n;
+        s_anc[tid] = cust ? a : 0;
+        s_rt[tid] = cust ? d.brec[a].route : -1;
+        s_xr[tid] = cust ? d.xrec[a] : xrec_none();
+    }
+    const int q = cb * kXswapThreads + tid;
+    const int b = q < d.Wp ? d.seq[q] : d.W;
+    const bool bcust = b >= 1 && b <= d.n;
+    const XRec xb = bcust ? d.xrec[b] : xrec_none();
+    const int Br = bcust ? d.brec[b].route : -2;
+    __syncthreads();
+    int best = kBestInit;
+    unsigned bidx = 0xffffffffu;
+    if (bcust && xb.S2 < (kBig >> 1)) {       // both ranks need the run b b+
+        const unsigned mask = d.op_mask;
+        const unsigned W = (unsigned)d.W, W2 = W * W;
+        const int wL = d.wL, wT = d.wT;
+        const int *pc = d.pcol + kColOff + q;
+        const size_t ldp = (size_t)d.ldp;
+#pragma unroll 2
+        for (int i = 0; i < kXswapRows; ++i) {
+            const int a = s_anc[i];
+            if (a == 0 || s_rt[i] == Br) continue;
+            const XRec xa = s_xr[i];
+            const int am = s_node[i], ap = s_node[i + 2], app = s_node[i + 3];
+            const int c_amb = TGA_LDG(pc + (size_t)am * ldp);            // c(a-, b)
+            const int c_abm = TGA_LDG(pc + (size_t)a * ldp - 1);         // c(a, b-)
+            if (mask & 64u) {
+                const int c_apb1 = TGA_LDG(pc + (size_t)ap * ldp + 1);   // c(a+, b+1)
+                const int c_ab2 = TGA_LDG(pc + (size_t)a * ldp + 2);     // c(a, b+2)
+                int dl = xa.S1 + c_amb + xb.RC2 + c_apb1 + xb.S2 + c_abm + c_ab2 +
+                         wL * (max(xa.LQd1 + xb.ld2, 0) + max(xb.LQd2 + xa.d, 0));
+                if (TW) {
+                    const int x1 = xa.tauP + c_amb, w1 = max(x1 - xb.L2, 0);
+                    const int x2 = max(x1, xb.E2) - w1 + xb.Dm2 + c_apb1, w2 = max(x2 - xa.Lg1, 0);
+                    const int y1 = xb.tauP + c_abm, v1 = max(y1 - xa.l, 0);
+                    const int y2 = max(y1, xa.e) - v1 + xa.s + c_ab2, v2 = max(y2 - xb.Lg2, 0);
+                    dl += wT * (w1 + w2 + v1 + v2);
+                }
+                TGA_TRY(dl, 6u * W2 + (unsigned)a * W + (unsigned)b);
+            }
+            if ((mask & 128u) && p0 + i < q && xa.S2 < (kBig >> 1)) {
+                const int c_appb1 = TGA_LDG(pc + (size_t)app * ldp + 1); // c(a+2, b+1)
+                const int c_apb2 = TGA_LDG(pc + (size_t)ap * ldp + 2);   // c(a+1, b+2)
+                int dl = xa.S2 + c_amb + xb.RC2 + c_appb1 + xb.S2 + c_abm + xa.RC2 + c_apb2 +
+                         wL * (max(xa.LQd2 + xb.ld2, 0) + max(xb.LQd2 + xa.ld2, 0));
+                if (TW) {
+                    const int x1 = xa.tauP + c_amb, w1 = max(x1 - xb.L2, 0);
+                    const int x2 = max(x1, xb.E2) - w1 + xb.Dm2 + c_appb1, w2 = max(x2 - xa.Lg2, 0);
+                    const int y1 = xb.tauP + c_abm, v1 = max(y1 - xa.L2, 0);
+                    const int y2 = max(y1, xa.E2) - v1 + xa.Dm2 + c_apb2, v2 = max(y2 - xb.Lg2, 0);
+                    dl += wT * (w1 + w2 + v1 + v2);
+                }
+                TGA_TRY(dl, 7u * W2 + (unsigned)min(a, b) * W + (unsigned)max(a, b));
+            }
+        }
+    }
+    if (done) return;
+    const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
+    block_min_to(key, &d.ctl->best_key);
+    if (tail && threadIdx.x == 0) eval_tail(d, tail);
+}
+
 // ---------------------------------------------------------------------------
 // host-side launchers
 
@@ -266,8 +359,12 @@ int setup_kernel_attrs(int max_band) {
         e = cudaFuncSetAttribute(k_eval_inter<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_eval_inter<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_apply<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     (void)max_band;
     return e == cudaSuccess ? 0 : 1;
 }
@@ -326,9 +423,11 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
 // VRPTW: one block per route; CVRP: one warp per moved position, 8 per block.
 int intra_blocks(const Dev &d) { return d.has_tw ? d.m : (d.Wp - 1 + 7) / 8; }
 
+int xswap_blocks(const Dev &d);
+
 int eval_blocks(const Dev &d, int ntiles) {
     if (d.theta > 0) return (int)((edge_items(d) + 255) / 256) + intra_blocks(d);
-    return (ntiles > 0 ? ntiles : 0) + intra_blocks(d);
+    return (ntiles > 0 ? ntiles : 0) + intra_blocks(d) + xswap_blocks(d);
 }
 
 void launch_granular_setup(const Dev &d, unsigned char *rev, int *bad_dev, cudaStream_t s) {
@@ -338,17 +437,35 @@ void launch_granular_setup(const Dev &d, unsigned char *rev, int *bad_dev, cudaS
 }
 
 void launch_intra(const Dev &d, cudaStream_t s, int tail) {
+    const bool xs = (d.op_mask & kExtOps) != 0;
+    const size_t tab = kIntraTabSmemInts * sizeof(int);
     if (d.has_pd)
-        k_eval_intra<true><<<intra_blocks(d), kIntraWarps * 32, kIntraTabSmemIntsPD * sizeof(int), s>>>(d, tail);
-    else if (d.has_tw)
-        k_eval_intra<false><<<intra_blocks(d), kIntraWarps * 32, kIntraTabSmemInts * sizeof(int), s>>>(d, tail);
-    else k_eval_intra_cvrp<<<intra_blocks(d), 256, 0, s>>>(d, tail);
+        k_eval_intra<true, false><<<intra_blocks(d), kIntraWarps * 32, kIntraTabSmemIntsPD * sizeof(int), s>>>(d, tail);
+    else if (d.has_tw && xs) k_eval_intra<false, true><<<intra_blocks(d), kIntraWarps * 32, tab, s>>>(d, tail);
+    else if (d.has_tw) k_eval_intra<false, false><<<intra_blocks(d), kIntraWarps * 32, tab, s>>>(d, tail);
+    else if (xs) k_eval_intra_cvrp<true><<<intra_blocks(d), 256, 0, s>>>(d, tail);
+    else k_eval_intra_cvrp<false><<<intra_blocks(d), 256, 0, s>>>(d, tail);
+}
+
+// Swaps of runs between routes: the block walks kXswapRows row positions,
+// one thread per column position.
+int xswap_blocks(const Dev &d) {
+    if (!(d.op_mask & kExtOps)) return 0;
+    return ((d.Wp + kXswapRows - 1) / kXswapRows) * ((d.Wp + kXswapThreads - 1) / kXswapThreads);
+}
+
+void launch_xswap(const Dev &d, cudaStream_t s, int tail) {
+    const int blocks = xswap_blocks(d);
+    if (blocks <= 0) return;
+    if (d.has_tw) k_eval_xswap<true><<<blocks, kXswapThreads, 0, s>>>(d, tail);
+    else k_eval_xswap<false><<<blocks, kXswapThreads, 0, s>>>(d, tail);
 }
 
 void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs,
                  int tail) {
     launch_inter(d, tiles, ntiles, rows, warps, s, rs, tail);
     launch_intra(d, s, tail);
+    launch_xswap(d, s, tail);
 }
 
 int apply_grid(const Dev &d) {
@@ -359,8 +476,10 @@ int apply_grid(const Dev &d) {
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond, cudaStream_t s,
                   int pre) {
     const size_t sm = (size_t)band_smem_ints(d.Wp, 16) * sizeof(int);
-    if (d.has_pd) k_apply<true><<<apply_grid(d), 512, sm, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond, pre);
-    else k_apply<false><<<apply_grid(d), 512, sm, s>>>(d, ext, (cudaGraphConditionalHandle)cond, use_cond, pre);
+    const auto h = (cudaGraphConditionalHandle)cond;
+    if (d.has_pd) k_apply<true, false><<<apply_grid(d), 512, sm, s>>>(d, ext, h, use_cond, pre);
+    else if (d.op_mask & kExtOps) k_apply<false, true><<<apply_grid(d), 512, sm, s>>>(d, ext, h, use_cond, pre);
+    else k_apply<false, false><<<apply_grid(d), 512, sm, s>>>(d, ext, h, use_cond, pre);
 }
 
 void launch_sync_solution(const Dev &d, cudaStream_t s) {

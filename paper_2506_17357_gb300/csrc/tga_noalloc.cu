@@ -49,6 +49,7 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
     const size_t o_brec = take(sizeof(BRec) * (W + 1));
     const size_t o_erec = take(sizeof(ERec) * (W + 1));
     const size_t o_prec = take(sizeof(PRec) * (W + 1));
+    const size_t o_xrec = take(sizeof(XRec) * (W + 1));
     const size_t o_rrec = take(sizeof(RouteRec) * m);
     const size_t o_seen = take(sizeof(int) * (n + 1));
     const size_t o_intra = take(sizeof(int) * kIntraVecPD * (P + m));
@@ -61,6 +62,7 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
         d.brec = (BRec *)(base + o_brec);
         d.erec = (ERec *)(base + o_erec);
         d.prec = (PRec *)(base + o_prec);
+        d.xrec = (XRec *)(base + o_xrec);
         d.rrec = (RouteRec *)(base + o_rrec);
         d.seen = (int *)(base + o_seen);
         d.scr_intra = (int *)(base + o_intra);
@@ -75,7 +77,8 @@ size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
 constexpr size_t noalloc_max_bytes() {
     const size_t P = kNoAllocMaxPositions, N1 = P, M = P - 1, W1 = P + 1;
     return align256(sizeof(Control)) + align256(4 * P) + align256(4 * W1) + align256(sizeof(BRec) * W1) +
-           align256(sizeof(ERec) * W1) + align256(sizeof(PRec) * W1) + align256(sizeof(RouteRec) * M) +
+           align256(sizeof(ERec) * W1) + align256(sizeof(PRec) * W1) + align256(sizeof(XRec) * W1) +
+           align256(sizeof(RouteRec) * M) +
            align256(4 * N1) + align256(4 * kIntraVecPD * (P + M)) +
            align256(sizeof(int2) * tiles_upper_bound(P)) + align256(4 * N1 * ldp_for(P));
 }
@@ -132,10 +135,11 @@ extern "C" int tga_eval_best_move_noalloc(const tga_instance *inst, const tga_so
     if (!inst || !sol || !out_dev) return TGA_ERR_INVALID;
     const long long n = inst->n_customers, m = inst->n_routes;
     if (n < 1 || m < 1 || inst->capacity < 0 || inst->w_load < 0 || inst->w_tw < 0) return TGA_ERR_INVALID;
-    if (op_mask == 0 || op_mask >= 64u) return TGA_ERR_INVALID;
+    if (op_mask == 0 || op_mask >= 256u) return TGA_ERR_INVALID;
     if (!inst->dist || !inst->demand || !sol->tour || !sol->route_start) return TGA_ERR_INVALID;
     if (inst->has_tw && (!inst->service || !inst->tw_early || !inst->tw_late)) return TGA_ERR_INVALID;
     if (inst->pickup && !inst->has_tw) return TGA_ERR_INVALID;
+    if (inst->pickup && (op_mask & kExtOps)) return TGA_ERR_INVALID;
     if (n + m + 1 > kNoAllocMaxPositions) return TGA_ERR_RANGE;
 
     Dev d{};

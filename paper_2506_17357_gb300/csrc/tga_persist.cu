@@ -172,6 +172,7 @@ int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int wa
                    int *grid_out) {
     const int nt = warps * 32 * rs;
     if (d.theta > 0) return TGA_ERR_STATE;                // edge-based extraction: per-step path only
+    if (d.op_mask & kExtOps) return TGA_ERR_STATE;        // swaps of runs: per-step path only
     if (ntiles <= 0 || (nt != 128 && nt != 256)) return TGA_ERR_INVALID;   // apply needs >= 3 warps
     const int nw = nt / 32;
     const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0, pd = d.has_pd != 0;

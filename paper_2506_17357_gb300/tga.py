@@ -190,8 +190,10 @@ def tga_get_stats(ctx: int) -> dict:
 
 
 def tga_get_op_candidates(ctx: int):
-    """Candidates evaluated per operator rank (6 ints) over all evaluations."""
-    out = (ctypes.c_int64 * 6)()
+    """Candidates evaluated per operator rank (8 ints: relocate, swap, 2-opt,
+    2-opt*, or-opt 2, or-opt 3, customer/run-of-two swap, run/run swap) over
+    all evaluations."""
+    out = (ctypes.c_int64 * 8)()
     _check(_lib().tga_get_op_candidates(_P(ctx), out), "tga_get_op_candidates")
     return [int(v) for v in out]
 

@@ -70,6 +70,14 @@ def test_create_rejects_bad_arguments_on_host(lib):
     inst = tga.tga_instance(10, 2, 10, 0, 100, 100, 1, 1, None, None, None)
     rc = tga._lib().tga_create(ctypes.byref(inst), ctypes.byref(sol), 0, None, ctypes.byref(out))
     assert rc == tga.TGA_ERR_INVALID      # empty operator mask
+    rc = tga._lib().tga_create(ctypes.byref(inst), ctypes.byref(sol), 256, None, ctypes.byref(out))
+    assert rc == tga.TGA_ERR_INVALID      # operator ranks beyond 7
+    inst = tga.tga_instance(10, 2, 10, 1, 100, 100, 1, 1, 1, 1, 1, 1)
+    rc = tga._lib().tga_create(ctypes.byref(inst), ctypes.byref(sol), 0xFF, None, ctypes.byref(out))
+    assert rc == tga.TGA_ERR_INVALID      # pickups with the swaps of runs
+    inst = tga.tga_instance(23170, 2, 10, 0, 100, 100, 1, 1, None, None, None)
+    rc = tga._lib().tga_create(ctypes.byref(inst), ctypes.byref(sol), 0xFF, None, ctypes.byref(out))
+    assert rc == tga.TGA_ERR_RANGE        # 8 W^2 >= 2^32 with ranks 6 and 7
     inst = tga.tga_instance(10, 2, 10, 0, 100, 100, 1, 1, None, None, None, 1)
     rc = tga._lib().tga_create(ctypes.byref(inst), ctypes.byref(sol), 0x3F, None, ctypes.byref(out))
     assert rc == tga.TGA_ERR_INVALID      # pickups without time windows

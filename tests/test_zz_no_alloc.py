@@ -34,7 +34,8 @@ def test_noalloc_equals_context_path_on_consecutive_calls():
     sol1 = I.random_split_solution(inst1, 8)
     inst3 = I.vrpspdtw(500, 9)                       # with pickups
     sol3 = I.random_split_solution(inst3, 10)
-    cases = [(inst2, sol2, I.MASK_CONFIG2), (inst1, sol1, I.MASK_CVRP_MIXED), (inst3, sol3, I.MASK_ALL)]
+    cases = [(inst2, sol2, I.MASK_CONFIG2), (inst1, sol1, I.MASK_CVRP_MIXED), (inst3, sol3, I.MASK_ALL),
+             (inst2, sol2, I.MASK_EXT)]                # with the swaps of runs
     for inst, sol, mask in cases:                    # two calls in a row, different data
         ls = T.LocalSearch(inst, sol, mask).build()
         try:
