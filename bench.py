@@ -83,11 +83,17 @@ def inter_candidates(n, lens, mask):
         out[4] = int((np.maximum(lens - 1, 0) * other).sum())
     if mask & 32:
         out[5] = int((np.maximum(lens - 2, 0) * other).sum())
+    runs = np.maximum(lens - 1, 0)              # runs of two per route
+    if mask & 64:                               # a run with a customer of another route
+        out[6] = int((runs * (n - lens)).sum())
+    if mask & 128:                              # two runs in different routes
+        out[7] = int((runs.sum() ** 2 - (runs * runs).sum()) // 2)
     return out
 
 
-def algorithmic_ops(n, lens, mask, table):
-    return sum(table[op] * c for op, c in inter_candidates(n, lens, mask).items())
+def algorithmic_ops(n, lens, mask, table, ops=range(6)):
+    """Integer operations of the inter-route candidates of ranks ``ops``."""
+    return sum(table[op] * c for op, c in inter_candidates(n, lens, mask).items() if op in ops)
 
 
 def descent_ops(op_candidates, table):
@@ -420,6 +426,8 @@ def bench_gpu(args):
         restore()
         T.tga_build_attrs(ls.ctx)
         total_ops = total_ms = 0.0
+        x_ops = x_ms = 0.0                      # swaps of runs (ranks 6, 7)
+        xs = bool(mask & 0xC0)
         probes = 5
         n_steps = steps[-1]
         for j in range(probes):
@@ -430,19 +438,28 @@ def bench_gpu(args):
                 tour_h, rs_h = ls.solution()
                 lens = np.diff(rs_h)
                 total_ops += algorithmic_ops(inst.n, lens, mask, ops_table(inst))
+                if xs:
+                    x_ms += T.tga_profile_xswap(ls.ctx, reps=20)
+                    x_ops += algorithmic_ops(inst.n, lens, mask, ops_table(inst), ops=(6, 7))
             total_ms += ms
             if j + 1 < probes:
                 T.tga_descend(ls.ctx, max_steps=max(1, n_steps // (probes - 1)))
         achieved = total_ops / (total_ms / 1e3)
         kname = "k_eval_edges" if args.granular else "k_eval_inter"
-        return {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops, "peak_source": peak_desc,
-                "ms_per_launch": total_ms / probes, "ops_per_launch": total_ops / probes,
-                "work": "inter-route candidates of the state (per-candidate integer ops x candidates), "
-                        "mean over 5 states along the trajectory",
-                "traffic": measured_traffic(workload_name(args) + (f"-granular{args.granular}" if args.granular else ""),
-                                            kname),
-                "kernel_source_hash": kernel_source_hash()}
+        out = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+               "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops, "peak_source": peak_desc,
+               "ms_per_launch": total_ms / probes, "ops_per_launch": total_ops / probes,
+               "work": "inter-route candidates of the state (per-candidate integer ops x candidates), "
+                       "mean over 5 states along the trajectory",
+               "traffic": measured_traffic(workload_name(args) + (f"-granular{args.granular}" if args.granular else ""),
+                                           kname),
+               "kernel_source_hash": kernel_source_hash()}
+        if xs:
+            xa = x_ops / (x_ms / 1e3)
+            out["xswap_kernel"] = {"kernel": "k_eval_xswap", "achieved": xa / 1e12, "frac": xa / peak_ops,
+                                   "ms_per_launch": x_ms / probes, "ops_per_launch": x_ops / probes,
+                                   "traffic": measured_traffic(workload_name(args), "k_eval_xswap")}
+        return out
 
     inter_roof = inter_kernel_roof()
     if persistent:

@@ -287,6 +287,10 @@ int tga_get_tile_shape(tga_ctx *ctx, int32_t *rows, int32_t *col_warps, int32_t 
  * report the kernel's roofline fraction. */
 int tga_profile_inter(tga_ctx *ctx, int32_t reps, float *ms_per_launch);
 
+/* The same for the inter-route kernel of the swaps of runs (op ranks 6, 7);
+ * TGA_ERR_STATE when the context's operator mask has neither rank. */
+int tga_profile_xswap(tga_ctx *ctx, int32_t reps, float *ms_per_launch);
+
 /* Best move of one instance + solution WITHOUT allocating any memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory (a host framework that owns every device

@@ -338,6 +338,39 @@ int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *t
 
 }  // namespace
 
+// Mean milliseconds per launch of one evaluation kernel on the current state
+// (`launch` issues it on the context's stream); leaves no pending key and the
+// context's done flag as it was.
+template <class F>
+static int profile_launches(tga_ctx *c, int32_t reps, float *ms_per_launch, F launch) {
+    Control C;
+    int rc = read_control(c, &C);
+    if (rc) return rc;
+    const int was_done = C.done;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TGA_ERR_CUDA;
+    // the kernels return immediately on a finished context: clear the flag
+    cudaMemsetAsync(&c->d.ctl->done, 0, sizeof(int), c->stream);
+    launch();                                                    // warm-up
+    cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < reps; ++k) launch();
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_launch = ms / reps;
+    cudaMemsetAsync(&c->d.ctl->best_key, 0xff, sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(&c->d.ctl->done, 0, sizeof(int), c->stream);
+    if (was_done) {
+        int one = 1;
+        cudaMemcpyAsync(&c->d.ctl->done, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+    }
+    return check_launch();
+}
+
 extern "C" {
 
 const char *tga_strerror(int code) {
@@ -754,32 +787,15 @@ int tga_profile_inter(tga_ctx *c, int32_t reps, float *ms_per_launch) {
     if (!c || reps < 1 || !ms_per_launch) return TGA_ERR_INVALID;
     if (!c->built) return TGA_ERR_STATE;
     if (!c->tiles && c->d.Wp > 2) default_tiles(c);
-    Control C;
-    int rc = read_control(c, &C);
-    if (rc) return rc;
-    const int was_done = C.done;
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TGA_ERR_CUDA;
-    // the kernel returns immediately on a finished context: clear the flag
-    cudaMemsetAsync(&c->d.ctl->done, 0, sizeof(int), c->stream);
-    launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);   // warm-up
-    cudaEventRecord(e0, c->stream);
-    for (int k = 0; k < reps; ++k) launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
-    cudaEventRecord(e1, c->stream);
-    cudaEventSynchronize(e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    *ms_per_launch = ms / reps;
-    cudaMemsetAsync(&c->d.ctl->best_key, 0xff, sizeof(unsigned long long), c->stream);
-    cudaMemsetAsync(&c->d.ctl->done, 0, sizeof(int), c->stream);
-    if (was_done) {
-        int one = 1;
-        cudaMemcpyAsync(&c->d.ctl->done, &one, sizeof(int), cudaMemcpyHostToDevice, c->stream);
-        cudaStreamSynchronize(c->stream);
-    }
-    return check_launch();
+    return profile_launches(c, reps, ms_per_launch, [&] {
+        launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
+    });
+}
+
+int tga_profile_xswap(tga_ctx *c, int32_t reps, float *ms_per_launch) {
+    if (!c || reps < 1 || !ms_per_launch) return TGA_ERR_INVALID;
+    if (!c->built || !(c->d.op_mask & kExtOps)) return TGA_ERR_STATE;
+    return profile_launches(c, reps, ms_per_launch, [&] { launch_xswap(c->d, c->stream); });
 }
 
 int tga_debug_read(tga_ctx *c, int32_t what, void *host_dst, size_t bytes, size_t *size_out) {

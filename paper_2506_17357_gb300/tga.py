@@ -88,6 +88,7 @@ EXPORTS = [
     ("tga_eval_best_move_noalloc", ctypes.c_int, [ctypes.POINTER(tga_instance), ctypes.POINTER(tga_solution),
                                                   ctypes.c_uint32, _P, _P]),
     ("tga_profile_inter", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
+    ("tga_profile_xswap", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     ("tga_set_descent_mode", ctypes.c_int, [_P, ctypes.c_int32]),
     ("tga_get_descent_mode", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("tga_get_persistent_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
@@ -229,6 +230,13 @@ def tga_profile_inter(ctx: int, reps: int = 10) -> float:
     """Mean milliseconds per launch of the inter-route evaluation kernel."""
     ms = ctypes.c_float()
     _check(_lib().tga_profile_inter(_P(ctx), reps, ctypes.byref(ms)), "tga_profile_inter")
+    return ms.value
+
+
+def tga_profile_xswap(ctx: int, reps: int = 10) -> float:
+    """Mean milliseconds per launch of the swaps-of-runs kernel (ranks 6, 7)."""
+    ms = ctypes.c_float()
+    _check(_lib().tga_profile_xswap(_P(ctx), reps, ctypes.byref(ms)), "tga_profile_xswap")
     return ms.value
 
 
