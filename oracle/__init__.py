@@ -15,9 +15,11 @@ Functions and the passages they follow:
   None) the load excess is that of the largest load on board
   (``route_peak_load``).
 * ``best_move(method="def")``: the plain definition -- every candidate of
-  relocate / swap / 2-opt / 2-opt* / or-opt (Section 4.1) is built by route
-  surgery and costed from scratch; the smallest (delta, move index) wins
-  (best improvement, Section 5.3.4, Eq. "min_obj").
+  relocate / swap / 2-opt / 2-opt* / or-opt (Section 4.1), and of the
+  optional swaps of runs (ranks 6, 7: Section 5.3.1 Swap with run lengths 1
+  and 2, or 2 and 2), is built by route surgery and costed from scratch; the
+  smallest (delta, move index) wins (best improvement, Section 5.3.4, Eq.
+  "min_obj").
 * ``best_move(method="concat")``: the paper's sequence concatenation
   (Sections 4.2-4.3): per-route attribute matrices and the concatenation
   operator; must agree exactly with "def".
