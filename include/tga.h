@@ -3,9 +3,12 @@
  *
  * One local-search step evaluates the whole neighbourhood of the current
  * solution -- relocate, swap, intra-route 2-opt, inter-route 2-opt* and
- * or-opt (runs of 2 and 3 customers) -- scores every candidate with an
- * exact integer O(1) delta of distance + w_load * capacity excess +
- * w_tw * time warp, reduces to the best move, and applies it on the device.
+ * or-opt (runs of 2 and 3 customers), optionally also the swaps of runs --
+ * scores every candidate with an exact integer O(1) delta of distance +
+ * w_load * capacity excess + w_tw * time warp, reduces to the best move, and
+ * applies it on the device.  The CVRP, the VRPTW and the VRPSPDTW (pickups
+ * and deliveries; the capacity excess of the largest load on board) are
+ * supported.
  * The method is the node-based tensorised move evaluation of the paper
  * (Section 5.3, "node-based extraction", Eqs. "node_based1"/"node_based2"),
  * built on sequence concatenation (Section 4.3) over an attribute-based
@@ -29,7 +32,10 @@
  *      3 2-opt*    (anchors, route(a) < route(b): exchange the tails after a, b)
  *      4 or-opt 2, 5 or-opt 3 (a = first customer of the run, b anchor
  *        outside the run, b != pred(a): move the run after b)
- *    and move index idx = op*W*W + a*W + b (requires 6*W*W < 2^32).
+ *      6 swap of a customer a with the run of two starting at b (optional)
+ *      7 swap of the runs of two starting at a < b (optional)
+ *    and move index idx = op*W*W + a*W + b (requires 6*W*W < 2^32, or
+ *    8*W*W < 2^32 with ranks 6 and 7).
  *  - The best move is the smallest (delta, idx); a move is accepted iff
  *    delta < 0.
  *  - All pointers in tga_instance / tga_solution are DEVICE pointers owned by
