@@ -244,9 +244,11 @@ int tga_descend_async(tga_ctx *ctx, int64_t max_steps);
  * finished, 0 while some is pending.  Never blocks. */
 int tga_query(tga_ctx *ctx, int32_t *done_out);
 
-/* Device bytes a context for n customers and m routes allocates (its
- * workspace only; the caller's instance and solution arrays come on top).
- * Host-only arithmetic, for admission control by memory budget. */
+/* Device bytes a context for n customers and m routes allocates at most (its
+ * workspace only; the caller's instance and solution arrays come on top):
+ * the layout with the pickup and swaps-of-runs records, which a context
+ * allocates only when it uses them.  Host-only arithmetic, for admission
+ * control by memory budget. */
 size_t tga_workspace_bytes(int32_t n_customers, int32_t n_routes);
 
 /* Wait for the context's stream and report the device status. */

@@ -49,6 +49,33 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? TGA_OK : TGA_ERR_CUDA; }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The context workspace: one allocation carved into 256-byte aligned pieces.
+// pd: the pickup records; xs: the swaps-of-runs records.  Returns the bytes.
+struct WsLayout {
+    size_t ctl, seq, pos, brec, erec, prec, xrec, rrec, seen, intra, saved, pcol;
+};
+size_t workspace_layout(size_t n, size_t m, bool pd, bool xs, WsLayout *o) {
+    const size_t W = n + 1 + m, Wp = n + m + 1;
+    const size_t ldp = align_up(Wp, kMaxTileCols) + 16;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes, 256); return at; };
+    WsLayout L;
+    L.ctl = take(sizeof(Control));
+    L.seq = take(sizeof(int) * Wp);
+    L.pos = take(sizeof(int) * (W + 1));
+    L.brec = take(sizeof(BRec) * (W + 1));
+    L.erec = take(sizeof(ERec) * (W + 1));
+    L.prec = take(pd ? sizeof(PRec) * (W + 1) : 0);
+    L.xrec = take(xs ? sizeof(XRec) * (W + 1) : 0);
+    L.rrec = take(sizeof(RouteRec) * m);
+    L.seen = take(sizeof(int) * (n + 1));
+    L.intra = take(sizeof(int) * kIntraVecPD * (Wp + m));
+    L.saved = take(sizeof(int) * (n + m + 1));
+    L.pcol = take(sizeof(int) * (n + 1) * ldp);
+    if (o) *o = L;
+    return off;
+}
+
 int check_launch() {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -428,40 +455,26 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.ldp = (int)(align_up((size_t)d.Wp, kMaxTileCols) + 16);
     d.log = nullptr; d.log_cap = 0;
 
-    // one workspace allocation, carved into 256-byte aligned pieces
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    const size_t o_ctl = take(sizeof(Control));
-    const size_t o_seq = take(sizeof(int) * (size_t)d.Wp);
-    const size_t o_pos = take(sizeof(int) * (size_t)(W + 1));
-    const size_t o_brec = take(sizeof(BRec) * (size_t)(W + 1));
-    const size_t o_erec = take(sizeof(ERec) * (size_t)(W + 1));
-    const size_t o_prec = take(d.has_pd ? sizeof(PRec) * (size_t)(W + 1) : 0);
-    const size_t o_xrec = take((op_mask & kExtOps) ? sizeof(XRec) * (size_t)(W + 1) : 0);
-    const size_t o_rrec = take(sizeof(RouteRec) * (size_t)m);
-    const size_t o_seen = take(sizeof(int) * (size_t)(n + 1));
-    const size_t o_intra = take(sizeof(int) * kIntraVecPD * (size_t)(d.Wp + m));
-    const size_t o_saved = take(sizeof(int) * (size_t)(n + m + 1));
-    const size_t o_pcol = take(sizeof(int) * (size_t)(n + 1) * (size_t)d.ldp);
-    c->ws_bytes = off;
+    WsLayout L;
+    c->ws_bytes = workspace_layout((size_t)n, (size_t)m, d.has_pd != 0, (op_mask & kExtOps) != 0, &L);
     if (cudaMallocAsync(&c->ws, c->ws_bytes, c->stream) != cudaSuccess) {
         cudaGetLastError();
         tga_destroy(c);
         return TGA_ERR_NOMEM;
     }
     char *base = (char *)c->ws;
-    d.ctl = (Control *)(base + o_ctl);
-    d.seq = (int *)(base + o_seq);
-    d.pos_of = (int *)(base + o_pos);
-    d.brec = (BRec *)(base + o_brec);
-    d.erec = (ERec *)(base + o_erec);
-    d.prec = d.has_pd ? (PRec *)(base + o_prec) : nullptr;
-    d.xrec = (op_mask & kExtOps) ? (XRec *)(base + o_xrec) : nullptr;
-    d.rrec = (RouteRec *)(base + o_rrec);
-    d.seen = (int *)(base + o_seen);
-    d.scr_intra = (int *)(base + o_intra);
-    d.pcol = (int *)(base + o_pcol);
-    c->saved = (int *)(base + o_saved);
+    d.ctl = (Control *)(base + L.ctl);
+    d.seq = (int *)(base + L.seq);
+    d.pos_of = (int *)(base + L.pos);
+    d.brec = (BRec *)(base + L.brec);
+    d.erec = (ERec *)(base + L.erec);
+    d.prec = d.has_pd ? (PRec *)(base + L.prec) : nullptr;
+    d.xrec = (op_mask & kExtOps) ? (XRec *)(base + L.xrec) : nullptr;
+    d.rrec = (RouteRec *)(base + L.rrec);
+    d.seen = (int *)(base + L.seen);
+    d.scr_intra = (int *)(base + L.intra);
+    d.pcol = (int *)(base + L.pcol);
+    c->saved = (int *)(base + L.saved);
     if (cudaMemsetAsync(d.ctl, 0, sizeof(Control), c->stream) != cudaSuccess ||
         setup_kernel_attrs(d.Wp) != 0) {
         tga_destroy(c);
@@ -587,14 +600,8 @@ int tga_query(tga_ctx *c, int32_t *done_out) {
 
 size_t tga_workspace_bytes(int32_t n_customers, int32_t n_routes) {
     if (n_customers < 1 || n_routes < 1) return 0;
-    const size_t n = (size_t)n_customers, m = (size_t)n_routes, W = n + 1 + m, Wp = n + m + 1;
-    const size_t ldp = align_up(Wp, kMaxTileCols) + 16;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { off = align_up(off + bytes, 256); };
-    take(sizeof(Control)); take(4 * Wp); take(4 * (W + 1)); take(sizeof(BRec) * (W + 1));
-    take(sizeof(ERec) * (W + 1)); take(sizeof(RouteRec) * m);
-    take(4 * (n + 1)); take(4 * 10 * (Wp + m)); take(4 * (n + m + 1)); take(4 * (n + 1) * ldp);
-    return off;
+    // the largest layout (pickup and swaps-of-runs records included): an upper bound
+    return workspace_layout((size_t)n_customers, (size_t)n_routes, true, true, nullptr);
 }
 
 int tga_sync(tga_ctx *c) {
