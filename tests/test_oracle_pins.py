@@ -87,6 +87,25 @@ def test_generator_is_deterministic():
     assert a.capacity == -(-int(a.demand.sum()) // 8)
 
 
+def test_pickup_generator_and_split_rule():
+    """The VRPSPDTW recipe is the VRPTW one of the same seed plus pickups in
+    [1, 50]; the initial split keeps every route's total delivery and total
+    pickup within the capacity and opens a route only when the next customer
+    would break one of them."""
+    a, b, v = I.vrpspdtw(300, 9), I.vrpspdtw(300, 9), I.vrptw(300, 9)
+    assert (a.pickup == b.pickup).all() and (a.dist == v.dist).all() and (a.demand == v.demand).all()
+    assert a.pickup[0] == 0 and a.pickup[1:].min() >= 1 and a.pickup[1:].max() <= 50
+    sol = I.random_split_solution(a, 10)
+    routes = sol.routes()
+    for k, r in enumerate(routes):
+        sd = sum(int(a.demand[x]) for x in r)
+        sp = sum(int(a.pickup[x]) for x in r)
+        assert sd <= a.capacity and sp <= a.capacity
+        if k + 1 < len(routes):
+            nx = routes[k + 1][0]
+            assert sd + a.demand[nx] > a.capacity or sp + a.pickup[nx] > a.capacity
+
+
 # ----------------------------------------------------------------------------
 def test_hand_cvrp_swap():
     g = _golden("hand_cvrp_swap.json")
