@@ -23,6 +23,9 @@ Functions and the passages they follow:
 * ``best_move(method="concat")``: the paper's sequence concatenation
   (Sections 4.2-4.3): per-route attribute matrices and the concatenation
   operator; must agree exactly with "def".
+* ``best_move_slice``: ``best_move`` over one of several interleaved
+  slices of the same candidate set (the harness spreads one evaluation over
+  host processes with it; the arithmetic is unchanged).
 * ``descend``: the feasible/infeasible search loop of the appendix algorithm
   with best improvement: accept iff delta < 0, stop at a local optimum.
 * ``granular=nbr`` (every evaluating function): the edge-based extraction of
@@ -93,6 +96,10 @@ def _load():
         lib.orc_best_move.restype = ctypes.c_int
         lib.orc_best_move.argtypes = [ctypes.POINTER(_Inst), P, P, ctypes.c_uint32, ctypes.c_int,
                                       ctypes.POINTER(_Move), ctypes.POINTER(ctypes.c_int64)]
+        lib.orc_best_move_slice.restype = ctypes.c_int
+        lib.orc_best_move_slice.argtypes = [ctypes.POINTER(_Inst), P, P, ctypes.c_uint32, ctypes.c_int,
+                                            ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_Move),
+                                            ctypes.POINTER(ctypes.c_int64)]
         lib.orc_list_moves.restype = ctypes.c_int64
         lib.orc_list_moves.argtypes = [ctypes.POINTER(_Inst), P, P, ctypes.c_uint32, ctypes.c_int,
                                        P, P, ctypes.c_int64]
@@ -194,6 +201,21 @@ def best_move(inst, sol, op_mask: int, method: str = "def", granular=None):
     nc = ctypes.c_int64(0)
     _load().orc_best_move(oi.ref(), t.ctypes.data, rs.ctypes.data, op_mask, METHODS[method],
                           ctypes.byref(mv), ctypes.byref(nc))
+    return _move_dict(mv, nc.value)
+
+
+def best_move_slice(inst, sol, op_mask: int, phase: int, stride: int, method: str = "concat", granular=None):
+    """best_move over the slice `phase` of `stride` interleaved slices of
+    the candidate set (split by the outermost enumeration index); the
+    smallest key over all slices is best_move's."""
+    oi = _oi(inst, sol, granular)
+    t, rs = _c32(sol.tour), _c32(sol.route_start)
+    mv = _Move()
+    nc = ctypes.c_int64(0)
+    rc = _load().orc_best_move_slice(oi.ref(), t.ctypes.data, rs.ctypes.data, op_mask, METHODS[method],
+                                     int(phase), int(stride), ctypes.byref(mv), ctypes.byref(nc))
+    if rc != 0:
+        raise ValueError(f"bad slice {phase} of {stride}")
     return _move_dict(mv, nc.value)
 
 

@@ -491,7 +491,15 @@ typedef struct {
     /* listing */
     uint64_t *idx_out; int64_t *delta_out; int64_t cap;
     int count_only;
+    /* slice: visit only the candidates whose outermost enumeration index
+     * (u, a, b, route r or route A, per operator) is phase mod stride */
+    int32_t stride, phase;
 } scan_t;
+
+static int in_slice(const scan_t *s, int32_t outer)
+{
+    return s->stride <= 1 || outer % s->stride == s->phase;
+}
 
 /* Granular mask of the edge-based extraction (see tga_oracle.h). */
 static int in_mask(const orc_inst *in, int32_t x, int32_t y)
@@ -543,6 +551,7 @@ static void scan_all(scan_t *s, uint32_t mask)
         if (op == 0 || op == 4 || op == 5) {
             int32_t k = (op == 0) ? 1 : op - 2;
             for (int32_t u = 1; u <= n; ++u) {
+                if (!in_slice(s, u)) continue;
                 int32_t A = v->route_of[u], i = v->idx_of[u];
                 if (i + k > rlen(v, A)) continue;
                 const int32_t *ra = rnodes(v, A);
@@ -556,13 +565,16 @@ static void scan_all(scan_t *s, uint32_t mask)
                 }
             }
         } else if (op == 1) {
-            for (int32_t a = 1; a <= n; ++a)
+            for (int32_t a = 1; a <= n; ++a) {
+                if (!in_slice(s, a)) continue;
                 for (int32_t b = a + 1; b <= n; ++b) visit(s, 1, a, b);
+            }
         } else if (op == 6 || op == 7) {
             /* b starts a run of 2; a is a single customer (op 6) or starts a
              * run of 2 with a < b (op 7); the runs must not overlap */
             const int32_t k1 = (op == 6) ? 1 : 2;
             for (int32_t b = 1; b <= n; ++b) {
+                if (!in_slice(s, b)) continue;
                 int32_t B = v->route_of[b], j = v->idx_of[b];
                 if (j + 2 > rlen(v, B)) continue;
                 for (int32_t a = 1; a <= n; ++a) {
@@ -575,6 +587,7 @@ static void scan_all(scan_t *s, uint32_t mask)
             }
         } else if (op == 2) {
             for (int32_t r = 0; r < m; ++r) {
+                if (!in_slice(s, r)) continue;
                 const int32_t *rr = rnodes(v, r);
                 int32_t L = rlen(v, r);
                 for (int32_t i = 0; i < L; ++i)
@@ -582,7 +595,7 @@ static void scan_all(scan_t *s, uint32_t mask)
             }
         } else {   /* op 3 */
             for (int32_t A = 0; A < m; ++A)
-                for (int32_t B = A + 1; B < m; ++B) {
+                for (int32_t B = A + 1; B < m && in_slice(s, A); ++B) {
                     const int32_t *ra = rnodes(v, A), *rb = rnodes(v, B);
                     for (int32_t i = -1; i < rlen(v, A); ++i) {
                         int32_t a = (i < 0) ? n + 1 + A : ra[i];
@@ -616,6 +629,34 @@ int orc_best_move(const orc_inst *in, const int32_t *tour, const int32_t *rs, ui
     view_init(&v, in, tour, rs);
     memset(&s, 0, sizeof(s));
     s.in = in; s.v = &v; s.method = method;
+    s.mv.buf[0] = (int32_t *)malloc((size_t)(in->n + 3) * sizeof(int32_t));
+    s.mv.buf[1] = (int32_t *)malloc((size_t)(in->n + 3) * sizeof(int32_t));
+    if (method == ORC_CONCAT) {
+        s.am = (amat_t *)calloc((size_t)in->m, sizeof(amat_t));
+        for (int32_t r = 0; r < in->m; ++r)
+            amat_build(in, &s.am[r], tour + rs[r], rs[r + 1] - rs[r], (mask >> 2) & 1);
+    }
+    scan_all(&s, mask);
+    out->found = s.found;
+    out->delta = s.best_delta; out->idx = s.best_idx;
+    out->op = s.bop; out->a = s.ba; out->b = s.bb;
+    if (n_cands) *n_cands = s.count;
+    if (s.am) { for (int32_t r = 0; r < in->m; ++r) amat_free(&s.am[r]); free(s.am); }
+    free(s.mv.buf[0]); free(s.mv.buf[1]);
+    view_free(&v);
+    return 0;
+}
+
+int orc_best_move_slice(const orc_inst *in, const int32_t *tour, const int32_t *rs, uint32_t mask,
+                        int method, int32_t phase, int32_t stride, orc_move *out, int64_t *n_cands)
+{
+    if (stride < 1 || phase < 0 || phase >= stride) return -1;
+    scan_t s;
+    view_t v;
+    view_init(&v, in, tour, rs);
+    memset(&s, 0, sizeof(s));
+    s.in = in; s.v = &v; s.method = method;
+    s.stride = stride; s.phase = phase;
     s.mv.buf[0] = (int32_t *)malloc((size_t)(in->n + 3) * sizeof(int32_t));
     s.mv.buf[1] = (int32_t *)malloc((size_t)(in->n + 3) * sizeof(int32_t));
     if (method == ORC_CONCAT) {

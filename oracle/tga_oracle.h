@@ -74,6 +74,17 @@ int64_t orc_count_candidates(const orc_inst *in, const int32_t *tour,
                              const int32_t *route_start, uint32_t op_mask);
 int     orc_best_move(const orc_inst *in, const int32_t *tour, const int32_t *route_start,
                       uint32_t op_mask, int method, orc_move *out, int64_t *n_cands);
+/* The same over one slice of the candidate set: only the candidates whose
+ * outermost enumeration index -- the moved customer (relocate, or-opt), the
+ * first customer a (swap), the run's first b (ranks 6, 7), the route
+ * (2-opt) or the first route A (2-opt*) -- is phase modulo stride
+ * (0 <= phase < stride; else -1).  The stride slices partition the set, so
+ * the smallest (delta, idx) over all of them is orc_best_move's and their
+ * counts add up to its count.  Used to spread one evaluation over several
+ * processes (the CPU baseline on all host cores). */
+int     orc_best_move_slice(const orc_inst *in, const int32_t *tour, const int32_t *route_start,
+                            uint32_t op_mask, int method, int32_t phase, int32_t stride,
+                            orc_move *out, int64_t *n_cands);
 int64_t orc_list_moves(const orc_inst *in, const int32_t *tour, const int32_t *route_start,
                        uint32_t op_mask, int method, uint64_t *idx_out, int64_t *delta_out,
                        int64_t cap);

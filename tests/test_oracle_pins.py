@@ -483,3 +483,39 @@ def test_granular_descent_definition_equals_concatenation():
     assert (f1.tour == f2.tour).all() and O.check_solution(inst, f1) == 0
     # the restricted descent stops at a local optimum of the restricted set
     assert O.best_move(inst, f1, I.MASK_ALL, "def", granular=nbr)["delta"] >= 0
+
+
+@pytest.mark.parametrize("kind,mask", [("cvrp", I.MASK_CONFIG3), ("vrptw", I.MASK_ALL), ("cvrp", I.MASK_EXT),
+                                       ("vrpspdtw", I.MASK_ALL)])
+@pytest.mark.parametrize("stride", [1, 3, 7])
+def test_slices_partition_the_candidate_set(kind, mask, stride):
+    """The interleaved slices the harness spreads over host processes: their
+    counts add up to the full count, the smallest key among them is the full
+    evaluation's best move, and each slice's best is the smallest key of its
+    own candidates in the full listing (so no slice visits a candidate twice
+    or misses one)."""
+    inst, sol = _tiny(kind, 14, 5 + stride)
+    full = O.best_move(inst, sol, mask, "concat")
+    idx, delta = O.list_moves(inst, sol, mask, "concat")
+    keys = {int(i): O.pack_key(int(d), int(i)) for i, d in zip(idx, delta)}
+    parts = [O.best_move_slice(inst, sol, mask, ph, stride) for ph in range(stride)]
+    assert sum(p["candidates"] for p in parts) == full["candidates"] == len(idx)
+    assert min(p["key"] for p in parts) == full["key"]
+    # the slice rule restated: the outermost index of (op, a, b)
+    n, routes = inst.n, sol.routes()
+    W = n + 1 + len(routes)
+    route_of = {x: r for r, nodes in enumerate(routes) for x in nodes}
+    route_of.update({n + 1 + r: r for r in range(len(routes))})
+
+    def outer(i):
+        op, a, b = i // (W * W), (i % (W * W)) // W, i % W
+        if op in (2, 3):
+            return route_of[a]
+        return b if op in (6, 7) else a
+
+    for ph, p in enumerate(parts):
+        mine = [k for i, k in keys.items() if outer(i) % stride == ph]
+        assert p["candidates"] == len(mine)
+        assert p["key"] == (min(mine) if mine else O.NO_MOVE_KEY)
+    with pytest.raises(ValueError):
+        O.best_move_slice(inst, sol, mask, stride, stride)
