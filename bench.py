@@ -5,7 +5,16 @@ build the attribute representation from the initial solution, then evaluate
 the full neighbourhood (relocate, swap, 2-opt, 2-opt*, or-opt), apply the best
 move on the device, and repeat until no move improves (a local optimum).
 
-Default workload: VRPTW, 1 depot + 1000 customers (all five operators).
+Default run (no --workload): the headline is the largest single-GPU
+workload, clustered CVRP with 1 depot + 10000 customers (relocate, swap,
+2-opt*, or-opt; the distance matrix, 400 MB, exceeds L2), timed for --steps
+descents after --warmup untimed ones.  The same JSON line carries, under
+"configs", the other workloads measured in the same process: CVRP-100,
+VRPTW-1000 (moves/s, time to the local optimum, roofline), the batched
+launch of 256 jobs (jobs/s against 256 sequential descents) and the
+continuous-batching server (jobs/s and p50/p99 latency against one job at a
+time).
+
 metric = candidate moves evaluated per second over the whole descent; the
 line also carries time-to-local-optimum.  Inputs are device resident when the
 timed region starts; L2 (129 MB) is flushed between timed steps by writing a
@@ -13,17 +22,26 @@ timed region starts; L2 (129 MB) is flushed between timed steps by writing a
 with host arrays: pinned H2D copies of the instance and solution, build,
 descent, and a D2H read of the final tour, route boundaries and counters.
 
-``--impl reference`` times the CPU oracle (test infrastructure) on the host
-cores on a bounded sample of the same workload.
+Roofline: the evaluation path is integer arithmetic (no dense contraction),
+so its ceilings are the measured 32-bit integer issue rate of the GPU
+(tga_measure_int_peak: a dependency-free add/max stream over every SM) and
+the algorithmic bytes over the measured HBM bandwidth.
 
-Multi-GPU (torchrun): every rank runs an independent replica on its own
-instance seed (replicas only; the path is not sharded); value is the sum of
-all ranks' candidates over the slowest rank's time.
+``cpu_baseline``: the CPU oracle (test infrastructure) on the host cores --
+one core, and every core of the process's affinity set, where a pool of
+processes splits the same evaluations into interleaved slices and the
+smallest key is reduced exactly.  ``--impl reference`` times the oracle the
+same way (all cores) on the headline workload.
+
+Multi-GPU (torchrun): every rank runs an independent replica of the headline
+on its own instance seed (replicas only; the path is not sharded); value is
+the sum of all ranks' candidates over the slowest rank's time.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -45,6 +63,7 @@ WORKLOADS = {
     "vrpspdtw1000": ("VRPSPDTW 1 depot + 1000 customers with pickups and deliveries, all five operators",
                      I.config_spd, I.MASK_ALL),
 }
+HEADLINE = "cvrp10000"
 
 # Integer operations per inter-route candidate, counted from the delta
 # expressions (adds/subs, min/max, multiplies, plus one compare for the
@@ -58,6 +77,11 @@ WORKLOADS = {
 OPS_CVRP = {0: 8, 1: 13, 2: 6, 3: 13, 4: 8, 5: 8, 6: 15, 7: 15}
 OPS_TW = {0: 20, 1: 36, 2: 22, 3: 22, 4: 20, 5: 20, 6: 39, 7: 39}
 OPS_PD = {0: 25, 1: 44, 2: 36, 3: 26, 4: 25, 5: 25, 6: 0, 7: 0}      # ranks 6, 7 have no pickup variant
+
+# Algorithmic bytes of one evaluation: every distance entry c(x, y) is
+# needed by some candidate (relocate / swap pairs), 4 B each, plus the
+# per-anchor records read once (64 B base + 128 B hoisted constants).
+REC_BYTES_PER_ANCHOR = 192
 
 
 def ops_table(inst):
@@ -102,6 +126,11 @@ def descent_ops(op_candidates, table):
     return sum(table[op] * c for op, c in enumerate(op_candidates))
 
 
+def evaluation_bytes(n, m):
+    """Algorithmic bytes of one neighbourhood evaluation."""
+    return 4 * (n + 1) ** 2 + REC_BYTES_PER_ANCHOR * (n + 1 + m)
+
+
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
@@ -134,6 +163,13 @@ def load_peaks():
             return json.load(f), "measured"
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 class ClockSampler:
@@ -214,12 +250,29 @@ def dist_env():
     return ws, rank, local
 
 
+OP_NAMES = ["relocate", "swap", "2-opt", "2-opt*", "or-opt-2", "or-opt-3", "swap-1-2", "swap-2-2"]
+
+
+def workload(args, name=None):
+    """(description, generator, operator mask) of the chosen workload;
+    --extended-swaps adds ranks 6 and 7 (swaps of runs) to its mask."""
+    desc, make, mask = WORKLOADS[name or args.workload]
+    if getattr(args, "extended_swaps", False):
+        desc, mask = desc + ", plus the swaps of runs (ranks 6, 7)", mask | I.MASK_EXT
+    return desc, make, mask
+
+
+def workload_name(args, name=None):
+    return (name or args.workload) + ("-xswap" if getattr(args, "extended_swaps", False) else "")
+
+
 def only_descent(args):
     """One build + descent of the workload and nothing else (no timing): the
     command profilers run to list the per-step kernel launches."""
     import torch
     from paper_2506_17357_gb300 import tga as T
-    desc, make, mask = workload(args)
+    wl = HEADLINE if args.workload == "all" else args.workload
+    desc, make, mask = workload(args, wl)
     inst, sol = make(args.seed)
     nbr = I.granular_neighbors(inst, args.granular) if args.granular else None
     ls = T.LocalSearch(inst, sol, mask, granular=nbr).build()
@@ -229,35 +282,176 @@ def only_descent(args):
         tile = ls.set_tile(0, 0)                                   # autotune, as the timed bench does
     st = ls.descend(max_steps=args.descent_steps) if args.descent_steps else ls.descend()
     torch.cuda.synchronize()
-    print(json.dumps({"workload": workload_name(args), "tile": list(tile), "steps": st["steps"],
+    print(json.dumps({"workload": workload_name(args, wl), "tile": list(tile), "steps": st["steps"],
                       "evaluations": st["evaluations"],
                       "final_cost": st["final_cost"], "status": st["status"]}))
     ls.close()
 
 
-OP_NAMES = ["relocate", "swap", "2-opt", "2-opt*", "or-opt-2", "or-opt-3", "swap-1-2", "swap-2-2"]
+# ---------------------------------------------------------------------------
+# peaks
+
+def measure_int_peak(dev_index=0):
+    """Measured 32-bit integer rate of the GPU (tga_measure_int_peak) with the
+    SM clock sampled during the measurement; the nominal issue rate from the
+    device's SM count and clock is kept as a cross-check."""
+    import torch
+    from paper_2506_17357_gb300 import tga as T
+    props = torch.cuda.get_device_properties(dev_index)
+    nsm = int(props.multi_processor_count)
+    s = torch.cuda.Stream()
+    T.tga_measure_int_peak(0, s.cuda_stream, 64)              # load the code, ramp the clocks
+    with ClockSampler(dev_index) as clk:
+        add_max, ms0 = T.tga_measure_int_peak(0, s.cuda_stream, 4000)
+        add3, ms1 = T.tga_measure_int_peak(1, s.cuda_stream, 4000)
+        add_max2, _ = T.tga_measure_int_peak(0, s.cuda_stream, 4000)
+    clocks = clk.summary()
+    add_max = max(add_max, add_max2)
+    peaks, _ = load_peaks()
+    sm_max = float(clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0))
+    nominal = nsm * 4 * 32 * sm_max * 1e6
+    return {"ops_per_s": add_max, "kernel": "tga_measure_int_peak kind 0 (x = max(x + a, b), 8 independent "
+                                            "chains per thread, every SM)",
+            "add_max_ops_per_s": add_max, "add3_ops_per_s": add3, "ms": [ms0, ms1],
+            "nominal_issue_ops_per_s": nominal, "measured_over_nominal": add_max / nominal,
+            "sm_count": nsm, "clocks": clocks}
 
 
-def workload(args):
-    """(description, generator, operator mask) of the chosen workload;
-    --extended-swaps adds ranks 6 and 7 (swaps of runs) to its mask."""
-    desc, make, mask = WORKLOADS[args.workload]
-    if getattr(args, "extended_swaps", False):
-        desc, mask = desc + ", plus the swaps of runs (ranks 6, 7)", mask | I.MASK_EXT
-    return desc, make, mask
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle on one core and on all cores
+
+_W = {}
 
 
-def workload_name(args):
-    return args.workload + ("-xswap" if getattr(args, "extended_swaps", False) else "")
+def _cpu_worker_init(wl_name, seed, mask, states, granular):
+    import oracle as O
+    _, make, _ = WORKLOADS[wl_name]
+    inst, _ = make(seed)
+    _W.update(O=O, inst=inst, mask=mask, states=states,
+              nbr=I.granular_neighbors(inst, granular) if granular else None)
 
 
-def breakdown(inst, sol, mask, dev, stream, reps=20, step_count=200):
+def _cpu_worker_task(units):
+    """units: [(state index, phase, stride)]; returns (min key, candidates,
+    start, end) with host wall-clock times."""
+    O, inst, mask, states, nbr = _W["O"], _W["inst"], _W["mask"], _W["states"], _W["nbr"]
+    t0 = time.time()
+    best, cands = O.NO_MOVE_KEY, 0
+    for si, ph, st in units:
+        tour, rs = states[si]
+        r = O.best_move_slice(inst, I.Solution(tour, rs), mask, ph, st, "concat", granular=nbr)
+        best = min(best, r["key"])
+        cands += r["candidates"]
+    return best, cands, t0, time.time()
+
+
+def cpu_baseline(args, wl_name, seconds=15.0, all_core_target_s=5.0, per_op_seconds=1.0, pool_cores=None):
+    """The oracle's concatenation evaluator (plain single-threaded C) on the
+    host: best-improvement steps of the workload from its initial solution.
+    One core: evaluations along the trajectory (each split into slices when
+    one evaluation is long), as many as fit in ``seconds``.  All cores: the
+    same slices (repeated to fill about ``all_core_target_s`` seconds of wall
+    time) spread over a spawn pool of one process per core; the rate is the
+    candidates over the wall time from the first slice's start to the last
+    one's end."""
+    import multiprocessing as mp
+    import oracle as O
+    desc, make, mask = workload(args, wl_name)
+    inst, sol = make(args.seed)
+    theta = getattr(args, "granular", 0)
+    nbr = I.granular_neighbors(inst, theta) if theta else None
+    est = O.count_candidates(inst, sol, mask, granular=nbr) / 1e7      # rough seconds per evaluation
+    stride = max(1, int(math.ceil(est / 0.5)))
+    # ---- one core
+    states, units, unit_s = [(np.asarray(sol.tour, np.int32), np.asarray(sol.route_start, np.int32))], [], []
+    cur, si = sol, 0
+    cands, evals = 0, 0
+    t0 = time.perf_counter()
+    done = False
+    while not done:
+        best = None
+        for ph in range(stride):
+            t1 = time.perf_counter()
+            r = O.best_move_slice(inst, cur, mask, ph, stride, "concat", granular=nbr)
+            unit_s.append(time.perf_counter() - t1)
+            units.append((si, ph, stride))
+            cands += r["candidates"]
+            if r["found"] and (best is None or r["key"] < best["key"]):
+                best = r
+            if time.perf_counter() - t0 >= seconds:
+                done = True
+                break
+        if done:
+            break
+        evals += 1
+        if best is None or best["delta"] >= 0:                 # local optimum: start the trajectory over
+            cur = sol
+            si = 0
+        else:
+            cur = O.apply_move(inst, cur, best["op"], best["a"], best["b"])
+            states.append((np.asarray(cur.tour, np.int32), np.asarray(cur.route_start, np.int32)))
+            si = len(states) - 1
+    dt1 = time.perf_counter() - t0
+    single = cands / dt1
+    sample1 = (f"{len(units)} slices of 1/{stride} evaluation" if stride > 1 else f"{len(units)} evaluations") + \
+        f" along the trajectory of {workload_name(args, wl_name)} seed {args.seed}, {dt1:.1f} s"
+    # ---- all cores
+    K = pool_cores or host_cores()
+    reps = max(1, int(round(K * all_core_target_s / max(dt1, 1e-3))))
+    work = [(u, t) for _ in range(reps) for u, t in zip(units, unit_s)]
+    tasks, cur_task, acc = [], [], 0.0
+    for u, t in work:                                          # chunks of about 0.25 s of one core
+        cur_task.append(u)
+        acc += t
+        if acc >= 0.25:
+            tasks.append(cur_task)
+            cur_task, acc = [], 0.0
+    if cur_task:
+        tasks.append(cur_task)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(K, initializer=_cpu_worker_init,
+                  initargs=(wl_name, args.seed, mask, states, theta)) as pool:
+        pool.map(time.sleep, [0.05] * K)                       # every worker has started
+        res = pool.map(_cpu_worker_task, tasks, chunksize=1)
+    start = min(r[2] for r in res)
+    end = max(r[3] for r in res)
+    all_cands = sum(r[1] for r in res)
+    allv = all_cands / (end - start)
+    # per operator: the oracle's evaluation of the initial solution with only
+    # that operator enabled (about a second each; long evaluations in slices)
+    per_op = {}
+    for op in range(8):
+        if not (mask >> op) & 1 or per_op_seconds <= 0:
+            continue
+        t1 = time.perf_counter()
+        reps1 = c1 = 0
+        while time.perf_counter() - t1 < per_op_seconds:
+            c1 += O.best_move_slice(inst, sol, 1 << op, reps1 % stride, stride, "concat",
+                                    granular=nbr)["candidates"]
+            reps1 += 1
+        d1 = time.perf_counter() - t1
+        per_op[OP_NAMES[op]] = {"ms_per_evaluation": 1e3 * d1 / reps1 * stride, "candidates_per_s": c1 / d1}
+    return {"value": allv, "unit": "candidate moves/s", "cores": K, "kind": "oracle",
+            "cores_used": K, "host_cores": host_cores(), "os_cpu_count": os.cpu_count(),
+            "single_core": single, "all_cores": allv,
+            "sample": f"one core: {sample1}; all {K} cores: the same slices x{reps} in {len(tasks)} tasks of a "
+                      f"spawn pool, {end - start:.1f} s wall (concatenation evaluator"
+                      f"{', granular mask theta=%d' % theta if theta else ''})",
+            "per_operator": per_op}
+
+
+# ---------------------------------------------------------------------------
+# single-instance workloads
+
+def breakdown(inst, sol, mask, dev, stream, reps=200, step_count=200):
     """Per-operator and per-step GPU times of the workload, outside the timed
     region (the paper's per-operator and key-step analyses, Sections 6.6 and
     6.7).  Per operator: one neighbourhood evaluation with only that operator
-    enabled (tga_eval_best_move, per-step kernels, autotuned inter tile) on the
-    initial solution.  Per step: evaluation and update times of the first
-    steps of the descent through tga_eval_best_move / tga_apply_move."""
+    enabled (tga_eval_best_move: its kernels, autotuned inter tile) on the
+    initial solution, `reps` evaluations captured in one CUDA graph and
+    replayed, so the figure is the device time of the operator's kernels
+    without host launch gaps.  Per step: evaluation and update times of the
+    first steps of the descent through tga_eval_best_move / tga_apply_move."""
     import torch
     from paper_2506_17357_gb300 import tga as T
     e0 = torch.cuda.Event(enable_timing=True)
@@ -272,16 +466,28 @@ def breakdown(inst, sol, mask, dev, stream, reps=20, step_count=200):
         ls.set_tile(0, 0)
         T.tga_eval_best_move(ls.ctx, ls.move.data_ptr())
         torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(reps):
-            T.tga_eval_best_move(ls.ctx, ls.move.data_ptr())
-        e1.record(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(reps):
+                T.tga_eval_best_move(ls.ctx, ls.move.data_ptr())
+        # a replay is launched on the current stream: make it the context's
+        # stream, so the events bracket it and the context outlives it
+        with torch.cuda.stream(stream):
+            g.replay()                                          # warm
+            torch.cuda.synchronize()
+            st0 = ls.stats()
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
         e1.synchronize()
+        torch.cuda.synchronize()
         us = 1e3 * e0.elapsed_time(e1) / reps
         st = ls.stats()
-        cands = st["candidates"] / max(1, st["evaluations"])
+        cands = (st["candidates"] - st0["candidates"]) / max(1, st["evaluations"] - st0["evaluations"])
         per_op[OP_NAMES[op]] = {"us_per_evaluation": us, "candidates": int(cands),
                                 "candidates_per_s": cands / (us * 1e-6)}
+        del g
+        torch.cuda.synchronize()
         ls.close()
     ls = T.LocalSearch(inst, sol, mask, device=dev, stream=stream).build()
     ls.set_descent_mode(T.DESCENT_GRAPH)
@@ -301,23 +507,24 @@ def breakdown(inst, sol, mask, dev, stream, reps=20, step_count=200):
             break
     ls.close()
     return {"per_operator": per_op,
+            "per_operator_path": f"{reps} evaluations of the operator alone captured in one CUDA graph "
+                                 "(begin + inter + intra + finalize kernels each), replayed",
             "per_step": {"steps": len(ev), "evaluation_us_median": float(np.median(ev)),
                          "update_us_median": float(np.median(up)),
                          "path": "per-step kernels launched one call at a time (eval: begin + inter + intra + "
                                  "finalize; update: apply of the caller-given move + write-back)"}}
 
 
-def bench_gpu(args):
+def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown=True, cpu=None):
+    """Time `steps` whole descents of one workload (after `warmup` untimed
+    ones); returns the record (the JSON line's body for the headline)."""
     import torch
     import torch.distributed as dist
     from paper_2506_17357_gb300 import tga as T
 
     ws, rank, local = dist_env()
-    if ws > 1:
-        dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    desc, make, mask = workload(args)
+    desc, make, mask = workload(args, wl_name)
     seed = replica_seed(args.seed, rank)
     inst, sol = make(seed)
     nbr = I.granular_neighbors(inst, args.granular) if args.granular else None
@@ -341,19 +548,18 @@ def bench_gpu(args):
         T.tga_build_attrs(ls.ctx)
         return T.tga_descend(ls.ctx)
 
-    # warm-up (untimed)
-    for _ in range(args.warmup):
+    for _ in range(warmup):                                    # untimed
         restore()
         one_step()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
-    times, cands, steps, stats = [], 0, [], None
+    times, cands, nsteps, stats = [], 0, [], None
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1)                                      # evict L2 between timed steps
             restore()
             torch.cuda.synchronize()
@@ -363,13 +569,13 @@ def bench_gpu(args):
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
             cands += stats["candidates"]
-            steps.append(stats["steps"])
+            nsteps.append(stats["steps"])
         torch.cuda.synchronize()
     clocks = clk.summary()
     total = float(sum(times))
     t_max, c_all = reduce_replicas(total, cands, dev)
     value = c_all / t_max
-    tlo_ms = 1e3 * total / args.steps
+    tlo_ms = 1e3 * total / steps
     evals = stats["evaluations"]
     mode_used, grid = T.tga_get_descent_mode(ls.ctx)
     persistent = mode_used == T.DESCENT_PERSISTENT
@@ -381,9 +587,11 @@ def bench_gpu(args):
     pshape = T.tga_get_persistent_shape(ls.ctx)
 
     # ---- end to end through the public API with host buffers
+    e2e_reps = steps if e2e_reps is None else max(1, min(e2e_reps, steps))
+    e2e_warm = min(warmup, 1) if e2e_reps < steps else warmup
     e2e_times = []
     h2d = d2h = 0
-    for k in range(args.warmup + args.steps):
+    for k in range(e2e_warm + e2e_reps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2d = ls.reload(inst, sol)                         # pinned H2D + build
@@ -391,7 +599,7 @@ def bench_gpu(args):
         tour, rs = ls.solution()                           # D2H of the result
         t1 = time.perf_counter()
         d2h = (tour.nbytes + rs.nbytes + 48)
-        if k >= args.warmup:
+        if k >= e2e_warm:
             e2e_times.append(t1 - t0)
         assert st["candidates"] == stats["candidates"]
     e2e_value = stats["candidates"] * len(e2e_times) / sum(e2e_times)
@@ -402,9 +610,15 @@ def bench_gpu(args):
     # per operator.  Graph path: the inter-route evaluation kernel at states
     # along the trajectory.
     peaks, peak_src = load_peaks()
-    sm_mhz_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = 152 * 4 * 32 * sm_mhz_max * 1e6              # INT32 lane-ops/s at issue peak
-    peak_desc = f"152 SMs x 4 schedulers x 32 lanes x {sm_mhz_max:.0f} MHz (issue peak)"
+    peak_ops = peak["ops_per_s"]
+    peak_desc = (f"measured: {peak['kernel']}, {peak_ops / 1e12:.2f} T ops/s on {peak['sm_count']} SMs at "
+                 f"{peak['clocks'].get('sm_mhz')} MHz (nominal issue rate {peak['nominal_issue_ops_per_s'] / 1e12:.2f} T)")
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    def hbm_ceiling(bytes_per_launch, ms):
+        gbs = bytes_per_launch / (ms * 1e-3) / 1e9
+        return {"algorithmic_bytes": int(bytes_per_launch), "achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                "frac": gbs / hbm_peak, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
 
     def kept_inter_ops():
         """Edge-based extraction: integer ops of the inter-route candidates the
@@ -429,7 +643,7 @@ def bench_gpu(args):
         x_ops = x_ms = 0.0                      # swaps of runs (ranks 6, 7)
         xs = bool(mask & 0xC0)
         probes = 5
-        n_steps = steps[-1]
+        n_steps = nsteps[-1]
         for j in range(probes):
             ms = T.tga_profile_inter(ls.ctx, reps=20)
             if args.granular:
@@ -446,19 +660,22 @@ def bench_gpu(args):
                 T.tga_descend(ls.ctx, max_steps=max(1, n_steps // (probes - 1)))
         achieved = total_ops / (total_ms / 1e3)
         kname = "k_eval_edges" if args.granular else "k_eval_inter"
+        ms_l = total_ms / probes
         out = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops, "peak_source": peak_desc,
-               "ms_per_launch": total_ms / probes, "ops_per_launch": total_ops / probes,
+               "frac_of_nominal_issue": achieved / peak["nominal_issue_ops_per_s"],
+               "ms_per_launch": ms_l, "ops_per_launch": total_ops / probes,
                "work": "inter-route candidates of the state (per-candidate integer ops x candidates), "
                        "mean over 5 states along the trajectory",
-               "traffic": measured_traffic(workload_name(args) + (f"-granular{args.granular}" if args.granular else ""),
-                                           kname),
+               "hbm": hbm_ceiling(evaluation_bytes(inst.n, ls.m), ms_l),
+               "traffic": measured_traffic(workload_name(args, wl_name) +
+                                           (f"-granular{args.granular}" if args.granular else ""), kname),
                "kernel_source_hash": kernel_source_hash()}
         if xs:
             xa = x_ops / (x_ms / 1e3)
             out["xswap_kernel"] = {"kernel": "k_eval_xswap", "achieved": xa / 1e12, "frac": xa / peak_ops,
                                    "ms_per_launch": x_ms / probes, "ops_per_launch": x_ops / probes,
-                                   "traffic": measured_traffic(workload_name(args), "k_eval_xswap")}
+                                   "traffic": measured_traffic(workload_name(args, wl_name), "k_eval_xswap")}
         return out
 
     inter_roof = inter_kernel_roof()
@@ -478,33 +695,31 @@ def bench_gpu(args):
         achieved = ops / (ms / 1e3)
         roof = {"bound": "alu", "kernel": "k_persist", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                 "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops, "peak_source": peak_desc,
+                "frac_of_nominal_issue": achieved / peak["nominal_issue_ops_per_s"],
                 "ms_per_launch": ms, "ops_per_launch": ops, "grid": grid,
                 "work": "every candidate of every evaluation of the descent (per-operator device counters "
                         "x per-candidate integer ops); one launch = one whole descent",
-                "traffic": measured_traffic(workload_name(args), "k_persist"),
+                "hbm": hbm_ceiling(evaluation_bytes(inst.n, ls.m) * evals, ms),
+                "traffic": measured_traffic(workload_name(args, wl_name), "k_persist"),
                 "kernel_source_hash": kernel_source_hash(),
                 "inter_kernel": {k: inter_roof[k] for k in ("kernel", "achieved", "frac", "ms_per_launch",
-                                                             "ops_per_launch", "traffic")}}
+                                                             "ops_per_launch", "traffic", "hbm")}}
     else:
         roof = inter_roof
+    m_routes = ls.m
     ls.close()
-    brk = breakdown(inst, sol, mask, dev, stream) if rank == 0 and not args.granular else None
-
-    if ws > 1:
-        dist.barrier()
-    if rank != 0:
-        if ws > 1:
-            dist.destroy_process_group()
-        return
-    line = {
+    del flush
+    brk = breakdown(inst, sol, mask, dev, stream) if (with_breakdown and rank == 0 and not args.granular) else None
+    rec = {
         "metric": "move evals/s", "value": value, "unit": "candidate moves/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "n_gpus": ws, "steps": steps, "warmup": warmup,
+        "ms_per_step": 1e3 * t_max / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "time_to_local_optimum_ms": tlo_ms, "moves_applied": steps[-1], "evaluations": evals,
+        "time_to_local_optimum_ms": tlo_ms, "moves_applied": nsteps[-1], "evaluations": evals,
         "candidates_per_descent": stats["candidates"], "initial_cost": stats["initial_cost"],
         "final_cost": stats["final_cost"],
-        "config": {"workload": workload_name(args), "desc": desc, "instance_seed": args.seed,
+        "config": {"workload": workload_name(args, wl_name), "desc": desc, "instance_seed": seed,
+                   "n_customers": int(inst.n), "n_routes": int(m_routes),
                    "op_mask": mask, "tile_rows_warps": list(tile), "parallelism": f"replicas x{ws}",
                    "descent_path": T.DESCENT_NAMES[mode_used],
                    "extraction": (f"edge-based, granular mask of the {args.granular} nearest customers"
@@ -513,27 +728,30 @@ def bench_gpu(args):
                    "l2": "flushed between timed steps (512 MB write)"},
         "candidates_per_operator": op_cands,
         "e2e": {"value": e2e_value, "unit": "candidate moves/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "time_to_local_optimum_ms": 1e3 * float(np.mean(e2e_times))},
-        "gpu_launches": int(launches_per_step * args.steps),
+                "d2h_bytes_per_step": int(d2h), "time_to_local_optimum_ms": 1e3 * float(np.mean(e2e_times)),
+                "repeats": len(e2e_times),
+                "note": None if len(e2e_times) == steps else
+                f"{len(e2e_times)} timed end-to-end descents after {e2e_warm} untimed (each is a whole descent)"},
+        "gpu_launches": int(launches_per_step * steps),
         "clocks": clocks,
         "roofline": roof,
         "breakdown": brk,
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, seconds=args.cpu_seconds)
-    print(json.dumps(line), flush=True)
-    if ws > 1:
-        dist.destroy_process_group()
+    if cpu is not None and rank == 0 and ws == 1:
+        rec["cpu_baseline"] = cpu_baseline(args, wl_name, **cpu)
+    return rec
 
 
-def bench_batch(args):
+# ---------------------------------------------------------------------------
+# batched and served workloads
+
+def run_batch(args, steps, warmup):
     """Batched workload: 256 instances (sizes uniform in [100, 2000], half
     CVRP / half VRPTW) descended in one persistent launch, against 256
     sequential single-instance descents of the same jobs on the same GPU."""
     import torch
     from paper_2506_17357_gb300 import tga as T
     dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
     count = args.batch_jobs
     jobs = I.batch_jobs(count=count, seed=4, lo=100, hi=2000)
     stream = torch.cuda.Stream(dev)
@@ -551,12 +769,12 @@ def bench_batch(args):
 
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         restore()
         T.tga_descend_batch(ctxs)
     times, stats = [], None
     with ClockSampler(0) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             restore()
             torch.cuda.synchronize()
             e0.record(stream)
@@ -578,7 +796,8 @@ def bench_batch(args):
     e1.record(stream)
     e1.synchronize()
     t_seq = e0.elapsed_time(e1) / 1e3
-    exact = all(a["final_cost"] == b["final_cost"] and a["steps"] == b["steps"] for a, b in zip(stats, seq_stats))
+    exact = all(a["final_cost"] == b["final_cost"] and a["steps"] == b["steps"] and
+                a["candidates"] == b["candidates"] for a, b in zip(stats, seq_stats))
     # end to end: host instances/solutions -> batch -> host results
     t0 = time.perf_counter()
     h2d = 0
@@ -593,21 +812,21 @@ def bench_batch(args):
     sizes = [inst.n for inst, _ in jobs]
     for ls in lss:
         ls.close()
-    line = {"metric": "batched jobs/s", "value": count / t_batch, "unit": "jobs/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
+    return {"metric": "batched jobs/s", "value": count / t_batch, "unit": "jobs/s", "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * t_batch, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "sequential_jobs_per_s": count / t_seq, "speedup_vs_sequential": t_seq / t_batch,
             "move_evals_per_s": cands / t_batch, "bit_exact_vs_sequential": bool(exact),
             "config": {"workload": "batch256", "jobs": count, "sizes": [min(sizes), max(sizes)],
                        "mix": "alternating CVRP/VRPTW", "tile_rows_by_job": sorted(set(rows)),
+                       "descent": "one persistent launch; the step loop runs on the device (no graph needed)",
                        "l2": "inputs (1.4 GB of matrices) exceed L2"},
             "e2e": {"value": count / t_e2e, "unit": "jobs/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "clocks": clocks}
-    print(json.dumps(line), flush=True)
 
 
-def bench_serve(args):
+def run_serve(args, warmup):
     """Serving workload: a seeded Poisson stream of jobs (sizes log-uniform in
     [100, 5000], 70% CVRP / 30% VRPTW) through the continuous-batching server
     (memory budget 1 GiB, up to 32 slots) against the one-at-a-time path on the
@@ -616,7 +835,6 @@ def bench_serve(args):
     one-at-a-time queue grows)."""
     import torch
     from paper_2506_17357_gb300 import serving as S
-    torch.cuda.set_device(0)
     count = args.serve_jobs
     sizes, kinds = I.serving_sizes(count, seed=5)
     reqs = []
@@ -631,7 +849,7 @@ def bench_serve(args):
         srv = S.Server(budget_bytes=budget, max_slots=slots, keep_solutions=False)
         return S.summarize(srv.serve(rs, pinned=pinned)), srv
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         S.Server(budget_bytes=budget, max_slots=4, keep_solutions=False).serve(
             [S.Request(r.rid, 0.0, r.inst, r.sol, r.op_mask) for r in reqs[:6]], pinned=pinned)
     zero = np.zeros(count)
@@ -647,80 +865,123 @@ def bench_serve(args):
             sweep[str(mult)] = {"rate_jobs_per_s": mult * mu1, "one_at_a_time": one, "continuous": cont}
     clocks = clk.summary()
     head = sweep["2.0"]["continuous"]
-    line = {"metric": "served jobs/s", "value": head["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1,
-            "steps": 1, "warmup": args.warmup, "ms_per_step": 1e3 * head["makespan_s"],
+    return {"metric": "served jobs/s", "value": head["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1,
+            "steps": 1, "warmup": warmup, "ms_per_step": 1e3 * head["makespan_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic", "p50_latency_ms": head["p50_latency_ms"], "p99_latency_ms": head["p99_latency_ms"],
+            "one_at_a_time_at_2x": sweep["2.0"]["one_at_a_time"],
             "saturated_capacity_jobs_per_s": {"one_at_a_time": mu1, "continuous": capN["jobs_per_s"]},
             "sweep": sweep,
             "config": {"workload": "serve", "jobs": count, "sizes": "log-uniform [100, 5000]",
                        "mix": "70% CVRP / 30% VRPTW", "budget_bytes": budget, "max_slots": 32,
                        "arrivals": "seeded Poisson at 0.8x and 2x the one-at-a-time capacity"},
             "clocks": clocks}
-    print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(args, seconds=15.0, per_op_seconds=1.0):
-    """The oracle's concatenation evaluator (plain single-threaded C) on the
-    host: best-improvement steps of the same workload from the same initial
-    solution, as many as fit in ``seconds``."""
-    import oracle as O
-    desc, make, mask = workload(args)
-    inst, sol = make(args.seed)
-    theta = getattr(args, "granular", 0)
-    nbr = I.granular_neighbors(inst, theta) if theta else None
-    cur = sol
-    t0 = time.perf_counter()
-    cands = 0
-    k = 0
-    while time.perf_counter() - t0 < seconds:
-        bm = O.best_move(inst, cur, mask, "concat", granular=nbr)
-        cands += bm["candidates"]
-        k += 1
-        if not bm["found"] or bm["delta"] >= 0:
-            break
-        cur = O.apply_move(inst, cur, bm["op"], bm["a"], bm["b"])
-    dt = time.perf_counter() - t0
-    # per operator: the oracle's evaluation of the initial solution with only
-    # that operator enabled (about a second each)
-    per_op = {}
-    for op in range(8):
-        if not (mask >> op) & 1 or per_op_seconds <= 0:
-            continue
-        t1 = time.perf_counter()
-        reps = c1 = 0
-        while time.perf_counter() - t1 < per_op_seconds:
-            c1 += O.best_move(inst, sol, 1 << op, "concat", granular=nbr)["candidates"]
-            reps += 1
-        d1 = time.perf_counter() - t1
-        per_op[OP_NAMES[op]] = {"ms_per_evaluation": 1e3 * d1 / reps, "candidates_per_s": c1 / d1}
-    return {"value": cands / dt, "unit": "candidate moves/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {k} best-improvement evaluations of {workload_name(args)} seed {args.seed} "
-                      f"(concatenation evaluator{', granular mask theta=%d' % theta if theta else ''}), {dt:.1f} s",
-            "per_operator": per_op}
+# ---------------------------------------------------------------------------
+# entry points
+
+def _init_gpu():
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    return ws, rank, local
+
+
+def bench_default(args):
+    """Headline (clustered CVRP-10000) + the other workloads in one line."""
+    import torch.distributed as dist
+    ws, rank, local = _init_gpu()
+    peak = measure_int_peak(local)
+    line = run_single(args, HEADLINE, args.steps, args.warmup, peak, e2e_reps=args.e2e_reps,
+                      cpu=None if args.no_cpu_baseline else dict(seconds=args.cpu_seconds))
+    line["int32_peak"] = peak
+    line["host"] = {"cpu_count": os.cpu_count(), "affinity_cores": host_cores(), "sm_count": peak["sm_count"]}
+    if ws == 1 and not args.headline_only:
+        cpu_small = None if args.no_cpu_baseline else dict(seconds=4.0, all_core_target_s=3.0, per_op_seconds=0.3)
+        configs = {}
+        for wl in ("cvrp100", "vrptw1000"):
+            configs[wl] = run_single(args, wl, args.steps, args.warmup, peak, with_breakdown=(wl == "vrptw1000"),
+                                     cpu=cpu_small)
+        configs["batch256"] = run_batch(args, steps=min(args.steps, 3), warmup=1)
+        configs["serve"] = run_serve(args, warmup=1)
+        line["configs"] = configs
+    if ws > 1:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def bench_one(args):
+    """One workload alone (--workload NAME): the profiling commands' form."""
+    import torch.distributed as dist
+    ws, rank, local = _init_gpu()
+    if args.workload == "batch256":
+        line = run_batch(args, args.steps, args.warmup)
+    elif args.workload == "serve":
+        line = run_serve(args, args.warmup)
+    else:
+        peak = measure_int_peak(local)
+        line = run_single(args, args.workload, args.steps, args.warmup, peak, e2e_reps=args.e2e_reps,
+                          cpu=None if args.no_cpu_baseline else dict(seconds=args.cpu_seconds))
+        line["int32_peak"] = peak
+    if ws > 1:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
 
 
 def bench_reference(args):
+    """The reference arm: the CPU oracle (there is no published code) on the
+    host cores, on the headline workload.  Each step is one whole
+    neighbourhood evaluation of the initial solution spread over a spawn
+    pool of one process per core (interleaved slices, exact minimum key);
+    warm-up steps evaluate one slice per process."""
+    import multiprocessing as mp
+    import oracle as O
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    desc, make, mask = workload(args)
-    per = max(2.0, args.cpu_seconds / max(1, args.steps))
-    for _ in range(args.warmup):
-        cpu_baseline(args, seconds=min(per, 2.0), per_op_seconds=0.0)
-    vals = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(args, seconds=per, per_op_seconds=0.0))
-    dt = time.perf_counter() - t0
-    value = float(np.mean([v["value"] for v in vals]))
+    wl = HEADLINE if args.workload == "all" else args.workload
+    desc, make, mask = workload(args, wl)
+    inst, sol = make(args.seed)
+    K = host_cores()
+    est = O.count_candidates(inst, sol, mask) / 1e7
+    stride = max(K, K * int(math.ceil(est / (0.5 * K))))
+    states = [(np.asarray(sol.tour, np.int32), np.asarray(sol.route_start, np.int32))]
+    full = [[(0, ph, stride)] for ph in range(stride)]
+    ctx = mp.get_context("spawn")
+    vals, walls, key = [], [], None
+    with ctx.Pool(K, initializer=_cpu_worker_init, initargs=(wl, args.seed, mask, states, 0)) as pool:
+        pool.map(time.sleep, [0.05] * K)
+        for k in range(args.warmup + args.steps):
+            tasks = full[:K] if k < args.warmup else full
+            res = pool.map(_cpu_worker_task, tasks, chunksize=1)
+            wall = max(r[3] for r in res) - min(r[2] for r in res)
+            if k >= args.warmup:
+                vals.append(sum(r[1] for r in res) / wall)
+                walls.append(wall)
+                key = min(r[0] for r in res)
+    value = float(sum(vals) / len(vals))
+    dkey, didx = O.unpack_key(key)
     line = {"impl": "reference", "metric": "move evals/s", "value": value, "unit": "candidate moves/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": workload_name(args), "desc": desc, "instance_seed": args.seed,
-                                            "op_mask": mask},
-            "cpu_baseline": {"value": value, "unit": "candidate moves/s", "cores": 1, "kind": "oracle",
-                             "sample": vals[-1]["sample"]},
+            "data": "synthetic", "config": {"workload": workload_name(args, wl), "desc": desc,
+                                            "instance_seed": args.seed, "op_mask": mask},
+            "first_best_move": {"delta": dkey, "move_index": didx},
+            "cpu_baseline": {"value": value, "unit": "candidate moves/s", "cores": K, "kind": "oracle",
+                             "host_cores": host_cores(), "os_cpu_count": os.cpu_count(),
+                             "sample": f"each step: one whole evaluation of the initial solution of "
+                                       f"{workload_name(args, wl)} seed {args.seed} in {stride} interleaved slices "
+                                       f"over a spawn pool of {K} processes (concatenation evaluator)"},
             "e2e": {"value": value, "unit": "candidate moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -731,7 +992,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tga", choices=["tga", "reference"])
-    ap.add_argument("--workload", default="vrptw1000", choices=sorted(WORKLOADS) + ["batch256", "serve"])
+    ap.add_argument("--workload", default="all", choices=["all"] + sorted(WORKLOADS) + ["batch256", "serve"],
+                    help="all (default): the clustered CVRP-10000 headline plus every other workload in one line")
+    ap.add_argument("--headline-only", action="store_true", help="with --workload all: skip the other workloads")
+    ap.add_argument("--e2e-reps", type=int, default=3,
+                    help="timed end-to-end descents of the headline (each a whole descent through the API)")
     ap.add_argument("--serve-jobs", type=int, default=120)
     ap.add_argument("--only-descent", action="store_true",
                     help="run one descent of the workload without timing (for profiler launch lists)")
@@ -752,12 +1017,10 @@ def main():
         only_descent(args)
     elif args.impl == "reference":
         bench_reference(args)
-    elif args.workload == "batch256":
-        bench_batch(args)
-    elif args.workload == "serve":
-        bench_serve(args)
+    elif args.workload == "all":
+        bench_default(args)
     else:
-        bench_gpu(args)
+        bench_one(args)
 
 
 if __name__ == "__main__":

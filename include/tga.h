@@ -299,6 +299,25 @@ int tga_profile_inter(tga_ctx *ctx, int32_t reps, float *ms_per_launch);
  * TGA_ERR_STATE when the context's operator mask has neither rank. */
 int tga_profile_xswap(tga_ctx *ctx, int32_t reps, float *ms_per_launch);
 
+/* Measured 32-bit integer throughput of the current device: the denominator
+ * of the evaluation kernels' roofline fractions.  The paper has no
+ * counterpart (it reports speedups, not rooflines); the evaluation path
+ * issues integer additions and minima/maxima only (no tensor-core
+ * contraction), so its ceiling is the rate at which the SMs retire such
+ * operations.  Launches one dependency-free stream kernel sized to fill
+ * every SM (the SM count is read from the device): each thread runs eight
+ * independent chains of `iters` x 8 links,
+ *   kind 0: x = max(x + a, b)   (one add and one max per link: two-input
+ *           operations, one per issued lane -- the issue peak),
+ *   kind 1: x = x + x' + a      (two adds per link, which may execute as one
+ *           three-input add: more source operations than issued lanes),
+ * and writes the best of three timed launches (CUDA events on `stream`,
+ * after one warm-up launch) as source integer operations per second
+ * (*ops_per_s, two per link) and milliseconds (*ms_out, may be NULL).
+ * Synchronous.  TGA_ERR_INVALID for another kind, iters < 1 or a NULL
+ * ops_per_s; TGA_ERR_CUDA when a launch fails. */
+int tga_measure_int_peak(int32_t kind, tga_stream_t stream, int32_t iters, double *ops_per_s, float *ms_out);
+
 /* Best move of one instance + solution WITHOUT allocating any memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory (a host framework that owns every device
@@ -344,6 +363,19 @@ int tga_set_granular(tga_ctx *ctx, const int32_t *nbr_dev, int32_t theta);
  * distance copy ((n+1) rows of row_pitch int32), 7 tile list (int2).
  * Copies min(bytes, size) bytes; *size_out (may be NULL) gets the size. */
 int tga_debug_read(tga_ctx *ctx, int32_t what, void *host_dst, size_t bytes, size_t *size_out);
+
+/* Failure detection (the paper has none; the library's device-side waits
+ * are its own): set the time limit of every bounded device wait of this
+ * context -- the persistent descent's plan publication and grid barrier
+ * (default 5 s), the apply launch's plan flag (1 s) and, for batched
+ * descents that include this context, the idle chunk polling (20 s; the
+ * smallest limit of the batch's contexts applies).  limit_ns < 0 restores
+ * the defaults.  A wait that runs out makes the kernel stop its work and
+ * return; the descent or batch then reports TGA_ERR_TIMEOUT, the caller's
+ * solution keeps its last written-back state, and tga_build_attrs makes the
+ * context usable again.  Meant for tests of this failure path (a tiny
+ * limit) and for callers that want a tighter bound. */
+int tga_set_wait_limit(tga_ctx *ctx, int64_t limit_ns);
 
 /* Release the context's workspace (not the caller's arrays). */
 int tga_destroy(tga_ctx *ctx);

@@ -65,8 +65,7 @@ __device__ void run_chunk(const BatchJob &J, int c, int *smem, int &best, unsign
     if (c < J.ninter) {
         const int t0 = J.chunk_t0[c], t1 = J.chunk_t0[c + 1];
         for (int I = t0; I < t1; ++I) {
-            long long j0 = ((long long)I * TR + 1 + TC - 1) / TC - 1;
-            if (j0 < 0) j0 = 0;
+            const long long j0 = ((long long)I * TR + 1) / TC;     // first J with (J+1)*TC-1 > I*TR
             for (int Jc = (int)j0; Jc < J.nct; ++Jc) {
                 if (OR) inter_tile<TW, true>(d, I * TR, Jc * TC, TR, 1, smem, best, bidx);
                 else inter_tile<TW, false>(d, I * TR, Jc * TC, TR, 1, smem, best, bidx);
@@ -288,7 +287,7 @@ size_t batch_smem_bytes(int max_tr, int max_wp) {
 }
 
 int launch_batch(const BatchJob *jobs_dev, int njobs, BatchState *state_dev, long long max_steps, int mode,
-                 int max_tr, int max_wp, cudaStream_t s) {
+                 int max_tr, int max_wp, long long idle_limit_ns, cudaStream_t s) {
     const size_t sm = batch_smem_bytes(max_tr, max_wp);
     if (sm > 200 * 1024) return TGA_ERR_RANGE;
     if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
@@ -300,8 +299,7 @@ int launch_batch(const BatchJob *jobs_dev, int njobs, BatchState *state_dev, lon
     if (per < 1) return TGA_ERR_RANGE;
     const int grid = nsm * per;
     k_batch_init<<<(njobs + 127) / 128, 128, 0, s>>>(jobs_dev, njobs, state_dev);
-    k_batch<<<grid, kBatchThreads, sm, s>>>(jobs_dev, njobs, state_dev, max_steps, mode,
-                                            20LL * 1000 * 1000 * 1000);
+    k_batch<<<grid, kBatchThreads, sm, s>>>(jobs_dev, njobs, state_dev, max_steps, mode, idle_limit_ns);
     return cudaGetLastError() == cudaSuccess ? TGA_OK : TGA_ERR_CUDA;
 }
 

@@ -49,33 +49,6 @@ int cuda_err(cudaError_t e) { return e == cudaSuccess ? TGA_OK : TGA_ERR_CUDA; }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// The context workspace: one allocation carved into 256-byte aligned pieces.
-// pd: the pickup records; xs: the swaps-of-runs records.  Returns the bytes.
-struct WsLayout {
-    size_t ctl, seq, pos, brec, erec, prec, xrec, rrec, seen, intra, saved, pcol;
-};
-size_t workspace_layout(size_t n, size_t m, bool pd, bool xs, WsLayout *o) {
-    const size_t W = n + 1 + m, Wp = n + m + 1;
-    const size_t ldp = align_up(Wp, kMaxTileCols) + 16;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes, 256); return at; };
-    WsLayout L;
-    L.ctl = take(sizeof(Control));
-    L.seq = take(sizeof(int) * Wp);
-    L.pos = take(sizeof(int) * (W + 1));
-    L.brec = take(sizeof(BRec) * (W + 1));
-    L.erec = take(sizeof(ERec) * (W + 1));
-    L.prec = take(pd ? sizeof(PRec) * (W + 1) : 0);
-    L.xrec = take(xs ? sizeof(XRec) * (W + 1) : 0);
-    L.rrec = take(sizeof(RouteRec) * m);
-    L.seen = take(sizeof(int) * (n + 1));
-    L.intra = take(sizeof(int) * kIntraVecPD * (Wp + m));
-    L.saved = take(sizeof(int) * (n + m + 1));
-    L.pcol = take(sizeof(int) * (n + 1) * ldp);
-    if (o) *o = L;
-    return off;
-}
-
 int check_launch() {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -212,7 +185,7 @@ long long count_tiles(int Wp, int rows, int TC) {
     const long long Wa = Wp - 1, nrt = (Wa + rows - 1) / rows, nct = (Wa + TC - 1) / TC;
     long long t = 0;
     for (long long I = 0; I < nrt; ++I) {
-        const long long j0 = (I * rows) / TC;
+        const long long j0 = (I * rows + 1) / TC;            // first J with (J+1)*TC-1 > I*rows
         t += nct > j0 ? nct - j0 : 0;
     }
     return t;
@@ -251,6 +224,7 @@ int descend_launch(tga_ctx *c, int64_t max_steps) {
     if (mode == TGA_DESCENT_PERSISTENT) {
         const int rc = try_persist(c);
         if (rc == TGA_OK) {
+            launch_sync_solution(c->d, c->stream);
             c->last_mode = TGA_DESCENT_PERSISTENT;
             return check_launch();
         }
@@ -295,6 +269,7 @@ int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *t
     std::vector<std::vector<int>> bounds((size_t)n);
     int max_tr = 16, max_wp = 1;
     size_t nbounds = 0;
+    long long idle_ns = kWaitBatchNs;
     for (int i = 0; i < n; ++i) {
         tga_ctx *c = ctxs[i];
         const int tr = tr_override ? tr_override[i] : (c->batch_tr ? c->batch_tr : default_batch_tr(c->d.Wp));
@@ -309,8 +284,7 @@ int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *t
         b.push_back(0);
         long long acc = 0;
         for (int I = 0; I < J.nrt; ++I) {
-            long long j0 = ((long long)I * tr + 1 + kBatchThreads - 1) / kBatchThreads - 1;
-            if (j0 < 0) j0 = 0;
+            const long long j0 = ((long long)I * tr + 1) / kBatchThreads;   // first J with (J+1)*TC-1 > I*tr
             acc += (long long)(J.nct - j0) * tr * kBatchThreads;
             if (acc >= kChunkPairs && I + 1 < J.nrt) { b.push_back(I + 1); acc = 0; }
         }
@@ -323,6 +297,7 @@ int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *t
         J.chunk_t0 = nullptr;
         nbounds += b.size();
         if (tr > max_tr) max_tr = tr;
+        idle_ns = std::min(idle_ns, wait_limit(c->d.wait_ns, kWaitBatchNs));
         if (c->d.Wp > max_wp) max_wp = c->d.Wp;
         if (mode != 2 && cudaMemsetAsync(c->d.ctl, 0, sizeof(Control), s) != cudaSuccess) return TGA_ERR_CUDA;
     }
@@ -352,14 +327,15 @@ int run_batch(tga_ctx **ctxs, int n, long long max_steps, int mode, const int *t
     if (cudaMemcpyAsync(jdev, ordered.data(), sizeof(BatchJob) * (size_t)n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(bdev, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
         rc = TGA_ERR_CUDA;
-    if (!rc) rc = launch_batch(jdev, n, sdev, max_steps, mode, max_tr, max_wp, s);
+    if (!rc) rc = launch_batch(jdev, n, sdev, max_steps, mode, max_tr, max_wp, idle_ns, s);
     BatchState st{};
     if (cudaStreamSynchronize(s) != cudaSuccess) rc = rc ? rc : TGA_ERR_CUDA;
     if (cudaMemcpy(&st, sdev, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) rc = rc ? rc : TGA_ERR_CUDA;
     cudaFree(buf);
-    if (mode != 2)
-        for (int i = 0; i < n; ++i) ctxs[i]->built = true;
     if (!rc && st.status) rc = st.status;
+    // a failed launch may stop jobs mid-step: rebuild them on their next use
+    if (mode != 2)
+        for (int i = 0; i < n; ++i) ctxs[i]->built = rc == TGA_OK;
     return rc;
 }
 
@@ -452,11 +428,17 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.service = inst->service; d.early = inst->tw_early; d.late = inst->tw_late;
     d.pickup = inst->pickup;
     d.tour = sol->tour; d.route_start = sol->route_start;
-    d.ldp = (int)(align_up((size_t)d.Wp, kMaxTileCols) + 16);
+    d.ldp = (int)pcol_pitch((size_t)d.Wp);
     d.log = nullptr; d.log_cap = 0;
+    d.wait_ns = -1;
+    if (cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || d.nsm < 1) {
+        cudaGetLastError();
+        tga_destroy(c);
+        return TGA_ERR_CUDA;
+    }
 
-    WsLayout L;
-    c->ws_bytes = workspace_layout((size_t)n, (size_t)m, d.has_pd != 0, (op_mask & kExtOps) != 0, &L);
+    const WsLayout L = workspace_layout((size_t)n, (size_t)m, d.has_pd != 0, (op_mask & kExtOps) != 0);
+    c->ws_bytes = L.bytes;
     if (cudaMallocAsync(&c->ws, c->ws_bytes, c->stream) != cudaSuccess) {
         cudaGetLastError();
         tga_destroy(c);
@@ -601,7 +583,7 @@ int tga_query(tga_ctx *c, int32_t *done_out) {
 size_t tga_workspace_bytes(int32_t n_customers, int32_t n_routes) {
     if (n_customers < 1 || n_routes < 1) return 0;
     // the largest layout (pickup and swaps-of-runs records included): an upper bound
-    return workspace_layout((size_t)n_customers, (size_t)n_routes, true, true, nullptr);
+    return workspace_layout((size_t)n_customers, (size_t)n_routes, true, true).bytes;
 }
 
 int tga_sync(tga_ctx *c) {
@@ -862,6 +844,13 @@ int tga_set_granular(tga_ctx *c, const int32_t *nbr_dev, int32_t theta) {
         return e != cudaSuccess ? TGA_ERR_CUDA : TGA_ERR_INVALID;
     }
     c->d.theta = theta; c->d.nbr = nbr_dev; c->d.nbr_rev = rev;
+    return TGA_OK;
+}
+
+int tga_set_wait_limit(tga_ctx *c, int64_t limit_ns) {
+    if (!c) return TGA_ERR_INVALID;
+    c->d.wait_ns = limit_ns < 0 ? -1 : (long long)limit_ns;
+    drop_graph(c);                     // the captured launches carry the limit
     return TGA_OK;
 }
 

@@ -2339,6 +2339,7 @@ __device__ void band_plan_rows(const Dev &d, const StepPlan &S, int *smem, int r
 // Write the caller's giant tour and route offsets from the device state
 // (positions, per-anchor routes, route start positions); grid-stride.
 __device__ void sync_solution_range(const Dev &d, long long t0, long long stride) {
+    if (*(volatile int *)&d.ctl->status != 0) return;     // an error leaves the caller's solution as it was
     for (long long q = t0; q < d.Wp - 1; q += stride) {
         const int a = d.seq[q];
         if (a >= 1 && a <= d.n) d.tour[q - d.brec[a].route - 1] = a;

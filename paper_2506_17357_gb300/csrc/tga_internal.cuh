@@ -151,9 +151,58 @@ struct Control {
     unsigned long long gcount[6];
 };
 
+// The device workspace of one instance: every array a context (or the
+// allocation-free entry point) carves out of one block of device memory,
+// each piece 256-byte aligned.  Sized for n1 = n+1 nodes, m routes,
+// w1 = W+1 anchor records and p = n+m+1 positions; pd adds the pickup
+// records, xs the swaps-of-runs records.  Every offset and the total grow
+// monotonically with each argument, so the layout at upper bounds of the
+// four sizes bounds the layout of every instance below them.
+struct WsLayout {
+    size_t ctl, seq, pos, brec, erec, prec, xrec, rrec, seen, intra, saved, pcol, bytes;
+};
+
+constexpr size_t ws_align(size_t x) { return (x + 255) / 256 * 256; }
+
+// Row pitch (ints) of the position-ordered distance copy for p positions.
+constexpr size_t pcol_pitch(size_t p) { return (p + kMaxTileCols - 1) / kMaxTileCols * kMaxTileCols + 16; }
+
+constexpr WsLayout workspace_pieces(size_t n1, size_t m, size_t w1, size_t p, bool pd, bool xs) {
+    WsLayout L{};
+    size_t off = 0;
+    L.ctl = off;   off = ws_align(off + sizeof(Control));
+    L.seq = off;   off = ws_align(off + sizeof(int) * p);
+    L.pos = off;   off = ws_align(off + sizeof(int) * w1);
+    L.brec = off;  off = ws_align(off + sizeof(BRec) * w1);
+    L.erec = off;  off = ws_align(off + sizeof(ERec) * w1);
+    L.prec = off;  off = ws_align(off + (pd ? sizeof(PRec) * w1 : 0));
+    L.xrec = off;  off = ws_align(off + (xs ? sizeof(XRec) * w1 : 0));
+    L.rrec = off;  off = ws_align(off + sizeof(RouteRec) * m);
+    L.seen = off;  off = ws_align(off + sizeof(int) * n1);
+    L.intra = off; off = ws_align(off + sizeof(int) * kIntraVecPD * (p + m));
+    L.saved = off; off = ws_align(off + sizeof(int) * p);
+    L.pcol = off;  off = ws_align(off + sizeof(int) * n1 * pcol_pitch(p));
+    L.bytes = off;
+    return L;
+}
+
+constexpr WsLayout workspace_layout(size_t n, size_t m, bool pd, bool xs) {
+    return workspace_pieces(n + 1, m, n + m + 2, n + m + 1, pd, xs);
+}
+
 // Everything a kernel needs, passed by value.
+// Default limits of the bounded device waits (nanoseconds).
+constexpr long long kWaitPersistNs = 5LL * 1000 * 1000 * 1000;    // persistent descent: plan, grid barrier
+constexpr long long kWaitApplyNs = 1LL * 1000 * 1000 * 1000;      // apply launch: plan publication
+constexpr long long kWaitBatchNs = 20LL * 1000 * 1000 * 1000;     // batched descent: idle chunk polling
+__host__ __device__ inline long long wait_limit(long long override_ns, long long dflt) {
+    return override_ns < 0 ? dflt : override_ns;
+}
+
 struct Dev {
     int n, m, W, Wp, ldp;
+    int nsm;                  // SMs of the device (grid caps of the helper launches)
+    long long wait_ns;        // limit of every bounded device wait; < 0: each wait's default
     int Q, wL, wT, has_tw;
     int has_pd;               // pickups (VRPSPDTW; requires has_tw)
     unsigned op_mask;
@@ -371,7 +420,7 @@ struct BatchState {
 // mode 0: build + descend; 1: build + one evaluation; 2: one evaluation of
 // already-built jobs (autotuner timing)
 int launch_batch(const BatchJob *jobs_dev, int njobs, BatchState *state_dev, long long max_steps, int mode,
-                 int max_tr, int max_wp, cudaStream_t s);
+                 int max_tr, int max_wp, long long idle_limit_ns, cudaStream_t s);
 
 // Kernel entry points (tga_kernels.cu).
 void launch_check_instance(const Dev &d, cudaStream_t s);

@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(512) k_apply(Dev d, const tga_move *ext, cudaG
         apply_plan_block<PD, XS>(d, sP, smem, ext != nullptr, cond, use_cond);
     } else {
         if (tid == 0) {
-            s_ok = wait_flag(&C->plan_ready, 1000LL * 1000 * 1000);
+            s_ok = wait_flag(&C->plan_ready, wait_limit(d.wait_ns, kWaitApplyNs));
             if (!s_ok) set_status(C, TGA_ERR_TIMEOUT);
         }
         __syncthreads();
@@ -372,7 +372,7 @@ int setup_kernel_attrs(int max_band) {
 void launch_check_instance(const Dev &d, cudaStream_t s) {
     const long long nt = (d.n + 1 + 31) / 32;
     long long blocks = nt * nt;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > (long long)d.nsm * 16) blocks = (long long)d.nsm * 16;
     k_check_instance<<<(int)blocks, 256, 0, s>>>(d);
 }
 
@@ -384,7 +384,7 @@ void launch_build(const Dev &d, cudaStream_t s) {
     k_build_finish<<<1, 1024, 0, s>>>(d);
     long long tot = (long long)(d.n + 1) * d.ldp;
     long long blocks = (tot + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > (long long)d.nsm * 32) blocks = (long long)d.nsm * 32;
     k_pcol_init<<<(int)blocks, 256, 0, s>>>(d);
 }
 
@@ -470,7 +470,7 @@ void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warp
 
 int apply_grid(const Dev &d) {
     const int rows = (d.n + 1 + 15) / 16;           // a warp per row, 16 warps per CTA
-    return 1 + (rows < 3 * 152 ? rows : 3 * 152);
+    return 1 + (rows < 3 * d.nsm ? rows : 3 * d.nsm);
 }
 
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond, cudaStream_t s,
@@ -484,7 +484,7 @@ void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, in
 
 void launch_sync_solution(const Dev &d, cudaStream_t s) {
     int blocks = (d.Wp + 255) / 256;
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > d.nsm * 4) blocks = d.nsm * 4;
     k_sync_solution<<<blocks, 256, 0, s>>>(d);
 }
 

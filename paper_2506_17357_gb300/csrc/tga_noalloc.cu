@@ -26,64 +26,44 @@ namespace {
 constexpr int kNoAllocMaxPositions = 1280;     // n + m + 1
 constexpr int kNoAllocRows = 16, kNoAllocWarps = 4;
 
-constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-
-constexpr size_t ldp_for(size_t positions) {
-    return (positions + kMaxTileCols - 1) / kMaxTileCols * kMaxTileCols + 16;
-}
-
 constexpr size_t tiles_upper_bound(size_t positions) {
     const size_t TC = kNoAllocWarps * 32;
     return ((positions + kNoAllocRows - 1) / kNoAllocRows) * ((positions + TC - 1) / TC);
 }
 
-// Scratch layout for n customers, m routes: the arrays of a context plus
-// the tile list.  Returns the bytes; fills d's pointers when base != null.
-size_t noalloc_layout(Dev &d, int2 **tiles, char *base) {
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    const size_t n = (size_t)d.n, m = (size_t)d.m, W = (size_t)d.W, P = (size_t)d.Wp;
-    const size_t o_ctl = take(sizeof(Control));
-    const size_t o_seq = take(sizeof(int) * P);
-    const size_t o_pos = take(sizeof(int) * (W + 1));
-    const size_t o_brec = take(sizeof(BRec) * (W + 1));
-    const size_t o_erec = take(sizeof(ERec) * (W + 1));
-    const size_t o_prec = take(sizeof(PRec) * (W + 1));
-    const size_t o_xrec = take(sizeof(XRec) * (W + 1));
-    const size_t o_rrec = take(sizeof(RouteRec) * m);
-    const size_t o_seen = take(sizeof(int) * (n + 1));
-    const size_t o_intra = take(sizeof(int) * kIntraVecPD * (P + m));
-    const size_t o_tiles = take(sizeof(int2) * tiles_upper_bound(P));
-    const size_t o_pcol = take(sizeof(int) * (n + 1) * (size_t)d.ldp);
-    if (base) {
-        d.ctl = (Control *)(base + o_ctl);
-        d.seq = (int *)(base + o_seq);
-        d.pos_of = (int *)(base + o_pos);
-        d.brec = (BRec *)(base + o_brec);
-        d.erec = (ERec *)(base + o_erec);
-        d.prec = (PRec *)(base + o_prec);
-        d.xrec = (XRec *)(base + o_xrec);
-        d.rrec = (RouteRec *)(base + o_rrec);
-        d.seen = (int *)(base + o_seen);
-        d.scr_intra = (int *)(base + o_intra);
-        d.pcol = (int *)(base + o_pcol);
-        *tiles = (int2 *)(base + o_tiles);
-    }
-    return off;
+// Scratch bytes for n customers and m routes: the workspace of a context
+// (the same layout, with the pickup and swaps-of-runs records) followed by
+// the inter-route tile list.
+constexpr size_t noalloc_bytes(const WsLayout &L, size_t positions) {
+    return L.bytes + ws_align(sizeof(int2) * tiles_upper_bound(positions));
 }
 
-// Bytes at the largest admitted sizes, each piece bounded independently
-// (n+1 <= 1280, m <= 1279, W+1 <= 1281, positions <= 1280).
-constexpr size_t noalloc_max_bytes() {
-    const size_t P = kNoAllocMaxPositions, N1 = P, M = P - 1, W1 = P + 1;
-    return align256(sizeof(Control)) + align256(4 * P) + align256(4 * W1) + align256(sizeof(BRec) * W1) +
-           align256(sizeof(ERec) * W1) + align256(sizeof(PRec) * W1) + align256(sizeof(XRec) * W1) +
-           align256(sizeof(RouteRec) * M) +
-           align256(4 * N1) + align256(4 * kIntraVecPD * (P + M)) +
-           align256(sizeof(int2) * tiles_upper_bound(P)) + align256(4 * N1 * ldp_for(P));
-}
+// The array's size: the layout at the largest admitted sizes, each bounded
+// on its own (n+1 <= 1280 nodes, m <= 1279 routes, W+1 <= 1281 anchor
+// records, 1280 positions).  The layout grows with each of them, so this
+// bounds the scratch of every admitted instance.
+constexpr size_t kNoAllocBytes =
+    noalloc_bytes(workspace_pieces(kNoAllocMaxPositions, kNoAllocMaxPositions - 1, kNoAllocMaxPositions + 1,
+                                   kNoAllocMaxPositions, true, true),
+                  kNoAllocMaxPositions);
+static_assert(kNoAllocBytes < (size_t)8 << 20, "the allocation-free scratch stays below 8 MB");
 
-constexpr size_t kNoAllocBytes = noalloc_max_bytes();
+// Point d's arrays (and *tiles) into the scratch at base.
+void noalloc_carve(Dev &d, int2 **tiles, char *base) {
+    const WsLayout L = workspace_layout((size_t)d.n, (size_t)d.m, true, true);
+    d.ctl = (Control *)(base + L.ctl);
+    d.seq = (int *)(base + L.seq);
+    d.pos_of = (int *)(base + L.pos);
+    d.brec = (BRec *)(base + L.brec);
+    d.erec = (ERec *)(base + L.erec);
+    d.prec = (PRec *)(base + L.prec);
+    d.xrec = (XRec *)(base + L.xrec);
+    d.rrec = (RouteRec *)(base + L.rrec);
+    d.seen = (int *)(base + L.seen);
+    d.scr_intra = (int *)(base + L.intra);
+    d.pcol = (int *)(base + L.pcol);
+    *tiles = (int2 *)(base + L.bytes);
+}
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -112,16 +92,15 @@ int scratch_for_current_device(char **out) {
 __global__ void k_noalloc_tiles(int2 *tiles, int nrt, int nct, int rows, int cols) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nrt) return;
-    // tiles of row tiles 0..I-1 precede row tile I; row tile J0 is the first
-    // column tile with a pair p < q
+    // tiles of row tiles 0..I-1 precede row tile I; in row tile k the first
+    // column tile holding a pair p < q is the first J with
+    // (J+1)*cols - 1 > k*rows, i.e. J = floor((k*rows + 1) / cols)
     long long before = 0;
     for (int k = 0; k < I; ++k) {
-        const long long j0 = ((long long)k * rows + 1 + cols - 1) / cols - 1;   // first J with (J+1)*cols-1 > k*rows
-        const long long jj = j0 < 0 ? 0 : j0;
-        before += nct > jj ? nct - jj : 0;
+        const long long j0 = ((long long)k * rows + 1) / cols;
+        before += nct > j0 ? nct - j0 : 0;
     }
-    long long j0 = ((long long)I * rows + 1 + cols - 1) / cols - 1;
-    if (j0 < 0) j0 = 0;
+    const long long j0 = ((long long)I * rows + 1) / cols;
     for (long long J = j0; J < nct; ++J) tiles[before + (J - j0)] = make_int2(I, (int)J);
 }
 
@@ -151,15 +130,23 @@ extern "C" int tga_eval_best_move_noalloc(const tga_instance *inst, const tga_so
     d.has_pd = inst->pickup ? 1 : 0;
     d.pickup = inst->pickup;
     d.tour = sol->tour; d.route_start = sol->route_start;
-    d.ldp = (int)ldp_for((size_t)d.Wp);
+    d.ldp = (int)pcol_pitch((size_t)d.Wp);
     d.log = nullptr; d.log_cap = 0;
+    d.wait_ns = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || d.nsm < 1) {
+        cudaGetLastError();
+        return TGA_ERR_CUDA;
+    }
 
     int2 *tiles = nullptr;
-    if (noalloc_layout(d, &tiles, nullptr) > kNoAllocBytes) return TGA_ERR_RANGE;
+    if (noalloc_bytes(workspace_layout((size_t)n, (size_t)m, true, true), (size_t)d.Wp) > kNoAllocBytes)
+        return TGA_ERR_RANGE;
     char *base = nullptr;
     int rc = scratch_for_current_device(&base);
     if (rc) return rc;
-    noalloc_layout(d, &tiles, base);
+    noalloc_carve(d, &tiles, base);
     if (setup_kernel_attrs(d.Wp) != 0) return TGA_ERR_CUDA;
 
     const int Wa = d.Wp - 1, TC = kNoAllocWarps * 32;
@@ -180,9 +167,11 @@ extern "C" int tga_eval_best_move_noalloc(const tga_instance *inst, const tga_so
     launch_eval(d, tiles, (int)ntiles, kNoAllocRows, kNoAllocWarps, s);
     launch_finalize(d, out_dev, s);
     if (cudaGetLastError() != cudaSuccess) return TGA_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TGA_ERR_CUDA;
+    // the status word is read on the caller's stream only, so work queued on
+    // other streams is not waited for
     int status = 0;
-    if (cudaMemcpy(&status, &d.ctl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpyAsync(&status, &d.ctl->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
         return TGA_ERR_CUDA;
     return status;
 }

@@ -19,8 +19,9 @@
 //                positions and the <= 2 touched routes); the other CTAs
 //                permute the columns of the position-ordered distance copy;
 //   barrier      then the next step, until the move is not improving or the
-//                step limit is reached; finally every CTA writes its share of
-//                the caller's giant tour back.
+//                step limit is reached.  The caller's giant tour is written
+//                back by the next launch on the stream (k_sync_solution),
+//                once every CTA has stopped, and only if no wait ran out.
 //
 // A cooperative launch guarantees that all CTAs are resident at once, so
 // the grid barriers cannot deadlock; each wait still has a time limit after
@@ -144,11 +145,13 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const 
     if (!ok) {
         if (tid == 0) {
             set_status(C, TGA_ERR_TIMEOUT);
+            __threadfence();                           // the status is visible before the stop flag
             C->done = 1;
         }
         return;
     }
-    sync_solution_range(d, (long long)cta * blockDim.x + tid, (long long)G * blockDim.x);
+    // the caller's solution is written back by the launch that follows
+    // (k_sync_solution), which sees the final status of every CTA
 }
 
 namespace {
@@ -204,7 +207,7 @@ int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int wa
     Dev dd = d;
     const int2 *tp = tiles;
     int nti = ntiles, tr = rows, rsv = rs, ni = nintra;
-    long long limit = 5LL * 1000 * 1000 * 1000;
+    long long limit = wait_limit(d.wait_ns, kWaitPersistNs);
     void *args[] = {&dd, &tp, &nti, &tr, &rsv, &ni, &limit};
     const cudaError_t e = cudaLaunchCooperativeKernel((const void *)fn, dim3((unsigned)G), dim3((unsigned)nt), args,
                                                       sm, s);

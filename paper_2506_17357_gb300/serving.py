@@ -59,11 +59,28 @@ class Result:
         return self.finished_s - self.arrival_s
 
 
+# Device allocators hand out memory in 2 MiB granules: torch's caching
+# allocator rounds each large block up to them (small arrays share 2 MiB
+# segments) and so does the stream-ordered pool behind the library's
+# workspace.  A job's descent graph and its streams take a little device
+# memory of their own.
+_GRANULE = 2 << 20
+_GRAPH_ALLOWANCE = 16 << 20
+
+
+def _granules(nbytes: int) -> int:
+    return -(-int(nbytes) // _GRANULE) * _GRANULE
+
+
 def footprint_bytes(n: int, m: int) -> int:
-    """Device bytes one job holds while admitted: instance arrays, solution
-    arrays, the move slot and the context workspace."""
-    arrays = 4 * ((n + 1) * (n + 1) + 4 * (n + 1) + n + (m + 1) + 8)
-    return arrays + T.tga_workspace_bytes(n, m)
+    """Device bytes one job holds while admitted: the instance matrix, the
+    small instance and solution arrays (one shared 2 MiB segment counted per
+    job), the context workspace and its tile list, each rounded up to the
+    allocators' 2 MiB granules, plus an allowance for the descent graph."""
+    matrix = _granules(4 * (n + 1) * (n + 1))
+    small = _GRANULE
+    tiles = _granules(8 * (-(-(n + m) // 8)) * (-(-(n + m) // 64)))     # largest tile list of the default shapes
+    return matrix + small + _granules(T.tga_workspace_bytes(n, m)) + tiles + _GRAPH_ALLOWANCE
 
 
 class _Pinned:

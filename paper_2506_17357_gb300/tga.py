@@ -89,6 +89,8 @@ EXPORTS = [
                                                   ctypes.c_uint32, _P, _P]),
     ("tga_profile_inter", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
     ("tga_profile_xswap", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_float)]),
+    ("tga_measure_int_peak", ctypes.c_int, [ctypes.c_int32, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_float)]),
     ("tga_set_descent_mode", ctypes.c_int, [_P, ctypes.c_int32]),
     ("tga_get_descent_mode", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     ("tga_get_persistent_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
@@ -98,6 +100,7 @@ EXPORTS = [
                                           ctypes.POINTER(ctypes.c_int32)]),
     ("tga_debug_read", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t)]),
+    ("tga_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int64]),
     ("tga_destroy", ctypes.c_int, [_P]),
     ("tga_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -240,6 +243,16 @@ def tga_profile_xswap(ctx: int, reps: int = 10) -> float:
     return ms.value
 
 
+def tga_measure_int_peak(kind: int, stream: int = 0, iters: int = 4000):
+    """(integer operations per second, milliseconds) of the dependency-free
+    stream `kind` (0: add + max, 1: three-input adds) on the current device."""
+    ops = ctypes.c_double()
+    ms = ctypes.c_float()
+    _check(_lib().tga_measure_int_peak(kind, _P(stream or None), iters, ctypes.byref(ops), ctypes.byref(ms)),
+           "tga_measure_int_peak")
+    return float(ops.value), float(ms.value)
+
+
 def tga_set_descent_mode(ctx: int, mode: int):
     _check(_lib().tga_set_descent_mode(_P(ctx), mode), "tga_set_descent_mode")
 
@@ -276,6 +289,10 @@ def tga_debug_read(ctx: int, what: int) -> np.ndarray:
     buf = np.zeros(max(1, size.value // 4), dtype=np.int32)
     _check(_lib().tga_debug_read(_P(ctx), what, buf.ctypes.data, size.value, None), "tga_debug_read")
     return buf
+
+
+def tga_set_wait_limit(ctx: int, limit_ns: int):
+    _check(_lib().tga_set_wait_limit(_P(ctx), int(limit_ns)), "tga_set_wait_limit")
 
 
 def tga_destroy(ctx: int):

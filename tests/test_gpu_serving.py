@@ -36,7 +36,7 @@ def _alone(req):
         ls.close()
 
 
-@pytest.mark.parametrize("budget_mb,slots", [(256, 6), (12, 6)])
+@pytest.mark.parametrize("budget_mb,slots", [(256, 6), (60, 6)])   # 60 MiB: two or three jobs at a time
 def test_served_results_equal_alone(budget_mb, slots):
     reqs = _requests(14, 30, 600, seed=7, spread_s=0.02)
     srv = S.Server(budget_bytes=budget_mb << 20, max_slots=slots, log_capacity=1 << 15)
@@ -78,3 +78,37 @@ def test_request_above_budget_is_rejected():
     reqs = _requests(2, 500, 600, seed=9, spread_s=0.0)
     with pytest.raises(ValueError):
         S.Server(budget_bytes=1 << 20, max_slots=2).serve(reqs)
+
+
+def test_admitted_job_holds_no_more_than_its_footprint():
+    """The admission budget's per-job figure (footprint_bytes, built on
+    tga_workspace_bytes and the allocators' 2 MiB granules) against the
+    device memory a job really takes: the drop of free device memory when
+    one job is admitted is at most its footprint and not far below it.  A
+    footprint that missed the instance matrix or the position-ordered
+    distance copy (each about 80-100 MB here) would fail.  The first
+    admission of each kind is a warm-up (kernel code loaded on first use is
+    not a per-job cost)."""
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    slack = 32 << 20
+    for j, (n, tw) in enumerate([(4500, False), (4500, False), (5000, True), (5000, True)]):
+        inst, sol = I.serving_job(j, n, tw, seed=12)
+        req = S.Request(j, 0.0, inst, sol, I.mask_for(inst))
+        pinned = S._Pinned(torch, req)
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        job = S._Job(torch, dev, stream, req, pinned, 0, T.DESCENT_GRAPH)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info(dev)[0]
+        need = S.footprint_bytes(n, int(np.asarray(sol.route_start).size - 1))
+        while not job.done():
+            pass
+        st, _, _, _ = job.finish(False)
+        assert st["status"] == 0
+        used = free0 - free1
+        if j % 2 == 0:
+            continue                                     # warm-up admission
+        assert used <= need, (n, used, need)
+        assert used >= need - slack, (n, used, need)
