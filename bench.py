@@ -659,7 +659,7 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
             if j + 1 < probes:
                 T.tga_descend(ls.ctx, max_steps=max(1, n_steps // (probes - 1)))
         achieved = total_ops / (total_ms / 1e3)
-        kname = "k_eval_edges" if args.granular else "k_eval_inter"
+        kname = "k_eval_edges" if args.granular else ("k_eval_strip" if tile[2] == 0 else "k_eval_inter")
         ms_l = total_ms / probes
         out = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                "unit": "Tops/s (INT32 lane-ops)", "frac": achieved / peak_ops, "peak_source": peak_desc,

@@ -289,6 +289,19 @@ int tga_get_tile(tga_ctx *ctx, int32_t *rows, int32_t *warps);
 int tga_set_tile_shape(tga_ctx *ctx, int32_t rows, int32_t col_warps, int32_t row_split);
 int tga_get_tile_shape(tga_ctx *ctx, int32_t *rows, int32_t *col_warps, int32_t *row_split);
 
+/* Strip-major inter-route evaluation (the same candidates of Section 5.3.1
+ * node-based extraction, another schedule): the tiles (rows 16 or 32, 4 or 8
+ * column warps) are ordered column strip by column strip and a grid of
+ * resident CTAs walks them in contiguous ranges, keeping each strip's
+ * column-anchor constants in registers and copying the next tile's
+ * distance rows and row records into shared memory (cp.async, double
+ * buffered) while it evaluates the current one.  Used by the per-step
+ * descent paths and tga_eval_best_move; tga_get_tile_shape then reports
+ * row_split = 0.  The autotuner (tga_set_tile(ctx, 0, 0)) times these
+ * shapes beside the one-CTA-per-tile ones.  TGA_ERR_INVALID for other
+ * shapes. */
+int tga_set_tile_strip(tga_ctx *ctx, int32_t rows, int32_t col_warps);
+
 /* Time the inter-route evaluation kernel alone on the current state:
  * `reps` launches bracketed by CUDA events on the context's stream; writes the
  * mean milliseconds per launch.  Leaves no pending move behind.  Used to

@@ -23,6 +23,7 @@ struct tga_ctx {
     bool built = false;
     // inter-route tiles
     int tile_rows = 0, tile_warps = 0, tile_rs = 1, ntiles = 0;
+    int strip = 0;                     // strip-major inter kernel: its grid (0: one CTA per tile)
     int2 *tiles = nullptr;
     std::vector<int2> tiles_host;      // kept alive for the asynchronous upload
     // descent graph
@@ -66,10 +67,13 @@ void drop_graph(tga_ctx *c) {
     c->graph_ready = false;
 }
 
-int set_tiles(tga_ctx *c, int rows, int warps, int rs = 1) {
+// strip: run the tiles with the strip-major kernel (rows 16 or 32, 4 or 8
+// warps, no row split).
+int set_tiles(tga_ctx *c, int rows, int warps, int rs = 1, bool strip = false) {
     if (!(rows == 8 || rows == 16 || rows == 32 || rows == 64) || !(warps == 2 || warps == 4 || warps == 8) ||
         !(rs == 1 || rs == 2 || rs == 4) || warps * rs > 8 || rows % rs != 0)
         return TGA_ERR_INVALID;
+    if (strip && (rs != 1 || !(rows == 16 || rows == 32) || !(warps == 4 || warps == 8))) return TGA_ERR_INVALID;
     const int Wa = c->d.Wp - 1;   // anchor positions
     const int TC = warps * 32;
     const int nrt = (Wa + rows - 1) / rows, nct = (Wa + TC - 1) / TC;
@@ -96,20 +100,25 @@ int set_tiles(tga_ctx *c, int rows, int warps, int rs = 1) {
     c->tile_rows = rows;
     c->tile_warps = warps;
     c->tile_rs = rs;
+    c->strip = strip ? strip_grid(c->d, rows, warps, c->ntiles) : 0;
     drop_graph(c);
+    if (strip && c->ntiles > 0 && c->strip == 0) return TGA_ERR_CUDA;
     return TGA_OK;
 }
 
+// Shapes measured fastest on a GB300 before any autotuning: one CTA per
+// 16 x 64 tile for small instances (a single wave), the strip-major kernel
+// with 16-row tiles otherwise (column strips of 128 or 256 positions).
 void default_tiles(tga_ctx *c) {
     const long long pairs = (long long)c->d.Wp * c->d.Wp / 2;
     if (pairs < 2000000) set_tiles(c, 16, 2);
-    else if (pairs < 20000000) set_tiles(c, 32, 4);
-    else set_tiles(c, 32, 8);
+    else if (pairs < 20000000) set_tiles(c, 16, 4, 1, true);
+    else set_tiles(c, 16, 8, 1, true);
 }
 
 int step_once(tga_ctx *c, unsigned long long cond, int use_cond, cudaStream_t s) {
     launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, s, c->tile_rs,
-                eval_blocks(c->d, c->ntiles));
+                eval_blocks(c->d, c->ntiles, c->strip), c->strip);
     launch_apply(c->d, nullptr, cond, use_cond, s, 1);
     return check_launch();
 }
@@ -134,8 +143,8 @@ int build_graph(tga_ctx *c) {
             // branches; both fold into the same packed best key
             cudaEventRecord(c->ev_fork, c->cap);
             cudaStreamWaitEvent(c->cap2, c->ev_fork, 0);
-            const int tail = eval_blocks(c->d, c->ntiles);
-            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap, c->tile_rs, tail);
+            const int tail = eval_blocks(c->d, c->ntiles, c->strip);
+            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->cap, c->tile_rs, tail, c->strip);
             launch_intra(c->d, c->cap2, tail);
             launch_xswap(c->d, c->cap2, tail);
             cudaEventRecord(c->ev_join, c->cap2);
@@ -480,7 +489,7 @@ int tga_eval_best_move(tga_ctx *c, tga_move *out_dev) {
     if (!c->built) return TGA_ERR_STATE;
     if (!c->tiles && c->d.Wp > 2) default_tiles(c);
     launch_begin(c->d, 1, c->stream);
-    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
+    launch_eval(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs, 0, c->strip);
     launch_finalize(c->d, out_dev, c->stream);
     return check_launch();
 }
@@ -692,30 +701,33 @@ int tga_set_tile(tga_ctx *c, int32_t rows, int32_t warps) {
     if (!c->built) return TGA_ERR_STATE;
     // autotune: time every shape on the current state (evaluation only; the
     // solution is not touched), keep the fastest.
-    static const int shapes[][3] = {{8, 2, 1},  {16, 2, 1}, {16, 2, 2}, {16, 2, 4}, {16, 4, 1}, {16, 4, 2},
-                                    {32, 2, 2}, {32, 2, 4}, {32, 4, 1}, {32, 4, 2}, {64, 4, 1}, {64, 4, 2},
-                                    {32, 8, 1}, {64, 8, 1}};
+    // rows, column warps, row split, strip-major kernel
+    static const int shapes[][4] = {{8, 2, 1, 0},  {16, 2, 1, 0}, {16, 2, 2, 0}, {16, 2, 4, 0}, {16, 4, 1, 0},
+                                    {16, 4, 2, 0}, {32, 2, 2, 0}, {32, 2, 4, 0}, {32, 4, 1, 0}, {32, 4, 2, 0},
+                                    {64, 4, 1, 0}, {64, 4, 2, 0}, {32, 8, 1, 0}, {64, 8, 1, 0}, {16, 4, 1, 1},
+                                    {16, 8, 1, 1}, {32, 4, 1, 1}, {32, 8, 1, 1}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float bestms = 1e30f;
-    int br = 32, bw = 4, brs = 1;
+    int br = 32, bw = 4, brs = 1, bst = 0;
     for (const auto &s : shapes) {
-        if (set_tiles(c, s[0], s[1], s[2]) != TGA_OK) continue;
+        if (set_tiles(c, s[0], s[1], s[2], s[3] != 0) != TGA_OK) continue;
         launch_begin(c->d, 1, c->stream);
-        launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
+        launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs, 0, c->strip);
         cudaEventRecord(e0, c->stream);
         for (int k = 0; k < 5; ++k)
-            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
+            launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs, 0,
+                         c->strip);
         cudaEventRecord(e1, c->stream);
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < bestms) { bestms = ms; br = s[0]; bw = s[1]; brs = s[2]; }
+        if (ms < bestms) { bestms = ms; br = s[0]; bw = s[1]; brs = s[2]; bst = s[3]; }
     }
     // leave the context as it was before tuning (no pending key)
     cudaMemsetAsync(&c->d.ctl->best_key, 0xff, sizeof(unsigned long long), c->stream);
-    int rc = set_tiles(c, br, bw, brs);
+    int rc = set_tiles(c, br, bw, brs, bst != 0);
     if (!rc && c->mode == TGA_DESCENT_AUTO) rc = tune_descent(c, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -760,8 +772,13 @@ int tga_get_tile_shape(tga_ctx *c, int32_t *rows, int32_t *col_warps, int32_t *r
     if (!c->tiles && c->built && c->d.Wp > 2) default_tiles(c);
     *rows = c->tile_rows;
     *col_warps = c->tile_warps;
-    *row_split = c->tile_rs;
+    *row_split = c->strip ? 0 : c->tile_rs;
     return TGA_OK;
+}
+
+int tga_set_tile_strip(tga_ctx *c, int32_t rows, int32_t col_warps) {
+    if (!c) return TGA_ERR_INVALID;
+    return set_tiles(c, rows, col_warps, 1, true);
 }
 
 int tga_get_tile(tga_ctx *c, int32_t *rows, int32_t *warps) {
@@ -777,7 +794,7 @@ int tga_profile_inter(tga_ctx *c, int32_t reps, float *ms_per_launch) {
     if (!c->built) return TGA_ERR_STATE;
     if (!c->tiles && c->d.Wp > 2) default_tiles(c);
     return profile_launches(c, reps, ms_per_launch, [&] {
-        launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs);
+        launch_inter(c->d, c->tiles, c->ntiles, c->tile_rows, c->tile_warps, c->stream, c->tile_rs, 0, c->strip);
     });
 }
 

@@ -584,55 +584,46 @@ __device__ __forceinline__ int2 tile_of(int bid, int Wp, int TR, int TC) {
     return make_int2(lo, lo / g + (int)(bid - before(lo)));
 }
 
-// One tile of the inter-route pair triangle: rows p0..p0+TR-1, columns
-// q0..q0+32*NWc-1 with NWc = warps / RS.  Warp w owns the 32 columns of slice
-// w % NWc and the rows of group w / NWc (TR/RS rows each).  Every thread folds
-// its column's candidates into (best, bidx); smem must hold
-// inter_smem_bytes(TR, NWc, PD).  PD: pickups (requires TW); every load
-// excess is that of the new route's largest load (PRec constants).
-template <bool TW, bool OR, bool PD = false>
-__device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *smem, int &best, unsigned &bidx) {
-    constexpr int NG = PD ? 12 : 8;                           // int4 records per row
-    const int NW = blockDim.x >> 5, NWc = NW / RS, TC = NWc * 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cw = warp % NWc, rg = warp / NWc, rows_per = TR / RS;
-    const int i0 = rg * rows_per, i1 = i0 + rows_per;
-    const int LDT = TC + 8;
-    int *sT = smem;                                           // (TR+4) x LDT distances
-    int4 *sR = reinterpret_cast<int4 *>(smem + (TR + 4) * LDT);   // TR row records (ERec, then PRec)
-    __syncthreads();                                          // previous user of smem is done
+// The column side of an inter-route tile: the anchor av at position q and
+// its hoisted constants (ERec groups; PRec with pickups), held in registers
+// while a warp walks the rows.
+struct InterCol {
+    int q, av;
+    int4 v0, v1, v2, v3, v4, v5, v6;
+    int4 w0, w1, w2, w3;
+};
 
-    // Extraction: rows p0-1 .. p0+TR+2, positions q0-4 .. q0+TC+3
-    for (int rr = warp; rr < TR + 4; rr += NW) {
-        const int p = p0 - 1 + rr;
-        const int node = (p >= 0 && p < d.Wp) ? node_of(d.seq[p], d.n) : 0;
-        const int4 *src = reinterpret_cast<const int4 *>(d.pcol + (size_t)node * d.ldp + q0);
-        int4 *dst = reinterpret_cast<int4 *>(sT + rr * LDT);
-        for (int c = lane; c < (LDT >> 2); c += 32) dst[c] = TGA_LDG(src + c);
-    }
+template <bool TW, bool OR, bool PD>
+__device__ __forceinline__ void inter_col_load(const Dev &d, int q, InterCol &c) {
+    c.q = q;
+    c.av = (q < d.Wp) ? d.seq[q] : d.W;
+    const int4 *vr = reinterpret_cast<const int4 *>(d.erec + c.av);
+    c.v0 = TGA_LDG(vr + 0); c.v1 = TGA_LDG(vr + 1); c.v2 = TGA_LDG(vr + 2);
+    c.v3 = make_int4(0, 0, 0, 0); c.v4 = c.v3; c.v5 = c.v3; c.v6 = c.v3;
+    if (OR) c.v3 = TGA_LDG(vr + 3);
+    if (TW) { c.v4 = TGA_LDG(vr + 4); c.v5 = TGA_LDG(vr + 5); }
+    if (TW && OR) c.v6 = TGA_LDG(vr + 6);
+    c.w0 = make_int4(0, 0, 0, 0); c.w1 = c.w0; c.w2 = c.w0; c.w3 = c.w0;
     if (PD) {
-        for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
-            const int row = i / NG, g = i - row * NG;
-            const int p = p0 + row;
-            const int a = (p < d.Wp) ? d.seq[p] : d.W;
-            sR[i] = g < 8 ? TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + g)
-                          : TGA_LDG(reinterpret_cast<const int4 *>(d.prec + a) + (g - 8));
-        }
-    } else {
-        for (int i = threadIdx.x; i < TR * 8; i += blockDim.x) {
-            const int p = p0 + (i >> 3);
-            const int a = (p < d.Wp) ? d.seq[p] : d.W;
-            sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + (i & 7));
-        }
+        const int4 *pr = reinterpret_cast<const int4 *>(d.prec + c.av);
+        c.w0 = TGA_LDG(pr + 0); c.w1 = TGA_LDG(pr + 1); c.w2 = TGA_LDG(pr + 2);
+        if (OR) c.w3 = TGA_LDG(pr + 3);
     }
-    const int q = q0 + cw * 32 + lane;
-    const int av = (q < d.Wp) ? d.seq[q] : d.W;
-    const int4 *vr = reinterpret_cast<const int4 *>(d.erec + av);
-    const int4 v0 = TGA_LDG(vr + 0), v1 = TGA_LDG(vr + 1), v2 = TGA_LDG(vr + 2);
-    int4 v3 = make_int4(0, 0, 0, 0), v4 = v3, v5 = v3, v6 = v3;
-    if (OR) v3 = TGA_LDG(vr + 3);
-    if (TW) { v4 = TGA_LDG(vr + 4); v5 = TGA_LDG(vr + 5); }
-    if (TW && OR) v6 = TGA_LDG(vr + 6);
+}
+
+// Rows i0..i1-1 of a staged tile against one column: row i is the anchor at
+// position p0 + i with its records at sR[i*NG ..] (ERec groups, then PRec
+// with pickups); col points at the column's distance in the tile's row
+// "p0 - 1" (row stride LDT), so row i's stencil sits at col[(i+1)*LDT + ...].
+// Every candidate of every pair with p < q in different routes is folded
+// into (best, bidx).
+template <bool TW, bool OR, bool PD = false>
+__device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, const int *col, const int4 *sR, int LDT,
+                                           int p0, int i0, int i1, int &best, unsigned &bidx) {
+    constexpr int NG = PD ? 12 : 8;                           // int4 records per row
+    const int q = c.q, av = c.av;
+    const int4 v0 = c.v0, v1 = c.v1, v2 = c.v2, v3 = c.v3, v4 = c.v4, v5 = c.v5, v6 = c.v6;
+    const int4 w0 = c.w0, w1 = c.w1, w2 = c.w2, w3 = c.w3;
     // column fields
     const int Vroute = v0.x, Vd = v0.y, Vrem1 = v0.z, VK1 = v0.w;
     const int VLQ = v1.x, VK2 = v1.y, VLQd = v1.z, VFc = v1.w;
@@ -641,17 +632,9 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
     const int Ve = v4.x, Vl = v4.y, Vs = v4.z, Vtau = v4.w;
     const int VLg = v5.x, VtauP = v5.y, VE2 = v5.z, VL2 = v5.w;
     const int VDm2 = v6.x, VE3 = v6.y, VL3 = v6.z, VDm3 = v6.w;
-    int4 w0 = make_int4(0, 0, 0, 0), w1 = w0, w2 = w0, w3 = w0;
-    if (PD) {
-        const int4 *pr = reinterpret_cast<const int4 *>(d.prec + av);
-        w0 = TGA_LDG(pr + 0); w1 = TGA_LDG(pr + 1); w2 = TGA_LDG(pr + 2);
-        if (OR) w3 = TGA_LDG(pr + 3);
-    }
-    __syncthreads();
-
+    (void)w3;
     const int wL = d.wL, wT = d.wT;
     const unsigned W = (unsigned)d.W, W2 = W * W;
-    const int *col = sT + cw * 32 + lane + 4;
     const int *c0 = col + i0 * LDT;                           // window at row i0
     int tm10 = c0[0];
     int t0m1 = c0[LDT - 1], t00 = c0[LDT], t01 = c0[LDT + 1];
@@ -800,6 +783,53 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
         t12 = col[(i + 3) * LDT + 2];
         t21 = col[(i + 4) * LDT + 1];
     }
+}
+
+// One tile of the inter-route pair triangle: rows p0..p0+TR-1, columns
+// q0..q0+32*NWc-1 with NWc = warps / RS.  Warp w owns the 32 columns of slice
+// w % NWc and the rows of group w / NWc (TR/RS rows each).  Every thread folds
+// its column's candidates into (best, bidx); smem must hold
+// inter_smem_bytes(TR, NWc, PD).  PD: pickups (requires TW); every load
+// excess is that of the new route's largest load (PRec constants).
+template <bool TW, bool OR, bool PD = false>
+__device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *smem, int &best, unsigned &bidx) {
+    constexpr int NG = PD ? 12 : 8;                           // int4 records per row
+    const int NW = blockDim.x >> 5, NWc = NW / RS, TC = NWc * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cw = warp % NWc, rg = warp / NWc, rows_per = TR / RS;
+    const int i0 = rg * rows_per, i1 = i0 + rows_per;
+    const int LDT = TC + 8;
+    int *sT = smem;                                           // (TR+4) x LDT distances
+    int4 *sR = reinterpret_cast<int4 *>(smem + (TR + 4) * LDT);   // TR row records (ERec, then PRec)
+    __syncthreads();                                          // previous user of smem is done
+
+    // Extraction: rows p0-1 .. p0+TR+2, positions q0-4 .. q0+TC+3
+    for (int rr = warp; rr < TR + 4; rr += NW) {
+        const int p = p0 - 1 + rr;
+        const int node = (p >= 0 && p < d.Wp) ? node_of(d.seq[p], d.n) : 0;
+        const int4 *src = reinterpret_cast<const int4 *>(d.pcol + (size_t)node * d.ldp + q0);
+        int4 *dst = reinterpret_cast<int4 *>(sT + rr * LDT);
+        for (int c = lane; c < (LDT >> 2); c += 32) dst[c] = TGA_LDG(src + c);
+    }
+    if (PD) {
+        for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
+            const int row = i / NG, g = i - row * NG;
+            const int p = p0 + row;
+            const int a = (p < d.Wp) ? d.seq[p] : d.W;
+            sR[i] = g < 8 ? TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + g)
+                          : TGA_LDG(reinterpret_cast<const int4 *>(d.prec + a) + (g - 8));
+        }
+    } else {
+        for (int i = threadIdx.x; i < TR * 8; i += blockDim.x) {
+            const int p = p0 + (i >> 3);
+            const int a = (p < d.Wp) ? d.seq[p] : d.W;
+            sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + (i & 7));
+        }
+    }
+    InterCol c;
+    inter_col_load<TW, OR, PD>(d, q0 + cw * 32 + lane, c);
+    __syncthreads();
+    inter_rows<TW, OR, PD>(d, c, sT + cw * 32 + lane + 4, sR, LDT, p0, i0, i1, best, bidx);
 }
 
 // ---------------------------------------------------------------------------

@@ -337,6 +337,16 @@ __device__ inline void block_min_to(unsigned long long key, unsigned long long *
     }
 }
 
+// Strip-major order of the inter-route tiles (TR rows x TC columns with
+// g = TC / TR an integer, nrt row tiles): column strip J holds the row tiles
+// I that contain a pair p < q, i.e. I < n_J = min((J+1) g, nrt) -- the same
+// tiles as the row-major tile list.  strip_before(J) counts the tiles of
+// strips 0 .. J-1 (strips below nrt / g are not capped).
+__host__ __device__ inline long long strip_before(int J, int nrt, int g) {
+    const long long K = J < nrt / g ? J : nrt / g;
+    return (long long)g * K * (K + 1) / 2 + (long long)(J - K) * nrt;
+}
+
 // Candidates of one evaluation per operator rank from the route-length sums
 // (closed form; 0 for disabled operators).
 __host__ __device__ inline long long op_candidates(int op, long long n, long long m, unsigned mask,
@@ -428,14 +438,21 @@ void launch_build(const Dev &d, cudaStream_t s);
 // tail > 0: the evaluation of a descent step whose inter- and intra-route
 // launches have `tail` CTAs in total (eval_blocks); the last CTA to finish
 // decodes the step's plan for the apply launch that follows.
+// strip > 0: the strip-major inter-route kernel (k_eval_strip) with `strip`
+// CTAs (strip_grid); else one CTA per tile (k_eval_inter).
 void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
-                 cudaStream_t s, int rs = 1, int tail = 0);
+                 cudaStream_t s, int rs = 1, int tail = 0, int strip = 0);
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps,
-                  cudaStream_t s, int rs = 1, int tail = 0);
+                  cudaStream_t s, int rs = 1, int tail = 0, int strip = 0);
+// Grid of the strip-major kernel for a tile shape: every CTA the device can
+// hold at once, at most one per tile; 0 if the shape is not a strip shape
+// (rows 16 or 32, 4 or 8 warps).
+int strip_grid(const Dev &d, int rows, int warps, long long ntiles);
+size_t strip_smem_bytes(int rows, int warps, bool pd);
 void launch_intra(const Dev &d, cudaStream_t s, int tail = 0);
 // swaps of runs between routes (op ranks 6, 7; no-op unless enabled)
 void launch_xswap(const Dev &d, cudaStream_t s, int tail = 0);
-int eval_blocks(const Dev &d, int ntiles);
+int eval_blocks(const Dev &d, int ntiles, int strip = 0);
 // pre = 1: apply the plan decoded by the evaluation's last CTA (descent
 // steps); else decode *ext (or the best key) in the launch itself.
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond,

@@ -80,6 +80,126 @@ __global__ void __launch_bounds__(256) k_eval_inter(Dev d, int TR, int RS, int t
     if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
+// ---------------------------------------------------------------------------
+// Strip-major inter-route evaluation (the per-step paths).  The tiles of the
+// pair triangle are ordered column strip by column strip (strip J: the row
+// tiles I = 0 .. n_J - 1 that hold a pair p < q, see strip_before) and every
+// CTA of a grid sized to the resident capacity walks one contiguous range of
+// that order.  So a CTA keeps its column anchors' constants in registers for
+// a whole strip instead of gathering them for every tile, and it stages the
+// next tile's distance rows and row records with asynchronous copies
+// (cp.async, global -> shared, 16 B each) into the second of two buffers
+// while it computes the current tile.  The candidates and their order are
+// those of k_eval_inter (the same row loop, inter_rows).
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Anchor at position p for row staging (positions outside the sequence read
+// the dummy record W, whose node is the depot).
+__device__ __forceinline__ int strip_anchor(const Dev &d, int p) { return (p >= 0 && p < d.Wp) ? d.seq[p] : d.W; }
+
+// Issue the copies of one tile: TR+4 distance rows (the nodes of positions
+// p0-1 .. p0+TR+2, storage columns q0 .. q0+TC+7, i.e. positions
+// q0-4 .. q0+TC+3) and the TR row records (ERec, then PRec with pickups).
+template <bool PD>
+__device__ __forceinline__ void strip_stage(const Dev &d, int *buf, int TR, int q0, const int *s_anc) {
+    constexpr int NG = PD ? 12 : 8;
+    const int NW = blockDim.x >> 5, TC = NW * 32, LDT = TC + 8, C4 = LDT >> 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int4 *sR = reinterpret_cast<int4 *>(buf + (TR + 4) * LDT);
+    for (int r = warp; r < TR + 4; r += NW) {
+        const int node = node_of(s_anc[r], d.n);
+        const int4 *src = reinterpret_cast<const int4 *>(d.pcol + (size_t)node * d.ldp + q0);
+        int4 *dst = reinterpret_cast<int4 *>(buf + r * LDT);
+        for (int c = lane; c < C4; c += 32) cp_async16(dst + c, src + c);
+    }
+    for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
+        const int row = i / NG, g = i - row * NG;
+        const int a = s_anc[row + 1];
+        const int4 *src = g < 8 ? reinterpret_cast<const int4 *>(d.erec + a) + g
+                                : reinterpret_cast<const int4 *>(d.prec + a) + (g - 8);
+        cp_async16(sR + i, src);
+    }
+}
+
+template <bool TW, bool OR, bool PD = false>
+__global__ void __launch_bounds__(256, TW ? 3 : 4) k_eval_strip(Dev d, int TR, long long T, int tail) {
+    const int done = *(volatile int *)&d.ctl->done;
+    extern __shared__ __align__(16) int smem[];
+    constexpr int NG = PD ? 12 : 8;
+    const int NW = blockDim.x >> 5, TC = NW * 32, LDT = TC + 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int Wa = d.Wp - 1;
+    const int nrt = (Wa + TR - 1) / TR, nct = (Wa + TC - 1) / TC, g = TC / TR;
+    const int buf_ints = (TR + 4) * LDT + TR * NG * 4;
+    int *s_anc = smem + 2 * buf_ints;                    // two (TR+4)-entry anchor lists (positions p0-1 ..)
+    const long long t0 = (long long)blockIdx.x * T / gridDim.x;
+    const long long t1 = (long long)(blockIdx.x + 1) * T / gridDim.x;
+    int best = kBestInit;
+    unsigned bidx = 0xffffffffu;
+    if (t0 < t1) {
+        // strip and row tile of t0: the last strip that starts at or before t0
+        int lo = 0, hi = nct - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (strip_before(mid, nrt, g) <= t0) lo = mid;
+            else hi = mid - 1;
+        }
+        int J = lo, I = (int)(t0 - strip_before(lo, nrt, g));
+        auto next = [&](int &j, int &i) {
+            if (++i >= min((j + 1) * g, nrt)) { ++j; i = 0; }
+        };
+        // prologue: anchors of tile t0, its copies, and the anchors of t0 + 1
+        if (tid < TR + 4) s_anc[tid] = strip_anchor(d, I * TR - 1 + tid);
+        int Jn = J, In = I;
+        next(Jn, In);
+        int a_next = (t0 + 1 < t1 && tid < TR + 4) ? strip_anchor(d, In * TR - 1 + tid) : 0;
+        __syncthreads();
+        strip_stage<PD>(d, smem, TR, J * TC, s_anc);
+        cp_async_commit();
+        InterCol c;
+        int Jc = -1;
+        for (long long k = t0; k < t1; ++k) {
+            const int b = (int)((k - t0) & 1);
+            int *cur = smem + b * buf_ints;
+            const bool more = k + 1 < t1;
+            if (more) {
+                int *nanc = s_anc + (b ^ 1) * (TR + 4);
+                if (tid < TR + 4) nanc[tid] = a_next;
+                __syncthreads();                         // anchors written; the other buffer is free
+                strip_stage<PD>(d, smem + (b ^ 1) * buf_ints, TR, Jn * TC, nanc);
+                cp_async_commit();
+                int Jnn = Jn, Inn = In;
+                next(Jnn, Inn);
+                if (k + 2 < t1 && tid < TR + 4) a_next = strip_anchor(d, Inn * TR - 1 + tid);
+                cp_async_wait<1>();                      // this tile's copies are done
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();                             // ... for every thread of the block
+            if (J != Jc) {                               // a new strip: its column anchors
+                inter_col_load<TW, OR, PD>(d, J * TC + warp * 32 + lane, c);
+                Jc = J;
+            }
+            inter_rows<TW, OR, PD>(d, c, cur + warp * 32 + lane + 4,
+                                   reinterpret_cast<const int4 *>(cur + (TR + 4) * LDT), LDT, I * TR, 0, TR,
+                                   best, bidx);
+            J = Jn; I = In;
+            next(Jn, In);
+        }
+    }
+    if (done) return;
+    const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
+    block_min_to(key, &d.ctl->best_key);
+    if (tail && threadIdx.x == 0) eval_tail(d, tail);
+}
+
 // Edge-based extraction: one thread per kept pair (u, v), u a customer and
 // v one of the theta entries of u's mask row or one of the m start depots.
 // The per-operator candidate counts are folded into the control block before
@@ -359,6 +479,14 @@ int setup_kernel_attrs(int max_band) {
         e = cudaFuncSetAttribute(k_eval_inter<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_eval_inter<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_strip<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_strip<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_strip<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_strip<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eval_strip<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_eval_strip<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_apply<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
@@ -390,8 +518,35 @@ void launch_build(const Dev &d, cudaStream_t s) {
 
 long long edge_items(const Dev &d) { return (long long)d.n * (d.theta + d.m); }
 
+size_t strip_smem_bytes(int rows, int warps, bool pd) {
+    const int LDT = warps * 32 + 8;
+    const size_t buf = (size_t)(rows + 4) * LDT * sizeof(int) + (size_t)rows * (pd ? 12 : 8) * 16;
+    return 2 * buf + 2 * (size_t)(rows + 4) * sizeof(int);
+}
+
+namespace {
+const void *strip_fn(const Dev &d) {
+    const bool orr = (d.op_mask & 48u) != 0;
+    if (d.has_pd) return orr ? (const void *)k_eval_strip<true, true, true> : (const void *)k_eval_strip<true, false, true>;
+    if (d.has_tw) return orr ? (const void *)k_eval_strip<true, true> : (const void *)k_eval_strip<true, false>;
+    return orr ? (const void *)k_eval_strip<false, true> : (const void *)k_eval_strip<false, false>;
+}
+}  // namespace
+
+int strip_grid(const Dev &d, int rows, int warps, long long ntiles) {
+    if (!(rows == 16 || rows == 32) || !(warps == 4 || warps == 8) || ntiles <= 0) return 0;
+    const size_t sm = strip_smem_bytes(rows, warps, d.has_pd != 0);
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_fn(d), warps * 32, sm) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    const long long g = (long long)per * d.nsm;
+    return (int)(g < ntiles ? g : ntiles);
+}
+
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs,
-                  int tail) {
+                  int tail, int strip) {
     if (d.theta > 0) {          // edge-based extraction
         const int blocks = (int)((edge_items(d) + 255) / 256);
         const bool orr = (d.op_mask & 48u) != 0;
@@ -405,8 +560,23 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
         return;
     }
     if (ntiles <= 0) return;
-    const size_t sm = inter_smem_bytes(rows, warps, d.has_pd != 0);
     const bool orr = (d.op_mask & 48u) != 0;
+    if (strip > 0) {            // strip-major kernel: TC = 32 * warps columns, one row group
+        const size_t sm = strip_smem_bytes(rows, warps, d.has_pd != 0);
+        const int nt = warps * 32;
+        if (d.has_pd) {
+            if (orr) k_eval_strip<true, true, true><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
+            else k_eval_strip<true, false, true><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
+        } else if (d.has_tw) {
+            if (orr) k_eval_strip<true, true><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
+            else k_eval_strip<true, false><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
+        } else {
+            if (orr) k_eval_strip<false, true><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
+            else k_eval_strip<false, false><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
+        }
+        return;
+    }
+    const size_t sm = inter_smem_bytes(rows, warps, d.has_pd != 0);
     const int nt = warps * 32 * rs;
     if (d.has_pd) {             // pickups come with time windows
         if (orr) k_eval_inter<true, true, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
@@ -425,9 +595,10 @@ int intra_blocks(const Dev &d) { return d.has_tw ? d.m : (d.Wp - 1 + 7) / 8; }
 
 int xswap_blocks(const Dev &d);
 
-int eval_blocks(const Dev &d, int ntiles) {
+int eval_blocks(const Dev &d, int ntiles, int strip) {
     if (d.theta > 0) return (int)((edge_items(d) + 255) / 256) + intra_blocks(d);
-    return (ntiles > 0 ? ntiles : 0) + intra_blocks(d) + xswap_blocks(d);
+    const int inter = ntiles <= 0 ? 0 : (strip > 0 ? strip : ntiles);
+    return inter + intra_blocks(d) + xswap_blocks(d);
 }
 
 void launch_granular_setup(const Dev &d, unsigned char *rev, int *bad_dev, cudaStream_t s) {
@@ -462,8 +633,8 @@ void launch_xswap(const Dev &d, cudaStream_t s, int tail) {
 }
 
 void launch_eval(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs,
-                 int tail) {
-    launch_inter(d, tiles, ntiles, rows, warps, s, rs, tail);
+                 int tail, int strip) {
+    launch_inter(d, tiles, ntiles, rows, warps, s, rs, tail, strip);
     launch_intra(d, s, tail);
     launch_xswap(d, s, tail);
 }

@@ -101,6 +101,7 @@ EXPORTS = [
     ("tga_debug_read", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t)]),
     ("tga_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("tga_set_tile_strip", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tga_destroy", ctypes.c_int, [_P]),
     ("tga_strerror", ctypes.c_char_p, [ctypes.c_int]),
 ]
@@ -291,6 +292,10 @@ def tga_debug_read(ctx: int, what: int) -> np.ndarray:
     return buf
 
 
+def tga_set_tile_strip(ctx: int, rows: int, col_warps: int):
+    _check(_lib().tga_set_tile_strip(_P(ctx), rows, col_warps), "tga_set_tile_strip")
+
+
 def tga_set_wait_limit(ctx: int, limit_ns: int):
     _check(_lib().tga_set_wait_limit(_P(ctx), int(limit_ns)), "tga_set_wait_limit")
 
@@ -419,8 +424,12 @@ class LocalSearch:
         return tga_get_stats(self.ctx)
 
     def set_tile(self, rows=0, warps=0, row_split=None):
+        """Inter-route tile shape; row_split = 0 selects the strip-major
+        kernel (tga_set_tile_strip)."""
         if row_split is None:
             tga_set_tile(self.ctx, rows, warps)
+        elif row_split == 0:
+            tga_set_tile_strip(self.ctx, rows, warps)
         else:
             tga_set_tile_shape(self.ctx, rows, warps, row_split)
         return tga_get_tile_shape(self.ctx)

@@ -136,7 +136,7 @@ def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None, mode=None):
 
 @pytest.mark.parametrize("mode", [0, 2])       # automatic (persistent at this size), graph
 @pytest.mark.parametrize("tile", [None, (16, 2), (32, 4), (64, 8), (0, 0), (8, 2, 1), (16, 2, 2),
-                                  (32, 2, 4), (64, 4, 2)])
+                                  (32, 2, 4), (64, 4, 2), (16, 4, 0), (32, 8, 0)])    # row split 0: strip-major
 def test_config1_full_trajectory(tile, mode):
     inst, sol = I.config1(1)
     st, log, fin = _descend_gpu(inst, sol, I.MASK_CONFIG1, tile=tile, mode=mode)
@@ -183,6 +183,72 @@ def test_descent_paths_agree(kind, limit):
         for k in ("steps", "evaluations", "candidates", "final_cost", "local_optimum", "status"):
             assert sg[k] == sh[k], (mode, k)
         assert np.array_equal(lg, lh) and np.array_equal(tg, th) and np.array_equal(rg, rh), mode
+
+
+@pytest.mark.parametrize("kind", ["cvrp", "vrptw", "vrpspdtw"])
+@pytest.mark.parametrize("shape", [(16, 4), (16, 8), (32, 4), (32, 8)])
+def test_strip_kernel_stepwise(kind, shape):
+    """The strip-major inter-route kernel: every step against the oracle on
+    random instances whose tile walks span several strips, CTAs that cross
+    strip boundaries, and ragged last strips and row tiles."""
+    from paper_2506_17357_gb300 import tga as T
+    rng = np.random.default_rng(100 * ["cvrp", "vrptw", "vrpspdtw"].index(kind) + 10 * shape[0] + shape[1])
+    for rep in range(2):
+        n = int(rng.integers(40, 260))
+        if kind == "vrpspdtw":
+            inst = I.vrpspdtw(n, 500 + rep)
+            inst.capacity = 120
+            mask = I.MASK_ALL
+        elif kind == "vrptw":
+            inst = I.vrptw(n, 510 + rep)
+            inst.capacity = 120
+            mask = I.MASK_ALL
+        else:
+            inst = I.cvrp_uniform(n, 520 + rep)
+            inst.capacity = -(-int(inst.demand.sum()) // 9)
+            mask = I.MASK_CVRP_MIXED
+        sol = I.random_split_solution(inst, 530 + rep)
+        ls = LocalSearch(inst, sol, mask).build()
+        cur = sol
+        try:
+            ls.set_tile(shape[0], shape[1], 0)
+            assert ls.set_tile(shape[0], shape[1], 0) == (shape[0], shape[1], 0)
+            for step in range(40):
+                mv = ls.eval_best_move()
+                om = O.best_move(inst, cur, mask, "concat")
+                assert (mv["delta"], mv["move_index"]) == (om["delta"], om["idx"]), (n, step)
+                if om["delta"] >= 0:
+                    break
+                ls.apply_current_move()
+                cur = O.apply_move(inst, cur, om["op"], om["a"], om["b"])
+            assert ls.stats()["status"] == 0
+        finally:
+            ls.close()
+
+
+@pytest.mark.parametrize("kind", ["vrptw", "cvrp"])
+def test_strip_kernel_full_descent_equals_tile_kernel(kind):
+    """A whole descent on the graph path with the strip-major kernel gives the
+    move log, solution and counters of the one-CTA-per-tile kernel."""
+    from paper_2506_17357_gb300 import tga as T
+    if kind == "vrptw":
+        inst, sol = I.config2(2)
+        mask = I.MASK_CONFIG2
+    else:
+        inst = I.cvrp_clustered(2500, 7)
+        sol = I.random_split_solution(inst, I.solution_seed(7))
+        mask = I.MASK_CONFIG3
+    res = []
+    for tile in ((32, 4), (32, 8, 0), (16, 8, 0)):
+        st, log, fin = _descend_gpu(inst, sol, mask, tile=tile, mode=T.DESCENT_GRAPH)
+        res.append((st, log, fin))
+    st0, log0, fin0 = res[0]
+    assert st0["status"] == 0 and st0["local_optimum"] == 1
+    for st, log, fin in res[1:]:
+        for k in ("steps", "evaluations", "candidates", "final_cost", "status"):
+            assert st[k] == st0[k], k
+        assert np.array_equal(log, log0)
+        assert np.array_equal(fin.tour, fin0.tour) and np.array_equal(fin.route_start, fin0.route_start)
 
 
 def test_persistent_descent_resumes_and_reports_its_grid():

@@ -51,6 +51,30 @@ def test_noalloc_equals_context_path_on_consecutive_calls():
             ls.close()
 
 
+def test_noalloc_allocates_nothing_on_a_warm_call():
+    """The entry point's defining property: once its first call on the device
+    has looked up the scratch address, a call changes neither the device's
+    free memory nor torch's reserved memory (no cudaMalloc, no stream-ordered
+    pool growth, no allocation through torch)."""
+    inst, sol = I.config2(1)
+    ls = T.LocalSearch(inst, sol, I.MASK_CONFIG2).build()
+    try:
+        first = _noalloc(ls, I.MASK_CONFIG2)                 # warm: scratch address looked up
+        out = torch.zeros(6, dtype=torch.int32, device=ls.device)
+        torch.cuda.synchronize()
+        free0, reserved0 = torch.cuda.mem_get_info(ls.device)[0], torch.cuda.memory_reserved(ls.device)
+        for _ in range(3):
+            T.tga_eval_best_move_noalloc(ls.c_inst, ls.c_sol, I.MASK_CONFIG2, ls.stream.cuda_stream,
+                                         out.data_ptr())
+        torch.cuda.synchronize()
+        free1, reserved1 = torch.cuda.mem_get_info(ls.device)[0], torch.cuda.memory_reserved(ls.device)
+        assert (free1, reserved1) == (free0, reserved0)
+        v = out.cpu().numpy()
+        assert (int(v[0]), int(v[2]), int(v[3]), int(v[4])) == (first["delta"], first["op"], first["a"], first["b"])
+    finally:
+        ls.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     inst = I.cvrp_uniform(1300, 3)                   # n + m + 1 > 1280
     sol = I.random_split_solution(inst, 4)
