@@ -616,8 +616,10 @@ __device__ __forceinline__ void inter_col_load(const Dev &d, int q, InterCol &c)
 // with pickups); col points at the column's distance in the tile's row
 // "p0 - 1" (row stride LDT), so row i's stencil sits at col[(i+1)*LDT + ...].
 // Every candidate of every pair with p < q in different routes is folded
-// into (best, bidx).
-template <bool TW, bool OR, bool PD = false>
+// into (best, bidx).  UNR: row-loop unrolling (lets the compiler issue the
+// next rows' shared loads early; the strip kernel gains from it, the
+// one-wave persistent descent does not).
+template <bool TW, bool OR, bool PD = false, int UNR = 1>
 __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, const int *col, const int4 *sR, int LDT,
                                            int p0, int i0, int i1, int &best, unsigned &bidx) {
     constexpr int NG = PD ? 12 : 8;                           // int4 records per row
@@ -642,7 +644,7 @@ __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, cons
     int t21 = c0[3 * LDT + 1];
     int wbest = __reduce_min_sync(0xffffffffu, best);
 
-#pragma unroll 1
+#pragma unroll UNR
     for (int i = i0; i < i1; ++i) {
         const int p = p0 + i;
         const int4 u0 = sR[i * NG + 0], u1 = sR[i * NG + 1], u2 = sR[i * NG + 2];

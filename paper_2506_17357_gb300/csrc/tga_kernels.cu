@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256, TW ? 3 : 4) k_eval_strip(Dev d, int TR, l
                 inter_col_load<TW, OR, PD>(d, J * TC + warp * 32 + lane, c);
                 Jc = J;
             }
-            inter_rows<TW, OR, PD>(d, c, cur + warp * 32 + lane + 4,
+            inter_rows<TW, OR, PD, TW ? 1 : 4>(d, c, cur + warp * 32 + lane + 4,
                                    reinterpret_cast<const int4 *>(cur + (TR + 4) * LDT), LDT, I * TR, 0, TR,
                                    best, bidx);
             J = Jn; I = In;
