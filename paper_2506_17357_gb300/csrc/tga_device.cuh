@@ -2006,25 +2006,18 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
 __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
     Control *C = d.ctl;
     S.act = 0;
-    if (C->done && !ext) return;
-    if (!ext && C->status != 0) {              // an error found during the last step ends the descent
+    // the stop flag, the status and the best key in one round trip (the
+    // loads are issued together, before any of them is tested)
+    const int done = *(volatile int *)&C->done;
+    const int status = *(volatile int *)&C->status;
+    const unsigned long long best = *(volatile unsigned long long *)&C->best_key;
+    if (done && !ext) return;
+    if (!ext && status != 0) {                 // an error found during the last step ends the descent
         C->done = 1;
         return;
     }
-    unsigned long long key;
-    if (ext) {
-        key = ext->valid ? pack_key(ext->delta, ext->move_index) : kNoKey;
-    } else {
-        key = *(volatile unsigned long long *)&C->best_key;
-        if (d.log && C->evals < d.log_cap) d.log[C->evals] = key;
-        count_evaluation(d, C);
-    }
-    C->best_key = kNoKey;
-    if (key == kNoKey || key_delta(key) >= 0) {
-        C->done = 1;
-        C->local_opt = 1;
-        return;
-    }
+    const unsigned long long key = ext ? (ext->valid ? pack_key(ext->delta, ext->move_index) : kNoKey) : best;
+    const bool improving = key != kNoKey && key_delta(key) < 0;
     const unsigned idx = (unsigned)(key & 0xffffffffu);
     const unsigned W = (unsigned)d.W, W2 = W * W;
     MovePlan pl;
@@ -2032,13 +2025,29 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
     pl.a = (int)((idx % W2) / W);
     pl.b = (int)(idx % W);
     pl.delta = key_delta(key);
-    bool ok = pl.op < 8 && ((d.op_mask >> pl.op) & 1u) && pl.a >= 1 && pl.b >= 1;
+    bool ok = improving && pl.op < 8 && ((d.op_mask >> pl.op) & 1u) && pl.a >= 1 && pl.b >= 1 &&
+              pl.a < d.W && pl.b < d.W;
     int costA = 0, costB = 0;
+    BRec ba{}, bb{};
+    int qa = 0, qb = 0;
     if (ok) {
         // one round trip: the anchors' records carry route, index, route
         // length and cost; the start depot sits idx positions before the anchor
-        const BRec ba = d.brec[pl.a], bb = d.brec[pl.b];
-        const int qa = d.pos_of[pl.a], qb = d.pos_of[pl.b];
+        ba = d.brec[pl.a]; bb = d.brec[pl.b];
+        qa = d.pos_of[pl.a]; qb = d.pos_of[pl.b];
+    }
+    // the evaluation's bookkeeping, while the records are in flight
+    if (!ext) {
+        if (d.log && C->evals < d.log_cap) d.log[C->evals] = key;
+        count_evaluation(d, C);
+    }
+    C->best_key = kNoKey;
+    if (!improving) {
+        C->done = 1;
+        C->local_opt = 1;
+        return;
+    }
+    if (ok) {
         pl.A = ba.route; pl.B = bb.route; pl.i = ba.idx; pl.j = bb.idx;
         pl.LA = ba.rlen; pl.LB = bb.rlen;
         pl.pA = qa - ba.idx; pl.pB = qb - bb.idx;
