@@ -71,7 +71,9 @@ enum {
     TGA_ERR_NOMEM = 3,     /* device allocation failed */
     TGA_ERR_CUDA = 4,      /* a CUDA runtime call failed */
     TGA_ERR_TIMEOUT = 5,   /* a bounded device-side wait ran out */
-    TGA_ERR_STATE = 6      /* call not allowed in the context's current state */
+    TGA_ERR_STATE = 6,     /* call not allowed in the context's current state */
+    TGA_ERR_CHECK = 7,     /* internal consistency check: an applied move's delta differs from its evaluation */
+    TGA_ERR_BOUNDS = 8     /* index-checked build only: a device-side index check failed (tga_get_bounds_report) */
 };
 
 /* Problem data (Section 2).  has_tw = 0 is the CVRP: service, tw_early and
@@ -376,6 +378,21 @@ int tga_set_granular(tga_ctx *ctx, const int32_t *nbr_dev, int32_t theta);
  * distance copy ((n+1) rows of row_pitch int32), 7 tile list (int2).
  * Copies min(bytes, size) bytes; *size_out (may be NULL) gets the size. */
 int tga_debug_read(tga_ctx *ctx, int32_t what, void *host_dst, size_t bytes, size_t *size_out);
+
+/* Diagnostic of the index-checked build (SURVEY's stand-in for a memory
+ * checker; the paper has no counterpart).  libtga_check.so is the same
+ * library compiled with -DTGA_BOUNDS_CHECK: every indexed device access of
+ * the search state and the instance is checked against its array's extent;
+ * the first failed check is recorded and sets TGA_ERR_BOUNDS, and the access
+ * reads or writes element 0 instead, so nothing outside an array is touched.
+ * Synchronises the context's stream and writes out[0] = 1 if this library
+ * was built with the checks (0: release build, out[1..3] = 0), out[1] = the
+ * site of the first failure (file id * 100000 + source line: file ids 1
+ * tga_internal.cuh, 2 tga_device.cuh, 3 tga_kernels.cu, 4 tga_persist.cu,
+ * 5 tga_batch.cu, 6 tga_noalloc.cu; 0 = no failure), out[2] = its index,
+ * out[3] = the array's extent.  Returns TGA_ERR_INVALID for a NULL
+ * argument, TGA_ERR_CUDA if the copy fails. */
+int tga_get_bounds_report(tga_ctx *ctx, int64_t out[4]);
 
 /* Failure detection (the paper has none; the library's device-side waits
  * are its own): set the time limit of every bounded device wait of this

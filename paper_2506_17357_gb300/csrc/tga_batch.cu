@@ -16,6 +16,8 @@
 // since a job's state is rewritten by whichever SM applied the last move.
 #define TGA_LDG(p) (*(p))
 #include "tga_device.cuh"
+#undef TGA_FILE_ID
+#define TGA_FILE_ID 5
 
 namespace tga {
 
@@ -28,7 +30,7 @@ __device__ void build_job(const Dev &d, long long max_steps) {
     const int warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
     check_instance_tiles(d, 0, 1);
     __syncthreads();
-    for (int x = tid; x <= d.n; x += nthr) d.seen[x] = 0;
+    for (int x = tid; x <= d.n; x += nthr) d.seen[TGA_IX(x, d.n + 1)] = 0;
     __syncthreads();
     for (int r = tid; r < d.m; r += nthr) build_positions_route(d, r);
     __syncthreads();

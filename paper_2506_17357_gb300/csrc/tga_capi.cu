@@ -7,9 +7,24 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tga_internal.cuh"
 
 using namespace tga;
+
+namespace {
+// NVTX range around one entry point (host time: the enqueue for the
+// asynchronous calls, the whole call for the synchronising ones).  The NVTX
+// header is self-contained: without a profiler attached each range costs a
+// function-pointer test.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+}  // namespace
 
 struct tga_ctx {
     Dev d{};
@@ -394,7 +409,8 @@ const char *tga_strerror(int code) {
         case TGA_ERR_CUDA: return "CUDA runtime error";
         case TGA_ERR_TIMEOUT: return "bounded device wait expired";
         case TGA_ERR_STATE: return "call not allowed in the current state";
-        case 7: return "internal consistency check failed (applied delta differs from evaluated delta)";
+        case TGA_ERR_CHECK: return "internal consistency check failed (applied delta differs from evaluated delta)";
+        case TGA_ERR_BOUNDS: return "device index check failed (index-checked build)";
         default: return "unknown error";
     }
 }
@@ -476,6 +492,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
 }
 
 int tga_build_attrs(tga_ctx *c) {
+    const Range range("tga_build_attrs");
     if (!c) return TGA_ERR_INVALID;
     if (cudaMemsetAsync(c->d.ctl, 0, sizeof(Control), c->stream) != cudaSuccess) return TGA_ERR_CUDA;
     launch_check_instance(c->d, c->stream);
@@ -485,6 +502,7 @@ int tga_build_attrs(tga_ctx *c) {
 }
 
 int tga_eval_best_move(tga_ctx *c, tga_move *out_dev) {
+    const Range range("tga_eval_best_move");
     if (!c || !out_dev) return TGA_ERR_INVALID;
     if (!c->built) return TGA_ERR_STATE;
     if (!c->tiles && c->d.Wp > 2) default_tiles(c);
@@ -495,6 +513,7 @@ int tga_eval_best_move(tga_ctx *c, tga_move *out_dev) {
 }
 
 int tga_apply_move(tga_ctx *c, const tga_move *move_dev) {
+    const Range range("tga_apply_move");
     if (!c || !move_dev) return TGA_ERR_INVALID;
     if (!c->built) return TGA_ERR_STATE;
     launch_apply(c->d, move_dev, 0, 0, c->stream);
@@ -503,6 +522,7 @@ int tga_apply_move(tga_ctx *c, const tga_move *move_dev) {
 }
 
 int tga_descend(tga_ctx *c, int64_t max_steps, tga_stats *out_host) {
+    const Range range("tga_descend");
     if (!c || max_steps < 0) return TGA_ERR_INVALID;
     int rc = descend_launch(c, max_steps);
     if (rc) return rc;
@@ -514,6 +534,7 @@ int tga_descend(tga_ctx *c, int64_t max_steps, tga_stats *out_host) {
 }
 
 int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_host) {
+    const Range range("tga_descend_batch");
     if (!ctxs || n < 0 || max_steps < 0) return TGA_ERR_INVALID;
     if (n == 0) return TGA_OK;
     for (int i = 0; i < n; ++i) {
@@ -536,6 +557,7 @@ int tga_descend_batch(tga_ctx **ctxs, int n, int64_t max_steps, tga_stats *out_h
 }
 
 int tga_batch_autotune(tga_ctx **ctxs, int n, int32_t *rows_out) {
+    const Range range("tga_batch_autotune");
     if (!ctxs || n < 0) return TGA_ERR_INVALID;
     static const int bounds[] = {400, 800, 1400, 1 << 30};
     static const int trs[] = {16, 32, 64};
@@ -577,6 +599,7 @@ int tga_batch_autotune(tga_ctx **ctxs, int n, int32_t *rows_out) {
 }
 
 int tga_descend_async(tga_ctx *c, int64_t max_steps) {
+    const Range range("tga_descend_async");
     if (!c || max_steps < 0) return TGA_ERR_INVALID;
     return descend_launch(c, max_steps);
 }
@@ -696,6 +719,7 @@ static int tune_descent(tga_ctx *c, cudaEvent_t e0, cudaEvent_t e1) {
 }
 
 int tga_set_tile(tga_ctx *c, int32_t rows, int32_t warps) {
+    const Range range("tga_set_tile");
     if (!c) return TGA_ERR_INVALID;
     if (rows != 0 || warps != 0) return set_tiles(c, rows, warps);
     if (!c->built) return TGA_ERR_STATE;
@@ -826,6 +850,21 @@ int tga_debug_read(tga_ctx *c, int32_t what, void *host_dst, size_t bytes, size_
         if (cudaMemcpy(host_dst, src, bytes < size ? bytes : size, cudaMemcpyDeviceToHost) != cudaSuccess)
             return TGA_ERR_CUDA;
     }
+    return TGA_OK;
+}
+
+int tga_get_bounds_report(tga_ctx *c, int64_t out[4]) {
+    if (!c || !out) return TGA_ERR_INVALID;
+    out[0] = out[1] = out[2] = out[3] = 0;
+#ifdef TGA_BOUNDS_CHECK
+    out[0] = 1;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return TGA_ERR_CUDA;
+    Control h;
+    if (cudaMemcpy(&h, c->d.ctl, sizeof(Control), cudaMemcpyDeviceToHost) != cudaSuccess) return TGA_ERR_CUDA;
+    out[1] = h.bad_site;
+    out[2] = h.bad_index;
+    out[3] = h.bad_limit;
+#endif
     return TGA_OK;
 }
 

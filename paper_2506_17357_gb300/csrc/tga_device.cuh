@@ -19,6 +19,8 @@
 #endif
 
 #include "tga_internal.cuh"
+#undef TGA_FILE_ID
+#define TGA_FILE_ID 2
 
 namespace tga {
 // internal linkage: each translation unit compiles these with its own TGA_LDG
@@ -120,7 +122,7 @@ __device__ __forceinline__ Ld shfl_ld_idx(const Ld &s, int src) {
 }
 
 __device__ __forceinline__ int route_node(const Dev &d, int start, int L, int k) {
-    return (k <= 0 || k > L) ? 0 : d.seq[start + k];
+    return (k <= 0 || k > L) ? 0 : d.seq[TGA_IX(start + k, d.Wp)];
 }
 
 __device__ __forceinline__ int route_anchor(const Dev &d, int r, int start, int L, int k) {
@@ -163,7 +165,7 @@ __device__ __forceinline__ XRec xrec_none() {
 // XS: also the constants of the swaps of runs (XRec).
 template <bool PD, bool XS = false>
 __device__ void rebuild_route(const Dev &d, int r, int lane) {
-    const RouteRec rr = d.rrec[r];
+    const RouteRec rr = d.rrec[TGA_IX(r, d.m)];
     const int st = rr.start, L = rr.len, E = L + 2;
     const bool tw = d.has_tw != 0;
     constexpr bool pd = PD;
@@ -198,7 +200,7 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
         if (valid) {
             if (k <= L) {
                 const int a = route_anchor(d, r, st, L, k);
-                BRec *b = d.brec + a;
+                BRec *b = d.brec + TGA_IX(a, d.W + 1);
                 b->node = x; b->route = r; b->idx = k;
                 b->tau = tw ? s.E + s.D - s.TW : 0;
                 b->twf = tw ? s.TW : 0;
@@ -206,7 +208,7 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
                 b->loadf = s.load;
                 if (pd) { b->lof = l.o; b->lmf = l.m; }
             } else {
-                RouteRec *R = d.rrec + r;
+                RouteRec *R = d.rrec + TGA_IX(r, d.m);
                 const int twr = tw ? s.TW : 0;
                 const int lm = pd ? l.m : s.load;
                 R->load = s.load;
@@ -248,7 +250,7 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
         }
         if (valid && k >= 1) {
             const int a = route_anchor(d, r, st, L, k - 1);
-            BRec *b = d.brec + a;
+            BRec *b = d.brec + TGA_IX(a, d.W + 1);
             b->Lg = tw ? s.L : 0;
             b->twg = tw ? s.TW : 0;
             b->distg = s.dist;
@@ -261,18 +263,20 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
     }
     __syncwarp();
     // ---- hoisted constants per anchor
-    const RouteRec R = d.rrec[r];
+    const RouteRec R = d.rrec[TGA_IX(r, d.m)];
     const unsigned mask = d.op_mask;
     const int Q = d.Q;
     for (int k = lane; k <= L; k += 32) {
         const int a = route_anchor(d, r, st, L, k);
         const int x = k == 0 ? 0 : a;
-        const BRec b = d.brec[a];
+        const BRec b = d.brec[TGA_IX(a, d.W + 1)];
         ERec e;
         PRec pr{};
-        e.route = r; e.anchor = a; e.node = x; e.idx = k; e.pad0 = 0; e.pad1 = 0;
-        d.brec[a].rlen = L;
-        d.brec[a].rcost = R.cost;
+        e.route = r; e.anchor = a; e.node = x; e.idx = k;
+        e.succ = k + 1 <= L ? route_node(d, st, L, k + 1) : 0;
+        e.succ2 = k + 2 <= L ? route_node(d, st, L, k + 2) : 0;
+        d.brec[TGA_IX(a, d.W + 1)].rlen = L;
+        d.brec[TGA_IX(a, d.W + 1)].rcost = R.cost;
         e.d = __ldg(d.demand + x);
         e.e = tw ? __ldg(d.early + x) : 0;
         e.l = tw ? __ldg(d.late + x) : 0;
@@ -297,10 +301,10 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
         }
         if (k == 0) {
             e.rem1 = kBig; e.K2 = kBig; e.LQd = 0; e.tauP = 0;
-            if (XS) d.xrec[a] = xrec_none();
+            if (XS) d.xrec[TGA_IX(a, d.W + 1)] = xrec_none();
         } else {
             const int xm = route_node(d, st, L, k - 1);
-            const BRec bp = d.brec[route_anchor(d, r, st, L, k - 1)];
+            const BRec bp = d.brec[TGA_IX(route_anchor(d, r, st, L, k - 1), d.W + 1)];
             const int xn = route_node(d, st, L, k + 1);
             const int cmn = dmat(d, xm, xn);
             if (XS) {
@@ -309,11 +313,11 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
                 int d1 = 0, g1dist = 0, g1tw = 0, g1L = 0;
                 if (has1) {
                     run = seg_cat(seg_node(d, x, dmat(d, x, xn)), seg_node(d, xn, 0));
-                    const BRec b1 = d.brec[xn];
+                    const BRec b1 = d.brec[TGA_IX(xn, d.W + 1)];
                     d1 = __ldg(d.demand + xn);
                     g1dist = b1.distg; g1tw = b1.twg; g1L = b1.Lg;
                 }
-                d.xrec[a] = make_xrec(wTe, R.cost, R.load, Q, bp.distf, bp.twf, bp.tau, b.distg, b.twg, b.Lg, has1,
+                d.xrec[TGA_IX(a, d.W + 1)] = make_xrec(wTe, R.cost, R.load, Q, bp.distf, bp.twf, bp.tau, b.distg, b.twg, b.Lg, has1,
                                       g1dist, g1tw, g1L, run, d1, e.e, e.l, e.s, e.d);
             }
             const int twr = tw ? bp.twf + b.twg + max(bp.tau + cmn - b.Lg, 0) : 0;
@@ -338,7 +342,7 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
                     if (pd) rl = ld_cat(rl, ld_node(d, y));
                 }
                 const int w = route_node(d, st, L, k + K - 1);
-                const BRec bw = d.brec[w];
+                const BRec bw = d.brec[TGA_IX(w, d.W + 1)];
                 const int wn = route_node(d, st, L, k + K);
                 const int c2 = dmat(d, xm, wn);
                 const int twk = tw ? bp.twf + bw.twg + max(bp.tau + c2 - bw.Lg, 0) : 0;
@@ -356,8 +360,8 @@ __device__ void rebuild_route(const Dev &d, int r, int lane) {
                 }
             }
         }
-        d.erec[a] = e;
-        if (pd) d.prec[a] = pr;
+        d.erec[TGA_IX(a, d.W + 1)] = e;
+        if (pd) d.prec[TGA_IX(a, d.W + 1)] = pr;
     }
 }
 
@@ -446,28 +450,28 @@ __device__ void check_instance_tiles(const Dev &d, int part, int nparts) {
 __device__ void build_positions_route(const Dev &d, int r) {
     Control *C = d.ctl;
     if (r == 0) {
-        if (d.route_start[0] != 0 || d.route_start[d.m] != d.n) set_status(C, TGA_ERR_INVALID);
-        d.seq[d.n + d.m] = d.W;   // sentinel (end depot of the last route)
+        if (d.route_start[TGA_IX(0, d.m + 1)] != 0 || d.route_start[TGA_IX(d.m, d.m + 1)] != d.n) set_status(C, TGA_ERR_INVALID);
+        d.seq[TGA_IX(d.n + d.m, d.Wp)] = d.W;   // sentinel (end depot of the last route)
     }
     if (r >= d.m) return;
-    const int a = d.route_start[r], b = d.route_start[r + 1];
+    const int a = d.route_start[TGA_IX(r, d.m + 1)], b = d.route_start[TGA_IX(r + 1, d.m + 1)];
     if (a < 0 || b < a || b > d.n) { set_status(C, TGA_ERR_INVALID); return; }
     const int p = a + r;
-    d.seq[p] = d.n + 1 + r;
-    d.pos_of[d.n + 1 + r] = p;
-    d.rrec[r].start = p;
-    d.rrec[r].len = b - a;
+    d.seq[TGA_IX(p, d.Wp)] = d.n + 1 + r;
+    d.pos_of[TGA_IX(d.n + 1 + r, d.W + 1)] = p;
+    d.rrec[TGA_IX(r, d.m)].start = p;
+    d.rrec[TGA_IX(r, d.m)].len = b - a;
     for (int t = a; t < b; ++t) {
-        const int x = d.tour[t];
+        const int x = d.tour[TGA_IX(t, d.n)];
         if (x < 1 || x > d.n) { set_status(C, TGA_ERR_INVALID); continue; }
-        d.seq[t + r + 1] = x;
-        d.pos_of[x] = t + r + 1;
-        atomicAdd(&d.seen[x], 1);
+        d.seq[TGA_IX(t + r + 1, d.Wp)] = x;
+        d.pos_of[TGA_IX(x, d.W + 1)] = t + r + 1;
+        atomicAdd(&d.seen[TGA_IX(x, d.n + 1)], 1);
     }
 }
 
 __device__ __forceinline__ void check_perm_one(const Dev &d, int x) {
-    if (x >= 1 && x <= d.n && d.seen[x] != 1) set_status(d.ctl, TGA_ERR_INVALID);
+    if (x >= 1 && x <= d.n && d.seen[TGA_IX(x, d.n + 1)] != 1) set_status(d.ctl, TGA_ERR_INVALID);
 }
 
 
@@ -479,7 +483,7 @@ __device__ void finish_block(const Dev &d) {
     int maxL = 0, maxLoad = 0;
     if (C->status == 0) {
         for (int r = threadIdx.x; r < d.m; r += blockDim.x) {
-            const RouteRec R = d.rrec[r];
+            const RouteRec R = d.rrec[TGA_IX(r, d.m)];
             cost += R.cost;
             l2 += (long long)R.len * R.len;
             l1 += max(R.len - 1, 0);
@@ -532,12 +536,12 @@ __device__ void finish_block(const Dev &d) {
         ERec e{};
         e.route = -1; e.anchor = d.W;
         e.rem1 = kBig; e.K1 = kBig; e.K2 = kBig; e.Fc = kBig; e.C2 = kBig; e.C3 = kBig;
-        d.erec[d.W] = e;
+        d.erec[TGA_IX(d.W, d.W + 1)] = e;
         BRec b{};
         b.route = -1;
-        d.brec[d.W] = b;
-        if (d.has_pd) d.prec[d.W] = PRec{};
-        if (d.op_mask & kExtOps) d.xrec[d.W] = xrec_none();
+        d.brec[TGA_IX(d.W, d.W + 1)] = b;
+        if (d.has_pd) d.prec[TGA_IX(d.W, d.W + 1)] = PRec{};
+        if (d.op_mask & kExtOps) d.xrec[TGA_IX(d.W, d.W + 1)] = xrec_none();
     }
 }
 
@@ -548,8 +552,8 @@ __device__ void pcol_init_range(const Dev &d, long long t0, long long stride) {
     for (long long t = t0; t < tot; t += stride) {
         const int x = (int)(t / d.ldp), c = (int)(t - (long long)x * d.ldp);
         const int q = c - kColOff;
-        const int node = (q >= 0 && q < d.Wp) ? node_of(d.seq[q], d.n) : 0;
-        d.pcol[t] = dmat(d, x, node);
+        const int node = (q >= 0 && q < d.Wp) ? node_of(d.seq[TGA_IX(q, d.Wp)], d.n) : 0;
+        d.pcol[TGA_IX(t, (long long)(d.n + 1) * d.ldp)] = dmat(d, x, node);
     }
 }
 
@@ -596,8 +600,8 @@ struct InterCol {
 template <bool TW, bool OR, bool PD>
 __device__ __forceinline__ void inter_col_load(const Dev &d, int q, InterCol &c) {
     c.q = q;
-    c.av = (q < d.Wp) ? d.seq[q] : d.W;
-    const int4 *vr = reinterpret_cast<const int4 *>(d.erec + c.av);
+    c.av = (q < d.Wp) ? d.seq[TGA_IX(q, d.Wp)] : d.W;
+    const int4 *vr = reinterpret_cast<const int4 *>(d.erec + TGA_IX(c.av, d.W + 1));
     c.v0 = TGA_LDG(vr + 0); c.v1 = TGA_LDG(vr + 1); c.v2 = TGA_LDG(vr + 2);
     c.v3 = make_int4(0, 0, 0, 0); c.v4 = c.v3; c.v5 = c.v3; c.v6 = c.v3;
     if (OR) c.v3 = TGA_LDG(vr + 3);
@@ -605,7 +609,7 @@ __device__ __forceinline__ void inter_col_load(const Dev &d, int q, InterCol &c)
     if (TW && OR) c.v6 = TGA_LDG(vr + 6);
     c.w0 = make_int4(0, 0, 0, 0); c.w1 = c.w0; c.w2 = c.w0; c.w3 = c.w0;
     if (PD) {
-        const int4 *pr = reinterpret_cast<const int4 *>(d.prec + c.av);
+        const int4 *pr = reinterpret_cast<const int4 *>(d.prec + TGA_IX(c.av, d.W + 1));
         c.w0 = TGA_LDG(pr + 0); c.w1 = TGA_LDG(pr + 1); c.w2 = TGA_LDG(pr + 2);
         if (OR) c.w3 = TGA_LDG(pr + 3);
     }
@@ -701,7 +705,16 @@ __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, cons
                 dO3b += wL * max(max(max(UIA + Vld3, UIB + VLM3), UIC + VLO3), 0);
             }
         }
-        if (TW) {
+        const bool skip = (Uroute == Vroute) | (p >= q);
+        // Every time-window term below adds a non-negative warp penalty, so
+        // the deltas without them bound the pair's deltas from below.  When
+        // no lane's bound can tie or beat the warp's best so far, no
+        // candidate of this row can hold the argmin: the terms are skipped
+        // for the whole warp, and the minimum test further down then fails
+        // for every lane, exactly as it would with the terms added.
+        int lb = min(min(dR1, dR2), min(dS, dX));
+        if (OR) lb = min(lb, min(min(dO2a, dO2b), min(dO3a, dO3b)));
+        if (TW && __any_sync(0xffffffffu, !skip && lb <= wbest)) {
             const int4 u4 = sR[i * NG + 4], u5 = sR[i * NG + 5];
             const int Ue = u4.x, Ul = u4.y, Us = u4.z, Utau = u4.w;
             const int ULg = u5.x, UtauP = u5.y;
@@ -751,7 +764,6 @@ __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, cons
         }
         int m = min(min(dR1, dR2), min(dS, dX));
         if (OR) m = min(m, min(min(dO2a, dO2b), min(dO3a, dO3b)));
-        const bool skip = (Uroute == Vroute) | (p >= q);
         // Only a pair that can tie or beat the warp's best so far can hold the
         // final argmin (every lane's best bounds the global minimum from
         // above), so the packed keys are formed only then; filtering on the
@@ -808,8 +820,9 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
     // Extraction: rows p0-1 .. p0+TR+2, positions q0-4 .. q0+TC+3
     for (int rr = warp; rr < TR + 4; rr += NW) {
         const int p = p0 - 1 + rr;
-        const int node = (p >= 0 && p < d.Wp) ? node_of(d.seq[p], d.n) : 0;
-        const int4 *src = reinterpret_cast<const int4 *>(d.pcol + (size_t)node * d.ldp + q0);
+        const int node = (p >= 0 && p < d.Wp) ? node_of(d.seq[TGA_IX(p, d.Wp)], d.n) : 0;
+        const int4 *src =
+            reinterpret_cast<const int4 *>(d.pcol + (size_t)TGA_IX(node, d.n + 1) * d.ldp + TGA_IX(q0, d.ldp - LDT + 1));
         int4 *dst = reinterpret_cast<int4 *>(sT + rr * LDT);
         for (int c = lane; c < (LDT >> 2); c += 32) dst[c] = TGA_LDG(src + c);
     }
@@ -817,15 +830,15 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
         for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
             const int row = i / NG, g = i - row * NG;
             const int p = p0 + row;
-            const int a = (p < d.Wp) ? d.seq[p] : d.W;
-            sR[i] = g < 8 ? TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + g)
-                          : TGA_LDG(reinterpret_cast<const int4 *>(d.prec + a) + (g - 8));
+            const int a = (p < d.Wp) ? d.seq[TGA_IX(p, d.Wp)] : d.W;
+            sR[i] = g < 8 ? TGA_LDG(reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + g)
+                          : TGA_LDG(reinterpret_cast<const int4 *>(d.prec + TGA_IX(a, d.W + 1)) + (g - 8));
         }
     } else {
         for (int i = threadIdx.x; i < TR * 8; i += blockDim.x) {
             const int p = p0 + (i >> 3);
-            const int a = (p < d.Wp) ? d.seq[p] : d.W;
-            sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + a) + (i & 7));
+            const int a = (p < d.Wp) ? d.seq[TGA_IX(p, d.Wp)] : d.W;
+            sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + (i & 7));
         }
     }
     InterCol c;
@@ -836,106 +849,98 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
 
 // ---------------------------------------------------------------------------
 // inter-route evaluation, edge-based extraction (Section 5.3.1): the
-// candidates of one directed mask edge u -> v (v a customer in u's mask row)
-// or of u and the start depot v of another route, with the expressions of
-// inter_tile and the stencil distances gathered from the matrix by the
-// positional index.  Kept per edge: u (and its runs of 2 and 3) moved after
-// v; swap and 2-opt* on a customer edge once per unordered pair (rev: the
-// reverse entry exists, so only the edge with u < v takes them); 2-opt* of u
-// with a start depot.  Intra-route pairs are left to the route kernels.
-// Returns a bit mask of the operator ranks evaluated (one candidate each).
+// candidates of one pair of a customer u and an anchor v of another route --
+// v a customer of u's mask row (a directed mask edge u -> v) or the start
+// depot of another route -- with the expressions of inter_tile.  The caller
+// supplies u's ERec groups g0..g6, v's groups g0, g1, g2, g4, g5 and the
+// stencil distances
+//   t00 = c(u, v)   t01 = c(u, v+)   t10 = c(u+, v)   t11 = c(u+, v+)
+//   t21 = c(u++, v+)   tm10 = c(u-, v)   t0m1 = c(u, v-)
+// (x+ / x- the nodes after / before x in the giant sequence, a depot being
+// node 0; tm10 and t0m1 are read only for a customer v).  Kept per pair: u
+// and its runs of 2 and 3 moved after v; swap and 2-opt* once per unordered
+// customer pair (pair_once); 2-opt* of u with a start depot.  Intra-route
+// pairs are left to the route kernels.  Returns a bit mask of the operator
+// ranks evaluated (one candidate each).
+struct EdgeStencil {
+    int t00, t01, t10, t11, t21, tm10, t0m1;
+};
+
 template <bool TW, bool OR>
-__device__ unsigned edge_candidates(const Dev &d, int u, int v, bool rev, int &best, unsigned &bidx) {
+__device__ __forceinline__ unsigned edge_pair(const Dev &d, int u, int v, bool vcust, bool pair_once,
+                                              const int4 &u0, const int4 &u1, const int4 &u2, const int4 &u3,
+                                              const int4 &u4, const int4 &u5, const int4 &u6, const int4 &v0,
+                                              const int4 &v1, const int4 &v2, const int4 &v4, const int4 &v5,
+                                              const EdgeStencil &t, int &best, unsigned &bidx) {
     const unsigned mask = d.op_mask;
-    const int4 *ur = reinterpret_cast<const int4 *>(d.erec + u);
-    const int4 *vr = reinterpret_cast<const int4 *>(d.erec + v);
-    const int4 u0 = TGA_LDG(ur + 0), u1 = TGA_LDG(ur + 1), u2 = TGA_LDG(ur + 2);
-    const int4 v0 = TGA_LDG(vr + 0), v1 = TGA_LDG(vr + 1), v2 = TGA_LDG(vr + 2);
-    int4 u3 = make_int4(0, 0, 0, 0), u4 = u3, u5 = u3, u6 = u3, v4 = u3, v5 = u3;
-    if (OR) u3 = TGA_LDG(ur + 3);
-    if (TW) { u4 = TGA_LDG(ur + 4); u5 = TGA_LDG(ur + 5); v4 = TGA_LDG(vr + 4); v5 = TGA_LDG(vr + 5); }
-    if (TW && OR) u6 = TGA_LDG(ur + 6);
-    const int pu = TGA_LDG(d.pos_of + u), pv = TGA_LDG(d.pos_of + v);
     const int Uroute = u0.x, Vroute = v0.x;
     unsigned evaluated = 0;
-    if (Uroute != Vroute) {
-        const bool vcust = v <= d.n;
-        // neighbours in the giant sequence (the next route's start depot stands
-        // for the end depot; past the sentinel, the depot)
-        auto nd = [&](int p) { return (p >= 0 && p < d.Wp) ? node_of(TGA_LDG(d.seq + p), d.n) : 0; };
-        const int xu = u, xv = vcust ? v : 0;
-        const int um = nd(pu - 1), up = nd(pu + 1), upp = nd(pu + 2);
-        const int vm = vcust ? nd(pv - 1) : 0, vp = nd(pv + 1), vpp = nd(pv + 2);
-        const int t00 = dmat(d, xu, xv), t01 = dmat(d, xu, vp), t10 = dmat(d, up, xv), t11 = dmat(d, up, vp);
-        const int t21 = dmat(d, upp, vp), t12 = dmat(d, up, vpp), tm10 = dmat(d, um, xv), t0m1 = dmat(d, xu, vm);
-        const int wL = d.wL, wT = d.wT;
-        const unsigned W = (unsigned)d.W, W2 = W * W;
-        const int Ud = u0.y, Urem1 = u0.z, UK2 = u1.y, ULQd = u1.z, UFc = u1.w;
-        const int UGc = u2.x, Uloadf = u2.y, UloadgQ = u2.z;
-        const int Vd = v0.y, VK1 = v0.w, VLQ = v1.x, VK2 = v1.y, VLQd = v1.z, VFc = v1.w;
-        const int VGc = v2.x, Vloadf = v2.y, VloadgQ = v2.z;
-        const int Ue = u4.x, Ul = u4.y, Us = u4.z, Utau = u4.w, ULg = u5.x, UtauP = u5.y;
-        const int Ve = v4.x, Vl = v4.y, Vs = v4.z, Vtau = v4.w, VLg = v5.x, VtauP = v5.y;
-        const unsigned au = (unsigned)u, av = (unsigned)v;
-        // u moved after v
-        if ((mask & 1u) && Urem1 < (kBig >> 1)) {
-            int dl = Urem1 + VK1 + t00 + t01 + wL * max(VLQ + Ud, 0);
+    const int t00 = t.t00, t01 = t.t01, t10 = t.t10, t11 = t.t11, t21 = t.t21, tm10 = t.tm10, t0m1 = t.t0m1;
+    const int wL = d.wL, wT = d.wT;
+    const unsigned W = (unsigned)d.W, W2 = W * W;
+    const int Ud = u0.y, Urem1 = u0.z, UK2 = u1.y, ULQd = u1.z, UFc = u1.w;
+    const int UGc = u2.x, Uloadf = u2.y, UloadgQ = u2.z;
+    const int Vd = v0.y, VK1 = v0.w, VLQ = v1.x, VK2 = v1.y, VLQd = v1.z, VFc = v1.w;
+    const int VGc = v2.x, Vloadf = v2.y, VloadgQ = v2.z;
+    const int Ue = u4.x, Ul = u4.y, Us = u4.z, Utau = u4.w, ULg = u5.x, UtauP = u5.y;
+    const int Ve = v4.x, Vl = v4.y, Vs = v4.z, Vtau = v4.w, VLg = v5.x, VtauP = v5.y;
+    const unsigned au = (unsigned)u, av = (unsigned)v;
+    // u moved after v
+    if ((mask & 1u) && Urem1 < (kBig >> 1)) {
+        int dl = Urem1 + VK1 + t00 + t01 + wL * max(VLQ + Ud, 0);
+        if (TW) {
+            const int a1 = Vtau + t00, w1 = max(a1 - Ul, 0);
+            const int a2 = max(a1, Ue) - w1 + Us + t01, w2 = max(a2 - VLg, 0);
+            dl += wT * (w1 + w2);
+        }
+        evaluated |= 1u;
+        TGA_TRY(dl, au * W + av);
+    }
+    // the runs of 2 and 3 starting at u moved after v
+    if (OR) {
+        const int UC2 = u3.x, Uld2 = u3.y, UC3 = u3.z, Uld3 = u3.w;
+        if (UC2 < (kBig >> 1)) {
+            int dl = UC2 + VK1 + t00 + t11 + wL * max(VLQ + Uld2, 0);
             if (TW) {
-                const int a1 = Vtau + t00, w1 = max(a1 - Ul, 0);
-                const int a2 = max(a1, Ue) - w1 + Us + t01, w2 = max(a2 - VLg, 0);
+                const int UE2 = u5.z, UL2 = u5.w, UDm2 = u6.x;
+                const int a1 = Vtau + t00, w1 = max(a1 - UL2, 0);
+                const int a2 = max(a1, UE2) - w1 + UDm2 + t11, w2 = max(a2 - VLg, 0);
                 dl += wT * (w1 + w2);
             }
-            evaluated |= 1u;
-            TGA_TRY(dl, au * W + av);
+            evaluated |= 16u;
+            TGA_TRY(dl, 4u * W2 + au * W + av);
         }
-        // the runs of 2 and 3 starting at u moved after v
-        if (OR) {
-            const int UC2 = u3.x, Uld2 = u3.y, UC3 = u3.z, Uld3 = u3.w;
-            if (UC2 < (kBig >> 1)) {
-                int dl = UC2 + VK1 + t00 + t11 + wL * max(VLQ + Uld2, 0);
-                if (TW) {
-                    const int UE2 = u5.z, UL2 = u5.w, UDm2 = u6.x;
-                    const int a1 = Vtau + t00, w1 = max(a1 - UL2, 0);
-                    const int a2 = max(a1, UE2) - w1 + UDm2 + t11, w2 = max(a2 - VLg, 0);
-                    dl += wT * (w1 + w2);
-                }
-                evaluated |= 16u;
-                TGA_TRY(dl, 4u * W2 + au * W + av);
-            }
-            if (UC3 < (kBig >> 1)) {
-                int dl = UC3 + VK1 + t00 + t21 + wL * max(VLQ + Uld3, 0);
-                if (TW) {
-                    const int UE3 = u6.y, UL3 = u6.z, UDm3 = u6.w;
-                    const int a1 = Vtau + t00, w1 = max(a1 - UL3, 0);
-                    const int a2 = max(a1, UE3) - w1 + UDm3 + t21, w2 = max(a2 - VLg, 0);
-                    dl += wT * (w1 + w2);
-                }
-                evaluated |= 32u;
-                TGA_TRY(dl, 5u * W2 + au * W + av);
-            }
-        }
-        const bool pair_once = vcust && (!rev || au < av);
-        // swap u <-> v
-        if ((mask & 2u) && pair_once) {
-            int dl = UK2 + VK2 + tm10 + t10 + t0m1 + t01 + wL * (max(ULQd + Vd, 0) + max(VLQd + Ud, 0));
+        if (UC3 < (kBig >> 1)) {
+            int dl = UC3 + VK1 + t00 + t21 + wL * max(VLQ + Uld3, 0);
             if (TW) {
-                const int a1 = UtauP + tm10, w1 = max(a1 - Vl, 0);
-                const int a2 = max(a1, Ve) - w1 + Vs + t10, w2 = max(a2 - ULg, 0);
-                const int b1 = VtauP + t0m1, x1 = max(b1 - Ul, 0);
-                const int b2 = max(b1, Ue) - x1 + Us + t01, x2 = max(b2 - VLg, 0);
-                dl += wT * (w1 + w2 + x1 + x2);
+                const int UE3 = u6.y, UL3 = u6.z, UDm3 = u6.w;
+                const int a1 = Vtau + t00, w1 = max(a1 - UL3, 0);
+                const int a2 = max(a1, UE3) - w1 + UDm3 + t21, w2 = max(a2 - VLg, 0);
+                dl += wT * (w1 + w2);
             }
-            evaluated |= 2u;
-            TGA_TRY(dl, W2 + min(au, av) * W + max(au, av));
+            evaluated |= 32u;
+            TGA_TRY(dl, 5u * W2 + au * W + av);
         }
-        // 2-opt*: head(u) + tail after v, head(v) + tail after u
-        if ((mask & 8u) && (pair_once || !vcust)) {
-            int dl = UFc + VGc + VFc + UGc + t01 + t10 +
-                     wL * (max(Uloadf + VloadgQ, 0) + max(Vloadf + UloadgQ, 0));
-            if (TW) dl += wT * (max(Utau + t01 - VLg, 0) + max(Vtau + t10 - ULg, 0));
-            evaluated |= 8u;
-            TGA_TRY(dl, 3u * W2 + (Uroute < Vroute ? au * W + av : av * W + au));
+    }
+    // swap u <-> v
+    if ((mask & 2u) && vcust && pair_once) {
+        int dl = UK2 + VK2 + tm10 + t10 + t0m1 + t01 + wL * (max(ULQd + Vd, 0) + max(VLQd + Ud, 0));
+        if (TW) {
+            const int a1 = UtauP + tm10, w1 = max(a1 - Vl, 0);
+            const int a2 = max(a1, Ve) - w1 + Vs + t10, w2 = max(a2 - ULg, 0);
+            const int b1 = VtauP + t0m1, x1 = max(b1 - Ul, 0);
+            const int b2 = max(b1, Ue) - x1 + Us + t01, x2 = max(b2 - VLg, 0);
+            dl += wT * (w1 + w2 + x1 + x2);
         }
+        evaluated |= 2u;
+        TGA_TRY(dl, W2 + min(au, av) * W + max(au, av));
+    }
+    // 2-opt*: head(u) + tail after v, head(v) + tail after u
+    if ((mask & 8u) && (pair_once || !vcust)) {
+        int dl = UFc + VGc + VFc + UGc + t01 + t10 + wL * (max(Uloadf + VloadgQ, 0) + max(Vloadf + UloadgQ, 0));
+        if (TW) dl += wT * (max(Utau + t01 - VLg, 0) + max(Vtau + t10 - ULg, 0));
+        evaluated |= 8u;
+        TGA_TRY(dl, 3u * W2 + (Uroute < Vroute ? au * W + av : av * W + au));
     }
     return evaluated;
 }
@@ -1204,7 +1209,7 @@ __device__ void intra_anchor(const RouteView &V, int i, unsigned mask, int wT, i
 // S is this warp's kIntraSmemPerWarp ints of shared memory.
 template <bool TW, bool PD = false, bool XS = false>
 __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, unsigned &bidx) {
-    const RouteRec R = d.rrec[r];
+    const RouteRec R = d.rrec[TGA_IX(r, d.m)];
     const int L = R.len;
     if (L < 2) return;
     RouteView V;
@@ -1226,13 +1231,13 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
     int *lig = base + 13 * stride, *lmg = base + 14 * stride;
     V.lif = lif; V.lof = lof; V.lmf = lmf; V.lig = lig; V.lmg = lmg;
     for (int k = lane; k < E; k += 32) {
-        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[V.st + k] : -1);
+        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[TGA_IX(V.st + k, d.Wp)] : -1);
         const int x = (k >= 1 && k <= L) ? a : 0;
         node[k] = x;
         if (TW) { e[k] = __ldg(d.early + x); l[k] = __ldg(d.late + x); s[k] = __ldg(d.service + x); }
         else { e[k] = 0; l[k] = 0; s[k] = 0; }
         if (a >= 0) {
-            const BRec b = d.brec[a];
+            const BRec b = d.brec[TGA_IX(a, d.W + 1)];
             tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
             Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
             if (PD) { lif[k] = b.loadf; lof[k] = b.lof; lmf[k] = b.lmf; lig[k] = b.loadg; lmg[k] = b.lmg; }
@@ -1246,7 +1251,7 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
         int *D = S + NV * E;
         for (int t = lane; t < E * E; t += 32) {
             const int a = t / E, b = t - a * E;
-            D[t] = d.pcol[(size_t)node[a] * d.ldp + kColOff + V.st + b];
+            D[t] = d.pcol[(size_t)TGA_IX(node[a], d.n + 1) * d.ldp + TGA_IX(kColOff + V.st + b, d.ldp)];
         }
         V.D = D;
     } else {
@@ -1267,7 +1272,7 @@ __device__ void intra_route(const Dev &d, int r, int lane, int *S, int &best, un
 // spread over the warps.
 template <bool TW, bool PD = false, bool XS = false>
 __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsigned &bidx) {
-    const RouteRec R = d.rrec[r];
+    const RouteRec R = d.rrec[TGA_IX(r, d.m)];
     const int L = R.len;
     if (L < 2) return;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -1289,13 +1294,13 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
     int *lig = base + 13 * stride, *lmg = base + 14 * stride;
     V.lif = lif; V.lof = lof; V.lmf = lmf; V.lig = lig; V.lmg = lmg;
     for (int k = tid; k < E; k += nthr) {
-        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[V.st + k] : -1);
+        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[TGA_IX(V.st + k, d.Wp)] : -1);
         const int x = (k >= 1 && k <= L) ? a : 0;
         node[k] = x;
         if (TW) { e[k] = __ldg(d.early + x); l[k] = __ldg(d.late + x); s[k] = __ldg(d.service + x); }
         else { e[k] = 0; l[k] = 0; s[k] = 0; }
         if (a >= 0) {
-            const BRec b = d.brec[a];
+            const BRec b = d.brec[TGA_IX(a, d.W + 1)];
             tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
             Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
             if (PD) { lif[k] = b.loadf; lof[k] = b.lof; lmf[k] = b.lmf; lig[k] = b.loadg; lmg[k] = b.lmg; }
@@ -1309,7 +1314,7 @@ __device__ void intra_route_block(const Dev &d, int r, int *S, int &best, unsign
         int *D = S + NV * E;
         for (int t = tid; t < E * E; t += nthr) {
             const int a = t / E, b = t - a * E;
-            D[t] = d.pcol[(size_t)node[a] * d.ldp + kColOff + V.st + b];
+            D[t] = d.pcol[(size_t)TGA_IX(node[a], d.n + 1) * d.ldp + TGA_IX(kColOff + V.st + b, d.ldp)];
         }
         V.D = D;
     } else {
@@ -1371,7 +1376,7 @@ __device__ __forceinline__ int tw_enter(int a, const int4 g, int &warp) {
 // XS: also the swaps of runs inside the route (op ranks 6, 7).
 template <bool PD = false, bool XS = false>
 __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsigned &bidx) {
-    const RouteRec R = d.rrec[r];
+    const RouteRec R = d.rrec[TGA_IX(r, d.m)];
     const int L = R.len;
     if (L < 2) return;
     if (L > kTabMaxL) {
@@ -1394,12 +1399,12 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
     // position-ordered copy (row of element a, columns st .. st+E-1), both
     // issued right after the positions are known
     for (int k = tid; k < E; k += nthr) {
-        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[st + k] : -1);
+        const int a = (k == 0) ? d.n + 1 + r : (k <= L ? d.seq[TGA_IX(st + k, d.Wp)] : -1);
         const int x = (k >= 1 && k <= L) ? a : 0;
         node[k] = x;
         e[k] = __ldg(d.early + x); l[k] = __ldg(d.late + x); s[k] = __ldg(d.service + x);
         if (a >= 0) {
-            const BRec b = d.brec[a];
+            const BRec b = d.brec[TGA_IX(a, d.W + 1)];
             tau[k] = b.tau; twf[k] = b.twf; distf[k] = b.distf;
             Lg[k] = b.Lg; twg[k] = b.twg; distg[k] = b.distg;
             if (PD) { lif[k] = b.loadf; lof[k] = b.lof; lmf[k] = b.lmf; lig[k] = b.loadg; lmg[k] = b.lmg; }
@@ -1411,8 +1416,8 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
 #pragma unroll 4
     for (int t = tid; t < E * E; t += nthr) {
         const int a = t / E, b = t - a * E;
-        const int x = (a >= 1 && a <= L) ? d.seq[st + a] : 0;
-        D[t] = TGA_LDG(d.pcol + (size_t)x * d.ldp + kColOff + st + b);
+        const int x = (a >= 1 && a <= L) ? d.seq[TGA_IX(st + a, d.Wp)] : 0;
+        D[t] = TGA_LDG(d.pcol + (size_t)TGA_IX(x, d.n + 1) * d.ldp + TGA_IX(kColOff + st + b, d.ldp));
     }
     __syncthreads();
     // ---- tables: thread c < L extends forward row i = c+1, thread L + c the
@@ -1592,21 +1597,21 @@ __device__ void intra_route_table(const Dev &d, int r, int *S, int &best, unsign
 template <bool XS = false>
 __device__ void intra_cvrp_position(const Dev &d, int p, int lane, int &best, unsigned &bidx) {
     if (p >= d.Wp - 1) return;
-    const int ax = d.seq[p];
+    const int ax = d.seq[TGA_IX(p, d.Wp)];
     if (ax > d.n) return;                               // a start depot is never moved
-    const BRec bx = d.brec[ax];
+    const BRec bx = d.brec[TGA_IX(ax, d.W + 1)];
     const int r = bx.route, i = bx.idx;
-    const RouteRec R = d.rrec[r];
+    const RouteRec R = d.rrec[TGA_IX(r, d.m)];
     const int L = R.len, st = R.start;
     if (L < 2) return;
     const unsigned mask = d.op_mask;
     const unsigned W = (unsigned)d.W, W2 = W * W;
-    auto nodeAt = [&](int k) { return (k <= 0 || k > L) ? 0 : d.seq[st + k]; };
-    auto rowOf = [&](int node) { return d.pcol + (size_t)node * d.ldp + kColOff + st; };
+    auto nodeAt = [&](int k) { return (k <= 0 || k > L) ? 0 : d.seq[TGA_IX(st + k, d.Wp)]; };
+    auto rowOf = [&](int node) { return d.pcol + (size_t)TGA_IX(node, d.n + 1) * d.ldp + TGA_IX(kColOff + st, d.ldp); };
     // distance from the prefix through element k to element k+1
     auto dfAt = [&](int k) {
         if (k > L) return R.dist;
-        return d.brec[k == 0 ? d.n + 1 + r : d.seq[st + k]].distf;
+        return d.brec[TGA_IX(k == 0 ? d.n + 1 + r : d.seq[TGA_IX(st + k, d.Wp)], d.W + 1)].distf;
     };
     const int xi = ax, xm = nodeAt(i - 1), xn = nodeAt(i + 1);
     const int *rowI = rowOf(xi), *rowP = rowOf(xm), *rowN = rowOf(xn);
@@ -1623,8 +1628,8 @@ __device__ void intra_cvrp_position(const Dev &d, int p, int lane, int &best, un
         remk[k] = TGA_LDG(rowP + i + k) - e_prev - e_w;
     }
     for (int j = lane; j <= L; j += 32) {
-        const int aj = j == 0 ? d.n + 1 + r : d.seq[st + j];
-        const int df_j = j == 0 ? 0 : d.brec[aj].distf;
+        const int aj = j == 0 ? d.n + 1 + r : d.seq[TGA_IX(st + j, d.Wp)];
+        const int df_j = j == 0 ? 0 : d.brec[TGA_IX(aj, d.W + 1)].distf;
         const int e_j = dfAt(j + 1) - df_j;                // c(x_j, x_{j+1})
         const int cij = TGA_LDG(rowI + j);
         for (int k = 1; k <= 3; ++k) {
@@ -1928,7 +1933,7 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
     }
     if (k <= L) {
         const int a = k == 0 ? d.n + 1 + r : x;
-        int4 *bp = reinterpret_cast<int4 *>(d.brec + a);
+        int4 *bp = reinterpret_cast<int4 *>(d.brec + TGA_IX(a, d.W + 1));
         bp[0] = make_int4(x, r, k, L);
         bp[1] = make_int4(tau, twf, f.dist, f.load);
         bp[2] = make_int4(Lg, twg, gdist, gload);
@@ -1963,7 +1968,7 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
                 if (tw) { E3 = run3.E; L3 = run3.L; Dm3 = run3.D - run3.TW; }
             }
         }
-        int4 *ep = reinterpret_cast<int4 *>(d.erec + a);
+        int4 *ep = reinterpret_cast<int4 *>(d.erec + TGA_IX(a, d.W + 1));
         ep[0] = make_int4(r, dem, rem1, Fc + Gc);
         ep[1] = make_int4(Rload - d.Q, K2, LQd, Fc + ((mask & 8u) ? 0 : kBig));
         ep[2] = make_int4(Gc, f.load, gload - d.Q, a);
@@ -1971,16 +1976,16 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
         ep[4] = make_int4(ne, nl, ns, tau);
         ep[5] = make_int4(Lg, tauP, E2, L2);
         ep[6] = make_int4(Dm2, E3, L3, Dm3);
-        ep[7] = make_int4(x, k, 0, 0);
+        ep[7] = make_int4(x, k, k + 1 <= L ? xn : 0, k + 2 <= L ? x2 : 0);
         if (XS) {
-            d.xrec[a] = k == 0 ? xrec_none()
+            d.xrec[TGA_IX(a, d.W + 1)] = k == 0 ? xrec_none()
                                : make_xrec(wTe, Rcost, Rload, d.Q, pdist, ptwf, ptau, gdist, twg, Lg, k + 1 <= L,
                                            w2dist, w2tw, w2L, run2, dnext, ne, nl, ns, dem);
         }
         if (pd) {
             const int Q = d.Q;
             const int pk = ndl.o;
-            int4 *pp = reinterpret_cast<int4 *>(d.prec + a);
+            int4 *pp = reinterpret_cast<int4 *>(d.prec + TGA_IX(a, d.W + 1));
             pp[0] = make_int4(fl.m + glI - Q, fl.o + glI - Q, fl.o + glM - Q, pk);
             pp[1] = k >= 1 ? make_int4(plm + glI - Q, plo + glI - Q, plo + glM - Q, max(dem, pk))
                            : make_int4(0, 0, 0, max(dem, pk));
@@ -1990,7 +1995,7 @@ __device__ void rebuild_route_warp(const Dev &d, int r, int st, int L, const int
         }
     }
     if (lane == 0) {
-        RouteRec *R = d.rrec + r;
+        RouteRec *R = d.rrec + TGA_IX(r, d.m);
         R->load = Rload;
         if (pd) { R->lo = Rlo; R->lm = Rlm; }
         R->dist = Rdist;
@@ -2033,8 +2038,8 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
     if (ok) {
         // one round trip: the anchors' records carry route, index, route
         // length and cost; the start depot sits idx positions before the anchor
-        ba = d.brec[pl.a]; bb = d.brec[pl.b];
-        qa = d.pos_of[pl.a]; qb = d.pos_of[pl.b];
+        ba = d.brec[TGA_IX(pl.a, d.W + 1)]; bb = d.brec[TGA_IX(pl.b, d.W + 1)];
+        qa = d.pos_of[TGA_IX(pl.a, d.W + 1)]; qb = d.pos_of[TGA_IX(pl.b, d.W + 1)];
     }
     // the evaluation's bookkeeping, while the records are in flight
     if (!ext) {
@@ -2135,18 +2140,18 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
         const MovePlan pl = S.mp;
         const int tot = S.n1 + S.n2;
         // the anchor every changed position takes, all read before any write
-        for (int u = tid; u < tot; u += nthr) sbuf[u] = d.seq[plan_src(S, plan_pos(S, u))];
+        for (int u = tid; u < tot; u += nthr) sbuf[u] = d.seq[TGA_IX(plan_src(S, plan_pos(S, u)), d.Wp)];
         __syncthreads();
         for (int u = tid; u < tot; u += nthr) {
             const int q = plan_pos(S, u), a = sbuf[u];
-            d.seq[q] = a;
-            d.pos_of[a] = q;
+            d.seq[TGA_IX(q, d.Wp)] = a;
+            d.pos_of[TGA_IX(a, d.W + 1)] = q;
         }
         if (S.dl != 0)
-            for (int r = S.lo + 1 + tid; r <= S.hi; r += nthr) d.rrec[r].start += S.dl;
+            for (int r = S.lo + 1 + tid; r <= S.hi; r += nthr) d.rrec[TGA_IX(r, d.m)].start += S.dl;
         if (tid == 0) {
-            d.rrec[pl.A].len = pl.nLA;
-            if (pl.B != pl.A) d.rrec[pl.B].len = pl.nLB;
+            d.rrec[TGA_IX(pl.A, d.m)].len = pl.nLA;
+            if (pl.B != pl.A) d.rrec[TGA_IX(pl.B, d.m)].len = pl.nLB;
         }
         __syncthreads();
         const int warp = tid >> 5, lane = tid & 31;
@@ -2170,8 +2175,8 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
             int mL = 0, mLoad = 0;
             for (int r = tid - 64; r < d.m; r += nthr - 64) {
                 if (r == pl.A || r == pl.B) continue;
-                mL = max(mL, d.rrec[r].len);
-                const RouteRec &Rr = d.rrec[r];
+                mL = max(mL, d.rrec[TGA_IX(r, d.m)].len);
+                const RouteRec &Rr = d.rrec[TGA_IX(r, d.m)];
                 mLoad = max(mLoad, PD ? Rr.load + Rr.lo : Rr.load);
             }
             mL = __reduce_max_sync(0xffffffffu, mL);
@@ -2186,17 +2191,17 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
             const bool two = pl.B != pl.A;
             int costA, loadA, costB = 0, loadB = 0;
             // range load: the delivery total, plus the pickup total with pickups
-            auto rload = [&](int r) { return d.rrec[r].load + (PD ? d.rrec[r].lo : 0); };
+            auto rload = [&](int r) { return d.rrec[TGA_IX(r, d.m)].load + (PD ? d.rrec[TGA_IX(r, d.m)].lo : 0); };
             if (s_fast[0]) { costA = s_tot[0][3]; loadA = s_tot[0][0]; }
-            else { costA = d.rrec[pl.A].cost; loadA = rload(pl.A); }
+            else { costA = d.rrec[TGA_IX(pl.A, d.m)].cost; loadA = rload(pl.A); }
             if (two) {
                 if (s_fast[1]) { costB = s_tot[1][3]; loadB = s_tot[1][0]; }
-                else { costB = d.rrec[pl.B].cost; loadB = rload(pl.B); }
+                else { costB = d.rrec[TGA_IX(pl.B, d.m)].cost; loadB = rload(pl.B); }
             }
             const long long newcost = (long long)costA + costB;
             const long long dact = newcost - S.oldcost;
             int status = s_ci[0];
-            if (!ext && dact != pl.delta) { set_status(C, 7); status = 7; }
+            if (!ext && dact != pl.delta) { set_status(C, TGA_ERR_CHECK); status = TGA_ERR_CHECK; }
             const long long cost = s_cf[0] + dact, steps = s_cf[1] + 1;
             C->cost = cost;
             C->steps = steps;
@@ -2354,7 +2359,7 @@ __device__ void band_plan_rows(const Dev &d, const StepPlan &S, int *smem, int r
         if (K <= kBandWarpBuf) {
             int *wb = smem + 2 * kBandListMax + warp * kBandWarpBuf;
             for (int x = row_lo + cta * nw + warp; x < row_hi; x += ncta * nw) {
-                int *row = d.pcol + (size_t)x * d.ldp + kColOff;
+                int *row = d.pcol + (size_t)TGA_IX(x, d.n + 1) * d.ldp + kColOff;
                 for (int e = lane; e < K; e += 32) wb[e] = row[ss[e]];
                 __syncwarp();
                 if (shift) shift_row_warp(row, P.s0, P.s1, P.dl, lane);
@@ -2368,7 +2373,7 @@ __device__ void band_plan_rows(const Dev &d, const StepPlan &S, int *smem, int r
     // long routes: a block per row, sources recomputed per element
     int *vb = smem;
     for (int x = row_lo + cta; x < row_hi; x += ncta) {
-        int *row = d.pcol + (size_t)x * d.ldp + kColOff;
+        int *row = d.pcol + (size_t)TGA_IX(x, d.n + 1) * d.ldp + kColOff;
         for (int k = tid; k < nL; k += nthr) vb[k] = row[plan_src(S, qk(k))];
         __syncthreads();
         if (shift) shift_row_block(row, P.s0, P.s1, P.dl);
@@ -2382,11 +2387,11 @@ __device__ void band_plan_rows(const Dev &d, const StepPlan &S, int *smem, int r
 __device__ void sync_solution_range(const Dev &d, long long t0, long long stride) {
     if (*(volatile int *)&d.ctl->status != 0) return;     // an error leaves the caller's solution as it was
     for (long long q = t0; q < d.Wp - 1; q += stride) {
-        const int a = d.seq[q];
-        if (a >= 1 && a <= d.n) d.tour[q - d.brec[a].route - 1] = a;
+        const int a = d.seq[TGA_IX(q, d.Wp)];
+        if (a >= 1 && a <= d.n) d.tour[TGA_IX(q - d.brec[TGA_IX(a, d.W + 1)].route - 1, d.n)] = a;
     }
     for (long long r = t0; r <= d.m; r += stride)
-        d.route_start[r] = r < d.m ? d.rrec[r].start - (int)r : d.n;
+        d.route_start[TGA_IX(r, d.m + 1)] = r < d.m ? d.rrec[TGA_IX(r, d.m)].start - (int)r : d.n;
 }
 
 __device__ __forceinline__ long long now_ns() {

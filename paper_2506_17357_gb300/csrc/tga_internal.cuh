@@ -51,6 +51,8 @@ struct __align__(16) BRec {
 
 // Per-anchor hoisted constants of the inter-route candidate expressions.
 // Groups g0..g3 are all a CVRP evaluation reads; g4..g6 add the time fields.
+// succ / succ2 are the nodes of the next two elements of x's route (0 past
+// its last customer, i.e. the end depot).
 struct __align__(16) ERec {
     int route, d, rem1, K1;                   // g0
     int LQ, K2, LQd, Fc;                      // g1
@@ -59,7 +61,7 @@ struct __align__(16) ERec {
     int e, l, s, tau;                         // g4
     int Lg, tauP, E2, L2;                     // g5
     int Dm2, E3, L3, Dm3;                     // g6
-    int node, idx, pad0, pad1;                // g7
+    int node, idx, succ, succ2;               // g7: x's node and index; the nodes after it and after those
 };
 
 // Per-anchor hoisted constants of the inter-route candidates with pickups
@@ -149,6 +151,10 @@ struct Control {
     // kept, per operator rank
     long long sumLm1sq, sumLm2sq;
     unsigned long long gcount[6];
+    // debug build with index checks (TGA_BOUNDS_CHECK): the first failed
+    // check -- site = file id * 100000 + source line, the index and the limit
+    int bad_site, pad6;
+    long long bad_index, bad_limit;
 };
 
 // The device workspace of one instance: every array a context (or the
@@ -231,8 +237,36 @@ struct Dev {
 
 __host__ __device__ inline int node_of(int anchor, int n) { return anchor <= n ? anchor : 0; }
 
+// Debug build (compiled with -DTGA_BOUNDS_CHECK): every indexed access of
+// the search state and the instance goes through TGA_IX(index, limit).  An
+// index outside [0, limit) records the first failure in the control block
+// (site = TGA_FILE_ID * 100000 + source line, the index, the limit), sets
+// the status TGA_ERR_BOUNDS, and the access uses index 0 instead, so nothing
+// outside the arrays is touched.  The release build compiles TGA_IX(i, lim)
+// to (i).  File ids: 1 this header, 2 tga_device.cuh, 3 tga_kernels.cu,
+// 4 tga_persist.cu, 5 tga_batch.cu, 6 tga_noalloc.cu.
+#ifdef TGA_BOUNDS_CHECK
+static __device__ __noinline__ long long tga_ix_fail(const Dev &d, long long i, long long lim, int site) {
+    Control *C = d.ctl;
+    if (atomicCAS(&C->bad_site, 0, site) == 0) {
+        C->bad_index = i;
+        C->bad_limit = lim;
+    }
+    atomicCAS(&C->status, 0, TGA_ERR_BOUNDS);
+    return 0;
+}
+__device__ __forceinline__ long long tga_ix(const Dev &d, long long i, long long lim, int site) {
+    return ((unsigned long long)i < (unsigned long long)lim) ? i : tga_ix_fail(d, i, lim, site);
+}
+#define TGA_IX(i, lim) tga_ix(d, (long long)(i), (long long)(lim), TGA_FILE_ID * 100000 + __LINE__)
+#else
+#define TGA_IX(i, lim) (i)
+#endif
+#undef TGA_FILE_ID
+#define TGA_FILE_ID 1
+
 __device__ __forceinline__ int dmat(const Dev &d, int i, int j) {
-    return __ldg(d.dist + (size_t)i * (d.n + 1) + j);
+    return __ldg(d.dist + (size_t)TGA_IX(i, d.n + 1) * (d.n + 1) + TGA_IX(j, d.n + 1));
 }
 
 // Time-window segment in the form of Section 4.3.3: earliest start E,
@@ -453,6 +487,13 @@ void launch_intra(const Dev &d, cudaStream_t s, int tail = 0);
 // swaps of runs between routes (op ranks 6, 7; no-op unless enabled)
 void launch_xswap(const Dev &d, cudaStream_t s, int tail = 0);
 int eval_blocks(const Dev &d, int ntiles, int strip = 0);
+// Edge-based extraction (theta > 0): threads per CTA, mask-entry CTAs, and
+// depot CTAs (row tiles of `rows` positions x `chunks` chunks of `dc` start
+// depots).
+struct EdgeGrid {
+    int threads, nmask, ndepot, rows, chunks, dc;
+};
+EdgeGrid edge_grid(const Dev &d);
 // pre = 1: apply the plan decoded by the evaluation's last CTA (descent
 // steps); else decode *ext (or the best key) in the launch itself.
 void launch_apply(const Dev &d, const tga_move *ext, unsigned long long cond, int use_cond,

@@ -29,6 +29,8 @@
 
 #define TGA_LDG(p) __ldg(p)
 #include "tga_device.cuh"
+#undef TGA_FILE_ID
+#define TGA_FILE_ID 3
 
 namespace tga {
 
@@ -102,7 +104,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Anchor at position p for row staging (positions outside the sequence read
 // the dummy record W, whose node is the depot).
-__device__ __forceinline__ int strip_anchor(const Dev &d, int p) { return (p >= 0 && p < d.Wp) ? d.seq[p] : d.W; }
+__device__ __forceinline__ int strip_anchor(const Dev &d, int p) { return (p >= 0 && p < d.Wp) ? d.seq[TGA_IX(p, d.Wp)] : d.W; }
 
 // Issue the copies of one tile: TR+4 distance rows (the nodes of positions
 // p0-1 .. p0+TR+2, storage columns q0 .. q0+TC+7, i.e. positions
@@ -115,15 +117,16 @@ __device__ __forceinline__ void strip_stage(const Dev &d, int *buf, int TR, int 
     int4 *sR = reinterpret_cast<int4 *>(buf + (TR + 4) * LDT);
     for (int r = warp; r < TR + 4; r += NW) {
         const int node = node_of(s_anc[r], d.n);
-        const int4 *src = reinterpret_cast<const int4 *>(d.pcol + (size_t)node * d.ldp + q0);
+        const int4 *src =
+            reinterpret_cast<const int4 *>(d.pcol + (size_t)TGA_IX(node, d.n + 1) * d.ldp + TGA_IX(q0, d.ldp - LDT + 1));
         int4 *dst = reinterpret_cast<int4 *>(buf + r * LDT);
         for (int c = lane; c < C4; c += 32) cp_async16(dst + c, src + c);
     }
     for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
         const int row = i / NG, g = i - row * NG;
         const int a = s_anc[row + 1];
-        const int4 *src = g < 8 ? reinterpret_cast<const int4 *>(d.erec + a) + g
-                                : reinterpret_cast<const int4 *>(d.prec + a) + (g - 8);
+        const int4 *src = g < 8 ? reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + g
+                                : reinterpret_cast<const int4 *>(d.prec + TGA_IX(a, d.W + 1)) + (g - 8);
         cp_async16(sR + i, src);
     }
 }
@@ -200,32 +203,165 @@ __global__ void __launch_bounds__(256, TW ? 3 : 4) k_eval_strip(Dev d, int TR, l
     if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
-// Edge-based extraction: one thread per kept pair (u, v), u a customer and
-// v one of the theta entries of u's mask row or one of the m start depots.
-// The per-operator candidate counts are folded into the control block before
-// the key, so the evaluation's last CTA sees them.
+// Edge-based extraction (ETGA, Section 5.3.1): the kept inter-route pairs
+// of a customer u are u's theta mask entries and the start depots of the
+// other routes.  One launch, two kinds of CTA (blockDim threads each):
+//
+//   mask CTAs (the first ceil(n*theta / blockDim)): one thread per directed
+//     mask entry (u, v).  Round 1 loads the entry, u's records and u's
+//     position; round 2 v's records and position and the distances that
+//     need only v (c(u,v), c(u+,v), c(u-,v) from the position-ordered copy's
+//     row v at u's predecessor position); round 3 the distances to v's
+//     successor (named in v's record) and c(u, v-) from row u of the copy at
+//     v's predecessor position.
+//   depot CTAs: the (customer, start depot) pairs are dense -- every
+//     customer with every other route -- so they are tiled like the
+//     node-based kernel.  A CTA takes R consecutive positions (rows) and a
+//     chunk of start depots, one per thread.  The rows' records sit in
+//     shared memory with the depot's distances to them (row 0 of the
+//     position-ordered copy); each thread holds its depot's record and the
+//     copy's row of the depot's successor node f across the R+4 positions,
+//     because c(u, f), c(u+, f), c(u++, f) of the row at position p are that
+//     row's columns p, p+1, p+2 (the matrix is symmetric).  No distance is
+//     gathered.
+//
+// The per-operator counts of the kept candidates are folded into the
+// control block before the key, so the evaluation's last CTA sees them.
+constexpr int kEdgeMaxThreads = 128;
+
 template <bool TW, bool OR>
-__global__ void __launch_bounds__(256) k_eval_edges(Dev d, int tail) {
+__device__ __forceinline__ void edge_mask_item(const Dev &d, long long item, int &best, unsigned &bidx,
+                                               unsigned &evaluated) {
+    const int th = d.theta;
+    const int u = (int)(item / th) + 1, k = (int)(item - (long long)(u - 1) * th);
+    const size_t e = (size_t)u * th + k;
+    const int v = __ldg(d.nbr + TGA_IX(e, (long long)(d.n + 1) * d.theta));
+    const bool rev = __ldg(d.nbr_rev + TGA_IX(e, (long long)(d.n + 1) * d.theta)) != 0;
+    const int4 *ur = reinterpret_cast<const int4 *>(d.erec + TGA_IX(u, d.W + 1));
+    const int4 u0 = __ldg(ur + 0), u1 = __ldg(ur + 1), u2 = __ldg(ur + 2), u7 = __ldg(ur + 7);
+    const int4 z = make_int4(0, 0, 0, 0);
+    const int4 u3 = OR ? __ldg(ur + 3) : z;
+    const int4 u4 = TW ? __ldg(ur + 4) : z, u5 = TW ? __ldg(ur + 5) : z;
+    const int4 u6 = (TW && OR) ? __ldg(ur + 6) : z;
+    const int pu = __ldg(d.pos_of + TGA_IX(u, d.W + 1));
+    // round 2: v's records, its position, and the distances that need only v
+    const int4 *vr = reinterpret_cast<const int4 *>(d.erec + TGA_IX(v, d.W + 1));
+    const int4 v0 = __ldg(vr + 0), v1 = __ldg(vr + 1), v2 = __ldg(vr + 2), v7 = __ldg(vr + 7);
+    const int4 v4 = TW ? __ldg(vr + 4) : z, v5 = TW ? __ldg(vr + 5) : z;
+    const int pv = __ldg(d.pos_of + TGA_IX(v, d.W + 1));
+    const int up = u7.z, upp = u7.w;
+    EdgeStencil t;
+    t.t00 = dmat(d, u, v);
+    t.t10 = dmat(d, up, v);
+    t.tm10 = __ldg(d.pcol + (size_t)TGA_IX(v, d.n + 1) * d.ldp + TGA_IX(pu - 1 + kColOff, d.ldp));
+    // round 3: the distances to v's successor, and c(u, v-)
+    const int vp = v7.z;
+    t.t01 = dmat(d, u, vp);
+    t.t11 = dmat(d, up, vp);
+    t.t21 = OR ? dmat(d, upp, vp) : 0;
+    t.t0m1 = __ldg(d.pcol + (size_t)TGA_IX(u, d.n + 1) * d.ldp + TGA_IX(pv - 1 + kColOff, d.ldp));
+    if (u0.x != v0.x) {
+        const bool pair_once = !rev || u < v;
+        evaluated |= edge_pair<TW, OR>(d, u, v, true, pair_once, u0, u1, u2, u3, u4, u5, u6, v0, v1, v2, v4, v5, t,
+                                       best, bidx);
+    }
+}
+
+template <bool TW, bool OR, int R>
+__device__ __forceinline__ void edge_depot_tile(const Dev &d, int p0, int r, bool active, int &best, unsigned &bidx,
+                                                unsigned *cnt) {
+    __shared__ int4 sU[R * 7];          // ERec g0..g6 of the anchors at positions p0 .. p0+R-1
+    __shared__ int sA[R];               // those anchors (W past the sequence)
+    __shared__ __align__(16) int sC0[R + 4];   // c(0, node at p0 + i)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // columns p0 .. p0+R+3 of a copy row, in int4 pieces; a piece is read
+    // only while it starts at or before position Wp (every row that holds a
+    // customer reads columns up to its position + 2 <= Wp)
+    const int pieces = (R + 4) / 4;
+    for (int i = tid; i < R * 7; i += nt) {
+        const int row = i / 7, g = i - row * 7;
+        const int p = p0 + row;
+        const int a = p < d.Wp ? d.seq[TGA_IX(p, d.Wp)] : d.W;
+        if (g == 0) sA[row] = a;
+        sU[i] = __ldg(reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + g);
+    }
+    for (int j = tid; j < pieces; j += nt) {
+        const int4 x = (4 * j <= d.Wp - p0) ? __ldg(reinterpret_cast<const int4 *>(d.pcol + TGA_IX(p0 + kColOff + 4 * j, d.ldp - 3)))
+                                            : make_int4(0, 0, 0, 0);
+        reinterpret_cast<int4 *>(sC0)[j] = x;
+    }
+    const int4 z = make_int4(0, 0, 0, 0);
+    int4 v0 = z, v1 = z, v2 = z, v4 = z, v5 = z;
+    int T[R + 4];
+    const int v = d.n + 1 + r;
+    if (active) {
+        const int4 *vr = reinterpret_cast<const int4 *>(d.erec + TGA_IX(v, d.W + 1));
+        v0 = __ldg(vr + 0); v1 = __ldg(vr + 1); v2 = __ldg(vr + 2);
+        if (TW) { v4 = __ldg(vr + 4); v5 = __ldg(vr + 5); }
+        const int f = __ldg(vr + 7).z;                       // first customer of route r (0: empty)
+        const int *row = d.pcol + (size_t)TGA_IX(f, d.n + 1) * d.ldp;
+#pragma unroll
+        for (int j = 0; j < (R + 4) / 4; ++j) {
+            const int4 x = (4 * j <= d.Wp - p0)
+                               ? __ldg(reinterpret_cast<const int4 *>(row + TGA_IX(p0 + kColOff + 4 * j, d.ldp - 3)))
+                               : z;
+            T[4 * j] = x.x; T[4 * j + 1] = x.y; T[4 * j + 2] = x.z; T[4 * j + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < R + 4; ++j) T[j] = 0;
+    }
+    __syncthreads();
+    if (!active) return;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int a = sA[i];
+        if (a < 1 || a > d.n) continue;                      // a start depot or past the sequence
+        const int4 u0 = sU[i * 7];
+        if (u0.x == r) continue;                             // v's own route
+        const int4 u1 = sU[i * 7 + 1], u2 = sU[i * 7 + 2];
+        const int4 u3 = OR ? sU[i * 7 + 3] : z;
+        const int4 u4 = TW ? sU[i * 7 + 4] : z, u5 = TW ? sU[i * 7 + 5] : z;
+        const int4 u6 = (TW && OR) ? sU[i * 7 + 6] : z;
+        EdgeStencil t;
+        t.t00 = sC0[i];                                      // c(u, 0)
+        t.t10 = sC0[i + 1];                                  // c(u+, 0)
+        t.t01 = T[i];                                        // c(u, f)
+        t.t11 = T[i + 1];                                    // c(u+, f)
+        t.t21 = T[i + 2];                                    // c(u++, f)
+        t.tm10 = 0;
+        t.t0m1 = 0;
+        const unsigned ev = edge_pair<TW, OR>(d, a, v, false, false, u0, u1, u2, u3, u4, u5, u6, v0, v1, v2, v4,
+                                              v5, t, best, bidx);
+#pragma unroll
+        for (int op = 0; op < 6; ++op) cnt[op] += (ev >> op) & 1u;
+    }
+}
+
+// nmask: CTAs of mask entries; chunks: start-depot chunks of dc depots per
+// row tile of R positions.
+template <bool TW, bool OR, int R>
+__global__ void __launch_bounds__(kEdgeMaxThreads) k_eval_edges(Dev d, int nmask, int chunks, int dc, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
-    const int per = d.theta + d.m;
-    const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    unsigned evaluated = 0;                   // bit op: this thread evaluated an op-rank candidate
-    if (item < (long long)d.n * per) {
-        const int u = (int)(item / per) + 1, col = (int)(item - (long long)(u - 1) * per);
-        int v = d.n + 1 + (col - d.theta);
-        bool rev = false;
-        if (col < d.theta) {
-            const size_t e = (size_t)u * d.theta + col;
-            v = __ldg(d.nbr + e);
-            rev = __ldg(d.nbr_rev + e) != 0;
-        }
-        evaluated = edge_candidates<TW, OR>(d, u, v, rev, best, bidx);
+    unsigned cnt[6] = {0, 0, 0, 0, 0, 0};
+    if ((int)blockIdx.x < nmask) {
+        const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        unsigned ev = 0;
+        if (item < (long long)d.n * d.theta) edge_mask_item<TW, OR>(d, item, best, bidx, ev);
+#pragma unroll
+        for (int op = 0; op < 6; ++op) cnt[op] = (ev >> op) & 1u;
+    } else {
+        const int b = (int)blockIdx.x - nmask;
+        const int tile = b / chunks, ch = b - tile * chunks;
+        const int r = ch * dc + (int)threadIdx.x;
+        edge_depot_tile<TW, OR, R>(d, tile * R, r, (int)threadIdx.x < dc && r < d.m, best, bidx, cnt);
     }
     if (done) return;
+#pragma unroll
     for (int op = 0; op < 6; ++op) {
-        const unsigned c = __popc(__ballot_sync(0xffffffffu, (evaluated >> op) & 1u));
+        const unsigned c = __reduce_add_sync(0xffffffffu, cnt[op]);
         if ((threadIdx.x & 31) == 0 && c) atomicAdd(&d.ctl->gcount[op], (unsigned long long)c);
     }
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
@@ -239,13 +375,13 @@ __global__ void k_granular_setup(Dev d, unsigned char *rev, int *bad) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)d.n * d.theta) return;
     const int u = (int)(t / d.theta) + 1;
-    const int v = d.nbr[(size_t)u * d.theta + (t - (long long)(u - 1) * d.theta)];
+    const int v = d.nbr[TGA_IX((size_t)u * d.theta + (t - (long long)(u - 1) * d.theta), (long long)(d.n + 1) * d.theta)];
     unsigned char r = 0;
     if (v < 1 || v > d.n || v == u) {
         atomicExch(bad, 1);
     } else {
         for (int k = 0; k < d.theta; ++k)
-            if (d.nbr[(size_t)v * d.theta + k] == u) r = 1;
+            if (d.nbr[TGA_IX((size_t)v * d.theta + k, (long long)(d.n + 1) * d.theta)] == u) r = 1;
     }
     rev[(size_t)u * d.theta + (t - (long long)(u - 1) * d.theta)] = r;
 }
@@ -392,21 +528,21 @@ __global__ void __launch_bounds__(kXswapThreads) k_eval_xswap(Dev d, int tail) {
     const int p0 = rb * kXswapRows, tid = threadIdx.x;
     if (tid < kXswapRows + 3) {
         const int pp = p0 - 1 + tid;
-        s_node[tid] = (pp >= 0 && pp < d.Wp) ? node_of(d.seq[pp], d.n) : 0;
+        s_node[tid] = (pp >= 0 && pp < d.Wp) ? node_of(d.seq[TGA_IX(pp, d.Wp)], d.n) : 0;
     }
     if (tid < kXswapRows) {
         const int p = p0 + tid;
-        const int a = p < d.Wp ? d.seq[p] : d.W;
+        const int a = p < d.Wp ? d.seq[TGA_IX(p, d.Wp)] : d.W;
         const bool cust = a >= 1 && a <= d.n;
         s_anc[tid] = cust ? a : 0;
-        s_rt[tid] = cust ? d.brec[a].route : -1;
-        s_xr[tid] = cust ? d.xrec[a] : xrec_none();
+        s_rt[tid] = cust ? d.brec[TGA_IX(a, d.W + 1)].route : -1;
+        s_xr[tid] = cust ? d.xrec[TGA_IX(a, d.W + 1)] : xrec_none();
     }
     const int q = cb * kXswapThreads + tid;
-    const int b = q < d.Wp ? d.seq[q] : d.W;
+    const int b = q < d.Wp ? d.seq[TGA_IX(q, d.Wp)] : d.W;
     const bool bcust = b >= 1 && b <= d.n;
-    const XRec xb = bcust ? d.xrec[b] : xrec_none();
-    const int Br = bcust ? d.brec[b].route : -2;
+    const XRec xb = bcust ? d.xrec[TGA_IX(b, d.W + 1)] : xrec_none();
+    const int Br = bcust ? d.brec[TGA_IX(b, d.W + 1)].route : -2;
     __syncthreads();
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
@@ -414,7 +550,7 @@ __global__ void __launch_bounds__(kXswapThreads) k_eval_xswap(Dev d, int tail) {
         const unsigned mask = d.op_mask;
         const unsigned W = (unsigned)d.W, W2 = W * W;
         const int wL = d.wL, wT = d.wT;
-        const int *pc = d.pcol + kColOff + q;
+        const int *pc = d.pcol + kColOff + TGA_IX(q, d.Wp + 4);
         const size_t ldp = (size_t)d.ldp;
 #pragma unroll 2
         for (int i = 0; i < kXswapRows; ++i) {
@@ -516,7 +652,26 @@ void launch_build(const Dev &d, cudaStream_t s) {
     k_pcol_init<<<(int)blocks, 256, 0, s>>>(d);
 }
 
-long long edge_items(const Dev &d) { return (long long)d.n * (d.theta + d.m); }
+// Launch shape of the edge-based extraction: threads per CTA (a multiple of
+// 32, at most kEdgeMaxThreads), the mask CTAs (one thread per entry), and the
+// depot CTAs: row tiles of R positions (R the largest of 32, 16, 8 that still
+// gives about eight CTAs per SM, else 8) times chunks of dc start depots.
+EdgeGrid edge_grid(const Dev &d) {
+    EdgeGrid g{};
+    const int chunks = (d.m + kEdgeMaxThreads - 1) / kEdgeMaxThreads;
+    g.chunks = chunks < 1 ? 1 : chunks;
+    g.dc = (d.m + g.chunks - 1) / g.chunks;
+    if (g.dc < 1) g.dc = 1;
+    g.threads = (g.dc + 31) / 32 * 32;
+    const long long entries = (long long)d.n * d.theta;
+    g.nmask = (int)((entries + g.threads - 1) / g.threads);
+    const int rows_pos = d.Wp - 1;                    // positions 0 .. Wp-2 (the sentinel holds no customer)
+    g.rows = 8;
+    for (int R = 32; R >= 16; R >>= 1)
+        if ((long long)((rows_pos + R - 1) / R) * g.chunks >= 8LL * d.nsm) { g.rows = R; break; }
+    g.ndepot = ((rows_pos + g.rows - 1) / g.rows) * g.chunks;
+    return g;
+}
 
 size_t strip_smem_bytes(int rows, int warps, bool pd) {
     const int LDT = warps * 32 + 8;
@@ -548,15 +703,23 @@ int strip_grid(const Dev &d, int rows, int warps, long long ntiles) {
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs,
                   int tail, int strip) {
     if (d.theta > 0) {          // edge-based extraction
-        const int blocks = (int)((edge_items(d) + 255) / 256);
+        const EdgeGrid g = edge_grid(d);
         const bool orr = (d.op_mask & 48u) != 0;
-        if (d.has_tw) {
-            if (orr) k_eval_edges<true, true><<<blocks, 256, 0, s>>>(d, tail);
-            else k_eval_edges<true, false><<<blocks, 256, 0, s>>>(d, tail);
-        } else {
-            if (orr) k_eval_edges<false, true><<<blocks, 256, 0, s>>>(d, tail);
-            else k_eval_edges<false, false><<<blocks, 256, 0, s>>>(d, tail);
-        }
+        const int blocks = g.nmask + g.ndepot;
+#define TGA_EDGES(R)                                                                                        \
+    do {                                                                                                    \
+        if (d.has_tw) {                                                                                     \
+            if (orr) k_eval_edges<true, true, R><<<blocks, g.threads, 0, s>>>(d, g.nmask, g.chunks, g.dc, tail); \
+            else k_eval_edges<true, false, R><<<blocks, g.threads, 0, s>>>(d, g.nmask, g.chunks, g.dc, tail); \
+        } else {                                                                                            \
+            if (orr) k_eval_edges<false, true, R><<<blocks, g.threads, 0, s>>>(d, g.nmask, g.chunks, g.dc, tail); \
+            else k_eval_edges<false, false, R><<<blocks, g.threads, 0, s>>>(d, g.nmask, g.chunks, g.dc, tail); \
+        }                                                                                                   \
+    } while (0)
+        if (g.rows == 8) TGA_EDGES(8);
+        else if (g.rows == 16) TGA_EDGES(16);
+        else TGA_EDGES(32);
+#undef TGA_EDGES
         return;
     }
     if (ntiles <= 0) return;
@@ -596,7 +759,10 @@ int intra_blocks(const Dev &d) { return d.has_tw ? d.m : (d.Wp - 1 + 7) / 8; }
 int xswap_blocks(const Dev &d);
 
 int eval_blocks(const Dev &d, int ntiles, int strip) {
-    if (d.theta > 0) return (int)((edge_items(d) + 255) / 256) + intra_blocks(d);
+    if (d.theta > 0) {
+        const EdgeGrid g = edge_grid(d);
+        return g.nmask + g.ndepot + intra_blocks(d);
+    }
     const int inter = ntiles <= 0 ? 0 : (strip > 0 ? strip : ntiles);
     return inter + intra_blocks(d) + xswap_blocks(d);
 }

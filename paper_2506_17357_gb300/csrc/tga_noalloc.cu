@@ -19,6 +19,8 @@
 #include <mutex>
 
 #include "tga_internal.cuh"
+#undef TGA_FILE_ID
+#define TGA_FILE_ID 6
 
 namespace tga {
 namespace {

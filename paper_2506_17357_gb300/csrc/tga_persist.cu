@@ -30,6 +30,8 @@
 // another SM rewrites the search state within the launch.
 #define TGA_LDG(p) (*(p))
 #include "tga_device.cuh"
+#undef TGA_FILE_ID
+#define TGA_FILE_ID 4
 
 namespace tga {
 

@@ -18,10 +18,11 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtga.so")
+# TGA_INDEX_CHECKS=1 loads the index-checked build of the same sources
+LIB_PATH = os.path.join(_HERE, "libtga_check.so" if os.environ.get("TGA_INDEX_CHECKS") == "1" else "libtga.so")
 
 TGA_OK, TGA_ERR_INVALID, TGA_ERR_RANGE, TGA_ERR_NOMEM, TGA_ERR_CUDA = 0, 1, 2, 3, 4
-TGA_ERR_TIMEOUT, TGA_ERR_STATE = 5, 6
+TGA_ERR_TIMEOUT, TGA_ERR_STATE, TGA_ERR_CHECK, TGA_ERR_BOUNDS = 5, 6, 7, 8
 DESCENT_AUTO, DESCENT_PERSISTENT, DESCENT_GRAPH, DESCENT_HOST = 0, 1, 2, 3
 DESCENT_NAMES = {0: "auto", 1: "persistent", 2: "graph", 3: "host"}
 NO_MOVE_KEY = (1 << 64) - 1
@@ -101,6 +102,7 @@ EXPORTS = [
     ("tga_debug_read", ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t,
                                       ctypes.POINTER(ctypes.c_size_t)]),
     ("tga_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int64]),
+    ("tga_get_bounds_report", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     ("tga_set_tile_strip", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tga_destroy", ctypes.c_int, [_P]),
     ("tga_strerror", ctypes.c_char_p, [ctypes.c_int]),
@@ -298,6 +300,12 @@ def tga_set_tile_strip(ctx: int, rows: int, col_warps: int):
 
 def tga_set_wait_limit(ctx: int, limit_ns: int):
     _check(_lib().tga_set_wait_limit(_P(ctx), int(limit_ns)), "tga_set_wait_limit")
+
+
+def tga_get_bounds_report(ctx: int) -> dict:
+    out = (ctypes.c_int64 * 4)()
+    _check(_lib().tga_get_bounds_report(ctx, out), "tga_get_bounds_report")
+    return {"checked": bool(out[0]), "site": int(out[1]), "index": int(out[2]), "limit": int(out[3])}
 
 
 def tga_destroy(ctx: int):

@@ -84,3 +84,15 @@ def test_create_rejects_bad_arguments_on_host(lib):
     rc = tga._lib().tga_eval_best_move_noalloc(ctypes.byref(inst), ctypes.byref(sol), 0x3F, None,
                                                ctypes.c_void_p(1))
     assert rc == tga.TGA_ERR_INVALID
+
+
+def test_index_checked_library_exports_every_declared_symbol(lib):
+    """libtga_check.so (the same sources with -DTGA_BOUNDS_CHECK) is built
+    beside libtga.so and exports the same boundary."""
+    from paper_2506_17357_gb300 import build
+    assert os.path.exists(build.LIB_CHECK)
+    chk = ctypes.CDLL(build.LIB_CHECK)
+    for name in _declared():
+        assert hasattr(chk, name), name
+    chk.tga_strerror.restype = ctypes.c_char_p
+    assert b"index" in chk.tga_strerror(8)
