@@ -450,8 +450,14 @@ def breakdown(inst, sol, mask, dev, stream, reps=200, step_count=200):
     enabled (tga_eval_best_move: its kernels, autotuned inter tile) on the
     initial solution, `reps` evaluations captured in one CUDA graph and
     replayed, so the figure is the device time of the operator's kernels
-    without host launch gaps.  Per step: evaluation and update times of the
-    first steps of the descent through tga_eval_best_move / tga_apply_move."""
+    without host launch gaps.  With one operator enabled the inter-route
+    kernels run their gated variants, which skip the other operators'
+    arithmetic, and an evaluation without an inter-route operator (2-opt)
+    launches no inter-route kernel; every figure still includes the
+    evaluation's fixed launches (begin, intra-route kernel, finalize), which
+    the 2-opt figure is close to.  Per step: evaluation and
+    update times of the first steps of the descent through
+    tga_eval_best_move / tga_apply_move."""
     import torch
     from paper_2506_17357_gb300 import tga as T
     e0 = torch.cuda.Event(enable_timing=True)
@@ -508,7 +514,7 @@ def breakdown(inst, sol, mask, dev, stream, reps=200, step_count=200):
     ls.close()
     return {"per_operator": per_op,
             "per_operator_path": f"{reps} evaluations of the operator alone captured in one CUDA graph "
-                                 "(begin + inter + intra + finalize kernels each), replayed",
+                                 "(begin + gated inter (none for 2-opt) + intra + finalize kernels each), replayed",
             "per_step": {"steps": len(ev), "evaluation_us_median": float(np.median(ev)),
                          "update_us_median": float(np.median(up)),
                          "path": "per-step kernels launched one call at a time (eval: begin + inter + intra + "

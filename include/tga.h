@@ -214,9 +214,20 @@ int tga_set_descent_mode(tga_ctx *ctx, int32_t mode);
 int tga_get_descent_mode(tga_ctx *ctx, int32_t *last_used, int32_t *grid_out);
 
 /* The tile shape the persistent path uses (rows, column warps, row split):
- * the one the autotuner measured fastest, else the inter-route tile with the
- * row split raised to at least 4 warps per block. */
+ * the one the autotuner measured fastest (or set below), else the
+ * inter-route tile with the row split raised to at least 4 warps per block.
+ * row_split 0 is the strip mode: every CTA walks a contiguous share of the
+ * strip-major tile order (the per-step strip kernel's evaluation inside the
+ * persistent launch). */
 int tga_get_persistent_shape(tga_ctx *ctx, int32_t *rows, int32_t *col_warps, int32_t *row_split);
+
+/* Set the persistent path's tile shape (no counterpart in the paper; a
+ * tuning control): rows 8, 16, 32 or 64, col_warps 2, 4 or 8, row_split 1, 2
+ * or 4 with col_warps * row_split * 32 = 128 or 256 threads; or row_split 0
+ * (strip mode) with rows 16 or 32 and col_warps 4 or 8.  rows = 0 clears
+ * the setting (the automatic choice applies again).  TGA_ERR_INVALID for
+ * any other shape.  The next persistent descent uses it. */
+int tga_set_persistent_shape(tga_ctx *ctx, int32_t rows, int32_t col_warps, int32_t row_split);
 
 /* Descend every context to a local optimum (at most max_steps moves each) in
  * ONE persistent launch on ctxs[0]'s stream (all contexts on one device).

@@ -685,8 +685,10 @@ static float time_path(tga_ctx *c, int steps, bool persistent, int rows, int war
 // per evaluation wins.  The caller's solution is restored and the
 // attributes rebuilt afterwards.
 static int tune_descent(tga_ctx *c, cudaEvent_t e0, cudaEvent_t e1) {
+    // rows, column warps, row split (0: strip mode)
     static const int pshapes[][3] = {{8, 2, 2},  {16, 2, 2}, {16, 4, 1}, {16, 4, 2}, {16, 2, 4},
-                                     {32, 2, 2}, {32, 4, 1}, {32, 4, 2}, {32, 8, 1}, {64, 4, 1}, {64, 8, 1}};
+                                     {32, 2, 2}, {32, 4, 1}, {32, 4, 2}, {32, 8, 1}, {64, 4, 1},
+                                     {64, 8, 1}, {16, 4, 0}, {16, 8, 0}, {32, 4, 0}, {32, 8, 0}};
     const int steps = 24;
     const size_t n = (size_t)c->d.n, m = (size_t)c->d.m;
     cudaMemcpyAsync(c->saved, c->d.tour, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream);
@@ -769,6 +771,27 @@ int tga_get_descent_mode(tga_ctx *c, int32_t *last_used, int32_t *grid_out) {
     if (!c || !last_used) return TGA_ERR_INVALID;
     *last_used = c->last_mode;
     if (grid_out) *grid_out = c->last_mode == TGA_DESCENT_PERSISTENT ? c->persist_grid : 0;
+    return TGA_OK;
+}
+
+int tga_set_persistent_shape(tga_ctx *c, int32_t rows, int32_t col_warps, int32_t row_split) {
+    if (!c) return TGA_ERR_INVALID;
+    if (rows == 0) {
+        c->ptile_rows = c->ptile_warps = c->ptile_rs = 0;
+        return TGA_OK;
+    }
+    const bool rows_ok = rows == 8 || rows == 16 || rows == 32 || rows == 64;
+    const bool warps_ok = col_warps == 2 || col_warps == 4 || col_warps == 8;
+    bool ok;
+    if (row_split == 0) {
+        ok = (rows == 16 || rows == 32) && (col_warps == 4 || col_warps == 8);
+    } else {
+        const int nt = col_warps * row_split * 32;
+        ok = rows_ok && warps_ok && (row_split == 1 || row_split == 2 || row_split == 4) && (nt == 128 || nt == 256) &&
+             rows % row_split == 0;
+    }
+    if (!ok) return TGA_ERR_INVALID;
+    c->ptile_rows = rows; c->ptile_warps = col_warps; c->ptile_rs = row_split;
     return TGA_OK;
 }
 

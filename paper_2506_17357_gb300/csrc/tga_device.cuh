@@ -588,6 +588,16 @@ __device__ __forceinline__ int2 tile_of(int bid, int Wp, int TR, int TC) {
     return make_int2(lo, lo / g + (int)(bid - before(lo)));
 }
 
+// Asynchronous global -> shared copies of 16 bytes (cp.async, L2 only: the
+// copies read what other SMs wrote before the last grid-wide hand-off).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // The column side of an inter-route tile: the anchor av at position q and
 // its hoisted constants (ERec groups; PRec with pickups), held in registers
 // while a warp walks the rows.
@@ -598,9 +608,9 @@ struct InterCol {
 };
 
 template <bool TW, bool OR, bool PD>
-__device__ __forceinline__ void inter_col_load(const Dev &d, int q, InterCol &c) {
+__device__ __forceinline__ void inter_col_fill(const Dev &d, int q, int av, InterCol &c) {
     c.q = q;
-    c.av = (q < d.Wp) ? d.seq[TGA_IX(q, d.Wp)] : d.W;
+    c.av = av;
     const int4 *vr = reinterpret_cast<const int4 *>(d.erec + TGA_IX(c.av, d.W + 1));
     c.v0 = TGA_LDG(vr + 0); c.v1 = TGA_LDG(vr + 1); c.v2 = TGA_LDG(vr + 2);
     c.v3 = make_int4(0, 0, 0, 0); c.v4 = c.v3; c.v5 = c.v3; c.v6 = c.v3;
@@ -615,6 +625,11 @@ __device__ __forceinline__ void inter_col_load(const Dev &d, int q, InterCol &c)
     }
 }
 
+template <bool TW, bool OR, bool PD>
+__device__ __forceinline__ void inter_col_load(const Dev &d, int q, InterCol &c) {
+    inter_col_fill<TW, OR, PD>(d, q, (q < d.Wp) ? d.seq[TGA_IX(q, d.Wp)] : d.W, c);
+}
+
 // Rows i0..i1-1 of a staged tile against one column: row i is the anchor at
 // position p0 + i with its records at sR[i*NG ..] (ERec groups, then PRec
 // with pickups); col points at the column's distance in the tile's row
@@ -623,7 +638,7 @@ __device__ __forceinline__ void inter_col_load(const Dev &d, int q, InterCol &c)
 // into (best, bidx).  UNR: row-loop unrolling (lets the compiler issue the
 // next rows' shared loads early; the strip kernel gains from it, the
 // one-wave persistent descent does not).
-template <bool TW, bool OR, bool PD = false, int UNR = 1>
+template <bool TW, bool OR, bool PD = false, int UNR = 1, bool GATE = false>
 __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, const int *col, const int4 *sR, int LDT,
                                            int p0, int i0, int i1, int &best, unsigned &bidx) {
     constexpr int NG = PD ? 12 : 8;                           // int4 records per row
@@ -647,6 +662,12 @@ __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, cons
     int t10 = c0[2 * LDT], t11 = c0[2 * LDT + 1], t12 = c0[2 * LDT + 2];
     int t21 = c0[3 * LDT + 1];
     int wbest = __reduce_min_sync(0xffffffffu, best);
+    // GATE: skip the operators the mask disables (their deltas stay kBig,
+    // above every valid delta); without it every operator of the variant is
+    // on and the code is the ungated one
+    const unsigned mk = d.op_mask;
+    const bool onR = !GATE || (mk & 1u), onS = !GATE || (mk & 2u), onX = !GATE || (mk & 8u);
+    const bool onO2 = !GATE || (mk & 16u), onO3 = !GATE || (mk & 32u);
 
 #pragma unroll UNR
     for (int i = i0; i < i1; ++i) {
@@ -660,23 +681,31 @@ __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, cons
         //   c(u+,v++)=t12 c(u-,v)=tm10 c(u,v-)=t0m1
         // relocate u -> after v, relocate v -> after u
         // (with pickups the load terms follow below)
-        int dR1 = Urem1 + VK1 + t00 + t01 + (PD ? 0 : wL * max(VLQ + Ud, 0));
-        int dR2 = Vrem1 + UK1 + t00 + t10 + (PD ? 0 : wL * max(ULQ + Vd, 0));
+        int dR1 = kBig, dR2 = kBig, dS = kBig, dX = kBig;
+        if (onR) {
+            dR1 = Urem1 + VK1 + t00 + t01 + (PD ? 0 : wL * max(VLQ + Ud, 0));
+            dR2 = Vrem1 + UK1 + t00 + t10 + (PD ? 0 : wL * max(ULQ + Vd, 0));
+        }
         // swap u <-> v
-        int dS = UK2 + VK2 + tm10 + t10 + t0m1 + t01 +
-                 (PD ? 0 : wL * (max(ULQd + Vd, 0) + max(VLQd + Ud, 0)));
+        if (onS)
+            dS = UK2 + VK2 + tm10 + t10 + t0m1 + t01 + (PD ? 0 : wL * (max(ULQd + Vd, 0) + max(VLQd + Ud, 0)));
         // 2-opt*: head(u)+tail after v, head(v)+tail after u
-        int dX = UFc + VGc + VFc + UGc + t01 + t10 +
+        if (onX)
+            dX = UFc + VGc + VFc + UGc + t01 + t10 +
                  (PD ? 0 : wL * (max(Uloadf + VloadgQ, 0) + max(Vloadf + UloadgQ, 0)));
-        int dO2a = 0, dO2b = 0, dO3a = 0, dO3b = 0;
+        int dO2a = kBig, dO2b = kBig, dO3a = kBig, dO3b = kBig;
         int4 u3 = make_int4(0, 0, 0, 0);
         if (OR) {
             u3 = sR[i * NG + 3];
             const int UC2 = u3.x, Uld2 = u3.y, UC3 = u3.z, Uld3 = u3.w;
-            dO2a = UC2 + VK1 + t00 + t11 + (PD ? 0 : wL * max(VLQ + Uld2, 0));
-            dO2b = VC2 + UK1 + t00 + t11 + (PD ? 0 : wL * max(ULQ + Vld2, 0));
-            dO3a = UC3 + VK1 + t00 + t21 + (PD ? 0 : wL * max(VLQ + Uld3, 0));
-            dO3b = VC3 + UK1 + t00 + t12 + (PD ? 0 : wL * max(ULQ + Vld3, 0));
+            if (onO2) {
+                dO2a = UC2 + VK1 + t00 + t11 + (PD ? 0 : wL * max(VLQ + Uld2, 0));
+                dO2b = VC2 + UK1 + t00 + t11 + (PD ? 0 : wL * max(ULQ + Vld2, 0));
+            }
+            if (onO3) {
+                dO3a = UC3 + VK1 + t00 + t21 + (PD ? 0 : wL * max(VLQ + Uld3, 0));
+                dO3b = VC3 + UK1 + t00 + t12 + (PD ? 0 : wL * max(ULQ + Vld3, 0));
+            }
         }
         if (PD) {
             // largest loads of the new routes (Section 4.3.2) from the PRec
@@ -689,20 +718,27 @@ __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, cons
             const int VIA = w0.x, VIB = w0.y, VIC = w0.z, Vpk = w0.w;
             const int VSA = w1.x, VSB = w1.y, VSC = w1.z, Vmx = w1.w;
             const int VHM = w2.x, VHO = w2.y, VTI = w2.z, VTM = w2.w;
-            dR1 += wL * max(max(max(VIA + Ud, VIB + Umx), VIC + Upk), 0);
-            dR2 += wL * max(max(max(UIA + Vd, UIB + Vmx), UIC + Vpk), 0);
-            dS += wL * (max(max(max(USA + Vd, USB + Vmx), USC + Vpk), 0) +
-                        max(max(max(VSA + Ud, VSB + Umx), VSC + Upk), 0));
-            dX += wL * (max(max(UHM + VTI, UHO + VTM), 0) + max(max(VHM + UTI, VHO + UTM), 0));
+            if (onR) {
+                dR1 += wL * max(max(max(VIA + Ud, VIB + Umx), VIC + Upk), 0);
+                dR2 += wL * max(max(max(UIA + Vd, UIB + Vmx), UIC + Vpk), 0);
+            }
+            if (onS)
+                dS += wL * (max(max(max(USA + Vd, USB + Vmx), USC + Vpk), 0) +
+                            max(max(max(VSA + Ud, VSB + Umx), VSC + Upk), 0));
+            if (onX) dX += wL * (max(max(UHM + VTI, UHO + VTM), 0) + max(max(VHM + UTI, VHO + UTM), 0));
             if (OR) {
                 const int4 x3 = sR[i * NG + 11];
                 const int ULO2 = x3.x, ULM2 = x3.y, ULO3 = x3.z, ULM3 = x3.w;
                 const int VLO2 = w3.x, VLM2 = w3.y, VLO3 = w3.z, VLM3 = w3.w;
                 const int Uld2 = u3.y, Uld3 = u3.w;
-                dO2a += wL * max(max(max(VIA + Uld2, VIB + ULM2), VIC + ULO2), 0);
-                dO2b += wL * max(max(max(UIA + Vld2, UIB + VLM2), UIC + VLO2), 0);
-                dO3a += wL * max(max(max(VIA + Uld3, VIB + ULM3), VIC + ULO3), 0);
-                dO3b += wL * max(max(max(UIA + Vld3, UIB + VLM3), UIC + VLO3), 0);
+                if (onO2) {
+                    dO2a += wL * max(max(max(VIA + Uld2, VIB + ULM2), VIC + ULO2), 0);
+                    dO2b += wL * max(max(max(UIA + Vld2, UIB + VLM2), UIC + VLO2), 0);
+                }
+                if (onO3) {
+                    dO3a += wL * max(max(max(VIA + Uld3, VIB + ULM3), VIC + ULO3), 0);
+                    dO3b += wL * max(max(max(UIA + Vld3, UIB + VLM3), UIC + VLO3), 0);
+                }
             }
         }
         const bool skip = (Uroute == Vroute) | (p >= q);
@@ -718,44 +754,44 @@ __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, cons
             const int4 u4 = sR[i * NG + 4], u5 = sR[i * NG + 5];
             const int Ue = u4.x, Ul = u4.y, Us = u4.z, Utau = u4.w;
             const int ULg = u5.x, UtauP = u5.y;
-            {   // u inserted between v and v+
+            if (onR) {   // u inserted between v and v+
                 const int a1 = Vtau + t00, w1 = max(a1 - Ul, 0);
                 const int a2 = max(a1, Ue) - w1 + Us + t01, w2 = max(a2 - VLg, 0);
                 dR1 += wT * (w1 + w2);
             }
-            {   // v inserted between u and u+
+            if (onR) {   // v inserted between u and u+
                 const int a1 = Utau + t00, w1 = max(a1 - Vl, 0);
                 const int a2 = max(a1, Ve) - w1 + Vs + t10, w2 = max(a2 - ULg, 0);
                 dR2 += wT * (w1 + w2);
             }
-            {   // v between u- and u+, u between v- and v+
+            if (onS) {   // v between u- and u+, u between v- and v+
                 const int a1 = UtauP + tm10, w1 = max(a1 - Vl, 0);
                 const int a2 = max(a1, Ve) - w1 + Vs + t10, w2 = max(a2 - ULg, 0);
                 const int b1 = VtauP + t0m1, x1 = max(b1 - Ul, 0);
                 const int b2 = max(b1, Ue) - x1 + Us + t01, x2 = max(b2 - VLg, 0);
                 dS += wT * (w1 + w2 + x1 + x2);
             }
-            dX += wT * (max(Utau + t01 - VLg, 0) + max(Vtau + t10 - ULg, 0));
+            if (onX) dX += wT * (max(Utau + t01 - VLg, 0) + max(Vtau + t10 - ULg, 0));
             if (OR) {
                 const int UE2 = u5.z, UL2 = u5.w;
                 const int4 u6 = sR[i * NG + 6];
                 const int UDm2 = u6.x, UE3 = u6.y, UL3 = u6.z, UDm3 = u6.w;
-                {
+                if (onO2) {
                     const int a1 = Vtau + t00, w1 = max(a1 - UL2, 0);
                     const int a2 = max(a1, UE2) - w1 + UDm2 + t11, w2 = max(a2 - VLg, 0);
                     dO2a += wT * (w1 + w2);
                 }
-                {
+                if (onO2) {
                     const int a1 = Utau + t00, w1 = max(a1 - VL2, 0);
                     const int a2 = max(a1, VE2) - w1 + VDm2 + t11, w2 = max(a2 - ULg, 0);
                     dO2b += wT * (w1 + w2);
                 }
-                {
+                if (onO3) {
                     const int a1 = Vtau + t00, w1 = max(a1 - UL3, 0);
                     const int a2 = max(a1, UE3) - w1 + UDm3 + t21, w2 = max(a2 - VLg, 0);
                     dO3a += wT * (w1 + w2);
                 }
-                {
+                if (onO3) {
                     const int a1 = Utau + t00, w1 = max(a1 - VL3, 0);
                     const int a2 = max(a1, VE3) - w1 + VDm3 + t12, w2 = max(a2 - ULg, 0);
                     dO3b += wT * (w1 + w2);
@@ -805,7 +841,7 @@ __device__ __forceinline__ void inter_rows(const Dev &d, const InterCol &c, cons
 // its column's candidates into (best, bidx); smem must hold
 // inter_smem_bytes(TR, NWc, PD).  PD: pickups (requires TW); every load
 // excess is that of the new route's largest load (PRec constants).
-template <bool TW, bool OR, bool PD = false>
+template <bool TW, bool OR, bool PD = false, bool GATE = false>
 __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *smem, int &best, unsigned &bidx) {
     constexpr int NG = PD ? 12 : 8;                           // int4 records per row
     const int NW = blockDim.x >> 5, NWc = NW / RS, TC = NWc * 32;
@@ -815,36 +851,141 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
     const int LDT = TC + 8;
     int *sT = smem;                                           // (TR+4) x LDT distances
     int4 *sR = reinterpret_cast<int4 *>(smem + (TR + 4) * LDT);   // TR row records (ERec, then PRec)
+    __shared__ int s_rnode[68];                               // nodes of positions p0-1 .. p0+TR+2 (TR <= 64)
+    __shared__ int s_ranc[64];                                // anchors of positions p0 .. p0+TR-1
+    // round 1: the anchors of the rows and of this thread's column
+    const int q = q0 + cw * 32 + lane;
+    const int av = (q < d.Wp) ? d.seq[TGA_IX(q, d.Wp)] : d.W;
     __syncthreads();                                          // previous user of smem is done
+    for (int t = threadIdx.x; t < TR + 4; t += blockDim.x) {
+        const int p = p0 - 1 + t;
+        const bool in = p >= 0 && p < d.Wp;
+        const int a = in ? d.seq[TGA_IX(p, d.Wp)] : d.W;
+        s_rnode[t] = in ? node_of(a, d.n) : 0;
+        if (t >= 1 && t <= TR) s_ranc[t - 1] = a;
+    }
+    __syncthreads();
+    // round 2, all issued before any is waited for: the extraction rows
+    // p0-1 .. p0+TR+2 over positions q0-4 .. q0+TC+3 and the row records
+    // (asynchronous copies), and the column's records (registers)
+    const int C4 = LDT >> 2;
+    for (int i = threadIdx.x; i < (TR + 4) * C4; i += blockDim.x) {
+        const int rr = i / C4, c4 = i - rr * C4;
+        cp_async16(sT + rr * LDT + 4 * c4,
+                   d.pcol + (size_t)TGA_IX(s_rnode[rr], d.n + 1) * d.ldp + TGA_IX(q0 + 4 * c4, d.ldp - 3));
+    }
+    for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
+        const int row = i / NG, g = i - row * NG;
+        const int a = s_ranc[row];
+        cp_async16(sR + i, g < 8 ? reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + g
+                                 : reinterpret_cast<const int4 *>(d.prec + TGA_IX(a, d.W + 1)) + (g - 8));
+    }
+    cp_async_commit();
+    InterCol c;
+    inter_col_fill<TW, OR, PD>(d, q, av, c);
+    cp_async_wait<0>();
+    __syncthreads();
+    inter_rows<TW, OR, PD, 1, GATE>(d, c, sT + cw * 32 + lane + 4, sR, LDT, p0, i0, i1, best, bidx);
+}
 
-    // Extraction: rows p0-1 .. p0+TR+2, positions q0-4 .. q0+TC+3
-    for (int rr = warp; rr < TR + 4; rr += NW) {
-        const int p = p0 - 1 + rr;
-        const int node = (p >= 0 && p < d.Wp) ? node_of(d.seq[TGA_IX(p, d.Wp)], d.n) : 0;
+// Anchor at position p for row staging (positions outside the sequence read
+// the dummy record W, whose node is the depot).
+__device__ __forceinline__ int strip_anchor(const Dev &d, int p) { return (p >= 0 && p < d.Wp) ? d.seq[TGA_IX(p, d.Wp)] : d.W; }
+
+// Issue the copies of one tile: TR+4 distance rows (the nodes of positions
+// p0-1 .. p0+TR+2, storage columns q0 .. q0+TC+7, i.e. positions
+// q0-4 .. q0+TC+3) and the TR row records (ERec, then PRec with pickups).
+template <bool PD>
+__device__ __forceinline__ void strip_stage(const Dev &d, int *buf, int TR, int q0, const int *s_anc) {
+    constexpr int NG = PD ? 12 : 8;
+    const int NW = blockDim.x >> 5, TC = NW * 32, LDT = TC + 8, C4 = LDT >> 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int4 *sR = reinterpret_cast<int4 *>(buf + (TR + 4) * LDT);
+    for (int r = warp; r < TR + 4; r += NW) {
+        const int node = node_of(s_anc[r], d.n);
         const int4 *src =
             reinterpret_cast<const int4 *>(d.pcol + (size_t)TGA_IX(node, d.n + 1) * d.ldp + TGA_IX(q0, d.ldp - LDT + 1));
-        int4 *dst = reinterpret_cast<int4 *>(sT + rr * LDT);
-        for (int c = lane; c < (LDT >> 2); c += 32) dst[c] = TGA_LDG(src + c);
+        int4 *dst = reinterpret_cast<int4 *>(buf + r * LDT);
+        for (int c = lane; c < C4; c += 32) cp_async16(dst + c, src + c);
     }
-    if (PD) {
-        for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
-            const int row = i / NG, g = i - row * NG;
-            const int p = p0 + row;
-            const int a = (p < d.Wp) ? d.seq[TGA_IX(p, d.Wp)] : d.W;
-            sR[i] = g < 8 ? TGA_LDG(reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + g)
-                          : TGA_LDG(reinterpret_cast<const int4 *>(d.prec + TGA_IX(a, d.W + 1)) + (g - 8));
+    for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
+        const int row = i / NG, g = i - row * NG;
+        const int a = s_anc[row + 1];
+        const int4 *src = g < 8 ? reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + g
+                                : reinterpret_cast<const int4 *>(d.prec + TGA_IX(a, d.W + 1)) + (g - 8);
+        cp_async16(sR + i, src);
+    }
+}
+
+// Walk the tiles t0 .. t1-1 of the strip-major order (TR rows x TC =
+// 32 * warps columns each): the anchors of each tile, its copies into one of
+// two buffers while the other is computed, the strip's column anchors in
+// registers, and the row loop of inter_rows.  smem: strip_smem_bytes(TR,
+// warps, PD); every thread of the block calls.  Used by the per-step kernel
+// (k_eval_strip) and by the persistent descent's strip mode.
+template <bool TW, bool OR, bool PD = false, bool GATE = false, int UNR = TW ? 1 : 4>
+__device__ void strip_walk(const Dev &d, int TR, long long T, long long t0, long long t1, int *smem, int &best,
+                           unsigned &bidx) {
+    constexpr int NG = PD ? 12 : 8;
+    const int NW = blockDim.x >> 5, TC = NW * 32, LDT = TC + 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
+    const int Wa = d.Wp - 1;
+    const int nrt = (Wa + TR - 1) / TR, nct = (Wa + TC - 1) / TC, g = TC / TR;
+    const int buf_ints = (TR + 4) * LDT + TR * NG * 4;
+    int *s_anc = smem + 2 * buf_ints;                    // two (TR+4)-entry anchor lists (positions p0-1 ..)
+    (void)T;
+    __syncthreads();                                     // the previous user of smem is done
+    if (t0 < t1) {
+        // strip and row tile of t0: the last strip that starts at or before t0
+        int lo = 0, hi = nct - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (strip_before(mid, nrt, g) <= t0) lo = mid;
+            else hi = mid - 1;
         }
-    } else {
-        for (int i = threadIdx.x; i < TR * 8; i += blockDim.x) {
-            const int p = p0 + (i >> 3);
-            const int a = (p < d.Wp) ? d.seq[TGA_IX(p, d.Wp)] : d.W;
-            sR[i] = TGA_LDG(reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + (i & 7));
+        int J = lo, I = (int)(t0 - strip_before(lo, nrt, g));
+        auto next = [&](int &j, int &i) {
+            if (++i >= min((j + 1) * g, nrt)) { ++j; i = 0; }
+        };
+        // prologue: anchors of tile t0, its copies, and the anchors of t0 + 1
+        if (tid < TR + 4) s_anc[tid] = strip_anchor(d, I * TR - 1 + tid);
+        int Jn = J, In = I;
+        next(Jn, In);
+        int a_next = (t0 + 1 < t1 && tid < TR + 4) ? strip_anchor(d, In * TR - 1 + tid) : 0;
+        __syncthreads();
+        strip_stage<PD>(d, smem, TR, J * TC, s_anc);
+        cp_async_commit();
+        InterCol c;
+        int Jc = -1;
+        for (long long k = t0; k < t1; ++k) {
+            const int b = (int)((k - t0) & 1);
+            int *cur = smem + b * buf_ints;
+            const bool more = k + 1 < t1;
+            if (more) {
+                int *nanc = s_anc + (b ^ 1) * (TR + 4);
+                if (tid < TR + 4) nanc[tid] = a_next;
+                __syncthreads();                         // anchors written; the other buffer is free
+                strip_stage<PD>(d, smem + (b ^ 1) * buf_ints, TR, Jn * TC, nanc);
+                cp_async_commit();
+                int Jnn = Jn, Inn = In;
+                next(Jnn, Inn);
+                if (k + 2 < t1 && tid < TR + 4) a_next = strip_anchor(d, Inn * TR - 1 + tid);
+                cp_async_wait<1>();                      // this tile's copies are done
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();                             // ... for every thread of the block
+            if (J != Jc) {                               // a new strip: its column anchors
+                inter_col_load<TW, OR, PD>(d, J * TC + warp * 32 + lane, c);
+                Jc = J;
+            }
+            inter_rows<TW, OR, PD, UNR, GATE>(d, c, cur + warp * 32 + lane + 4,
+                                   reinterpret_cast<const int4 *>(cur + (TR + 4) * LDT), LDT, I * TR, 0, TR,
+                                   best, bidx);
+            J = Jn; I = In;
+            next(Jn, In);
         }
     }
-    InterCol c;
-    inter_col_load<TW, OR, PD>(d, q0 + cw * 32 + lane, c);
-    __syncthreads();
-    inter_rows<TW, OR, PD>(d, c, sT + cw * 32 + lane + 4, sR, LDT, p0, i0, i1, best, bidx);
 }
 
 // ---------------------------------------------------------------------------
@@ -1697,6 +1838,78 @@ __device__ void intra_cvrp_position(const Dev &d, int p, int lane, int &best, un
     }
 }
 
+// Intra-route candidates of a whole CVRP route r with one warp (all lanes
+// call; relocate, or-opt, swap and 2-opt, no swaps of runs).  Lane k reads
+// the node of element k (0 = start depot, L+1 = end depot) and then element
+// k's column of the route's (L+2) x (L+2) distance block, row by row, from
+// the position-ordered copy (row x_a, columns st .. st+L+1: contiguous over
+// the lanes).  The block sits in shared memory (sD, 32 x 33 ints per warp;
+// sA, 32 anchors), and every candidate (i, j) is then an O(1) edge formula
+// over it -- the same expressions as intra_cvrp_position:
+//   relocate / or-opt run i..i+k-1 after j: c(x_i-1, x_i+k) - e(i-1) - e(i+k-1)
+//       + c(x_j, x_i) + c(x_i+k-1, x_j+1) - e(j)
+//   swap i < j, 2-opt i < j (reversal of i..j)
+// with e(k) = c(x_k, x_k+1).  Routes of more than 30 customers take
+// intra_cvrp_position for each of their customers.
+constexpr int kCvrpRouteInts = 32 * 33;                 // per warp: the distance block of one route
+
+__device__ void intra_cvrp_route(const Dev &d, int r, int lane, int *sD, int *sA, int &best, unsigned &bidx) {
+    if (r >= d.m) return;
+    const RouteRec R = d.rrec[TGA_IX(r, d.m)];
+    const int L = R.len, st = R.start, E = L + 2;
+    if (L < 2) return;
+    if (E > 32) {
+        for (int k = 1; k <= L; ++k) intra_cvrp_position<false>(d, st + k, lane, best, bidx);
+        return;
+    }
+    constexpr int LD = 33;
+    const int x = lane < E ? node_of(d.seq[TGA_IX(st + lane, d.Wp)], d.n) : 0;
+    sA[lane] = lane == 0 ? d.n + 1 + r : x;             // anchor of element k (customers: their node)
+    // eight rows per round: the loads of a round are all issued before the
+    // first of them is stored
+    for (int a0 = 0; a0 < E; a0 += 8) {
+        int v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int xa = __shfl_sync(0xffffffffu, x, (a0 + u) & 31);
+            v[u] = (a0 + u < E && lane < E)
+                       ? TGA_LDG(d.pcol + (size_t)TGA_IX(xa, d.n + 1) * d.ldp + TGA_IX(kColOff + st + lane, d.ldp))
+                       : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (a0 + u < E) sD[(a0 + u) * LD + lane] = v[u];
+    }
+    __syncwarp();
+    const unsigned mask = d.op_mask;
+    const unsigned W = (unsigned)d.W, W2 = W * W;
+    auto D = [&](int a, int b) { return sD[a * LD + b]; };
+    auto e = [&](int k) { return sD[k * LD + k + 1]; };
+    const int T = L * (L + 1);
+    for (int t = lane; t < T; t += 32) {
+        const int i = t / (L + 1) + 1, j = t - (i - 1) * (L + 1);
+        const unsigned xi = (unsigned)sA[i], aj = (unsigned)sA[j];
+        const int cji = D(j, i), ej = e(j);
+        for (int k = 1; k <= 3; ++k) {
+            const int op = k == 1 ? 0 : k + 2;
+            if (!(mask & (1u << op)) || i + k - 1 > L) continue;
+            if (j >= i - 1 && j <= i + k - 1) continue;
+            const int delta = D(i - 1, i + k) - e(i - 1) - e(i + k - 1) + cji + D(i + k - 1, j + 1) - ej;
+            TGA_TRY(delta, (unsigned)op * W2 + xi * W + aj);
+        }
+        if (j > i) {
+            const int cpj = D(i - 1, j), ci_j1 = D(i, j + 1);
+            if (mask & 2u) {
+                const int delta = j == i + 1 ? cpj + ci_j1 - e(i - 1) - ej
+                                             : cpj + D(i + 1, j) + D(i, j - 1) + ci_j1 - e(i - 1) - e(i) - e(j - 1) - ej;
+                TGA_TRY(delta, W2 + min(xi, aj) * W + max(xi, aj));
+            }
+            if (mask & 4u) TGA_TRY(cpj + ci_j1 - e(i - 1) - ej, 2u * W2 + xi * W + aj);
+        }
+    }
+    __syncwarp();                                        // sD, sA are reused by the next route
+}
+
 // ---------------------------------------------------------------------------
 // apply (tensor update of Section 5.3.5)
 //
@@ -2123,12 +2336,14 @@ __device__ void decode_plan(const Dev &d, const tga_move *ext, StepPlan &S) {
 // sbuf when a route fits one warp, else with the chunked scans -- while the
 // other warps find the longest route and heaviest load of the rest and one
 // thread prefetches the counters.  Thread 0 then updates cost and counters
-// and ends the step (done flag, graph condition).  ext: the move came from
-// the caller, whose delta is not checked against the rebuilt routes.
+// and ends the step (done flag, graph condition); it returns 1 when the
+// descent ends with this step (other threads return 0).  ext: the move came
+// from the caller, whose delta is not checked against the rebuilt routes.
 template <bool PD, bool XS = false>
-__device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, bool ext,
-                                 cudaGraphConditionalHandle cond, int use_cond) {
+__device__ int apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, bool ext,
+                                cudaGraphConditionalHandle cond, int use_cond) {
     Control *C = d.ctl;
+    int stop = 0;                             // thread 0: the descent ends with this step
     __shared__ int s_maxL, s_maxLoad;
     __shared__ int s_tot[2][4];
     __shared__ int s_fast[2];
@@ -2227,15 +2442,17 @@ __device__ void apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, boo
                 set_status(C, TGA_ERR_RANGE);
                 status = TGA_ERR_RANGE;
             }
-            if (status != 0 || steps >= s_cf[5]) C->done = 1;
-            if (use_cond) cudaGraphSetConditional(cond, (status == 0 && steps < s_cf[5]) ? 1u : 0u);
+            stop = status != 0 || steps >= s_cf[5];
+            if (stop) C->done = 1;
+            if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
         } else {
             // a stop (error or step limit) also ends host-launched descents
             if (C->status != 0 || C->steps >= C->step_limit) C->done = 1;
-            if (use_cond)
-                cudaGraphSetConditional(cond, (!C->done && C->steps < C->step_limit) ? 1u : 0u);
+            stop = *(volatile int *)&C->done != 0 || C->steps >= C->step_limit;
+            if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
         }
     }
+    return stop;
 }
 
 // row[t + dl] = row[t] for t in [s0, s1], one warp: passes of 8 x 32 values

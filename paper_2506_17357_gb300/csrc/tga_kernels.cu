@@ -17,7 +17,7 @@
 //                  (route-based extraction of Section 5.3.1): one CTA per
 //                  route builds the route's subsequence tables (Section 4.2)
 //                  in shared memory and takes the (i, j) pairs in parallel;
-//                  k_eval_intra_cvrp: one warp per moved CVRP customer.
+//                  k_eval_intra_cvrp: one warp per CVRP route.
 //   k_apply        Tensor update (Section 5.3.5) on the device: CTA 0 decodes
 //                  the best key, rewrites the positions and rebuilds the
 //                  attributes of the <= 2 touched routes; the other CTAs keep
@@ -67,7 +67,7 @@ __global__ void k_pcol_init(Dev d) {
 // The finished-descent flag is loaded first but tested only before the key
 // is folded in, so its round trip overlaps the staging loads (a launch on a
 // finished descent does its work and discards it).
-template <bool TW, bool OR, bool PD = false>
+template <bool TW, bool OR, bool PD = false, bool GATE = false>
 __global__ void __launch_bounds__(256) k_eval_inter(Dev d, int TR, int RS, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
     extern __shared__ __align__(16) int smem[];
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) k_eval_inter(Dev d, int TR, int RS, int t
     const int2 tl = tile_of(blockIdx.x, d.Wp, TR, TC);
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    inter_tile<TW, OR, PD>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
+    inter_tile<TW, OR, PD, GATE>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
     if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
@@ -94,109 +94,16 @@ __global__ void __launch_bounds__(256) k_eval_inter(Dev d, int TR, int RS, int t
 // while it computes the current tile.  The candidates and their order are
 // those of k_eval_inter (the same row loop, inter_rows).
 
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Anchor at position p for row staging (positions outside the sequence read
-// the dummy record W, whose node is the depot).
-__device__ __forceinline__ int strip_anchor(const Dev &d, int p) { return (p >= 0 && p < d.Wp) ? d.seq[TGA_IX(p, d.Wp)] : d.W; }
-
-// Issue the copies of one tile: TR+4 distance rows (the nodes of positions
-// p0-1 .. p0+TR+2, storage columns q0 .. q0+TC+7, i.e. positions
-// q0-4 .. q0+TC+3) and the TR row records (ERec, then PRec with pickups).
-template <bool PD>
-__device__ __forceinline__ void strip_stage(const Dev &d, int *buf, int TR, int q0, const int *s_anc) {
-    constexpr int NG = PD ? 12 : 8;
-    const int NW = blockDim.x >> 5, TC = NW * 32, LDT = TC + 8, C4 = LDT >> 2;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int4 *sR = reinterpret_cast<int4 *>(buf + (TR + 4) * LDT);
-    for (int r = warp; r < TR + 4; r += NW) {
-        const int node = node_of(s_anc[r], d.n);
-        const int4 *src =
-            reinterpret_cast<const int4 *>(d.pcol + (size_t)TGA_IX(node, d.n + 1) * d.ldp + TGA_IX(q0, d.ldp - LDT + 1));
-        int4 *dst = reinterpret_cast<int4 *>(buf + r * LDT);
-        for (int c = lane; c < C4; c += 32) cp_async16(dst + c, src + c);
-    }
-    for (int i = threadIdx.x; i < TR * NG; i += blockDim.x) {
-        const int row = i / NG, g = i - row * NG;
-        const int a = s_anc[row + 1];
-        const int4 *src = g < 8 ? reinterpret_cast<const int4 *>(d.erec + TGA_IX(a, d.W + 1)) + g
-                                : reinterpret_cast<const int4 *>(d.prec + TGA_IX(a, d.W + 1)) + (g - 8);
-        cp_async16(sR + i, src);
-    }
-}
-
-template <bool TW, bool OR, bool PD = false>
+template <bool TW, bool OR, bool PD = false, bool GATE = false>
 __global__ void __launch_bounds__(256, TW ? 3 : 4) k_eval_strip(Dev d, int TR, long long T, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
     extern __shared__ __align__(16) int smem[];
-    constexpr int NG = PD ? 12 : 8;
-    const int NW = blockDim.x >> 5, TC = NW * 32, LDT = TC + 8;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, tid = threadIdx.x;
-    const int Wa = d.Wp - 1;
-    const int nrt = (Wa + TR - 1) / TR, nct = (Wa + TC - 1) / TC, g = TC / TR;
-    const int buf_ints = (TR + 4) * LDT + TR * NG * 4;
-    int *s_anc = smem + 2 * buf_ints;                    // two (TR+4)-entry anchor lists (positions p0-1 ..)
     const long long t0 = (long long)blockIdx.x * T / gridDim.x;
     const long long t1 = (long long)(blockIdx.x + 1) * T / gridDim.x;
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    if (t0 < t1) {
-        // strip and row tile of t0: the last strip that starts at or before t0
-        int lo = 0, hi = nct - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (strip_before(mid, nrt, g) <= t0) lo = mid;
-            else hi = mid - 1;
-        }
-        int J = lo, I = (int)(t0 - strip_before(lo, nrt, g));
-        auto next = [&](int &j, int &i) {
-            if (++i >= min((j + 1) * g, nrt)) { ++j; i = 0; }
-        };
-        // prologue: anchors of tile t0, its copies, and the anchors of t0 + 1
-        if (tid < TR + 4) s_anc[tid] = strip_anchor(d, I * TR - 1 + tid);
-        int Jn = J, In = I;
-        next(Jn, In);
-        int a_next = (t0 + 1 < t1 && tid < TR + 4) ? strip_anchor(d, In * TR - 1 + tid) : 0;
-        __syncthreads();
-        strip_stage<PD>(d, smem, TR, J * TC, s_anc);
-        cp_async_commit();
-        InterCol c;
-        int Jc = -1;
-        for (long long k = t0; k < t1; ++k) {
-            const int b = (int)((k - t0) & 1);
-            int *cur = smem + b * buf_ints;
-            const bool more = k + 1 < t1;
-            if (more) {
-                int *nanc = s_anc + (b ^ 1) * (TR + 4);
-                if (tid < TR + 4) nanc[tid] = a_next;
-                __syncthreads();                         // anchors written; the other buffer is free
-                strip_stage<PD>(d, smem + (b ^ 1) * buf_ints, TR, Jn * TC, nanc);
-                cp_async_commit();
-                int Jnn = Jn, Inn = In;
-                next(Jnn, Inn);
-                if (k + 2 < t1 && tid < TR + 4) a_next = strip_anchor(d, Inn * TR - 1 + tid);
-                cp_async_wait<1>();                      // this tile's copies are done
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncthreads();                             // ... for every thread of the block
-            if (J != Jc) {                               // a new strip: its column anchors
-                inter_col_load<TW, OR, PD>(d, J * TC + warp * 32 + lane, c);
-                Jc = J;
-            }
-            inter_rows<TW, OR, PD, TW ? 1 : 4>(d, c, cur + warp * 32 + lane + 4,
-                                   reinterpret_cast<const int4 *>(cur + (TR + 4) * LDT), LDT, I * TR, 0, TR,
-                                   best, bidx);
-            J = Jn; I = In;
-            next(Jn, In);
-        }
-    }
+    strip_walk<TW, OR, PD, GATE>(d, TR, T, t0, t1, smem, best, bidx);
     if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
@@ -402,13 +309,23 @@ __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d, int tail
     if (tail && threadIdx.x == 0) eval_tail(d, tail);
 }
 
+// CVRP intra-route moves: one warp per route (the route's distance block in
+// shared memory, intra_cvrp_route); with the swaps of runs, one warp per
+// moved customer (intra_cvrp_position).
 template <bool XS>
 __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
-    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int best = kBestInit;
     unsigned bidx = 0xffffffffu;
-    intra_cvrp_position<XS>(d, p, threadIdx.x & 31, best, bidx);
+    if constexpr (XS) {
+        intra_cvrp_position<XS>(d, wid, threadIdx.x & 31, best, bidx);
+    } else {
+        __shared__ int sD[8][32 * 33];
+        __shared__ int sA[8][32];
+        const int w = threadIdx.x >> 5;
+        intra_cvrp_route(d, wid, threadIdx.x & 31, sD[w], sA[w], best, bidx);
+    }
     if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
     block_min_to(key, &d.ctl->best_key);
@@ -604,25 +521,57 @@ size_t inter_smem_bytes(int rows, int warps, bool pd) {
     return (size_t)(rows + 4) * LDT * sizeof(int) + (size_t)rows * (sizeof(ERec) + (pd ? sizeof(PRec) : 0));
 }
 
+namespace {
+using InterFn = void (*)(Dev, int, int, int);
+using StripFn = void (*)(Dev, int, long long, int);
+
+template <bool G>
+InterFn inter_fn_g(bool tw, bool orr, bool pd) {
+    if (pd) return orr ? k_eval_inter<true, true, true, G> : k_eval_inter<true, false, true, G>;
+    if (tw) return orr ? k_eval_inter<true, true, false, G> : k_eval_inter<true, false, false, G>;
+    return orr ? k_eval_inter<false, true, false, G> : k_eval_inter<false, false, false, G>;
+}
+template <bool G>
+StripFn strip_fn_g(bool tw, bool orr, bool pd) {
+    if (pd) return orr ? k_eval_strip<true, true, true, G> : k_eval_strip<true, false, true, G>;
+    if (tw) return orr ? k_eval_strip<true, true, false, G> : k_eval_strip<true, false, false, G>;
+    return orr ? k_eval_strip<false, true, false, G> : k_eval_strip<false, false, false, G>;
+}
+
+// Whether the operator mask leaves out an inter-route operator that the
+// kernel variant evaluates (relocate, swap, 2-opt*, and the or-opts in the
+// or-opt variants): those launches take the gated kernels, which skip the
+// disabled operators' arithmetic.
+bool inter_gated(const Dev &d) {
+    const unsigned ops = 0x0Bu | ((d.op_mask & 48u) ? 0x30u : 0u);
+    return (d.op_mask & ops) != ops;
+}
+
+InterFn inter_fn(const Dev &d) {
+    const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0, pd = d.has_pd != 0;
+    return inter_gated(d) ? inter_fn_g<true>(tw, orr, pd) : inter_fn_g<false>(tw, orr, pd);
+}
+StripFn strip_fn(const Dev &d) {
+    const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0, pd = d.has_pd != 0;
+    return inter_gated(d) ? strip_fn_g<true>(tw, orr, pd) : strip_fn_g<false>(tw, orr, pd);
+}
+}  // namespace
+
+// Any inter-route operator enabled (relocate, swap, 2-opt*, or-opt)?  Without
+// one the inter-route launch is left out of the evaluation.
+bool has_inter_ops(const Dev &d) { return (d.op_mask & 0x3Bu) != 0; }
+
 int setup_kernel_attrs(int max_band) {
     const int big = 200 * 1024;
     cudaError_t e = cudaSuccess;
-    e = cudaFuncSetAttribute(k_eval_inter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_inter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_eval_inter<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_eval_inter<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_strip<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_strip<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_strip<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_eval_strip<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_eval_strip<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_eval_strip<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    for (int k = 0; k < 16 && e == cudaSuccess; ++k) {
+        const bool tw = (k & 1) != 0, orr = (k & 2) != 0, pd = (k & 4) != 0, g = (k & 8) != 0;
+        if (pd && !tw) continue;                               // pickups come with time windows
+        const void *fi = g ? (const void *)inter_fn_g<true>(tw, orr, pd) : (const void *)inter_fn_g<false>(tw, orr, pd);
+        const void *fs = g ? (const void *)strip_fn_g<true>(tw, orr, pd) : (const void *)strip_fn_g<false>(tw, orr, pd);
+        e = cudaFuncSetAttribute(fi, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fs, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_apply<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
@@ -679,20 +628,12 @@ size_t strip_smem_bytes(int rows, int warps, bool pd) {
     return 2 * buf + 2 * (size_t)(rows + 4) * sizeof(int);
 }
 
-namespace {
-const void *strip_fn(const Dev &d) {
-    const bool orr = (d.op_mask & 48u) != 0;
-    if (d.has_pd) return orr ? (const void *)k_eval_strip<true, true, true> : (const void *)k_eval_strip<true, false, true>;
-    if (d.has_tw) return orr ? (const void *)k_eval_strip<true, true> : (const void *)k_eval_strip<true, false>;
-    return orr ? (const void *)k_eval_strip<false, true> : (const void *)k_eval_strip<false, false>;
-}
-}  // namespace
 
 int strip_grid(const Dev &d, int rows, int warps, long long ntiles) {
     if (!(rows == 16 || rows == 32) || !(warps == 4 || warps == 8) || ntiles <= 0) return 0;
     const size_t sm = strip_smem_bytes(rows, warps, d.has_pd != 0);
     int per = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, strip_fn(d), warps * 32, sm) != cudaSuccess || per < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)strip_fn(d), warps * 32, sm) != cudaSuccess || per < 1) {
         cudaGetLastError();
         return 0;
     }
@@ -702,6 +643,7 @@ int strip_grid(const Dev &d, int rows, int warps, long long ntiles) {
 
 void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, cudaStream_t s, int rs,
                   int tail, int strip) {
+    if (!has_inter_ops(d)) return;
     if (d.theta > 0) {          // edge-based extraction
         const EdgeGrid g = edge_grid(d);
         const bool orr = (d.op_mask & 48u) != 0;
@@ -723,47 +665,30 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
         return;
     }
     if (ntiles <= 0) return;
-    const bool orr = (d.op_mask & 48u) != 0;
     if (strip > 0) {            // strip-major kernel: TC = 32 * warps columns, one row group
         const size_t sm = strip_smem_bytes(rows, warps, d.has_pd != 0);
-        const int nt = warps * 32;
-        if (d.has_pd) {
-            if (orr) k_eval_strip<true, true, true><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
-            else k_eval_strip<true, false, true><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
-        } else if (d.has_tw) {
-            if (orr) k_eval_strip<true, true><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
-            else k_eval_strip<true, false><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
-        } else {
-            if (orr) k_eval_strip<false, true><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
-            else k_eval_strip<false, false><<<strip, nt, sm, s>>>(d, rows, ntiles, tail);
-        }
+        strip_fn(d)<<<strip, warps * 32, sm, s>>>(d, rows, ntiles, tail);
         return;
     }
     const size_t sm = inter_smem_bytes(rows, warps, d.has_pd != 0);
-    const int nt = warps * 32 * rs;
-    if (d.has_pd) {             // pickups come with time windows
-        if (orr) k_eval_inter<true, true, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
-        else k_eval_inter<true, false, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
-    } else if (d.has_tw) {
-        if (orr) k_eval_inter<true, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
-        else k_eval_inter<true, false><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
-    } else {
-        if (orr) k_eval_inter<false, true><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
-        else k_eval_inter<false, false><<<ntiles, nt, sm, s>>>(d, rows, rs, tail);
-    }
+    inter_fn(d)<<<ntiles, warps * 32 * rs, sm, s>>>(d, rows, rs, tail);
 }
 
-// VRPTW: one block per route; CVRP: one warp per moved position, 8 per block.
-int intra_blocks(const Dev &d) { return d.has_tw ? d.m : (d.Wp - 1 + 7) / 8; }
+// VRPTW: one block per route; CVRP: one warp per route (8 per block), or one
+// warp per moved position with the swaps of runs.
+int intra_blocks(const Dev &d) {
+    if (d.has_tw) return d.m;
+    return (d.op_mask & kExtOps) ? (d.Wp - 1 + 7) / 8 : (d.m + 7) / 8;
+}
 
 int xswap_blocks(const Dev &d);
 
 int eval_blocks(const Dev &d, int ntiles, int strip) {
     if (d.theta > 0) {
         const EdgeGrid g = edge_grid(d);
-        return g.nmask + g.ndepot + intra_blocks(d);
+        return (has_inter_ops(d) ? g.nmask + g.ndepot : 0) + intra_blocks(d);
     }
-    const int inter = ntiles <= 0 ? 0 : (strip > 0 ? strip : ntiles);
+    const int inter = (ntiles <= 0 || !has_inter_ops(d)) ? 0 : (strip > 0 ? strip : ntiles);
     return inter + intra_blocks(d) + xswap_blocks(d);
 }
 

@@ -39,23 +39,30 @@ namespace {
 
 // Grid barrier: each CTA adds one to an arrival count that only grows
 // within the launch; the k-th barrier (k = 1, 2, ...) is passed when the
-// count reaches k * G.  One thread per CTA waits, at most limit_ns.
-__device__ bool grid_barrier(unsigned long long *count, unsigned long long target, long long limit_ns) {
+// count reaches k * G.  The CTA that ends the descent adds kStopFlag beside
+// its arrival, so every CTA learns of the stop from the load that passes the
+// barrier (no further read of the stop flag).  One thread per CTA waits, at
+// most limit_ns.  Returns 0 on timeout, 1 when passed, 2 when passed and the
+// descent ends.
+constexpr unsigned long long kStopFlag = 1ull << 40;
+
+__device__ int grid_barrier(unsigned long long *count, unsigned long long target, bool stop, long long limit_ns) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        red_add_release(count, 1ull);                  // publishes the block's writes
+        red_add_release(count, stop ? kStopFlag + 1 : 1ull);   // publishes the block's writes
         int ok = 1;
-        if (ld_acquire(count) < target) {
+        unsigned long long v = ld_acquire(count);
+        if ((v & (kStopFlag - 1)) < target) {
             const long long t0 = now_ns();
-            while (ld_acquire(count) < target) {
+            while (((v = ld_acquire(count)) & (kStopFlag - 1)) < target) {
                 if (now_ns() - t0 > limit_ns) { ok = 0; break; }
             }
         }
-        s_ok = ok;
+        s_ok = ok ? (v >= kStopFlag ? 2 : 1) : 0;
     }
     __syncthreads();
-    return s_ok != 0;
+    return s_ok;
 }
 
 // Wait (one thread) until *seq == want, at most limit_ns (acquire).
@@ -72,10 +79,14 @@ __device__ bool wait_seq(const int *seq, int want, long long limit_ns) {
 
 // ntiles inter-route tiles (TR rows x 32 * warps / RS columns each) and
 // nintra intra-route items: one route per item with time windows, else
-// blockDim/32 moved positions per item (one warp each).
+// blockDim/32 routes per item (one warp each, intra_cvrp_route).
+// STRIP (RS = 0): strip mode -- after the intra-route items every CTA walks its
+// contiguous share of the ntiles tiles of the strip-major order (TR rows x
+// 32 * warps columns, strip_walk), as the per-step strip kernel does, so a
+// large instance runs its whole descent in this one launch too.
 // PD: pickups (with time windows).
-template <bool TW, bool OR, int NT, bool PD>
-__global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const int2 *__restrict__ tiles, int ntiles,
+template <bool TW, bool OR, int NT, bool PD, bool STRIP = false>
+__global__ void __launch_bounds__(NT, STRIP ? (NT == 128 ? 4 : 2) : (NT == 128 ? 6 : 3)) k_persist(Dev d, const int2 *__restrict__ tiles, int ntiles,
                                                                    int TR, int RS, int nintra, long long limit_ns) {
     extern __shared__ __align__(16) int smem[];
     __shared__ StepPlan sP;
@@ -83,29 +94,33 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const 
     Control *C = d.ctl;
     const int tid = threadIdx.x, G = gridDim.x, cta = blockIdx.x;
     const int nw = blockDim.x >> 5, warp = tid >> 5, lane = tid & 31;
-    const int TC = (nw / RS) * 32;
-    const int items = ntiles + nintra;
+    const int TC = (STRIP ? nw : nw / RS) * 32;
+    const int items = STRIP ? nintra : ntiles + nintra;
     unsigned long long target = 0;
     bool ok = true;
-    for (int step = 1;; ++step) {
-        if (tid == 0) s_go = *(volatile int *)&C->done == 0;
-        __syncthreads();
-        if (!s_go) break;
+    if (tid == 0) s_go = *(volatile int *)&C->done == 0;  // later steps learn of a stop at the barrier
+    __syncthreads();
+    for (int step = 1; s_go; ++step) {
         // ---- evaluation (every CTA)
         int best = kBestInit;
         unsigned bidx = 0xffffffffu;
         // intra-route items first: their dependent loads take longest
         for (int t = cta; t < items; t += G) {
-            if (t >= nintra) {
+            if (!STRIP && t >= nintra) {
                 const int2 tl = tile_of(t - nintra, d.Wp, TR, TC);
                 inter_tile<TW, OR, PD>(d, tl.x * TR, tl.y * TC, TR, RS, smem, best, bidx);
             } else if (TW) {
                 __syncthreads();                       // smem of the previous item is free
                 intra_route_table<PD>(d, t, smem, best, bidx);
             } else {
-                intra_cvrp_position(d, t * nw + warp, lane, best, bidx);
+                __syncthreads();
+                intra_cvrp_route(d, t * nw + warp, lane, smem + warp * kCvrpRouteInts,
+                                 smem + nw * kCvrpRouteInts + warp * 32, best, bidx);
             }
         }
+        if (STRIP)
+            strip_walk<TW, OR, PD>(d, TR, ntiles, (long long)cta * ntiles / G, (long long)(cta + 1) * ntiles / G,
+                                   smem, best, bidx);
         const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
         block_min_to(key, &C->best_key);
         // ---- the last CTA to finish decodes and publishes the plan, then
@@ -132,8 +147,9 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const 
         if (s_ok == 2) load_plan(C, &sP);
         __syncthreads();
         // ---- update
+        int stop = 0;                                  // thread 0 of the applying CTA
         if (s_ok == 1) {
-            apply_plan_block<PD>(d, sP, smem, false, 0, 0);
+            stop = apply_plan_block<PD>(d, sP, smem, false, 0, 0);
             if (G == 1) {
                 __syncthreads();
                 band_plan_rows(d, sP, smem, 0, d.n + 1, 0, 1);
@@ -142,7 +158,9 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 6 : 3) k_persist(Dev d, const 
             band_plan_rows(d, sP, smem, 0, d.n + 1, cta < s_app ? cta : cta - 1, G - 1);
         }
         target += G;
-        if (!grid_barrier(&C->bar_count, target, limit_ns)) { ok = false; break; }
+        const int passed = grid_barrier(&C->bar_count, target, tid == 0 && stop != 0, limit_ns);
+        if (!passed) { ok = false; break; }
+        if (passed == 2) break;
     }
     if (!ok) {
         if (tid == 0) {
@@ -160,35 +178,40 @@ namespace {
 
 using PersistFn = void (*)(Dev, const int2 *, int, int, int, int, long long);
 
-PersistFn persist_fn(bool tw, bool orr, int nt, bool pd) {
-    if (nt == 128) {
-        if (pd) return orr ? k_persist<true, true, 128, true> : k_persist<true, false, 128, true>;
-        if (tw) return orr ? k_persist<true, true, 128, false> : k_persist<true, false, 128, false>;
-        return orr ? k_persist<false, true, 128, false> : k_persist<false, false, 128, false>;
-    }
-    if (pd) return orr ? k_persist<true, true, 256, true> : k_persist<true, false, 256, true>;
-    if (tw) return orr ? k_persist<true, true, 256, false> : k_persist<true, false, 256, false>;
-    return orr ? k_persist<false, true, 256, false> : k_persist<false, false, 256, false>;
+template <int NT, bool S>
+PersistFn persist_fn_t(bool tw, bool orr, bool pd) {
+    if (pd) return orr ? k_persist<true, true, NT, true, S> : k_persist<true, false, NT, true, S>;
+    if (tw) return orr ? k_persist<true, true, NT, false, S> : k_persist<true, false, NT, false, S>;
+    return orr ? k_persist<false, true, NT, false, S> : k_persist<false, false, NT, false, S>;
+}
+
+PersistFn persist_fn(bool tw, bool orr, int nt, bool pd, bool strip) {
+    if (strip) return nt == 128 ? persist_fn_t<128, true>(tw, orr, pd) : persist_fn_t<256, true>(tw, orr, pd);
+    return nt == 128 ? persist_fn_t<128, false>(tw, orr, pd) : persist_fn_t<256, false>(tw, orr, pd);
 }
 
 }  // namespace
 
 int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int warps, int rs, cudaStream_t s,
                    int *grid_out) {
-    const int nt = warps * 32 * rs;
+    const bool strip = rs == 0;                           // strip-major walk of the ntiles tiles
+    const int nt = warps * 32 * (strip ? 1 : rs);
     if (d.theta > 0) return TGA_ERR_STATE;                // edge-based extraction: per-step path only
     if (d.op_mask & kExtOps) return TGA_ERR_STATE;        // swaps of runs: per-step path only
     if (ntiles <= 0 || (nt != 128 && nt != 256)) return TGA_ERR_INVALID;   // apply needs >= 3 warps
+    if (strip && !((rows == 16 || rows == 32) && (warps == 4 || warps == 8))) return TGA_ERR_INVALID;
     const int nw = nt / 32;
     const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0, pd = d.has_pd != 0;
-    const int nintra = tw ? d.m : (d.Wp - 1 + nw - 1) / nw;
-    size_t sm = inter_smem_bytes(rows, warps, pd);
+    const int nintra = tw ? d.m : (d.m + nw - 1) / nw;
+    size_t sm = strip ? strip_smem_bytes(rows, warps, pd) : inter_smem_bytes(rows, warps, pd);
+    const size_t cvrp_intra = (size_t)nw * (kCvrpRouteInts + 32) * sizeof(int);
+    if (!tw && cvrp_intra > sm) sm = cvrp_intra;
     const size_t band = (size_t)band_smem_ints(d.Wp, nw) * sizeof(int);
     if (band > sm) sm = band;
     const size_t tab = (size_t)(pd ? kIntraTabSmemIntsPD : kIntraTabSmemInts) * sizeof(int);
     if (tw && tab > sm) sm = tab;
     if (sm > 200 * 1024) return TGA_ERR_RANGE;
-    PersistFn fn = persist_fn(tw, orr, nt, pd);
+    PersistFn fn = persist_fn(tw, orr, nt, pd, strip);
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
         cudaGetLastError();
         return TGA_ERR_CUDA;

@@ -103,6 +103,7 @@ EXPORTS = [
                                       ctypes.POINTER(ctypes.c_size_t)]),
     ("tga_set_wait_limit", ctypes.c_int, [_P, ctypes.c_int64]),
     ("tga_get_bounds_report", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    ("tga_set_persistent_shape", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     ("tga_set_tile_strip", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     ("tga_destroy", ctypes.c_int, [_P]),
     ("tga_strerror", ctypes.c_char_p, [ctypes.c_int]),
@@ -300,6 +301,10 @@ def tga_set_tile_strip(ctx: int, rows: int, col_warps: int):
 
 def tga_set_wait_limit(ctx: int, limit_ns: int):
     _check(_lib().tga_set_wait_limit(_P(ctx), int(limit_ns)), "tga_set_wait_limit")
+
+
+def tga_set_persistent_shape(ctx: int, rows: int, col_warps: int, row_split: int):
+    _check(_lib().tga_set_persistent_shape(ctx, rows, col_warps, row_split), "tga_set_persistent_shape")
 
 
 def tga_get_bounds_report(ctx: int) -> dict:

@@ -119,13 +119,16 @@ def test_integer_headroom_is_enforced():
     ls.close()
 
 
-def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None, mode=None):
+def _descend_gpu(inst, sol, mask, cap=1 << 20, tile=None, mode=None, pshape=None):
+    from paper_2506_17357_gb300 import tga as T
     ls = LocalSearch(inst, sol, mask, log_capacity=cap).build()
     try:
         if tile is not None:
             ls.set_tile(*tile)
         if mode is not None:
             ls.set_descent_mode(mode)
+        if pshape is not None:
+            T.tga_set_persistent_shape(ls.ctx, *pshape)
         st = ls.descend()
         log = ls.move_log()
         tour, rs = ls.solution()
@@ -183,6 +186,55 @@ def test_descent_paths_agree(kind, limit):
         for k in ("steps", "evaluations", "candidates", "final_cost", "local_optimum", "status"):
             assert sg[k] == sh[k], (mode, k)
         assert np.array_equal(lg, lh) and np.array_equal(tg, th) and np.array_equal(rg, rh), mode
+
+
+@pytest.mark.parametrize("kind", ["cvrp", "vrptw", "vrpspdtw"])
+@pytest.mark.parametrize("shape", [(16, 4, 0), (32, 8, 0), (16, 4, 1), (8, 2, 2)])
+def test_persistent_shapes_equal_the_graph_path(kind, shape):
+    """The persistent descent under a set shape -- strip mode (row split 0:
+    every CTA walks a share of the strip-major tile order) or one tile per
+    item -- gives the graph path's move log, solution and counters."""
+    from paper_2506_17357_gb300 import tga as T
+    if kind == "vrptw":
+        inst = I.vrptw(300, 14)
+    elif kind == "vrpspdtw":
+        inst = I.vrpspdtw(250, 15)
+    else:
+        inst = I.cvrp_uniform(450, 16)
+    mask = I.MASK_CONFIG3 if kind == "cvrp" else I.MASK_ALL
+    sol = I.random_split_solution(inst, I.solution_seed(14))
+    out = {}
+    for mode in (T.DESCENT_GRAPH, T.DESCENT_PERSISTENT):
+        ls = LocalSearch(inst, sol, mask, log_capacity=1 << 16).build()
+        try:
+            ls.set_descent_mode(mode)
+            if mode == T.DESCENT_PERSISTENT:
+                T.tga_set_persistent_shape(ls.ctx, *shape)
+                assert tuple(T.tga_get_persistent_shape(ls.ctx)) == shape
+            st = ls.descend()
+            assert ls.descent_mode()[0] == mode
+            out[mode] = (st, ls.move_log(), ls.solution())
+        finally:
+            ls.close()
+    sg, lg, (tg, rg) = out[T.DESCENT_GRAPH]
+    sp, lp, (tp, rp) = out[T.DESCENT_PERSISTENT]
+    assert sg["local_optimum"] == 1 and sg["status"] == 0
+    for k in ("steps", "evaluations", "candidates", "final_cost", "local_optimum", "status"):
+        assert sg[k] == sp[k], k
+    assert np.array_equal(lg, lp) and np.array_equal(tg, tp) and np.array_equal(rg, rp)
+
+
+def test_persistent_shape_setter_rejects_bad_shapes():
+    from paper_2506_17357_gb300 import tga as T
+    inst = I.cvrp_uniform(30, 3)
+    ls = LocalSearch(inst, I.random_split_solution(inst, 4), I.MASK_ALL).build()
+    try:
+        for bad in ((12, 4, 1), (16, 3, 1), (16, 8, 2), (64, 4, 0), (16, 2, 0), (8, 2, 1)):
+            with pytest.raises(TGAError):
+                T.tga_set_persistent_shape(ls.ctx, *bad)
+        T.tga_set_persistent_shape(ls.ctx, 0, 0, 0)                 # back to the automatic choice
+    finally:
+        ls.close()
 
 
 @pytest.mark.parametrize("kind", ["cvrp", "vrptw", "vrpspdtw"])
@@ -436,3 +488,11 @@ def test_config3_sampled_steps_and_local_optimum():
     states = [kept[k] for k in picks]
     _verify_pool(3, 1, dict(zip(picks, states)), log, picks, I.MASK_CONFIG3, "concat")
     print(f"cvrp10000: {len(picks)} of {len(log)} evaluations re-evaluated by the oracle")
+    # the persistent descent in strip mode (the path the timed bench takes at
+    # this size) gives the same move log, solution and counters
+    from paper_2506_17357_gb300 import tga as T
+    sp, logp, finp = _descend_gpu(inst, sol, I.MASK_CONFIG3, mode=T.DESCENT_PERSISTENT, pshape=(32, 8, 0))
+    assert np.array_equal(logp, log) and np.array_equal(finp.tour, fin.tour)
+    assert np.array_equal(finp.route_start, fin.route_start)
+    for k in ("steps", "evaluations", "candidates", "final_cost", "local_optimum", "status"):
+        assert sp[k] == st[k], k
