@@ -2573,6 +2573,48 @@ __device__ void band_plan_rows(const Dev &d, const StepPlan &S, int *smem, int r
         }
         __syncthreads();
         const int K = s_cnt;
+        if (K <= 32 && (!shift || P.s1 - P.s0 < 256)) {
+            // one pass per row: a warp issues the loads of two rows (the
+            // rewritten elements' sources and the block between the routes)
+            // before any store, then shifts, then writes the elements
+            const int src = lane < K ? ss[lane] : 0, dst = lane < K ? sq[lane] : 0;
+            const int stride = ncta * nw;
+            for (int x0 = row_lo + cta * nw + warp; x0 < row_hi; x0 += 2 * stride) {
+                int g[2], v[2][8];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int x = x0 + r * stride;
+                    const bool ok = x < row_hi;
+                    const int *row = d.pcol + (size_t)TGA_IX(ok ? x : 0, d.n + 1) * d.ldp + kColOff;
+                    g[r] = (ok && lane < K) ? row[TGA_IX(src, d.ldp - kColOff)] : 0;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int t = P.s0 + 32 * k + lane;
+                        v[r][k] = (ok && shift && t <= P.s1) ? row[TGA_IX(t, d.ldp - kColOff)] : 0;
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int x = x0 + r * stride;
+                    if (x >= row_hi) continue;
+                    int *row = d.pcol + (size_t)TGA_IX(x, d.n + 1) * d.ldp + kColOff;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int t = P.s0 + 32 * k + lane;
+                        if (shift && t <= P.s1) row[TGA_IX(t + P.dl, d.ldp - kColOff)] = v[r][k];
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int x = x0 + r * stride;
+                    if (x < row_hi && lane < K) d.pcol[(size_t)TGA_IX(x, d.n + 1) * d.ldp + kColOff + TGA_IX(dst, d.ldp - kColOff)] = g[r];
+                }
+                __syncwarp();
+            }
+            return;
+        }
         if (K <= kBandWarpBuf) {
             int *wb = smem + 2 * kBandListMax + warp * kBandWarpBuf;
             for (int x = row_lo + cta * nw + warp; x < row_hi; x += ncta * nw) {
