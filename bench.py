@@ -280,9 +280,15 @@ def only_descent(args):
         tile = ls.set_tile(*[int(x) for x in args.tile.split(",")])
     else:
         tile = ls.set_tile(0, 0)                                   # autotune, as the timed bench does
+    if args.persistent_shape:                                      # the persistent path under a set shape
+        T.tga_set_persistent_shape(ls.ctx, *[int(x) for x in args.persistent_shape.split(",")])
+        ls.set_descent_mode(T.DESCENT_PERSISTENT)
     st = ls.descend(max_steps=args.descent_steps) if args.descent_steps else ls.descend()
     torch.cuda.synchronize()
+    mode_used, grid = T.tga_get_descent_mode(ls.ctx)
     print(json.dumps({"workload": workload_name(args, wl), "tile": list(tile), "steps": st["steps"],
+                      "descent_path": T.DESCENT_NAMES[mode_used], "grid": grid,
+                      "persistent_shape": list(T.tga_get_persistent_shape(ls.ctx)),
                       "evaluations": st["evaluations"],
                       "final_cost": st["final_cost"], "status": st["status"]}))
     ls.close()
@@ -1010,6 +1016,9 @@ def main():
                     help="with --only-descent: stop after this many moves (0: run to the local optimum)")
     ap.add_argument("--tile", default="",
                     help="inter tile shape rows,warps,row_split (default: autotune on the initial state)")
+    ap.add_argument("--persistent-shape", default="",
+                    help="with --only-descent: run the persistent path under this shape rows,warps,row_split "
+                         "(row_split 0: strip mode)")
     ap.add_argument("--extended-swaps", action="store_true",
                     help="add op ranks 6, 7 (a customer with a run of two, two runs of two) to the workload")
     ap.add_argument("--granular", type=int, default=0,

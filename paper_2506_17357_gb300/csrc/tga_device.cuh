@@ -2355,15 +2355,37 @@ __device__ int apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, bool
         const MovePlan pl = S.mp;
         const int tot = S.n1 + S.n2;
         // the anchor every changed position takes, all read before any write
-        for (int u = tid; u < tot; u += nthr) sbuf[u] = d.seq[TGA_IX(plan_src(S, plan_pos(S, u)), d.Wp)];
+        // (eight per thread and round, their loads issued together)
+        for (int u0 = tid; u0 < tot; u0 += 8 * nthr) {
+            int v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int u = u0 + k * nthr;
+                v[k] = u < tot ? d.seq[TGA_IX(plan_src(S, plan_pos(S, u)), d.Wp)] : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (u0 + k * nthr < tot) sbuf[u0 + k * nthr] = v[k];
+        }
         __syncthreads();
         for (int u = tid; u < tot; u += nthr) {
             const int q = plan_pos(S, u), a = sbuf[u];
             d.seq[TGA_IX(q, d.Wp)] = a;
             d.pos_of[TGA_IX(a, d.W + 1)] = q;
         }
-        if (S.dl != 0)
-            for (int r = S.lo + 1 + tid; r <= S.hi; r += nthr) d.rrec[TGA_IX(r, d.m)].start += S.dl;
+        if (S.dl != 0) {
+            for (int r0 = S.lo + 1 + tid; r0 <= S.hi; r0 += 8 * nthr) {
+                int v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int r = r0 + k * nthr;
+                    v[k] = r <= S.hi ? d.rrec[TGA_IX(r, d.m)].start : 0;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (r0 + k * nthr <= S.hi) d.rrec[TGA_IX(r0 + k * nthr, d.m)].start = v[k] + S.dl;
+            }
+        }
         if (tid == 0) {
             d.rrec[TGA_IX(pl.A, d.m)].len = pl.nLA;
             if (pl.B != pl.A) d.rrec[TGA_IX(pl.B, d.m)].len = pl.nLB;
@@ -2387,12 +2409,24 @@ __device__ int apply_plan_block(const Dev &d, const StepPlan &S, int *sbuf, bool
                 s_ci[3] = C->maxe; s_ci[4] = C->maxs; s_ci[5] = C->maxd;
             }
             // meanwhile: longest route and heaviest load of the other routes
+            // (eight routes per thread and round, their loads issued together)
             int mL = 0, mLoad = 0;
-            for (int r = tid - 64; r < d.m; r += nthr - 64) {
-                if (r == pl.A || r == pl.B) continue;
-                mL = max(mL, d.rrec[TGA_IX(r, d.m)].len);
-                const RouteRec &Rr = d.rrec[TGA_IX(r, d.m)];
-                mLoad = max(mLoad, PD ? Rr.load + Rr.lo : Rr.load);
+            const int rstep = nthr - 64;
+            for (int r0 = tid - 64; r0 < d.m; r0 += 8 * rstep) {
+                int len[8], ld[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int r = r0 + u * rstep;
+                    const bool in = r < d.m && r != pl.A && r != pl.B;
+                    const RouteRec *Rr = d.rrec + TGA_IX(in ? r : 0, d.m);
+                    len[u] = in ? Rr->len : 0;
+                    ld[u] = in ? (PD ? Rr->load + Rr->lo : Rr->load) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    mL = max(mL, len[u]);
+                    mLoad = max(mLoad, ld[u]);
+                }
             }
             mL = __reduce_max_sync(0xffffffffu, mL);
             mLoad = __reduce_max_sync(0xffffffffu, mLoad);
