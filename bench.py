@@ -251,6 +251,12 @@ def dist_env():
 
 
 OP_NAMES = ["relocate", "swap", "2-opt", "2-opt*", "or-opt-2", "or-opt-3", "swap-1-2", "swap-2-2"]
+_T0 = time.time()
+
+
+def progress(msg):
+    """One line per bench phase on stderr (wall seconds since start), so a slow phase shows."""
+    print(f"[bench {time.time() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
 
 
 def workload(args, name=None):
@@ -498,6 +504,7 @@ def breakdown(inst, sol, mask, dev, stream, reps=200, step_count=200):
         cands = (st["candidates"] - st0["candidates"]) / max(1, st["evaluations"] - st0["evaluations"])
         per_op[OP_NAMES[op]] = {"us_per_evaluation": us, "candidates": int(cands),
                                 "candidates_per_s": cands / (us * 1e-6)}
+        progress(f"breakdown: {OP_NAMES[op]} {us:.1f} us")
         del g
         torch.cuda.synchronize()
         ls.close()
@@ -539,6 +546,7 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
     desc, make, mask = workload(args, wl_name)
     seed = replica_seed(args.seed, rank)
     inst, sol = make(seed)
+    progress(f"{wl_name}: instance ready")
     nbr = I.granular_neighbors(inst, args.granular) if args.granular else None
     stream = torch.cuda.Stream(dev)
     ls = T.LocalSearch(inst, sol, mask, device=dev, stream=stream, granular=nbr).build()
@@ -547,6 +555,7 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
     else:
         tile = ls.set_tile(0, 0)                               # autotune on the initial state
     torch.cuda.synchronize()
+    progress(f"{wl_name}: tuned {tile}, path {T.DESCENT_NAMES[T.tga_get_descent_mode(ls.ctx)[0]]}")
     tour0 = ls.tour.clone()
     rs0 = ls.route_start.clone()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
@@ -584,6 +593,7 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
             nsteps.append(stats["steps"])
         torch.cuda.synchronize()
     clocks = clk.summary()
+    progress(f"{wl_name}: {steps} timed descents done")
     total = float(sum(times))
     t_max, c_all = reduce_replicas(total, cands, dev)
     value = c_all / t_max
@@ -615,6 +625,7 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
             e2e_times.append(t1 - t0)
         assert st["candidates"] == stats["candidates"]
     e2e_value = stats["candidates"] * len(e2e_times) / sum(e2e_times)
+    progress(f"{wl_name}: end-to-end done")
 
     # ---- roofline of the dominant kernel, timed live with CUDA events on the
     # context's stream.  Persistent path: the one launch that runs the whole
@@ -691,6 +702,7 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
         return out
 
     inter_roof = inter_kernel_roof()
+    progress(f"{wl_name}: inter-route kernel timed")
     if persistent:
         kms = []
         for _ in range(3):
@@ -721,7 +733,9 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
     m_routes = ls.m
     ls.close()
     del flush
+    progress(f"{wl_name}: roofline done")
     brk = breakdown(inst, sol, mask, dev, stream) if (with_breakdown and rank == 0 and not args.granular) else None
+    progress(f"{wl_name}: breakdown done")
     rec = {
         "metric": "move evals/s", "value": value, "unit": "candidate moves/s",
         "n_gpus": ws, "steps": steps, "warmup": warmup,
@@ -751,6 +765,7 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
     }
     if cpu is not None and rank == 0 and ws == 1:
         rec["cpu_baseline"] = cpu_baseline(args, wl_name, **cpu)
+        progress(f"{wl_name}: CPU baseline done")
     return rec
 
 
@@ -769,7 +784,9 @@ def run_batch(args, steps, warmup):
     stream = torch.cuda.Stream(dev)
     lss = [T.LocalSearch(inst, sol, I.mask_for(inst), device=dev, stream=stream) for inst, sol in jobs]
     ctxs = [ls.ctx for ls in lss]
+    progress("batch256: jobs ready")
     rows = T.tga_batch_autotune(ctxs)
+    progress("batch256: tuned")
     init = [(ls.tour.clone(), ls.route_start.clone()) for ls in lss]
     torch.cuda.synchronize()
 
@@ -795,6 +812,7 @@ def run_batch(args, steps, warmup):
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
     clocks = clk.summary()
+    progress("batch256: timed")
     t_batch = float(np.mean(times))
     cands = sum(s["candidates"] for s in stats)
     # sequential single-instance descents of the same jobs
@@ -865,8 +883,11 @@ def run_serve(args, warmup):
         S.Server(budget_bytes=budget, max_slots=4, keep_solutions=False).serve(
             [S.Request(r.rid, 0.0, r.inst, r.sol, r.op_mask) for r in reqs[:6]], pinned=pinned)
     zero = np.zeros(count)
+    progress("serve: jobs ready")
     cap1, _ = run(1, zero)
+    progress("serve: one-at-a-time capacity done")
     capN, _ = run(32, zero)
+    progress("serve: continuous capacity done")
     mu1 = cap1["jobs_per_s"]
     sweep = {}
     with ClockSampler(0) as clk:
@@ -875,6 +896,7 @@ def run_serve(args, warmup):
             one, _ = run(1, arr)
             cont, _ = run(32, arr)
             sweep[str(mult)] = {"rate_jobs_per_s": mult * mu1, "one_at_a_time": one, "continuous": cont}
+            progress(f"serve: {mult}x rate done")
     clocks = clk.summary()
     head = sweep["2.0"]["continuous"]
     return {"metric": "served jobs/s", "value": head["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1,

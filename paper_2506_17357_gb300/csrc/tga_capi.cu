@@ -453,6 +453,7 @@ int tga_create(const tga_instance *inst, const tga_solution *sol, uint32_t op_ma
     d.service = inst->service; d.early = inst->tw_early; d.late = inst->tw_late;
     d.pickup = inst->pickup;
     d.tour = sol->tour; d.route_start = sol->route_start;
+    d.cvrp_by_route = cvrp_intra_by_route(d.n, d.m, d.has_tw, d.op_mask);
     d.ldp = (int)pcol_pitch((size_t)d.Wp);
     d.log = nullptr; d.log_cap = 0;
     d.wait_ns = -1;

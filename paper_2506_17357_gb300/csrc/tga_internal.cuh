@@ -211,6 +211,7 @@ struct Dev {
     long long wait_ns;        // limit of every bounded device wait; < 0: each wait's default
     int Q, wL, wT, has_tw;
     int has_pd;               // pickups (VRPSPDTW; requires has_tw)
+    int cvrp_by_route;        // CVRP intra-route moves: one warp per route (short routes) instead of one per customer
     unsigned op_mask;
     const int *dist, *demand, *service, *early, *late;
     const int *pickup;        // [n+1] or null
@@ -236,6 +237,15 @@ struct Dev {
 };
 
 __host__ __device__ inline int node_of(int anchor, int n) { return anchor <= n ? anchor : 0; }
+
+// CVRP intra-route evaluation by route (a warp per route, the route's
+// distance block in shared memory) when routes are short on average (at most
+// 16 customers per route): long routes would serialise a whole route on one
+// warp, so instances with long routes keep a warp per moved customer.  The
+// swaps of runs always take the per-customer kernel.
+__host__ __device__ inline int cvrp_intra_by_route(int n, int m, int has_tw, unsigned op_mask) {
+    return (!has_tw && !(op_mask & kExtOps) && n <= 16 * m) ? 1 : 0;
+}
 
 // Debug build (compiled with -DTGA_BOUNDS_CHECK): every indexed access of
 // the search state and the instance goes through TGA_IX(index, limit).  An

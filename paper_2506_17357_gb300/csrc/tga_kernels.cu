@@ -310,8 +310,9 @@ __global__ void __launch_bounds__(kIntraWarps * 32) k_eval_intra(Dev d, int tail
 }
 
 // CVRP intra-route moves: one warp per route (the route's distance block in
-// shared memory, intra_cvrp_route); with the swaps of runs, one warp per
-// moved customer (intra_cvrp_position).
+// shared memory, intra_cvrp_route) when routes are short on average (Dev
+// cvrp_by_route); otherwise, and with the swaps of runs, one warp per moved
+// customer (intra_cvrp_position).
 template <bool XS>
 __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d, int tail) {
     const int done = *(volatile int *)&d.ctl->done;
@@ -324,7 +325,8 @@ __global__ void __launch_bounds__(256) k_eval_intra_cvrp(Dev d, int tail) {
         __shared__ int sD[8][32 * 33];
         __shared__ int sA[8][32];
         const int w = threadIdx.x >> 5;
-        intra_cvrp_route(d, wid, threadIdx.x & 31, sD[w], sA[w], best, bidx);
+        if (d.cvrp_by_route) intra_cvrp_route(d, wid, threadIdx.x & 31, sD[w], sA[w], best, bidx);
+        else intra_cvrp_position<false>(d, wid, threadIdx.x & 31, best, bidx);
     }
     if (done) return;
     const unsigned long long key = (bidx != 0xffffffffu) ? pack_key(best, bidx) : kNoKey;
@@ -675,10 +677,10 @@ void launch_inter(const Dev &d, const int2 *tiles, int ntiles, int rows, int war
 }
 
 // VRPTW: one block per route; CVRP: one warp per route (8 per block), or one
-// warp per moved position with the swaps of runs.
+// warp per moved position (long routes, or the swaps of runs).
 int intra_blocks(const Dev &d) {
     if (d.has_tw) return d.m;
-    return (d.op_mask & kExtOps) ? (d.Wp - 1 + 7) / 8 : (d.m + 7) / 8;
+    return d.cvrp_by_route ? (d.m + 7) / 8 : (d.Wp - 1 + 7) / 8;
 }
 
 int xswap_blocks(const Dev &d);

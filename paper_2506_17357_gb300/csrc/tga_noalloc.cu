@@ -132,6 +132,7 @@ extern "C" int tga_eval_best_move_noalloc(const tga_instance *inst, const tga_so
     d.has_pd = inst->pickup ? 1 : 0;
     d.pickup = inst->pickup;
     d.tour = sol->tour; d.route_start = sol->route_start;
+    d.cvrp_by_route = cvrp_intra_by_route(d.n, d.m, d.has_tw, d.op_mask);
     d.ldp = (int)pcol_pitch((size_t)d.Wp);
     d.log = nullptr; d.log_cap = 0;
     d.wait_ns = -1;

@@ -79,7 +79,8 @@ __device__ bool wait_seq(const int *seq, int want, long long limit_ns) {
 
 // ntiles inter-route tiles (TR rows x 32 * warps / RS columns each) and
 // nintra intra-route items: one route per item with time windows, else
-// blockDim/32 routes per item (one warp each, intra_cvrp_route).
+// blockDim/32 routes per item (one warp each, intra_cvrp_route) or, for long
+// CVRP routes, blockDim/32 moved customers per item (intra_cvrp_position).
 // STRIP (RS = 0): strip mode -- after the intra-route items every CTA walks its
 // contiguous share of the ntiles tiles of the strip-major order (TR rows x
 // 32 * warps columns, strip_walk), as the per-step strip kernel does, so a
@@ -112,10 +113,12 @@ __global__ void __launch_bounds__(NT, STRIP ? (NT == 128 ? 4 : 2) : (NT == 128 ?
             } else if (TW) {
                 __syncthreads();                       // smem of the previous item is free
                 intra_route_table<PD>(d, t, smem, best, bidx);
-            } else {
+            } else if (d.cvrp_by_route) {
                 __syncthreads();
                 intra_cvrp_route(d, t * nw + warp, lane, smem + warp * kCvrpRouteInts,
                                  smem + nw * kCvrpRouteInts + warp * 32, best, bidx);
+            } else {
+                intra_cvrp_position(d, t * nw + warp, lane, best, bidx);
             }
         }
         if (STRIP)
@@ -202,10 +205,10 @@ int launch_persist(const Dev &d, const int2 *tiles, int ntiles, int rows, int wa
     if (strip && !((rows == 16 || rows == 32) && (warps == 4 || warps == 8))) return TGA_ERR_INVALID;
     const int nw = nt / 32;
     const bool tw = d.has_tw != 0, orr = (d.op_mask & 48u) != 0, pd = d.has_pd != 0;
-    const int nintra = tw ? d.m : (d.m + nw - 1) / nw;
+    const int nintra = tw ? d.m : d.cvrp_by_route ? (d.m + nw - 1) / nw : (d.Wp - 1 + nw - 1) / nw;
     size_t sm = strip ? strip_smem_bytes(rows, warps, pd) : inter_smem_bytes(rows, warps, pd);
     const size_t cvrp_intra = (size_t)nw * (kCvrpRouteInts + 32) * sizeof(int);
-    if (!tw && cvrp_intra > sm) sm = cvrp_intra;
+    if (!tw && d.cvrp_by_route && cvrp_intra > sm) sm = cvrp_intra;
     const size_t band = (size_t)band_smem_ints(d.Wp, nw) * sizeof(int);
     if (band > sm) sm = band;
     const size_t tab = (size_t)(pd ? kIntraTabSmemIntsPD : kIntraTabSmemInts) * sizeof(int);

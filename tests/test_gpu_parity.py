@@ -105,6 +105,26 @@ def test_long_routes_multi_chunk_scans():
     _stepwise(inst2, _sol(sol2.tour, [0, 35, 70, 105, 105]), I.MASK_ALL, max_steps=20)
 
 
+def test_cvrp_route_kernel_with_one_long_route():
+    """CVRP intra-route evaluation by route (at most 16 customers per route
+    on average) with one route longer than a warp's distance block: that route
+    falls back to a warp per moved customer, inside the per-route kernel, on
+    the per-step and the persistent paths."""
+    from paper_2506_17357_gb300 import tga as T
+    inst = I.cvrp_uniform(120, 31)
+    inst.capacity = int(inst.demand.sum())            # no capacity pressure
+    sol = I.random_split_solution(inst, 32)
+    rs = [0, 40, 52, 64, 76, 88, 100, 110, 120]        # 8 routes, the first of 40 customers
+    case = _sol(sol.tour, rs)
+    _stepwise(inst, case, I.MASK_CONFIG3, max_steps=40)
+    st, log, fin = _descend_gpu(inst, case, I.MASK_CONFIG3, mode=T.DESCENT_PERSISTENT, pshape=(16, 4, 1))
+    sg, lg, fg = _descend_gpu(inst, case, I.MASK_CONFIG3, mode=T.DESCENT_GRAPH)
+    ofin, steps, olog, _ = O.descend(inst, case, I.MASK_CONFIG3, "def")
+    for s_, l_, f_ in ((st, log, fin), (sg, lg, fg)):
+        assert s_["status"] == 0 and s_["steps"] == steps and np.array_equal(l_, olog)
+        assert np.array_equal(f_.tour, ofin.tour) and np.array_equal(f_.route_start, ofin.route_start)
+
+
 def test_integer_headroom_is_enforced():
     """A VRPTW state whose routes are so long that a candidate route could
     cost 2^27 or more is refused with TGA_ERR_RANGE instead of risking int32
