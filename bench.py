@@ -603,8 +603,8 @@ def run_single(args, wl_name, steps, warmup, peak, e2e_reps=None, with_breakdown
     persistent = mode_used == T.DESCENT_PERSISTENT
     # gpu launches per descent: build (check, positions, perm, routes, finish,
     # pcol init) + begin, then one persistent launch, or 3 per evaluation
-    # (inter, intra, apply) + the write-back of the solution
-    launches_per_step = 6 + 1 + (1 if persistent else 3 * evals + 1)
+    # (inter, intra, apply), and the write-back of the solution
+    launches_per_step = 6 + 1 + (1 if persistent else 3 * evals) + 1
     op_cands = T.tga_get_op_candidates(ls.ctx)
     pshape = T.tga_get_persistent_shape(ls.ctx)
 
