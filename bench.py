@@ -132,11 +132,17 @@ def evaluation_bytes(n, m):
 
 
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources' code: comments and whitespace are removed
+    first, so an edit of a comment keeps recorded counters valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("tga_kernels.cu", "tga_persist.cu", "tga_device.cuh", "tga_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2506_17357_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2506_17357_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(re.sub(r"\s+", "", src).encode())
     return h.hexdigest()[:16]
 
 

@@ -390,7 +390,7 @@ int tga_set_granular(tga_ctx *ctx, const int32_t *nbr_dev, int32_t theta);
  * Copies min(bytes, size) bytes; *size_out (may be NULL) gets the size. */
 int tga_debug_read(tga_ctx *ctx, int32_t what, void *host_dst, size_t bytes, size_t *size_out);
 
-/* Diagnostic of the index-checked build (SURVEY's stand-in for a memory
+/* Diagnostic of the index-checked build (a stand-in for a device memory
  * checker; the paper has no counterpart).  libtga_check.so is the same
  * library compiled with -DTGA_BOUNDS_CHECK: every indexed device access of
  * the search state and the instance is checked against its array's extent;

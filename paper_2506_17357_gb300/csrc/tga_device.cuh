@@ -853,7 +853,7 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
     int4 *sR = reinterpret_cast<int4 *>(smem + (TR + 4) * LDT);   // TR row records (ERec, then PRec)
     __shared__ int s_rnode[68];                               // nodes of positions p0-1 .. p0+TR+2 (TR <= 64)
     __shared__ int s_ranc[64];                                // anchors of positions p0 .. p0+TR-1
-    // round 1: the anchors of the rows and of this thread's column
+    // first loads: the anchors of the rows and of this thread's column
     const int q = q0 + cw * 32 + lane;
     const int av = (q < d.Wp) ? d.seq[TGA_IX(q, d.Wp)] : d.W;
     __syncthreads();                                          // previous user of smem is done
@@ -865,7 +865,7 @@ __device__ void inter_tile(const Dev &d, int p0, int q0, int TR, int RS, int *sm
         if (t >= 1 && t <= TR) s_ranc[t - 1] = a;
     }
     __syncthreads();
-    // round 2, all issued before any is waited for: the extraction rows
+    // second loads, all issued before any is waited for: the extraction rows
     // p0-1 .. p0+TR+2 over positions q0-4 .. q0+TC+3 and the row records
     // (asynchronous copies), and the column's records (registers)
     const int C4 = LDT >> 2;

@@ -115,10 +115,10 @@ __global__ void __launch_bounds__(256, TW ? 3 : 4) k_eval_strip(Dev d, int TR, l
 // other routes.  One launch, two kinds of CTA (blockDim threads each):
 //
 //   mask CTAs (the first ceil(n*theta / blockDim)): one thread per directed
-//     mask entry (u, v).  Round 1 loads the entry, u's records and u's
-//     position; round 2 v's records and position and the distances that
+//     mask entry (u, v).  The first loads fetch the entry, u's records and
+//     u's position; the second v's records and position and the distances that
 //     need only v (c(u,v), c(u+,v), c(u-,v) from the position-ordered copy's
-//     row v at u's predecessor position); round 3 the distances to v's
+//     row v at u's predecessor position); the third the distances to v's
 //     successor (named in v's record) and c(u, v-) from row u of the copy at
 //     v's predecessor position.
 //   depot CTAs: the (customer, start depot) pairs are dense -- every
@@ -151,7 +151,7 @@ __device__ __forceinline__ void edge_mask_item(const Dev &d, long long item, int
     const int4 u4 = TW ? __ldg(ur + 4) : z, u5 = TW ? __ldg(ur + 5) : z;
     const int4 u6 = (TW && OR) ? __ldg(ur + 6) : z;
     const int pu = __ldg(d.pos_of + TGA_IX(u, d.W + 1));
-    // round 2: v's records, its position, and the distances that need only v
+    // second loads: v's records, its position, and the distances that need only v
     const int4 *vr = reinterpret_cast<const int4 *>(d.erec + TGA_IX(v, d.W + 1));
     const int4 v0 = __ldg(vr + 0), v1 = __ldg(vr + 1), v2 = __ldg(vr + 2), v7 = __ldg(vr + 7);
     const int4 v4 = TW ? __ldg(vr + 4) : z, v5 = TW ? __ldg(vr + 5) : z;
@@ -161,7 +161,7 @@ __device__ __forceinline__ void edge_mask_item(const Dev &d, long long item, int
     t.t00 = dmat(d, u, v);
     t.t10 = dmat(d, up, v);
     t.tm10 = __ldg(d.pcol + (size_t)TGA_IX(v, d.n + 1) * d.ldp + TGA_IX(pu - 1 + kColOff, d.ldp));
-    // round 3: the distances to v's successor, and c(u, v-)
+    // third loads: the distances to v's successor, and c(u, v-)
     const int vp = v7.z;
     t.t01 = dmat(d, u, vp);
     t.t11 = dmat(d, up, vp);
